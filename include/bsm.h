@@ -1,0 +1,180 @@
+/*
+ * bsm.h -- C ABI of libbsm: the local filtered block-sparse matrix multiply
+ *
+ *     C = beta * C + alpha * A . B      (products filtered on block norms)
+ *
+ * on one GB300 GPU (sm_103a).
+ *
+ * The operation is the local block multiplication of the paper's Sec. 2: the
+ * matrices are stored in blocked compressed sparse row form (elements grouped
+ * into blocks by block rows and block columns), the result pattern is not
+ * fixed beforehand but determined by the multiplication itself, and a block
+ * product A_ik . B_kj is only carried out when the product of the two block
+ * norms is not below the threshold eps (on-the-fly filtering). Algorithms 1
+ * and 2 call it once per tick as C = C + A . B; alpha and beta generalise this
+ * the BLAS way.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns BSM_OK (0) or a negative BSM_ERR_* code. Nothing is
+ *     thrown, nothing aborts. bsm_strerror() names a code.
+ *   - Handles (bsm_ctx, bsm_mat) belong to the library until *_destroy.
+ *     Arrays passed in are copied (host arrays) or only read (device arrays);
+ *     the caller keeps ownership of its buffers.
+ *   - Block values are column-major inside a block. A matrix is given as a
+ *     list of blocks (block row, block column) in any order; the values
+ *     argument holds the blocks concatenated in the order of that list.
+ *   - Block sizes are >= 1. Block row/column counts and block counts are
+ *     below 2^31; value counts may exceed 2^31.
+ *   - The canonical block norm is the Frobenius norm accumulated element by
+ *     element in column-major order, each multiply and add rounded separately,
+ *     followed by a correctly rounded square root. A product (i,k,j) is
+ *     dropped iff nrm(A_ik) * nrm(B_kj) < eps (a tie is kept, NaN is kept,
+ *     eps <= 0 drops nothing); alpha does not enter the test.
+ *   - With beta == 0 the previous contents of C (pattern and values) are
+ *     ignored. With beta != 0 the result pattern is the union of the kept
+ *     products' pattern and C's previous pattern.
+ *   - All device work of a context runs in stream order on the context's
+ *     stream (or the stream given in bsm_opts). Getters synchronise.
+ */
+#ifndef BSM_H
+#define BSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BSM_OK = 0,
+  BSM_ERR_INVALID_ARG = -1,     /* null handle, bad size, bad option, small cap */
+  BSM_ERR_DIM_MISMATCH = -2,    /* A's column sizes != B's row sizes, or C not r x c */
+  BSM_ERR_DUPLICATE_BLOCK = -3, /* the same (row, col) listed twice */
+  BSM_ERR_OUT_OF_RANGE = -4,    /* a block index outside the block grid */
+  BSM_ERR_ALIAS = -5,           /* C is the same handle as A or B (A == B is fine) */
+  BSM_ERR_NOMEM = -6,           /* device or pinned host allocation failed */
+  BSM_ERR_CUDA = -7,            /* a CUDA runtime error (details: bsm_last_cuda_error) */
+  BSM_ERR_TIMEOUT = -8,         /* a bounded device-side wait gave up */
+  BSM_ERR_UNSUPPORTED = -9      /* valid request this build does not handle */
+};
+
+/* Arithmetic of the block products (C accumulation is always FP64). */
+enum {
+  BSM_PREC_FP64 = 0,        /* FP64 FMA throughout */
+  BSM_PREC_SPLIT_BF16X3 = 1, /* 3 BF16 slices per operand, 6 slice products, FP32 sums */
+  BSM_PREC_SPLIT_TF32X2 = 2  /* 2 TF32 slices per operand, 3 slice products, FP32 sums */
+};
+
+/* How the numeric stacks are launched. */
+enum {
+  BSM_LAUNCH_PERSISTENT = 0, /* one persistent launch over all shape classes */
+  BSM_LAUNCH_PER_STACK = 1   /* one launch per (m,n) shape class, generic tiles */
+};
+
+typedef struct bsm_ctx_s *bsm_ctx;
+typedef struct bsm_mat_s *bsm_mat;
+
+/* Options of one multiply. A NULL bsm_opts* means all defaults (zeroes). */
+typedef struct {
+  int32_t precision; /* BSM_PREC_* */
+  int32_t launch;    /* BSM_LAUNCH_* */
+  int32_t blocking;  /* 1: return after the result is complete and checked */
+  int32_t autotune;  /* 1: pick per-shape tile variants from the tuner table */
+  void *stream;      /* cudaStream_t to use instead of the context stream, or NULL */
+} bsm_opts;
+
+/* Counters of one multiply (filled when bsm_stats* is not NULL; this makes
+ * the call blocking). FLOPs count 2*m*n*k per kept block product, the
+ * convention of the paper's Table 1. */
+typedef struct {
+  int64_t candidates; /* block products (i,k,j) with A_ik and B_kj present */
+  int64_t kept;       /* products that passed the filter */
+  int64_t dropped;    /* candidates - kept */
+  int64_t c_blocks;   /* blocks in the result pattern */
+  int64_t c_nnz;      /* scalars in the result */
+  double flops;       /* sum over kept products of 2*m*n*k */
+  float ms_total;     /* device time of the whole multiply (CUDA events) */
+  int32_t retries;    /* times the result buffers had to grow and rerun */
+  int32_t reserved;
+} bsm_stats;
+
+/* Create a context on CUDA device `device` with its own stream and
+ * workspace. *out receives the handle. */
+int bsm_ctx_create(int device, bsm_ctx *out);
+
+/* Wait for the context's work and free everything it owns, including every
+ * matrix still alive on it. */
+int bsm_ctx_destroy(bsm_ctx ctx);
+
+/* Create a block-sparse matrix from host arrays (Sec. 2: blocked CSR built
+ * from block row sizes, block column sizes and the list of present blocks).
+ *   nbrows, row_sizes[nbrows]   block row count and sizes (each >= 1)
+ *   nbcols, col_sizes[nbcols]   block column count and sizes (each >= 1)
+ *   nblocks, blk_row[], blk_col[]  the present blocks, any order, no duplicates
+ *   values   host array of the blocks' values, concatenated in list order,
+ *            each block column-major; NULL creates zero blocks.
+ * Errors: INVALID_ARG, OUT_OF_RANGE, DUPLICATE_BLOCK, NOMEM, CUDA. The arrays
+ * are copied; the call returns once the copy to the device is done. */
+int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_t nbcols,
+                   const int32_t *col_sizes, int64_t nblocks, const int32_t *blk_row,
+                   const int32_t *blk_col, const double *values, bsm_mat *out);
+
+/* Free a matrix (after the work that uses it has finished). */
+int bsm_mat_destroy(bsm_mat m);
+
+/* C = beta*C + alpha*A.B with the on-the-fly filter (Sec. 2, Algorithm 1's
+ * local step C_ij = C_ij + A_comp . B_comp).
+ *   A: r x s blocks, B: s x c blocks (A's column sizes must equal B's row
+ *   sizes), C: r x c blocks; C's pattern is replaced by the result pattern.
+ *   eps: filter threshold; opts, stats: may be NULL.
+ * C may not be A or B (ALIAS); A may be B. Without opts->blocking and without
+ * stats the call only enqueues work; C's result is complete at the next
+ * getter, bsm_sync, or use of C as an operand. Inputs must stay alive and
+ * unchanged until then. Errors: INVALID_ARG, DIM_MISMATCH, ALIAS, NOMEM,
+ * CUDA, UNSUPPORTED. */
+int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, bsm_mat C,
+                 double eps, const bsm_opts *opts, bsm_stats *stats);
+
+/* Number of stored blocks and scalars of m (synchronises m). */
+int bsm_mat_nblocks(bsm_mat m, int64_t *nblocks, int64_t *nnz);
+
+/* The pattern of m sorted by (row, col) into caller arrays of capacity cap
+ * (>= nblocks, else INVALID_ARG). Synchronises. */
+int bsm_mat_get_pattern(bsm_mat m, int64_t cap, int32_t *blk_row, int32_t *blk_col);
+
+/* The values of m in the order of bsm_mat_get_pattern, each block
+ * column-major, into a host array of capacity cap (>= nnz). Synchronises. */
+int bsm_mat_get_values(bsm_mat m, int64_t cap, double *values);
+
+/* Device-time profile of the multiplies of a context: CUDA events recorded
+ * on the launch stream at the phase boundaries of every multiply (block norms
+ * | symbolic count, scan and fill | numeric block products). */
+typedef struct {
+  double ms_norms;     /* sum over multiplies of the block-norm phase */
+  double ms_symbolic;  /* ... of the symbolic phase (count, scan, fill) */
+  double ms_numeric;   /* ... of the numeric phase */
+  double ms_total;     /* ... of whole multiplies */
+  int64_t multiplies;  /* multiplies profiled */
+  int64_t launches;    /* kernels launched by this context since profiling started */
+} bsm_profile;
+
+/* enable != 0: start profiling (totals reset); enable == 0: stop. */
+int bsm_ctx_profile(bsm_ctx ctx, int enable);
+
+/* Totals since the last bsm_ctx_profile(ctx, 1). Synchronises the context. */
+int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
+
+/* Wait for all work of the context and complete every pending result. */
+int bsm_sync(bsm_ctx ctx);
+
+/* Static text for a BSM_* code. */
+const char *bsm_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *bsm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSM_H */

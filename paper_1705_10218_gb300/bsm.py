@@ -1,0 +1,261 @@
+"""ctypes binding of libbsm (include/bsm.h). Argument marshalling only.
+
+The library must have been built (``paper_1705_10218_gb300/build.py`` or
+``__graft_entry__.build()``); there is no fallback of any kind: without the
+library, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "libbsm.so")
+
+BSM_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "DIM_MISMATCH", -3: "DUPLICATE_BLOCK", -4: "OUT_OF_RANGE",
+    -5: "ALIAS", -6: "NOMEM", -7: "CUDA", -8: "TIMEOUT", -9: "UNSUPPORTED",
+}
+BSM_PREC_FP64 = 0
+BSM_PREC_SPLIT_BF16X3 = 1
+BSM_PREC_SPLIT_TF32X2 = 2
+BSM_LAUNCH_PERSISTENT = 0
+BSM_LAUNCH_PER_STACK = 1
+
+
+class BsmError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        name = ERRORS.get(code, str(code))
+        detail = ""
+        if code == -7 and _lib is not None:
+            detail = ": " + _lib.bsm_last_cuda_error().decode()
+        super().__init__(f"{where}: BSM_ERR_{name}{detail}")
+        self.code = code
+        self.name = name
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("launch", ctypes.c_int32),
+        ("blocking", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [
+        ("candidates", ctypes.c_int64),
+        ("kept", ctypes.c_int64),
+        ("dropped", ctypes.c_int64),
+        ("c_blocks", ctypes.c_int64),
+        ("c_nnz", ctypes.c_int64),
+        ("flops", ctypes.c_double),
+        ("ms_total", ctypes.c_float),
+        ("retries", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [
+        ("ms_norms", ctypes.c_double),
+        ("ms_symbolic", ctypes.c_double),
+        ("ms_numeric", ctypes.c_double),
+        ("ms_total", ctypes.c_double),
+        ("multiplies", ctypes.c_int64),
+        ("launches", ctypes.c_int64),
+    ]
+
+
+@dataclass
+class Profile:
+    ms_norms: float
+    ms_symbolic: float
+    ms_numeric: float
+    ms_total: float
+    multiplies: int
+    launches: int
+
+
+@dataclass
+class Stats:
+    candidates: int
+    kept: int
+    dropped: int
+    c_blocks: int
+    c_nnz: int
+    flops: float
+    ms_total: float
+    retries: int
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "bsm_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P)]),
+    "bsm_ctx_destroy": (ctypes.c_int, [_P]),
+    "bsm_mat_create": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _I64, _P, _P, _P, ctypes.POINTER(_P)]),
+    "bsm_mat_destroy": (ctypes.c_int, [_P]),
+    "bsm_multiply": (ctypes.c_int, [_P, _D, _P, _P, _D, _P, _D, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats)]),
+    "bsm_mat_nblocks": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "bsm_mat_get_pattern": (ctypes.c_int, [_P, _I64, _P, _P]),
+    "bsm_mat_get_values": (ctypes.c_int, [_P, _I64, _P]),
+    "bsm_sync": (ctypes.c_int, [_P]),
+    "bsm_ctx_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "bsm_ctx_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(_Profile)]),
+    "bsm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "bsm_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded libbsm (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(lib_path):
+            raise RuntimeError(f"libbsm.so is not built ({lib_path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(lib_path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != BSM_OK:
+        raise BsmError(rc, where)
+
+
+def _vp(a: np.ndarray | None):
+    return None if a is None or a.size == 0 else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Context:
+    """A libbsm context: one device, one stream, one workspace."""
+
+    def __init__(self, device: int = 0):
+        h = _P()
+        _check(lib().bsm_ctx_create(int(device), ctypes.byref(h)), "bsm_ctx_create")
+        self._h = h
+        self.device = device
+        self._mats: list[Matrix] = []
+
+    @property
+    def handle(self):
+        return self._h
+
+    def matrix(self, row_sizes, col_sizes, blk_row, blk_col, values=None) -> "Matrix":
+        rs = np.ascontiguousarray(row_sizes, dtype=np.int32)
+        cs = np.ascontiguousarray(col_sizes, dtype=np.int32)
+        br = np.ascontiguousarray(blk_row, dtype=np.int32)
+        bc = np.ascontiguousarray(blk_col, dtype=np.int32)
+        if br.shape != bc.shape:
+            raise BsmError(-1, "bsm_mat_create")
+        v = None if values is None else np.ascontiguousarray(values, dtype=np.float64)
+        h = _P()
+        rc = lib().bsm_mat_create(self._h, len(rs), _vp(rs), len(cs), _vp(cs), len(br), _vp(br),
+                                  _vp(bc), _vp(v), ctypes.byref(h))
+        _check(rc, "bsm_mat_create")
+        m = Matrix(self, h, len(rs), len(cs))
+        self._mats.append(m)
+        return m
+
+    def from_blocks(self, M) -> "Matrix":
+        """From any object with row_sizes, col_sizes, blk_row, blk_col, values."""
+        return self.matrix(M.row_sizes, M.col_sizes, M.blk_row, M.blk_col, M.values)
+
+    def empty(self, row_sizes, col_sizes) -> "Matrix":
+        return self.matrix(row_sizes, col_sizes, np.zeros(0, np.int32), np.zeros(0, np.int32))
+
+    def multiply(self, alpha, A: "Matrix", B: "Matrix", beta, C: "Matrix", eps: float = 0.0, *,
+                 precision: int = BSM_PREC_FP64, launch: int = BSM_LAUNCH_PERSISTENT,
+                 blocking: bool = False, autotune: bool = False, stream=None,
+                 stats: bool = False) -> Stats | None:
+        o = _Opts(int(precision), int(launch), int(bool(blocking)), int(bool(autotune)),
+                  _stream_ptr(stream))
+        st = _Stats() if stats else None
+        rc = lib().bsm_multiply(self._h, float(alpha), A._h, B._h, float(beta), C._h, float(eps),
+                                ctypes.byref(o), ctypes.byref(st) if st is not None else None)
+        _check(rc, "bsm_multiply")
+        if st is None:
+            return None
+        return Stats(st.candidates, st.kept, st.dropped, st.c_blocks, st.c_nnz, st.flops,
+                     st.ms_total, st.retries)
+
+    def sync(self):
+        _check(lib().bsm_sync(self._h), "bsm_sync")
+
+    def profile(self, enable: bool = True):
+        _check(lib().bsm_ctx_profile(self._h, int(bool(enable))), "bsm_ctx_profile")
+
+    def profile_read(self) -> Profile:
+        p = _Profile()
+        _check(lib().bsm_ctx_profile_read(self._h, ctypes.byref(p)), "bsm_ctx_profile_read")
+        return Profile(p.ms_norms, p.ms_symbolic, p.ms_numeric, p.ms_total, p.multiplies, p.launches)
+
+    def close(self):
+        if self._h:
+            for m in self._mats:
+                m._h = None
+            lib().bsm_ctx_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Matrix:
+    def __init__(self, ctx: Context, h, nbr: int, nbc: int):
+        self.ctx = ctx
+        self._h = h
+        self.nbr = nbr
+        self.nbc = nbc
+
+    def nblocks(self) -> tuple[int, int]:
+        nb, nz = _I64(), _I64()
+        _check(lib().bsm_mat_nblocks(self._h, ctypes.byref(nb), ctypes.byref(nz)), "bsm_mat_nblocks")
+        return int(nb.value), int(nz.value)
+
+    def pattern(self) -> tuple[np.ndarray, np.ndarray]:
+        nb, _ = self.nblocks()
+        r = np.empty(nb, np.int32)
+        c = np.empty(nb, np.int32)
+        _check(lib().bsm_mat_get_pattern(self._h, nb, _vp(r), _vp(c)), "bsm_mat_get_pattern")
+        return r, c
+
+    def values(self, out: np.ndarray | None = None) -> np.ndarray:
+        _, nz = self.nblocks()
+        if out is None:
+            out = np.empty(nz, np.float64)
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < nz:
+            raise BsmError(-1, "bsm_mat_get_values")
+        _check(lib().bsm_mat_get_values(self._h, out.size, _vp(out)), "bsm_mat_get_values")
+        return out[:nz]
+
+    def destroy(self):
+        if self._h:
+            lib().bsm_mat_destroy(self._h)
+            self._h = None
+            if self in self.ctx._mats:
+                self.ctx._mats.remove(self)

@@ -1,0 +1,775 @@
+// bsm_api.cu -- host runtime behind include/bsm.h: contexts, matrices, the
+// multiply pipeline (norms -> symbolic count -> scan -> fill -> numeric), the
+// result-buffer capacities, and error mapping.
+//
+// Result buffers follow the reuse rule the paper gives for its panel buffers
+// (Sec. 3): they are kept between multiplies and only reallocated when the
+// needed size exceeds the current one. The device checks the sizes itself (the
+// scan pass compares the totals with the capacities), so a multiply into a C
+// whose buffers are already large enough needs no host round trip: it is one
+// stream-ordered sequence of launches. When a buffer is too small, later passes
+// skip their work, and the host grows the buffers and reruns the multiply when
+// it next looks at the result.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "bsm_internal.h"
+
+using namespace bsm;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e, const char *where) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return BSM_ERR_NOMEM;
+  return BSM_ERR_CUDA;
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <class T>
+int dev_alloc(T **p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, (size_t)n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return cuda_fail(e, "cudaMalloc");
+  }
+  return BSM_OK;
+}
+
+template <class T>
+void dev_free(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+}  // namespace
+
+// One set of pattern + value buffers of a matrix.
+struct Buf {
+  int32_t *row_ptr = nullptr;  // [nbr+1]
+  int32_t *col_idx = nullptr;  // [cap_blk]
+  int32_t *blk_row = nullptr;  // [cap_blk]
+  int64_t *blk_off = nullptr;  // [cap_blk]
+  double *norms = nullptr;     // [cap_blk]
+  double *vals = nullptr;      // [cap_nnz]
+  int64_t *hdr = nullptr;      // {nblk, nnz}
+  int64_t cap_blk = -1, cap_nnz = -1;  // -1: never sized
+
+  void release() {
+    dev_free(row_ptr);
+    dev_free(col_idx);
+    dev_free(blk_row);
+    dev_free(blk_off);
+    dev_free(norms);
+    dev_free(vals);
+    dev_free(hdr);
+    cap_blk = cap_nnz = -1;
+  }
+};
+
+struct Pending {
+  bool active = false;
+  bsm_mat A = nullptr, B = nullptr;
+  double alpha = 0, beta = 0, eps = 0;
+  bsm_opts opts{};
+  int slot = -1;
+};
+
+struct bsm_mat_s {
+  bsm_ctx ctx = nullptr;
+  int32_t nbr = 0, nbc = 0;
+  std::vector<int32_t> h_row_sizes, h_col_sizes;
+  int32_t *row_sizes = nullptr, *col_sizes = nullptr;
+  Buf front, back;
+  int64_t nblk = 0, nnz = 0;  // valid when !pend.active
+  int64_t hint_blk = 0, hint_nnz = 0;  // sizes of the last result computed into it
+  Pending pend;
+};
+
+constexpr int kSlots = 64;
+
+struct bsm_ctx_s {
+  int device = 0;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_last = nullptr;   // last work of this context (any stream)
+  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
+  DevStatus *d_status = nullptr;
+  DevStatus *h_slots = nullptr;    // pinned ring of status copies
+  cudaEvent_t slot_ev[kSlots] = {};
+  bsm_mat slot_owner[kSlots] = {};
+  int next_slot = 0;
+  // workspace
+  DevWs ws{};
+  int64_t cap_rows = 0, cap_cblk = -1;
+  int64_t hint_prod = 0;
+  std::vector<bsm_mat> mats;
+  // profiling
+  bool prof = false;
+  cudaEvent_t prof_ev[kSlots][4] = {};
+  bool prof_pending[kSlots] = {};
+  bsm_profile prof_tot{};
+  int64_t launches = 0;
+  int64_t launches_at_enable = 0;
+};
+
+// Add the phase times of slot s to the totals (once per recorded multiply).
+static int prof_collect(bsm_ctx ctx, int s) {
+  if (!ctx->prof_pending[s]) return BSM_OK;
+  ctx->prof_pending[s] = false;
+  CK(cudaEventSynchronize(ctx->prof_ev[s][3]));
+  float a = 0, b = 0, c = 0, t = 0;
+  CK(cudaEventElapsedTime(&a, ctx->prof_ev[s][0], ctx->prof_ev[s][1]));
+  CK(cudaEventElapsedTime(&b, ctx->prof_ev[s][1], ctx->prof_ev[s][2]));
+  CK(cudaEventElapsedTime(&c, ctx->prof_ev[s][2], ctx->prof_ev[s][3]));
+  CK(cudaEventElapsedTime(&t, ctx->prof_ev[s][0], ctx->prof_ev[s][3]));
+  ctx->prof_tot.ms_norms += a;
+  ctx->prof_tot.ms_symbolic += b;
+  ctx->prof_tot.ms_numeric += c;
+  ctx->prof_tot.ms_total += t;
+  ctx->prof_tot.multiplies += 1;
+  return BSM_OK;
+}
+
+static int ctx_set_device(bsm_ctx ctx) {
+  CK(cudaSetDevice(ctx->device));
+  return BSM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// workspace sizing
+// ---------------------------------------------------------------------------
+static int ws_rows(bsm_ctx ctx, int64_t nrows) {
+  if (ctx->cap_rows >= nrows + 1) return BSM_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  DevWs &w = ctx->ws;
+  dev_free(w.row_cblk);
+  dev_free(w.row_prod);
+  dev_free(w.row_nnz);
+  dev_free(w.row_cand);
+  dev_free(w.row_flops);
+  dev_free(w.prod_off);
+  dev_free(w.nnz_off);
+  const int64_t n = std::max<int64_t>(nrows + 1, 1024);
+  int rc;
+  if ((rc = dev_alloc(&w.row_cblk, n)) || (rc = dev_alloc(&w.row_prod, n)) ||
+      (rc = dev_alloc(&w.row_nnz, n)) || (rc = dev_alloc(&w.row_cand, n)) ||
+      (rc = dev_alloc(&w.row_flops, n)) || (rc = dev_alloc(&w.prod_off, n)) ||
+      (rc = dev_alloc(&w.nnz_off, n))) {
+    ctx->cap_rows = 0;
+    return rc;
+  }
+  ctx->cap_rows = n;
+  w.cap_rows = n;
+  return BSM_OK;
+}
+
+static int ws_grow(bsm_ctx ctx, int64_t nblk_c, int64_t nprod) {
+  DevWs &w = ctx->ws;
+  if (ctx->cap_cblk < nblk_c + 1) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    dev_free(w.cnt);
+    dev_free(w.c_cin);
+    dev_free(w.prod_ptr);
+    const int64_t n = nblk_c + nblk_c / 8 + 1024;
+    int rc;
+    if ((rc = dev_alloc(&w.cnt, n)) || (rc = dev_alloc(&w.c_cin, n)) ||
+        (rc = dev_alloc(&w.prod_ptr, n + 1))) {
+      ctx->cap_cblk = -1;
+      return rc;
+    }
+    ctx->cap_cblk = n;
+  }
+  if (w.cap_prod < nprod) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    dev_free(w.prods);
+    const int64_t n = nprod + nprod / 8 + 1024;
+    int rc;
+    if ((rc = dev_alloc(&w.prods, n))) {
+      w.cap_prod = 0;
+      return rc;
+    }
+    w.cap_prod = n;
+  }
+  return BSM_OK;
+}
+
+// Buffers sized for (nblk, nnz); row arrays for nbr rows.
+static int buf_grow(bsm_mat M, Buf &b, int64_t nblk, int64_t nnz, bool exact) {
+  if (!b.row_ptr) {
+    int rc;
+    if ((rc = dev_alloc(&b.row_ptr, (int64_t)M->nbr + 1)) || (rc = dev_alloc(&b.hdr, 2))) return rc;
+    cudaStream_t s = M->ctx->stream;
+    CK(cudaMemsetAsync(b.row_ptr, 0, ((size_t)M->nbr + 1) * sizeof(int32_t), s));
+    CK(cudaMemsetAsync(b.hdr, 0, 2 * sizeof(int64_t), s));
+  }
+  if (b.cap_blk < nblk) {
+    CK(cudaStreamSynchronize(M->ctx->stream));
+    dev_free(b.col_idx);
+    dev_free(b.blk_row);
+    dev_free(b.blk_off);
+    dev_free(b.norms);
+    const int64_t n = exact ? nblk : nblk + nblk / 8 + 64;
+    int rc;
+    if ((rc = dev_alloc(&b.col_idx, n)) || (rc = dev_alloc(&b.blk_row, n)) ||
+        (rc = dev_alloc(&b.blk_off, n)) || (rc = dev_alloc(&b.norms, n))) {
+      b.cap_blk = -1;
+      return rc;
+    }
+    b.cap_blk = n;
+  }
+  if (b.cap_nnz < nnz) {
+    CK(cudaStreamSynchronize(M->ctx->stream));
+    dev_free(b.vals);
+    const int64_t n = exact ? nnz : nnz + nnz / 8 + 1024;
+    int rc;
+    if ((rc = dev_alloc(&b.vals, n))) {
+      b.cap_nnz = -1;
+      return rc;
+    }
+    b.cap_nnz = n;
+  }
+  return BSM_OK;
+}
+
+static DevMat dev_view(bsm_mat M) {
+  DevMat v{};
+  v.nbr = M->nbr;
+  v.nbc = M->nbc;
+  v.row_sizes = M->row_sizes;
+  v.col_sizes = M->col_sizes;
+  v.row_ptr = M->front.row_ptr;
+  v.col_idx = M->front.col_idx;
+  v.blk_row = M->front.blk_row;
+  v.blk_off = M->front.blk_off;
+  v.vals = M->front.vals;
+  v.norms = M->front.norms;
+  v.hdr = M->front.hdr;
+  return v;
+}
+
+static DevOut dev_out(bsm_mat M, Buf &b) {
+  DevOut o{};
+  o.nbr = M->nbr;
+  o.nbc = M->nbc;
+  o.row_sizes = M->row_sizes;
+  o.col_sizes = M->col_sizes;
+  o.row_ptr = b.row_ptr;
+  o.col_idx = b.col_idx;
+  o.blk_row = b.blk_row;
+  o.blk_off = b.blk_off;
+  o.vals = b.vals;
+  o.hdr = b.hdr;
+  o.cap_blk = std::max<int64_t>(b.cap_blk, 0);
+  o.cap_nnz = std::max<int64_t>(b.cap_nnz, 0);
+  return o;
+}
+
+static int resolve(bsm_mat M, bsm_stats *timed = nullptr);
+
+// ---------------------------------------------------------------------------
+// the multiply pipeline
+// ---------------------------------------------------------------------------
+static int enqueue_norms(bsm_ctx ctx, bsm_mat M, cudaStream_t s) {
+  const int grid = ctx->nsm * 8;
+  CK(launch_block_norms(M->row_sizes, M->col_sizes, M->front.blk_row, M->front.col_idx,
+                        M->front.blk_off, M->front.vals, M->front.hdr, M->front.norms, grid, s));
+  return BSM_OK;
+}
+
+static int take_slot(bsm_ctx ctx, bsm_mat owner) {
+  const int s = ctx->next_slot;
+  ctx->next_slot = (ctx->next_slot + 1) % kSlots;
+  if (ctx->prof_pending[s]) {
+    int rc = prof_collect(ctx, s);
+    if (rc) return -1000 + rc;
+  }
+  if (ctx->slot_owner[s] && ctx->slot_owner[s]->pend.active && ctx->slot_owner[s]->pend.slot == s) {
+    int rc = resolve(ctx->slot_owner[s]);
+    if (rc) return -1000 + rc;
+  }
+  ctx->slot_owner[s] = owner;
+  return s;
+}
+
+// Enqueue one multiply. sync_sizes: read the totals back after the scan and
+// size the buffers exactly before the fill and numeric passes.
+static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, bsm_mat C,
+                        double eps, const bsm_opts &o, bool sync_sizes, int slot,
+                        bsm_stats *stats) {
+  cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->stream;
+  if (s != ctx->stream) CK(cudaStreamWaitEvent(s, ctx->ev_last, 0));
+  const bool use_cin = (beta != 0.0);
+  int rc;
+  if ((rc = ws_rows(ctx, A->nbr))) return rc;
+  if ((rc = buf_grow(C, C->back, 0, 0, true))) return rc;
+  if (ctx->cap_cblk < 0 && (rc = ws_grow(ctx, 0, 0))) return rc;
+  if (stats) CK(cudaEventRecord(ctx->ev_t0, s));
+  const bool prof = ctx->prof;
+  if (prof) CK(cudaEventRecord(ctx->prof_ev[slot][0], s));
+
+  if ((rc = enqueue_norms(ctx, A, s))) return rc;
+  ctx->launches++;
+  if (B != A) {
+    if ((rc = enqueue_norms(ctx, B, s))) return rc;
+    ctx->launches++;
+  }
+  if (prof) CK(cudaEventRecord(ctx->prof_ev[slot][1], s));
+
+  DevMat dA = dev_view(A), dB = dev_view(B), dC = dev_view(C);
+  const int sym_grid = ctx->nsm * 6;
+  CK(launch_symbolic_count(dA, dB, dC, use_cin ? 1 : 0, eps, ctx->ws, sym_grid, s));
+  ctx->launches++;
+
+  DevWs ws = ctx->ws;
+  ws.cap_prod = ctx->ws.cap_prod;
+  DevOut out = dev_out(C, C->back);
+  // capacities of the per-C-block scratch cap the block count as well
+  out.cap_blk = std::min<int64_t>(out.cap_blk, std::max<int64_t>(ctx->cap_cblk - 1, 0));
+  CK(launch_symbolic_scan(A->nbr, ws, out, ctx->d_status, s));
+  ctx->launches++;
+
+  if (sync_sizes) {
+    DevStatus h{};
+    CK(cudaMemcpyAsync(&h, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    C->hint_blk = h.nblk_c;
+    C->hint_nnz = h.nnz_c;
+    ctx->hint_prod = std::max(ctx->hint_prod, h.nprod);
+    if (h.overflow) {
+      if (h.nblk_c >= (int64_t)INT32_MAX) return BSM_ERR_UNSUPPORTED;
+      if ((rc = buf_grow(C, C->back, h.nblk_c, h.nnz_c, false))) return rc;
+      if ((rc = ws_grow(ctx, h.nblk_c, h.nprod))) return rc;
+      ws = ctx->ws;
+      out = dev_out(C, C->back);
+      out.cap_blk = std::min<int64_t>(out.cap_blk, std::max<int64_t>(ctx->cap_cblk - 1, 0));
+      CK(launch_symbolic_scan(A->nbr, ws, out, ctx->d_status, s));
+      ctx->launches++;
+    }
+  }
+  CK(launch_symbolic_fill(dA, dB, dC, use_cin ? 1 : 0, eps, ws, out, ctx->d_status, sym_grid, s));
+  ctx->launches++;
+  if (prof) CK(cudaEventRecord(ctx->prof_ev[slot][2], s));
+  CK(launch_numeric_fp64(dA, dB, out, dC, alpha, beta, ws, ctx->d_status, ctx->nsm * 3, s));
+  ctx->launches++;
+  if (prof) {
+    CK(cudaEventRecord(ctx->prof_ev[slot][3], s));
+    ctx->prof_pending[slot] = true;
+  }
+  if (stats) CK(cudaEventRecord(ctx->ev_t1, s));
+  CK(cudaMemcpyAsync(&ctx->h_slots[slot], ctx->d_status, sizeof(DevStatus),
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->slot_ev[slot], s));
+  CK(cudaEventRecord(ctx->ev_last, s));
+  if (s != ctx->stream) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_last, 0));
+  return BSM_OK;
+}
+
+// Wait for M's pending result; on overflow, grow and recompute (blocking).
+static int resolve(bsm_mat M, bsm_stats *timed) {
+  if (!M->pend.active) return BSM_OK;
+  bsm_ctx ctx = M->ctx;
+  Pending p = M->pend;
+  CK(cudaEventSynchronize(ctx->slot_ev[p.slot]));
+  DevStatus h = ctx->h_slots[p.slot];
+  M->pend.active = false;
+  M->hint_blk = std::max(M->hint_blk, h.nblk_c);
+  M->hint_nnz = std::max(M->hint_nnz, h.nnz_c);
+  ctx->hint_prod = std::max(ctx->hint_prod, h.nprod);
+  if (!h.overflow) {
+    M->nblk = h.nblk_c;
+    M->nnz = h.nnz_c;
+    return BSM_OK;
+  }
+  if (timed) timed->retries++;
+  // undo the swap (front = the previous contents), then recompute with exact sizes
+  std::swap(M->front, M->back);
+  if (p.A->pend.active) {
+    int rc = resolve(p.A);
+    if (rc) return rc;
+  }
+  if (p.B->pend.active) {
+    int rc = resolve(p.B);
+    if (rc) return rc;
+  }
+  int rc = run_multiply(ctx, p.alpha, p.A, p.B, p.beta, M, p.eps, p.opts, true, p.slot, timed);
+  if (rc) return rc;
+  CK(cudaEventSynchronize(ctx->slot_ev[p.slot]));
+  h = ctx->h_slots[p.slot];
+  if (h.overflow) return BSM_ERR_NOMEM;
+  std::swap(M->front, M->back);
+  M->nblk = h.nblk_c;
+  M->nnz = h.nnz_c;
+  return BSM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// public API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *bsm_strerror(int code) {
+  switch (code) {
+    case BSM_OK: return "ok";
+    case BSM_ERR_INVALID_ARG: return "invalid argument";
+    case BSM_ERR_DIM_MISMATCH: return "block sizes of the operands do not match";
+    case BSM_ERR_DUPLICATE_BLOCK: return "duplicate block in the block list";
+    case BSM_ERR_OUT_OF_RANGE: return "block index out of range";
+    case BSM_ERR_ALIAS: return "C aliases A or B";
+    case BSM_ERR_NOMEM: return "out of device or pinned host memory";
+    case BSM_ERR_CUDA: return "CUDA runtime error";
+    case BSM_ERR_TIMEOUT: return "device-side wait timed out";
+    case BSM_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown error";
+  }
+}
+
+const char *bsm_last_cuda_error(void) { return g_cuda_err; }
+
+int bsm_ctx_create(int device, bsm_ctx *out) {
+  if (!out) return BSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return BSM_ERR_INVALID_ARG;
+  bsm_ctx ctx = new (std::nothrow) bsm_ctx_s();
+  if (!ctx) return BSM_ERR_NOMEM;
+  ctx->device = device;
+  int rc = BSM_OK;
+  cudaError_t e;
+  if ((e = cudaSetDevice(device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device)) !=
+          cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&ctx->ev_last, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreate(&ctx->ev_t0)) != cudaSuccess ||
+      (e = cudaEventCreate(&ctx->ev_t1)) != cudaSuccess ||
+      (e = cudaMalloc((void **)&ctx->d_status, sizeof(DevStatus))) != cudaSuccess ||
+      (e = cudaMallocHost((void **)&ctx->h_slots, kSlots * sizeof(DevStatus))) != cudaSuccess) {
+    rc = cuda_fail(e, "bsm_ctx_create");
+  }
+  for (int i = 0; rc == BSM_OK && i < kSlots; i++) {
+    if ((e = cudaEventCreateWithFlags(&ctx->slot_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+      rc = cuda_fail(e, "cudaEventCreate");
+  }
+  if (rc == BSM_OK) {
+    memset(ctx->h_slots, 0, kSlots * sizeof(DevStatus));
+    e = cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset");
+  }
+  if (rc != BSM_OK) {
+    bsm_ctx_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return BSM_OK;
+}
+
+int bsm_mat_destroy(bsm_mat m);
+
+int bsm_ctx_destroy(bsm_ctx ctx) {
+  if (!ctx) return BSM_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  while (!ctx->mats.empty()) {
+    bsm_mat m = ctx->mats.back();
+    m->pend.active = false;
+    bsm_mat_destroy(m);
+  }
+  DevWs &w = ctx->ws;
+  dev_free(w.row_cblk);
+  dev_free(w.row_prod);
+  dev_free(w.row_nnz);
+  dev_free(w.row_cand);
+  dev_free(w.row_flops);
+  dev_free(w.prod_off);
+  dev_free(w.nnz_off);
+  dev_free(w.cnt);
+  dev_free(w.c_cin);
+  dev_free(w.prod_ptr);
+  dev_free(w.prods);
+  dev_free(ctx->d_status);
+  if (ctx->h_slots) cudaFreeHost(ctx->h_slots);
+  for (int i = 0; i < kSlots; i++) {
+    if (ctx->slot_ev[i]) cudaEventDestroy(ctx->slot_ev[i]);
+    for (int e = 0; e < 4; e++)
+      if (ctx->prof_ev[i][e]) cudaEventDestroy(ctx->prof_ev[i][e]);
+  }
+  if (ctx->ev_last) cudaEventDestroy(ctx->ev_last);
+  if (ctx->ev_t0) cudaEventDestroy(ctx->ev_t0);
+  if (ctx->ev_t1) cudaEventDestroy(ctx->ev_t1);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return BSM_OK;
+}
+
+int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_t nbcols,
+                   const int32_t *col_sizes, int64_t nblocks, const int32_t *blk_row,
+                   const int32_t *blk_col, const double *values, bsm_mat *out) {
+  if (!ctx || !out || nbrows < 0 || nbcols < 0 || nblocks < 0) return BSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((nbrows > 0 && !row_sizes) || (nbcols > 0 && !col_sizes)) return BSM_ERR_INVALID_ARG;
+  if (nblocks > 0 && (!blk_row || !blk_col)) return BSM_ERR_INVALID_ARG;
+  if (nblocks >= (int64_t)INT32_MAX) return BSM_ERR_UNSUPPORTED;
+  for (int32_t i = 0; i < nbrows; i++)
+    if (row_sizes[i] <= 0) return BSM_ERR_INVALID_ARG;
+  for (int32_t j = 0; j < nbcols; j++)
+    if (col_sizes[j] <= 0) return BSM_ERR_INVALID_ARG;
+  // list offsets, range check, CSR order
+  std::vector<int64_t> list_off((size_t)nblocks + 1, 0);
+  bool sorted = true;
+  for (int64_t b = 0; b < nblocks; b++) {
+    const int32_t i = blk_row[b], j = blk_col[b];
+    if (i < 0 || i >= nbrows || j < 0 || j >= nbcols) return BSM_ERR_OUT_OF_RANGE;
+    list_off[b + 1] = list_off[b] + (int64_t)row_sizes[i] * col_sizes[j];
+    if (b > 0 && (blk_row[b - 1] > i || (blk_row[b - 1] == i && blk_col[b - 1] >= j)))
+      sorted = false;
+  }
+  const int64_t nnz = list_off[nblocks];
+  std::vector<int64_t> order;
+  if (!sorted) {
+    order.resize(nblocks);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+      return blk_row[a] != blk_row[b] ? blk_row[a] < blk_row[b] : blk_col[a] < blk_col[b];
+    });
+    for (int64_t p = 1; p < nblocks; p++)
+      if (blk_row[order[p]] == blk_row[order[p - 1]] && blk_col[order[p]] == blk_col[order[p - 1]])
+        return BSM_ERR_DUPLICATE_BLOCK;
+  }
+  int rc = ctx_set_device(ctx);
+  if (rc) return rc;
+  bsm_mat M = new (std::nothrow) bsm_mat_s();
+  if (!M) return BSM_ERR_NOMEM;
+  M->ctx = ctx;
+  M->nbr = nbrows;
+  M->nbc = nbcols;
+  M->h_row_sizes.assign(row_sizes, row_sizes + nbrows);
+  M->h_col_sizes.assign(col_sizes, col_sizes + nbcols);
+  ctx->mats.push_back(M);
+  auto fail = [&](int code) {
+    bsm_mat_destroy(M);
+    return code;
+  };
+  if ((rc = dev_alloc(&M->row_sizes, nbrows)) || (rc = dev_alloc(&M->col_sizes, nbcols)))
+    return fail(rc);
+  if ((rc = buf_grow(M, M->front, nblocks, nnz, true))) return fail(rc);
+  // host-side CSR arrays in sorted order
+  std::vector<int32_t> h_row_ptr((size_t)nbrows + 1, 0), h_col((size_t)nblocks), h_row((size_t)nblocks);
+  std::vector<int64_t> h_off((size_t)nblocks);
+  std::vector<double> staged;
+  const double *vsrc = values;
+  if (!sorted && values) staged.resize((size_t)nnz);
+  int64_t acc = 0;
+  for (int64_t p = 0; p < nblocks; p++) {
+    const int64_t b = sorted ? p : order[p];
+    h_row[p] = blk_row[b];
+    h_col[p] = blk_col[b];
+    h_off[p] = acc;
+    const int64_t len = list_off[b + 1] - list_off[b];
+    if (!sorted && values) memcpy(&staged[acc], values + list_off[b], (size_t)len * sizeof(double));
+    acc += len;
+    h_row_ptr[blk_row[b] + 1]++;
+  }
+  for (int32_t i = 0; i < nbrows; i++) h_row_ptr[i + 1] += h_row_ptr[i];
+  if (!sorted && values) vsrc = staged.data();
+  cudaStream_t s = ctx->stream;
+  int64_t hdr[2] = {nblocks, nnz};
+  auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  cudaError_t e;
+  if ((e = cp(M->row_sizes, row_sizes, (size_t)nbrows * 4)) != cudaSuccess ||
+      (e = cp(M->col_sizes, col_sizes, (size_t)nbcols * 4)) != cudaSuccess ||
+      (e = cp(M->front.row_ptr, h_row_ptr.data(), ((size_t)nbrows + 1) * 4)) != cudaSuccess ||
+      (e = cp(M->front.col_idx, h_col.data(), (size_t)nblocks * 4)) != cudaSuccess ||
+      (e = cp(M->front.blk_row, h_row.data(), (size_t)nblocks * 4)) != cudaSuccess ||
+      (e = cp(M->front.blk_off, h_off.data(), (size_t)nblocks * 8)) != cudaSuccess ||
+      (e = cp(M->front.hdr, hdr, sizeof(hdr))) != cudaSuccess) {
+    return fail(cuda_fail(e, "bsm_mat_create copy"));
+  }
+  if (vsrc) {
+    if ((e = cp(M->front.vals, vsrc, (size_t)nnz * 8)) != cudaSuccess)
+      return fail(cuda_fail(e, "bsm_mat_create values"));
+  } else if (nnz > 0) {
+    if ((e = cudaMemsetAsync(M->front.vals, 0, (size_t)nnz * 8, s)) != cudaSuccess)
+      return fail(cuda_fail(e, "bsm_mat_create zero"));
+  }
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "bsm_mat_create sync"));
+  M->nblk = nblocks;
+  M->nnz = nnz;
+  *out = M;
+  return BSM_OK;
+}
+
+int bsm_mat_destroy(bsm_mat m) {
+  if (!m) return BSM_ERR_INVALID_ARG;
+  bsm_ctx ctx = m->ctx;
+  cudaSetDevice(ctx->device);
+  // any pending multiply may read this matrix: finish all work first
+  cudaStreamSynchronize(ctx->stream);
+  for (bsm_mat o : ctx->mats)
+    if (o != m && o->pend.active && (o->pend.A == m || o->pend.B == m)) resolve(o);
+  for (int i = 0; i < kSlots; i++)
+    if (ctx->slot_owner[i] == m) ctx->slot_owner[i] = nullptr;
+  m->front.release();
+  m->back.release();
+  dev_free(m->row_sizes);
+  dev_free(m->col_sizes);
+  auto &v = ctx->mats;
+  v.erase(std::remove(v.begin(), v.end(), m), v.end());
+  delete m;
+  return BSM_OK;
+}
+
+int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, bsm_mat C,
+                 double eps, const bsm_opts *opts, bsm_stats *stats) {
+  if (!ctx || !A || !B || !C) return BSM_ERR_INVALID_ARG;
+  if (A->ctx != ctx || B->ctx != ctx || C->ctx != ctx) return BSM_ERR_INVALID_ARG;
+  if (C == A || C == B) return BSM_ERR_ALIAS;
+  bsm_opts o{};
+  if (opts) o = *opts;
+  if (o.precision != BSM_PREC_FP64) return BSM_ERR_UNSUPPORTED;
+  if (o.launch != BSM_LAUNCH_PERSISTENT && o.launch != BSM_LAUNCH_PER_STACK)
+    return BSM_ERR_INVALID_ARG;
+  if (A->nbc != B->nbr || A->h_col_sizes != B->h_row_sizes) return BSM_ERR_DIM_MISMATCH;
+  if (C->nbr != A->nbr || C->nbc != B->nbc || C->h_row_sizes != A->h_row_sizes ||
+      C->h_col_sizes != B->h_col_sizes)
+    return BSM_ERR_DIM_MISMATCH;
+  int rc = ctx_set_device(ctx);
+  if (rc) return rc;
+  if ((rc = resolve(A)) || (rc = resolve(B))) return rc;
+  if (beta != 0.0) {
+    if ((rc = resolve(C))) return rc;
+  } else {
+    C->pend.active = false;  // superseded: the previous result is not read
+  }
+  const int slot = take_slot(ctx, C);
+  if (slot < 0) return slot + 1000;
+  // size the buffers exactly now when the last result computed into C (or the
+  // workspace's product count) would not fit; otherwise the device checks itself
+  const bool sync_sizes = C->back.cap_blk < 0 || C->back.cap_blk < C->hint_blk ||
+                          C->back.cap_nnz < C->hint_nnz || ctx->ws.cap_prod <= 0 ||
+                          ctx->ws.cap_prod < ctx->hint_prod || ctx->cap_cblk <= C->hint_blk;
+  if (stats) stats->retries = 0;
+  rc = run_multiply(ctx, alpha, A, B, beta, C, eps, o, sync_sizes, slot, stats);
+  if (rc) return rc;
+  std::swap(C->front, C->back);
+  C->pend.active = true;
+  C->pend.A = A;
+  C->pend.B = B;
+  C->pend.alpha = alpha;
+  C->pend.beta = beta;
+  C->pend.eps = eps;
+  C->pend.opts = o;
+  C->pend.slot = slot;
+  if (o.blocking || stats) {
+    if ((rc = resolve(C, stats))) return rc;
+  }
+  if (stats) {
+    const DevStatus &h = ctx->h_slots[slot];
+    stats->candidates = h.candidates;
+    stats->kept = h.kept;
+    stats->dropped = h.candidates - h.kept;
+    stats->c_blocks = h.nblk_c;
+    stats->c_nnz = h.nnz_c;
+    stats->flops = (double)h.flops;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev_t0, ctx->ev_t1));
+    stats->ms_total = ms;
+    stats->reserved = 0;
+  }
+  return BSM_OK;
+}
+
+int bsm_mat_nblocks(bsm_mat m, int64_t *nblocks, int64_t *nnz) {
+  if (!m || !nblocks || !nnz) return BSM_ERR_INVALID_ARG;
+  int rc = ctx_set_device(m->ctx);
+  if (rc || (rc = resolve(m))) return rc;
+  *nblocks = m->nblk;
+  *nnz = m->nnz;
+  return BSM_OK;
+}
+
+int bsm_mat_get_pattern(bsm_mat m, int64_t cap, int32_t *blk_row, int32_t *blk_col) {
+  if (!m) return BSM_ERR_INVALID_ARG;
+  int rc = ctx_set_device(m->ctx);
+  if (rc || (rc = resolve(m))) return rc;
+  if (cap < m->nblk || (m->nblk > 0 && (!blk_row || !blk_col))) return BSM_ERR_INVALID_ARG;
+  if (m->nblk == 0) return BSM_OK;
+  cudaStream_t s = m->ctx->stream;
+  CK(cudaMemcpyAsync(blk_row, m->front.blk_row, (size_t)m->nblk * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(blk_col, m->front.col_idx, (size_t)m->nblk * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return BSM_OK;
+}
+
+int bsm_mat_get_values(bsm_mat m, int64_t cap, double *values) {
+  if (!m) return BSM_ERR_INVALID_ARG;
+  int rc = ctx_set_device(m->ctx);
+  if (rc || (rc = resolve(m))) return rc;
+  if (cap < m->nnz || (m->nnz > 0 && !values)) return BSM_ERR_INVALID_ARG;
+  if (m->nnz == 0) return BSM_OK;
+  cudaStream_t s = m->ctx->stream;
+  CK(cudaMemcpyAsync(values, m->front.vals, (size_t)m->nnz * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return BSM_OK;
+}
+
+int bsm_ctx_profile(bsm_ctx ctx, int enable) {
+  if (!ctx) return BSM_ERR_INVALID_ARG;
+  int rc = ctx_set_device(ctx);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int s = 0; s < kSlots; s++) {
+    ctx->prof_pending[s] = false;
+    if (enable && !ctx->prof_ev[s][0])
+      for (int e = 0; e < 4; e++) CK(cudaEventCreate(&ctx->prof_ev[s][e]));
+  }
+  ctx->prof = enable != 0;
+  ctx->prof_tot = bsm_profile{};
+  ctx->launches_at_enable = ctx->launches;
+  return BSM_OK;
+}
+
+int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out) {
+  if (!ctx || !out) return BSM_ERR_INVALID_ARG;
+  int rc = ctx_set_device(ctx);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int s = 0; s < kSlots; s++)
+    if ((rc = prof_collect(ctx, s))) return rc;
+  *out = ctx->prof_tot;
+  out->launches = ctx->launches - ctx->launches_at_enable;
+  return BSM_OK;
+}
+
+int bsm_sync(bsm_ctx ctx) {
+  if (!ctx) return BSM_ERR_INVALID_ARG;
+  int rc = ctx_set_device(ctx);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (bsm_mat m : std::vector<bsm_mat>(ctx->mats))
+    if (m->pend.active && (rc = resolve(m))) return rc;
+  return BSM_OK;
+}
+
+}  // extern "C"

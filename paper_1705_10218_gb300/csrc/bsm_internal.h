@@ -1,0 +1,97 @@
+// bsm_internal.h -- device-side views and kernel launchers shared by the
+// translation units of libbsm. Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bsm.h"
+
+namespace bsm {
+
+// Block columns handled per pass of the per-row bitmap in the symbolic phase.
+constexpr int kWindowCols = 65536;
+constexpr int kSymThreads = 256;
+// Largest output tile one warp accumulates in registers (32 x 32 scalars).
+constexpr int kTile = 32;
+
+// Read-only device view of a block-sparse matrix in blocked CSR form.
+// Blocks of a row are sorted by column; blk_off[b] is the offset of block b's
+// column-major values in vals.
+struct DevMat {
+  int32_t nbr, nbc;
+  const int32_t *row_sizes;  // [nbr]
+  const int32_t *col_sizes;  // [nbc]
+  const int32_t *row_ptr;    // [nbr+1]
+  const int32_t *col_idx;    // [nblk]
+  const int32_t *blk_row;    // [nblk]
+  const int64_t *blk_off;    // [nblk]
+  const double *vals;        // [nnz]
+  const double *norms;       // [nblk] canonical block norms
+  const int64_t *hdr;        // device header {nblk, nnz}
+};
+
+// Where the symbolic phase writes the result pattern of C.
+struct DevOut {
+  int32_t nbr, nbc;
+  const int32_t *row_sizes;
+  const int32_t *col_sizes;
+  int32_t *row_ptr;  // [nbr+1]
+  int32_t *col_idx;  // [cap_blk]
+  int32_t *blk_row;  // [cap_blk]
+  int64_t *blk_off;  // [cap_blk]
+  double *vals;      // [cap_nnz]
+  int64_t *hdr;      // {nblk, nnz}
+  int64_t cap_blk, cap_nnz;
+};
+
+// Per-context scratch of one multiply.
+struct DevWs {
+  int32_t *row_cblk;   // [nbr] C blocks per row
+  int64_t *row_prod;   // [nbr] kept products per row
+  int64_t *row_nnz;    // [nbr] C scalars per row
+  int64_t *row_cand;   // [nbr] candidate products per row
+  int64_t *row_flops;  // [nbr] 2mnk of kept products per row
+  int64_t *prod_off;   // [nbr+1] first product of each row
+  int64_t *nnz_off;    // [nbr+1] first C scalar of each row
+  int32_t *cnt;        // [cap_blk] per-C-block product counter / cursor
+  int32_t *c_cin;      // [cap_blk] index of the matching C_in block or -1
+  int64_t *prod_ptr;   // [cap_blk+1] first product of each C block
+  int2 *prods;         // [cap_prod] (A block, B block) per kept product
+  int64_t cap_prod;
+  int64_t cap_rows;
+};
+
+// Device status of one multiply (written by the device, copied to pinned host).
+struct DevStatus {
+  int64_t nblk_c;
+  int64_t nnz_c;
+  int64_t nprod;
+  int64_t candidates;
+  int64_t kept;
+  int64_t flops;    // sum of 2*m*n*k over kept products (exact integer)
+  int32_t overflow; // 1: a capacity was too small; later phases skipped
+  int32_t error;    // nonzero: a device-side check failed
+};
+
+// ---- launchers (each enqueues on `stream`, returns cudaGetLastError()) ----
+cudaError_t launch_block_norms(const int32_t *row_sizes, const int32_t *col_sizes,
+                               const int32_t *blk_row, const int32_t *col_idx,
+                               const int64_t *blk_off, const double *vals, const int64_t *hdr,
+                               double *norms, int grid, cudaStream_t stream);
+
+cudaError_t launch_symbolic_count(DevMat A, DevMat B, DevMat Cin, int use_cin, double eps,
+                                  DevWs ws, int grid, cudaStream_t stream);
+
+cudaError_t launch_symbolic_scan(int32_t nbr, DevWs ws, DevOut C, DevStatus *st,
+                                 cudaStream_t stream);
+
+cudaError_t launch_symbolic_fill(DevMat A, DevMat B, DevMat Cin, int use_cin, double eps,
+                                 DevWs ws, DevOut C, const DevStatus *st, int grid,
+                                 cudaStream_t stream);
+
+cudaError_t launch_numeric_fp64(DevMat A, DevMat B, DevOut C, DevMat Cin, double alpha,
+                                double beta, DevWs ws, const DevStatus *st, int grid,
+                                cudaStream_t stream);
+
+}  // namespace bsm

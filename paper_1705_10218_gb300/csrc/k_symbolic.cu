@@ -1,0 +1,430 @@
+// k_symbolic.cu -- block norms, symbolic phase with the on-the-fly filter,
+// and the per-C-block grouping of the kept products.
+//
+// Sec. 2 of the paper: the result pattern is determined by the multiplication
+// itself, and a block product is only performed when the product of the two
+// block norms passes the threshold. Here that becomes three device passes:
+//   count: per C block row, the set of columns reached by a kept product
+//          (a bitmap in shared memory), the number of kept products, FLOPs;
+//   scan:  exclusive sums over block rows -> C's row pointers, product and
+//          value offsets, and the capacity check of the output buffers;
+//   fill:  per C block row, the sorted column list of C, every C block's
+//          value offset, and the kept products written grouped by C block in
+//          ascending k (a per-row counting sort), so that the numeric phase
+//          accumulates each C block in one place, without atomics.
+#include "bsm_internal.h"
+
+namespace bsm {
+
+// The filter of Sec. 2: drop iff nrm(A_ik)*nrm(B_kj) < eps (a tie and NaN are kept).
+__device__ __forceinline__ bool keep_product(double na, double nb, double eps) {
+  return !(__dmul_rn(na, nb) < eps);
+}
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int lo, int hi, int key) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ----------------------------------------------------------------------------
+// Block norms: canonical Frobenius norm, column-major, no fused multiply-add.
+// One thread per block, grid-stride; the block count is read on the device so
+// a matrix produced by an earlier multiply needs no host round trip.
+// ----------------------------------------------------------------------------
+__global__ void k_block_norms(const int32_t *__restrict__ row_sizes,
+                              const int32_t *__restrict__ col_sizes,
+                              const int32_t *__restrict__ blk_row,
+                              const int32_t *__restrict__ col_idx,
+                              const int64_t *__restrict__ blk_off,
+                              const double *__restrict__ vals, const int64_t *__restrict__ hdr,
+                              double *__restrict__ norms) {
+  const int64_t nblk = hdr[0];
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = (int64_t)row_sizes[blk_row[b]] * col_sizes[col_idx[b]];
+    const double *x = vals + blk_off[b];
+    double s = 0.0;
+    for (int64_t e = 0; e < n; e++) {
+      const double v = __ldg(x + e);
+      s = __dadd_rn(s, __dmul_rn(v, v));
+    }
+    norms[b] = __dsqrt_rn(s);
+  }
+}
+
+cudaError_t launch_block_norms(const int32_t *row_sizes, const int32_t *col_sizes,
+                               const int32_t *blk_row, const int32_t *col_idx,
+                               const int64_t *blk_off, const double *vals, const int64_t *hdr,
+                               double *norms, int grid, cudaStream_t stream) {
+  k_block_norms<<<grid, 256, 0, stream>>>(row_sizes, col_sizes, blk_row, col_idx, blk_off, vals,
+                                          hdr, norms);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Block-wide exclusive scan of one int64 per thread (blockDim a multiple of 32,
+// at most 1024). Returns the exclusive prefix; *total gets the block sum.
+// ----------------------------------------------------------------------------
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
+  __shared__ int64_t warp_sums[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = (lane < nwarps) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nwarps) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  const int64_t before = (warp > 0) ? warp_sums[warp - 1] : 0;
+  *total = warp_sums[nwarps - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__device__ int64_t block_sum(int64_t v) {
+  int64_t t;
+  block_exclusive_scan(v, &t);
+  return t;
+}
+
+// ----------------------------------------------------------------------------
+// The kept-column bitmap of C block row i over the window [w0, w0+wn):
+// bit (j-w0) is set iff some kept product (i,k,j) exists, or (when use_cin)
+// C_in holds block (i,j). Warps walk A's row i, lanes walk B's row k.
+// With COUNT, also counts candidates, kept products and their 2mnk.
+// ----------------------------------------------------------------------------
+template <bool COUNT>
+__device__ void row_bitmap(const DevMat &A, const DevMat &B, const DevMat &Cin, int use_cin,
+                           double eps, int i, int w0, int wn, bool whole, uint32_t *bitmap,
+                           int nwords, int64_t &cand, int64_t &kept, int64_t &flops) {
+  for (int t = threadIdx.x; t < nwords; t += blockDim.x) bitmap[t] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int m = A.row_sizes[i];
+  const int p0 = A.row_ptr[i], p1 = A.row_ptr[i + 1];
+  for (int p = p0 + warp; p < p1; p += nwarps) {
+    const int k = A.col_idx[p];
+    const double na = A.norms[p];
+    int q0 = B.row_ptr[k], q1 = B.row_ptr[k + 1];
+    if (!whole) {
+      q0 = lower_bound_i32(B.col_idx, q0, q1, w0);
+      q1 = lower_bound_i32(B.col_idx, q0, q1, w0 + wn);
+    }
+    const int64_t ms = (int64_t)m * B.row_sizes[k];
+    for (int q = q0 + lane; q < q1; q += 32) {
+      const int j = B.col_idx[q];
+      if (COUNT) cand++;
+      if (keep_product(na, B.norms[q], eps)) {
+        const int jj = j - w0;
+        atomicOr(&bitmap[jj >> 5], 1u << (jj & 31));
+        if (COUNT) {
+          kept++;
+          flops += 2 * ms * B.col_sizes[j];
+        }
+      }
+    }
+  }
+  if (use_cin) {
+    int c0 = Cin.row_ptr[i], c1 = Cin.row_ptr[i + 1];
+    if (!whole) {
+      c0 = lower_bound_i32(Cin.col_idx, c0, c1, w0);
+      c1 = lower_bound_i32(Cin.col_idx, c0, c1, w0 + wn);
+    }
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      const int jj = Cin.col_idx[c] - w0;
+      atomicOr(&bitmap[jj >> 5], 1u << (jj & 31));
+    }
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------
+// Count pass: one thread block per C block row (grid-stride).
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSymThreads) k_symbolic_count(DevMat A, DevMat B, DevMat Cin,
+                                                                int use_cin, double eps,
+                                                                DevWs ws) {
+  extern __shared__ uint32_t smem_bits[];
+  const int nbc = B.nbc;
+  const bool whole = nbc <= kWindowCols;
+  for (int i = blockIdx.x; i < A.nbr; i += gridDim.x) {
+    int64_t cand = 0, kept = 0, flops = 0, colsum = 0, nblk = 0;
+    for (int w0 = 0; w0 < nbc; w0 += kWindowCols) {
+      const int wn = min(kWindowCols, nbc - w0);
+      const int nwords = (wn + 31) >> 5;
+      row_bitmap<true>(A, B, Cin, use_cin, eps, i, w0, wn, whole, smem_bits, nwords, cand, kept,
+                       flops);
+      for (int t = threadIdx.x; t < nwords; t += blockDim.x) {
+        uint32_t bits = smem_bits[t];
+        nblk += __popc(bits);
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1;
+          colsum += B.col_sizes[w0 + 32 * t + b];
+        }
+      }
+      __syncthreads();
+    }
+    cand = block_sum(cand);
+    kept = block_sum(kept);
+    flops = block_sum(flops);
+    colsum = block_sum(colsum);
+    nblk = block_sum(nblk);
+    if (threadIdx.x == 0) {
+      ws.row_cblk[i] = (int32_t)nblk;
+      ws.row_prod[i] = kept;
+      ws.row_nnz[i] = (int64_t)A.row_sizes[i] * colsum;
+      ws.row_cand[i] = cand;
+      ws.row_flops[i] = flops;
+    }
+  }
+}
+
+cudaError_t launch_symbolic_count(DevMat A, DevMat B, DevMat Cin, int use_cin, double eps,
+                                  DevWs ws, int grid, cudaStream_t stream) {
+  const int nwords = (min(B.nbc, kWindowCols) + 31) / 32;
+  const size_t smem = (size_t)max(nwords, 1) * sizeof(uint32_t);
+  k_symbolic_count<<<grid, kSymThreads, smem, stream>>>(A, B, Cin, use_cin, eps, ws);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Scan pass: one thread block of 1024 threads. Exclusive sums over block rows,
+// totals, capacity check, C's header and the sentinel of the product ranges.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_symbolic_scan(int32_t nbr, DevWs ws, DevOut C,
+                                                        DevStatus *st) {
+  const int T = blockDim.x;
+  const int per = (nbr + T - 1) / T;
+  const int beg = min(nbr, (int)threadIdx.x * per), end = min(nbr, beg + per);
+  int64_t sb = 0, sp = 0, sn = 0, sc = 0, sf = 0;
+  for (int r = beg; r < end; r++) {
+    sb += ws.row_cblk[r];
+    sp += ws.row_prod[r];
+    sn += ws.row_nnz[r];
+    sc += ws.row_cand[r];
+    sf += ws.row_flops[r];
+  }
+  int64_t tb, tp, tn;
+  int64_t ob = block_exclusive_scan(sb, &tb);
+  int64_t op = block_exclusive_scan(sp, &tp);
+  int64_t on = block_exclusive_scan(sn, &tn);
+  const int64_t tc = block_sum(sc);
+  const int64_t tf = block_sum(sf);
+  for (int r = beg; r < end; r++) {
+    C.row_ptr[r] = (int32_t)ob;
+    ws.prod_off[r] = op;
+    ws.nnz_off[r] = on;
+    ob += ws.row_cblk[r];
+    op += ws.row_prod[r];
+    on += ws.row_nnz[r];
+  }
+  if (threadIdx.x == 0) {
+    C.row_ptr[nbr] = (int32_t)tb;
+    ws.prod_off[nbr] = tp;
+    ws.nnz_off[nbr] = tn;
+    const int overflow = (tb > C.cap_blk) || (tn > C.cap_nnz) || (tp > ws.cap_prod) ||
+                         (tb >= (int64_t)INT32_MAX);
+    st->nblk_c = tb;
+    st->nnz_c = tn;
+    st->nprod = tp;
+    st->candidates = tc;
+    st->kept = tp;
+    st->flops = tf;
+    st->overflow = overflow;
+    st->error = 0;
+    if (!overflow) {
+      C.hdr[0] = tb;
+      C.hdr[1] = tn;
+      ws.prod_ptr[tb] = tp;
+    }
+  }
+}
+
+cudaError_t launch_symbolic_scan(int32_t nbr, DevWs ws, DevOut C, DevStatus *st,
+                                 cudaStream_t stream) {
+  k_symbolic_scan<<<1, 1024, 0, stream>>>(nbr, ws, C, st);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Fill pass helpers.
+// ----------------------------------------------------------------------------
+// wpre[t] = number of set bits in bitmap[0..t); returns the total.
+__device__ int word_prefix(const uint32_t *bitmap, int32_t *wpre, int nwords) {
+  const int per = (nwords + blockDim.x - 1) / blockDim.x;
+  const int beg = min(nwords, (int)threadIdx.x * per), end = min(nwords, beg + per);
+  int64_t s = 0;
+  for (int t = beg; t < end; t++) s += __popc(bitmap[t]);
+  int64_t total;
+  int64_t run = block_exclusive_scan(s, &total);
+  for (int t = beg; t < end; t++) {
+    wpre[t] = (int32_t)run;
+    run += __popc(bitmap[t]);
+  }
+  __syncthreads();
+  return (int)total;
+}
+
+// Rank of column offset jj inside the window among the set bits.
+__device__ __forceinline__ int bit_rank(const uint32_t *bitmap, const int32_t *wpre, int jj) {
+  return wpre[jj >> 5] + __popc(bitmap[jj >> 5] & ((1u << (jj & 31)) - 1u));
+}
+
+// ----------------------------------------------------------------------------
+// Fill pass: one thread block per C block row (grid-stride).
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSymThreads) k_symbolic_fill(DevMat A, DevMat B, DevMat Cin,
+                                                               int use_cin, double eps, DevWs ws,
+                                                               DevOut C, const DevStatus *st) {
+  if (st->overflow) return;
+  extern __shared__ uint32_t smem_bits[];
+  const int nbc = B.nbc;
+  const bool whole = nbc <= kWindowCols;
+  const int nwords_max = (min(nbc, kWindowCols) + 31) >> 5;
+  uint32_t *bitmap = smem_bits;
+  int32_t *wpre = reinterpret_cast<int32_t *>(smem_bits + nwords_max);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int64_t dummy0 = 0, dummy1 = 0, dummy2 = 0;
+
+  for (int i = blockIdx.x; i < A.nbr; i += gridDim.x) {
+    const int g0 = C.row_ptr[i], g1 = C.row_ptr[i + 1];
+    if (g0 == g1) continue;
+    const int m = A.row_sizes[i];
+    const int p0 = A.row_ptr[i], p1 = A.row_ptr[i + 1];
+
+    // pass 1: C blocks of the row, per-block product counts, C_in map
+    int slot_base = 0;
+    for (int w0 = 0; w0 < nbc; w0 += kWindowCols) {
+      const int wn = min(kWindowCols, nbc - w0);
+      const int nwords = (wn + 31) >> 5;
+      row_bitmap<false>(A, B, Cin, use_cin, eps, i, w0, wn, whole, bitmap, nwords, dummy0, dummy1,
+                        dummy2);
+      const int nw = word_prefix(bitmap, wpre, nwords);
+      for (int t = threadIdx.x; t < nwords; t += blockDim.x) {
+        uint32_t bits = bitmap[t];
+        int g = g0 + slot_base + wpre[t];
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1;
+          C.col_idx[g] = w0 + 32 * t + b;
+          C.blk_row[g] = i;
+          ws.cnt[g] = 0;
+          ws.c_cin[g] = -1;
+          g++;
+        }
+      }
+      __syncthreads();
+      for (int p = p0 + warp; p < p1; p += nwarps) {
+        const int k = A.col_idx[p];
+        const double na = A.norms[p];
+        int q0 = B.row_ptr[k], q1 = B.row_ptr[k + 1];
+        if (!whole) {
+          q0 = lower_bound_i32(B.col_idx, q0, q1, w0);
+          q1 = lower_bound_i32(B.col_idx, q0, q1, w0 + wn);
+        }
+        for (int q = q0 + lane; q < q1; q += 32) {
+          if (keep_product(na, B.norms[q], eps)) {
+            const int g = g0 + slot_base + bit_rank(bitmap, wpre, B.col_idx[q] - w0);
+            atomicAdd(&ws.cnt[g], 1);
+          }
+        }
+      }
+      if (use_cin) {
+        int c0 = Cin.row_ptr[i], c1 = Cin.row_ptr[i + 1];
+        if (!whole) {
+          c0 = lower_bound_i32(Cin.col_idx, c0, c1, w0);
+          c1 = lower_bound_i32(Cin.col_idx, c0, c1, w0 + wn);
+        }
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+          const int g = g0 + slot_base + bit_rank(bitmap, wpre, Cin.col_idx[c] - w0);
+          ws.c_cin[g] = c;
+        }
+      }
+      __syncthreads();
+      slot_base += nw;
+    }
+
+    // pass 2: product ranges and value offsets of the row's C blocks
+    {
+      int64_t carry_p = ws.prod_off[i], carry_v = ws.nnz_off[i];
+      for (int base = g0; base < g1; base += blockDim.x) {
+        const int g = base + threadIdx.x;
+        const bool in = g < g1;
+        const int64_t cp = in ? ws.cnt[g] : 0;
+        const int64_t cv = in ? (int64_t)m * C.col_sizes[C.col_idx[g]] : 0;
+        int64_t tp, tv;
+        const int64_t ep = block_exclusive_scan(cp, &tp);
+        const int64_t ev = block_exclusive_scan(cv, &tv);
+        if (in) {
+          ws.prod_ptr[g] = carry_p + ep;
+          C.blk_off[g] = carry_v + ev;
+          ws.cnt[g] = 0;
+        }
+        carry_p += tp;
+        carry_v += tv;
+      }
+      __syncthreads();
+    }
+
+    // pass 3: kept products grouped by C block, ascending k inside a block
+    slot_base = 0;
+    for (int w0 = 0; w0 < nbc; w0 += kWindowCols) {
+      const int wn = min(kWindowCols, nbc - w0);
+      const int nwords = (wn + 31) >> 5;
+      int nw;
+      if (!whole) {
+        row_bitmap<false>(A, B, Cin, use_cin, eps, i, w0, wn, whole, bitmap, nwords, dummy0,
+                          dummy1, dummy2);
+        nw = word_prefix(bitmap, wpre, nwords);
+      } else {
+        nw = g1 - g0;
+      }
+      for (int p = p0; p < p1; p++) {
+        const int k = A.col_idx[p];
+        const double na = A.norms[p];
+        int q0 = B.row_ptr[k], q1 = B.row_ptr[k + 1];
+        if (!whole) {
+          q0 = lower_bound_i32(B.col_idx, q0, q1, w0);
+          q1 = lower_bound_i32(B.col_idx, q0, q1, w0 + wn);
+        }
+        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+          if (keep_product(na, B.norms[q], eps)) {
+            const int g = g0 + slot_base + bit_rank(bitmap, wpre, B.col_idx[q] - w0);
+            const int c = ws.cnt[g];
+            ws.cnt[g] = c + 1;
+            ws.prods[ws.prod_ptr[g] + c] = make_int2(p, q);
+          }
+        }
+        __syncthreads();
+      }
+      slot_base += nw;
+    }
+  }
+}
+
+cudaError_t launch_symbolic_fill(DevMat A, DevMat B, DevMat Cin, int use_cin, double eps,
+                                 DevWs ws, DevOut C, const DevStatus *st, int grid,
+                                 cudaStream_t stream) {
+  const int nwords = (min(B.nbc, kWindowCols) + 31) / 32;
+  const size_t smem = (size_t)max(nwords, 1) * 2 * sizeof(uint32_t);
+  k_symbolic_fill<<<grid, kSymThreads, smem, stream>>>(A, B, Cin, use_cin, eps, ws, C, st);
+  return cudaGetLastError();
+}
+
+}  // namespace bsm

@@ -18,3 +18,25 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def bsm_lib():
+    from paper_1705_10218_gb300 import build as _b
+
+    _b.build()
+    import paper_1705_10218_gb300 as P
+
+    P.lib()
+    return P
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx(bsm_lib):
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for tests marked gpu")
+    ctx = bsm_lib.Context(0)
+    yield ctx
+    ctx.close()

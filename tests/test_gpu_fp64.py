@@ -1,0 +1,205 @@
+"""GPU parity of the FP64 path against the CPU oracle, through the C ABI.
+
+The C pattern must match bit for bit (sorted (row, col) lists and the filter
+counters); values must match within 1e-12 relative Frobenius error over the
+whole of C (exactly, for small-integer inputs with eps = 0, where every sum is
+an exact integer)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from synth import BlockMatrix
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def run_gpu(ctx, A, B, alpha=1.0, beta=0.0, C=None, eps=0.0, **kw):
+    dA = ctx.from_blocks(A)
+    dB = dA if B is A else ctx.from_blocks(B)
+    dC = ctx.from_blocks(C) if C is not None else ctx.empty(A.row_sizes, B.col_sizes)
+    st = ctx.multiply(alpha, dA, dB, beta, dC, eps, stats=True, **kw)
+    r, c = dC.pattern()
+    v = dC.values()
+    for m in {id(dA): dA, id(dB): dB, id(dC): dC}.values():
+        m.destroy()
+    return r, c, v, st
+
+
+def check(ctx, oracle_mod, A, B, alpha=1.0, beta=0.0, C=None, eps=0.0, exact=False, **kw):
+    ref = oracle_mod.multiply(A, B, alpha=alpha, beta=beta, C=C, eps=eps)
+    r, c, v, st = run_gpu(ctx, A, B, alpha, beta, C, eps, **kw)
+    assert np.array_equal(r, ref.blk_row), "pattern rows differ"
+    assert np.array_equal(c, ref.blk_col), "pattern cols differ"
+    assert st.candidates == ref.candidates and st.kept == ref.kept and st.dropped == ref.dropped
+    assert st.c_blocks == len(ref.blk_row) and st.c_nnz == ref.nnz
+    assert st.flops == ref.flops
+    if exact:
+        assert np.array_equal(v, ref.values)
+    else:
+        assert H.rel_frobenius(v, ref.values) <= TOL
+    return ref, v, st
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (2.0, 1.0), (-1.0, -0.5)])
+def test_integer_exact(gpu_ctx, oracle_mod, seed, alpha, beta):
+    rng = np.random.default_rng(500 + seed)
+    sizes = (1, 2, 3, 5, 13)
+    rs, ks, cs = rng.choice(sizes, 9), rng.choice(sizes, 11), rng.choice(sizes, 10)
+    A = synth.random_blocks(rng, rs, ks, 0.4, kind="int", shuffle=True)
+    B = synth.random_blocks(rng, ks, cs, 0.4, kind="int", shuffle=True)
+    C = synth.random_blocks(rng, rs, cs, 0.3, kind="int", shuffle=True)
+    check(gpu_ctx, oracle_mod, A, B, alpha, beta, C, eps=0.0, exact=True)
+
+
+def test_water64_config(gpu_ctx, oracle_mod):
+    """64 water molecules, eps 1e-10 (the small water configuration)."""
+    A = synth.water(64, seed=0)
+    ref, v, st = check(gpu_ctx, oracle_mod, A, A, eps=1e-10)
+    assert st.c_blocks == A.nbr * A.nbc  # C is fully dense at this size
+
+
+def test_filter_active(gpu_ctx, oracle_mod):
+    """eps at the 30th percentile of the candidate norm products: the same
+    products must be dropped on both sides (bit-exact pattern and counters)."""
+    A = synth.water(24, seed=7, cutoff=5.0)
+    nA = oracle_mod.norms(A)
+    prods = []
+    for a in range(A.nblk):
+        sel = A.blk_row == A.blk_col[a]
+        prods.append(nA[a] * nA[sel])
+    eps = float(np.percentile(np.concatenate(prods), 30))
+    ref, _, st = check(gpu_ctx, oracle_mod, A, A, eps=eps)
+    assert 0 < st.dropped < st.candidates
+
+
+def test_filter_ties_and_nan(gpu_ctx, oracle_mod):
+    def single(v):
+        return BlockMatrix(np.array([1], np.int32), np.array([1], np.int32), np.array([0], np.int32),
+                           np.array([0], np.int32), np.array([v], np.float64))
+    A, B = single(2.0 ** -10), single(2.0 ** -20)
+    _, _, v, st = run_gpu(gpu_ctx, A, B, eps=2.0 ** -30)
+    assert st.kept == 1 and v[0] == 2.0 ** -30
+    r, _, _, st = run_gpu(gpu_ctx, A, B, eps=math.nextafter(2.0 ** -30, math.inf))
+    assert st.kept == 0 and len(r) == 0
+    _, _, v, st = run_gpu(gpu_ctx, single(np.nan), B, eps=1e300)
+    assert st.kept == 1 and np.isnan(v[0])
+
+
+def test_large_and_odd_blocks(gpu_ctx, oracle_mod):
+    """Block sizes above the 32 x 32 register tile and odd shapes."""
+    rng = np.random.default_rng(12)
+    sizes = (1, 7, 33, 40, 64, 65)
+    rs, ks, cs = rng.choice(sizes, 5), rng.choice(sizes, 6), rng.choice(sizes, 4)
+    A = synth.random_blocks(rng, rs, ks, 0.6, kind="normal")
+    B = synth.random_blocks(rng, ks, cs, 0.6, kind="normal")
+    C = synth.random_blocks(rng, rs, cs, 0.5, kind="normal")
+    check(gpu_ctx, oracle_mod, A, B, 0.75, 1.5, C, eps=0.0)
+
+
+def test_beta_zero_ignores_nan_c(gpu_ctx, oracle_mod):
+    rng = np.random.default_rng(4)
+    rs = rng.choice([2, 3, 13], 8)
+    A = synth.random_blocks(rng, rs, rs, 0.25, kind="normal")
+    C = synth.random_blocks(rng, rs, rs, 0.9, kind="normal")
+    C.values[:] = np.nan
+    ref, v, _ = check(gpu_ctx, oracle_mod, A, A, 1.0, 0.0, C, eps=0.0)
+    assert not np.isnan(v).any()
+
+
+def test_empty_and_degenerate(gpu_ctx, oracle_mod):
+    rs = np.array([2, 3, 5], np.int32)
+    E = BlockMatrix(rs, rs, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    C = synth.random_blocks(np.random.default_rng(0), rs, rs, 0.7, kind="int")
+    r, c, v, st = run_gpu(gpu_ctx, E, E)
+    assert len(r) == 0 and st.candidates == 0
+    check(gpu_ctx, oracle_mod, E, E, 1.0, 2.0, C, exact=True)
+    A = synth.random_blocks(np.random.default_rng(1), rs, rs, 0.7, kind="int")
+    check(gpu_ctx, oracle_mod, A, A, 0.0, -0.5, C, exact=True)  # alpha = 0
+    # a single block row / column
+    one = np.array([4], np.int32)
+    A1 = synth.random_blocks(np.random.default_rng(2), one, rs, 1.0, kind="int")
+    B1 = synth.random_blocks(np.random.default_rng(3), rs, one, 1.0, kind="int")
+    check(gpu_ctx, oracle_mod, A1, B1, exact=True)
+
+
+def test_ragged_many_rows(gpu_ctx, oracle_mod):
+    """Many block rows (several grid strides of the row-parallel passes) with
+    a ragged mix of sizes and empty rows."""
+    rng = np.random.default_rng(33)
+    n = 2500
+    rs = rng.choice([1, 5, 9, 13], n)
+    A = synth.random_blocks(rng, rs, rs, 0.004, kind="normal")
+    check(gpu_ctx, oracle_mod, A, A, eps=0.0)
+
+
+def test_chain_and_reuse(gpu_ctx, oracle_mod):
+    """C1 = A.A, then C2 = C1.A (a computed matrix as input), then the same C
+    handle reused for results of different sizes, asynchronously."""
+    A = synth.water(16, seed=9)
+    ctx = gpu_ctx
+    dA = ctx.from_blocks(A)
+    C1 = ctx.empty(A.row_sizes, A.col_sizes)
+    C2 = ctx.empty(A.row_sizes, A.col_sizes)
+    ctx.multiply(1.0, dA, dA, 0.0, C1, 1e-10)
+    ctx.multiply(1.0, C1, dA, 0.0, C2, 1e-10)
+    r1 = oracle_mod.multiply(A, A, eps=1e-10)
+    M1 = H.result_matrix(r1, A.row_sizes, A.col_sizes)
+    r2 = oracle_mod.multiply(M1, A, eps=1e-10)
+    r, c = C2.pattern()
+    assert np.array_equal(r, r2.blk_row) and np.array_equal(c, r2.blk_col)
+    assert H.rel_frobenius(C2.values(), r2.values) <= TOL
+    # reuse C2 for a smaller and then a larger result, then beta accumulation
+    S = synth.random_blocks(np.random.default_rng(5), A.row_sizes, A.col_sizes, 0.05, kind="normal")
+    dS = ctx.from_blocks(S)
+    ctx.multiply(1.0, dS, dS, 0.0, C2, 0.0)
+    ctx.multiply(1.0, dA, dA, 0.0, C2, 0.0)
+    ctx.multiply(2.0, dS, dA, 0.5, C2, 0.0)
+    ref_a = oracle_mod.multiply(A, A, eps=0.0)
+    ref = oracle_mod.multiply(S, A, alpha=2.0, beta=0.5, C=H.result_matrix(ref_a, A.row_sizes, A.col_sizes))
+    r, c = C2.pattern()
+    assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+    assert H.rel_frobenius(C2.values(), ref.values) <= TOL
+    for m in (dA, C1, C2, dS):
+        m.destroy()
+
+
+def test_errors(gpu_ctx, bsm_lib):
+    ctx = gpu_ctx
+    rs = np.array([2, 3], np.int32)
+    with pytest.raises(bsm_lib.BsmError) as e:
+        ctx.matrix(rs, rs, [0, 0], [1, 1], np.zeros(12))
+    assert e.value.name == "DUPLICATE_BLOCK"
+    with pytest.raises(bsm_lib.BsmError) as e:
+        ctx.matrix(rs, rs, [0], [2], np.zeros(6))
+    assert e.value.name == "OUT_OF_RANGE"
+    with pytest.raises(bsm_lib.BsmError) as e:
+        ctx.matrix(np.array([0, 3], np.int32), rs, [], [])
+    assert e.value.name == "INVALID_ARG"
+    A = ctx.matrix(rs, rs, [0, 1], [0, 1], np.ones(13))
+    B = ctx.matrix(np.array([3, 2], np.int32), rs, [0], [0], np.ones(6))
+    C = ctx.empty(rs, rs)
+    with pytest.raises(bsm_lib.BsmError) as e:
+        ctx.multiply(1.0, A, B, 0.0, C)
+    assert e.value.name == "DIM_MISMATCH"
+    with pytest.raises(bsm_lib.BsmError) as e:
+        ctx.multiply(1.0, A, A, 0.0, A)
+    assert e.value.name == "ALIAS"
+    with pytest.raises(bsm_lib.BsmError) as e:
+        ctx.multiply(1.0, A, A, 0.0, C, precision=7)
+    assert e.value.name in ("UNSUPPORTED", "INVALID_ARG")
+    for m in (A, B, C):
+        m.destroy()
+
+
+def test_torch_stream(gpu_ctx, oracle_mod):
+    """Work enqueued on a caller's stream (a torch stream) gives the same result."""
+    import torch
+
+    A = synth.water(20, seed=3)
+    s = torch.cuda.Stream()
+    ref, v, _ = check(gpu_ctx, oracle_mod, A, A, eps=1e-10, stream=s)
