@@ -33,6 +33,7 @@ FP64_PEAK_GFLOPS = 1250.0  # nominal FP64 (FMA) rate of one GB300
 WORKLOADS = {
     "water2048": dict(kind="water", n=2048, seed=1, eps=1e-10),
     "water64": dict(kind="water", n=64, seed=0, eps=1e-10),
+    "water512": dict(kind="water", n=512, seed=1, eps=1e-10),
     "amorphous4096": dict(kind="amorphous", n=4096, seed=2, eps=1e-8),
 }
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
