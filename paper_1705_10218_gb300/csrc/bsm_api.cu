@@ -96,6 +96,10 @@ struct bsm_mat_s {
   bsm_ctx ctx = nullptr;
   int32_t nbr = 0, nbc = 0;
   std::vector<int32_t> h_row_sizes, h_col_sizes;
+  int32_t max_row = 0, max_col = 0;  // largest block row / column size
+  // slices of the values for the split precisions (left / right operand layouts)
+  void *split_left = nullptr, *split_right = nullptr;
+  int64_t cap_left = 0, cap_right = 0;  // bytes
   int32_t *row_sizes = nullptr, *col_sizes = nullptr;
   Buf front, back;
   int64_t nblk = 0, nnz = 0;  // valid when !pend.active
@@ -294,6 +298,28 @@ static int enqueue_norms(bsm_ctx ctx, bsm_mat M, cudaStream_t s) {
   return BSM_OK;
 }
 
+// Slice buffers of M for the given layouts, sized for its current values.
+static int split_buffers(bsm_mat M, int precision, bool left, bool right) {
+  const int64_t need = std::max<int64_t>(M->nnz, 1) * split_bytes_per_value(precision);
+  auto grow = [&](void *&p, int64_t &cap) -> int {
+    if (cap >= need) return BSM_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, (size_t)need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, "cudaMalloc(slices)");
+    }
+    cap = need;
+    return BSM_OK;
+  };
+  int rc;
+  if (left && (rc = grow(M->split_left, M->cap_left))) return rc;
+  if (right && (rc = grow(M->split_right, M->cap_right))) return rc;
+  return BSM_OK;
+}
+
 static int take_slot(bsm_ctx ctx, bsm_mat owner) {
   const int s = ctx->next_slot;
   ctx->next_slot = (ctx->next_slot + 1) % kSlots;
@@ -331,6 +357,22 @@ static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double 
     if ((rc = enqueue_norms(ctx, B, s))) return rc;
     ctx->launches++;
   }
+  const bool split = o.precision != BSM_PREC_FP64;
+  if (split) {  // operand slices for the tensor-core products
+    if ((rc = split_buffers(A, o.precision, true, B == A))) return rc;
+    if (B != A && (rc = split_buffers(B, o.precision, false, true))) return rc;
+    const int grid = ctx->nsm * 16;
+    CK(launch_split(o.precision, A->row_sizes, A->col_sizes, A->front.blk_row, A->front.col_idx,
+                    A->front.blk_off, A->front.vals, A->front.hdr, A->split_left,
+                    B == A ? A->split_right : nullptr, grid, s));
+    ctx->launches++;
+    if (B != A) {
+      CK(launch_split(o.precision, B->row_sizes, B->col_sizes, B->front.blk_row, B->front.col_idx,
+                      B->front.blk_off, B->front.vals, B->front.hdr, nullptr, B->split_right,
+                      grid, s));
+      ctx->launches++;
+    }
+  }
   if (prof) CK(cudaEventRecord(ctx->prof_ev[slot][1], s));
 
   DevMat dA = dev_view(A), dB = dev_view(B), dC = dev_view(C);
@@ -367,7 +409,12 @@ static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double 
   CK(launch_symbolic_fill(dA, dB, dC, use_cin ? 1 : 0, eps, ws, out, ctx->d_status, sym_grid, s));
   ctx->launches++;
   if (prof) CK(cudaEventRecord(ctx->prof_ev[slot][2], s));
-  CK(launch_numeric_fp64(dA, dB, out, dC, alpha, beta, ws, ctx->d_status, ctx->nsm * 3, s));
+  const int max_dim = std::max(A->max_row, std::max(A->max_col, B->max_col));
+  if (split)
+    CK(launch_numeric_split(o.precision, dA, dB, out, dC, A->split_left, B->split_right, alpha,
+                            beta, ws, ctx->d_status, max_dim, ctx->nsm, s));
+  else
+    CK(launch_numeric_fp64(dA, dB, out, dC, alpha, beta, ws, ctx->d_status, max_dim, ctx->nsm, s));
   ctx->launches++;
   if (prof) {
     CK(cudaEventRecord(ctx->prof_ev[slot][3], s));
@@ -564,6 +611,8 @@ int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_
   M->nbc = nbcols;
   M->h_row_sizes.assign(row_sizes, row_sizes + nbrows);
   M->h_col_sizes.assign(col_sizes, col_sizes + nbcols);
+  for (int32_t v : M->h_row_sizes) M->max_row = std::max(M->max_row, v);
+  for (int32_t v : M->h_col_sizes) M->max_col = std::max(M->max_col, v);
   ctx->mats.push_back(M);
   auto fail = [&](int code) {
     bsm_mat_destroy(M);
@@ -632,6 +681,8 @@ int bsm_mat_destroy(bsm_mat m) {
     if (ctx->slot_owner[i] == m) ctx->slot_owner[i] = nullptr;
   m->front.release();
   m->back.release();
+  if (m->split_left) cudaFree(m->split_left);
+  if (m->split_right) cudaFree(m->split_right);
   dev_free(m->row_sizes);
   dev_free(m->col_sizes);
   auto &v = ctx->mats;
@@ -647,13 +698,19 @@ int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, b
   if (C == A || C == B) return BSM_ERR_ALIAS;
   bsm_opts o{};
   if (opts) o = *opts;
-  if (o.precision != BSM_PREC_FP64) return BSM_ERR_UNSUPPORTED;
+  if (o.precision != BSM_PREC_FP64 && o.precision != BSM_PREC_SPLIT_BF16X3 &&
+      o.precision != BSM_PREC_SPLIT_TF32X2)
+    return BSM_ERR_INVALID_ARG;
   if (o.launch != BSM_LAUNCH_PERSISTENT && o.launch != BSM_LAUNCH_PER_STACK)
     return BSM_ERR_INVALID_ARG;
   if (A->nbc != B->nbr || A->h_col_sizes != B->h_row_sizes) return BSM_ERR_DIM_MISMATCH;
   if (C->nbr != A->nbr || C->nbc != B->nbc || C->h_row_sizes != A->h_row_sizes ||
       C->h_col_sizes != B->h_col_sizes)
     return BSM_ERR_DIM_MISMATCH;
+  // the split-precision kernels cover blocks of up to 32 x 32
+  if (o.precision != BSM_PREC_FP64 &&
+      std::max(A->max_row, std::max(A->max_col, B->max_col)) > 32)
+    return BSM_ERR_UNSUPPORTED;
   int rc = ctx_set_device(ctx);
   if (rc) return rc;
   if ((rc = resolve(A)) || (rc = resolve(B))) return rc;

@@ -90,8 +90,28 @@ cudaError_t launch_symbolic_fill(DevMat A, DevMat B, DevMat Cin, int use_cin, do
                                  DevWs ws, DevOut C, const DevStatus *st, int grid,
                                  cudaStream_t stream);
 
+// max_dim: the largest block dimension (rows of A, columns of A and of B)
+// that can occur; it selects the kernel variant.
 cudaError_t launch_numeric_fp64(DevMat A, DevMat B, DevOut C, DevMat Cin, double alpha,
-                                double beta, DevWs ws, const DevStatus *st, int grid,
-                                cudaStream_t stream);
+                                double beta, DevWs ws, const DevStatus *st, int max_dim,
+                                int nsm, cudaStream_t stream);
+
+// Split precision (k_split.cu). left/right: slice layouts of the operand as a
+// left (row-major) or right (column-major) MMA operand; either may be null.
+cudaError_t launch_split(int precision, const int32_t *row_sizes, const int32_t *col_sizes,
+                         const int32_t *blk_row, const int32_t *col_idx, const int64_t *blk_off,
+                         const double *vals, const int64_t *hdr, void *left, void *right,
+                         int grid, cudaStream_t stream);
+
+cudaError_t launch_numeric_split(int precision, DevMat A, DevMat B, DevOut C, DevMat Cin,
+                                 const void *a_left, const void *b_right, double alpha,
+                                 double beta, DevWs ws, const DevStatus *st, int max_dim, int nsm,
+                                 cudaStream_t stream);
+
+// Bytes of slice storage per FP64 value of an operand (bf16x3: padded planes
+// at 12 halfwords per value; tf32x2: 2 words per value).
+inline int64_t split_bytes_per_value(int precision) {
+  return precision == BSM_PREC_SPLIT_BF16X3 ? 24 : 8;
+}
 
 }  // namespace bsm

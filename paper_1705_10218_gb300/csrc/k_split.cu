@@ -1,0 +1,433 @@
+// k_split.cu -- the numeric phase in split precision: every block product
+// A_ik . B_kj is carried out on the tensor cores as a sum of products of
+// low-precision slices of the operands (Ozaki-style multi-term products),
+// accumulated in FP32; C is formed in FP64:
+//
+//     C_ij = beta * C_in_ij + alpha * sum_k sum_{(p,q)} A_ik^(p) . B_kj^(q)
+//
+//   BF16x3: a = a1 + a2 + a3 (three BF16 slices of 8 significant bits each),
+//           the six slice products with p + q <= 4 (1-based) are kept;
+//   TF32x2: a = a1 + a2 (two TF32 slices of 11 significant bits),
+//           the three products a1 b1, a1 b2, a2 b1 are kept.
+//
+// The slices are cut by integer operations on the FP64 bit pattern
+// (truncation: each slice takes the next BITS significant bits of what the
+// previous slices left), so no FP64 arithmetic is spent on splitting; the
+// filter and the norms stay in FP64 (k_symbolic.cu).
+//
+// Slice layout. For every block b of r x c values (FP64 offset blk_off[b]),
+// the slices live at a fixed multiple of the FP64 offset, so no extra offset
+// table is needed:
+//   BF16: 3 planes of rp x cp elements (rp, cp = r, c rounded up to even;
+//         padding is zero) at 16-bit index 12*blk_off[b] (rp*cp <= 4*r*c);
+//         "left" layout (the block as a left operand) is row-major with
+//         stride cp, "right" layout (as a right operand) column-major with
+//         stride rp, so the two k-adjacent values of an MMA fragment register
+//         are one aligned 32-bit word.
+//   TF32: 2 planes of r x c 32-bit elements at 32-bit index 2*blk_off[b];
+//         left row-major, right column-major.
+#include <cstdint>
+
+#include "bsm_internal.h"
+
+namespace bsm {
+
+// ---------------------------------------------------------------------------
+// Splitting an FP64 value into slices of BITS significant bits (truncation).
+// Zeros and FP64 subnormals give zero slices; inf/NaN go to the first slice.
+// ---------------------------------------------------------------------------
+template <int NS, int BITS>
+struct Slices {
+  uint32_t s[NS];  // bf16 in the low 16 bits, or tf32 as FP32 bits
+};
+
+template <int NS, int BITS>
+__device__ __forceinline__ Slices<NS, BITS> split_value(double x) {
+  Slices<NS, BITS> out;
+#pragma unroll
+  for (int q = 0; q < NS; q++) out.s[q] = 0u;
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 63);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return out;
+  if (E == 0x7FF) {  // inf / NaN
+    const bool nan = (b & 0xFFFFFFFFFFFFFull) != 0;
+    out.s[0] = (BITS == 8) ? ((sign << 15) | 0x7F80u | (nan ? 0x40u : 0u))
+                           : ((sign << 31) | 0x7F800000u | (nan ? 0x400000u : 0u));
+    return out;
+  }
+  uint64_t rem = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // 53-bit significand
+  const int e = E - 1023;  // value = rem * 2^(e - 52)
+#pragma unroll
+  for (int q = 0; q < NS; q++) {
+    if (rem == 0) break;
+    const int p = 63 - __clzll((long long)rem);  // leading one
+    uint32_t h;
+    uint64_t low;
+    if (p >= BITS - 1) {
+      h = (uint32_t)(rem >> (p - (BITS - 1)));
+      low = rem & ((1ull << (p - (BITS - 1))) - 1ull);
+    } else {
+      h = (uint32_t)(rem << ((BITS - 1) - p));
+      low = 0;
+    }
+    // slice value = h * 2^(e - 52 + p - (BITS-1)), h has BITS bits, top bit set
+    const int ef = e - 52 + p + 127;  // biased exponent of the slice
+    if (ef >= 1 && ef <= 254) {
+      if (BITS == 8)
+        out.s[q] = (sign << 15) | ((uint32_t)ef << 7) | (h & 0x7Fu);
+      else
+        out.s[q] = (sign << 31) | ((uint32_t)ef << 23) | ((h & 0x3FFu) << 13);
+    } else if (ef > 254) {  // beyond the 8-bit exponent range: infinity
+      out.s[q] = (BITS == 8) ? ((sign << 15) | 0x7F80u) : ((sign << 31) | 0x7F800000u);
+      break;
+    }
+    rem = low;
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// Split every block of a matrix into the left and/or right slice layouts.
+// One warp per block (grid-stride), lanes over the padded positions.
+// ---------------------------------------------------------------------------
+__global__ void k_split_bf16x3(const int32_t *__restrict__ row_sizes,
+                               const int32_t *__restrict__ col_sizes,
+                               const int32_t *__restrict__ blk_row,
+                               const int32_t *__restrict__ col_idx,
+                               const int64_t *__restrict__ blk_off,
+                               const double *__restrict__ vals, const int64_t *__restrict__ hdr,
+                               uint16_t *__restrict__ left, uint16_t *__restrict__ right) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nblk = hdr[0];
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = w0; b < nblk; b += nw) {
+    const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
+    const int rp = r + (r & 1), cp = c + (c & 1);
+    const int plane = rp * cp;
+    const int64_t base = 12 * blk_off[b];
+    const double *x = vals + blk_off[b];
+    for (int e = lane; e < plane; e += 32) {
+      // position (row xr, col yc) in the padded rp x cp block, column-major order
+      const int xr = e % rp, yc = e / rp;
+      const double v = (xr < r && yc < c) ? x[xr + (int64_t)yc * r] : 0.0;
+      const Slices<3, 8> sl = split_value<3, 8>(v);
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        if (left) left[base + (int64_t)q * plane + xr * cp + yc] = (uint16_t)sl.s[q];
+        if (right) right[base + (int64_t)q * plane + yc * rp + xr] = (uint16_t)sl.s[q];
+      }
+    }
+  }
+}
+
+__global__ void k_split_tf32x2(const int32_t *__restrict__ row_sizes,
+                               const int32_t *__restrict__ col_sizes,
+                               const int32_t *__restrict__ blk_row,
+                               const int32_t *__restrict__ col_idx,
+                               const int64_t *__restrict__ blk_off,
+                               const double *__restrict__ vals, const int64_t *__restrict__ hdr,
+                               uint32_t *__restrict__ left, uint32_t *__restrict__ right) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nblk = hdr[0];
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = w0; b < nblk; b += nw) {
+    const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
+    const int plane = r * c;
+    const int64_t base = 2 * blk_off[b];
+    const double *x = vals + blk_off[b];
+    for (int e = lane; e < plane; e += 32) {
+      const int xr = e % r, yc = e / r;
+      const Slices<2, 11> sl = split_value<2, 11>(x[e]);
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        if (left) left[base + (int64_t)q * plane + xr * c + yc] = sl.s[q];
+        if (right) right[base + (int64_t)q * plane + e] = sl.s[q];
+      }
+    }
+  }
+}
+
+cudaError_t launch_split(int precision, const int32_t *row_sizes, const int32_t *col_sizes,
+                         const int32_t *blk_row, const int32_t *col_idx, const int64_t *blk_off,
+                         const double *vals, const int64_t *hdr, void *left, void *right,
+                         int grid, cudaStream_t stream) {
+  if (precision == BSM_PREC_SPLIT_BF16X3)
+    k_split_bf16x3<<<grid, 256, 0, stream>>>(row_sizes, col_sizes, blk_row, col_idx, blk_off, vals,
+                                             hdr, (uint16_t *)left, (uint16_t *)right);
+  else
+    k_split_tf32x2<<<grid, 256, 0, stream>>>(row_sizes, col_sizes, blk_row, col_idx, blk_off, vals,
+                                             hdr, (uint32_t *)left, (uint32_t *)right);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core fragments (mma.sync, FP32 accumulation).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                             uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_bf16_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0));
+}
+
+__device__ __forceinline__ void mma_tf32_k8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                            uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Exact FP32 -> FP64 conversion with integer operations only.
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint32_t ef = (u >> 23) & 0xFFu;
+  const uint64_t man = u & 0x7FFFFFu;
+  uint64_t bits;
+  if (ef == 0) {
+    if (man == 0) {
+      bits = sign;
+    } else {  // FP32 subnormal: man * 2^-149, normal in FP64
+      const int p = 63 - __clzll((long long)man);
+      bits = sign | ((uint64_t)(p - 149 + 1023) << 52) | ((man << (52 - p)) & 0xFFFFFFFFFFFFFull);
+    }
+  } else if (ef == 0xFF) {
+    bits = sign | (0x7FFull << 52) | (man << 29);
+  } else {
+    bits = sign | ((uint64_t)(ef + 896) << 52) | (man << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+// ---------------------------------------------------------------------------
+// Numeric kernel, BF16x3. One warp per C block; the C block (or its transpose,
+// whichever needs fewer MMA tiles) is covered by MT x NT tiles of 16 x 8; each
+// product contributes k-steps of 16 (and a final step of 8 when at most 8
+// remain) with six slice products per tile and step.
+//
+// Operands: L (M' x s) is read from a left layout (row-major, stride sp), R
+// (s x N') from a right layout (column-major, stride sp), where sp = s rounded
+// up to even. Not transposed: L = A_ik (A's left layout), R = B_kj (B's right
+// layout). Transposed (C^T = B^T A^T): L = B_kj^T = B's right layout read as
+// row-major, R = A_ik^T = A's left layout read as column-major.
+// ---------------------------------------------------------------------------
+template <int MT, int NT>
+__device__ __forceinline__ void bf16_block(const uint16_t *__restrict__ Lb,
+                                           const uint16_t *__restrict__ Rb, int Mp, int Np,
+                                           int s, int lplane, int rplane,
+                                           float (&acc)[MT][NT][4]) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int sp = s + (s & 1);
+  for (int kk = 0; kk < s; kk += 16) {
+    const bool k8 = (s - kk) <= 8;
+    // fragments of L: rows g (+8) of each M tile, k pairs 2t (+8)
+    uint32_t a[3][MT][4];
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+      for (int mt = 0; mt < MT; mt++) {
+        const int r0 = mt * 16 + g, r1 = r0 + 8;
+        const int k0 = kk + 2 * t, k1 = k0 + 8;
+        const uint32_t *P = reinterpret_cast<const uint32_t *>(Lb + (int64_t)q * lplane);
+        a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + ((r0 * sp + k0) >> 1)) : 0u;
+        a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + ((r1 * sp + k0) >> 1)) : 0u;
+        a[q][mt][2] = (!k8 && r0 < Mp && k1 < sp) ? __ldg(P + ((r0 * sp + k1) >> 1)) : 0u;
+        a[q][mt][3] = (!k8 && r1 < Mp && k1 < sp) ? __ldg(P + ((r1 * sp + k1) >> 1)) : 0u;
+      }
+    uint32_t bb[3][NT][2];
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++) {
+        const int c = nt * 8 + g;
+        const int k0 = kk + 2 * t, k1 = k0 + 8;
+        const uint32_t *P = reinterpret_cast<const uint32_t *>(Rb + (int64_t)q * rplane);
+        bb[q][nt][0] = (c < Np && k0 < sp) ? __ldg(P + ((c * sp + k0) >> 1)) : 0u;
+        bb[q][nt][1] = (!k8 && c < Np && k1 < sp) ? __ldg(P + ((c * sp + k1) >> 1)) : 0u;
+      }
+    // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
+    constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
+    constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++) {
+        if (mt * 16 >= Mp || nt * 8 >= Np) continue;
+#pragma unroll
+        for (int pq = 0; pq < 6; pq++) {
+          if (k8)
+            mma_bf16_k8(acc[mt][nt], a[PA[pq]][mt][0], a[PA[pq]][mt][1], bb[PB[pq]][nt][0]);
+          else
+            mma_bf16_k16(acc[mt][nt], a[PA[pq]][mt], bb[PB[pq]][nt][0], bb[PB[pq]][nt][1]);
+        }
+      }
+  }
+}
+
+template <int MT, int NT>
+__device__ __forceinline__ void tf32_block(const uint32_t *__restrict__ Lb,
+                                           const uint32_t *__restrict__ Rb, int Mp, int Np,
+                                           int s, int lplane, int rplane,
+                                           float (&acc)[MT][NT][4]) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  for (int kk = 0; kk < s; kk += 8) {
+    uint32_t a[2][MT][4];
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+      for (int mt = 0; mt < MT; mt++) {
+        const int r0 = mt * 16 + g, r1 = r0 + 8;
+        const int k0 = kk + t, k1 = k0 + 4;
+        const uint32_t *P = Lb + (int64_t)q * lplane;
+        a[q][mt][0] = (r0 < Mp && k0 < s) ? __ldg(P + r0 * s + k0) : 0u;
+        a[q][mt][1] = (r1 < Mp && k0 < s) ? __ldg(P + r1 * s + k0) : 0u;
+        a[q][mt][2] = (r0 < Mp && k1 < s) ? __ldg(P + r0 * s + k1) : 0u;
+        a[q][mt][3] = (r1 < Mp && k1 < s) ? __ldg(P + r1 * s + k1) : 0u;
+      }
+    uint32_t bb[2][NT][2];
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++) {
+        const int c = nt * 8 + g;
+        const int k0 = kk + t, k1 = k0 + 4;
+        const uint32_t *P = Rb + (int64_t)q * rplane;
+        bb[q][nt][0] = (c < Np && k0 < s) ? __ldg(P + c * s + k0) : 0u;
+        bb[q][nt][1] = (c < Np && k1 < s) ? __ldg(P + c * s + k1) : 0u;
+      }
+    // (2,1) (1,2) (1,1)
+    constexpr int PA[3] = {1, 0, 0};
+    constexpr int PB[3] = {0, 1, 0};
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++) {
+        if (mt * 16 >= Mp || nt * 8 >= Np) continue;
+#pragma unroll
+        for (int pq = 0; pq < 3; pq++)
+          mma_tf32_k8(acc[mt][nt], a[PA[pq]][mt], bb[PB[pq]][nt][0], bb[PB[pq]][nt][1]);
+      }
+  }
+}
+
+// One warp per C block (grid-stride). Block dimensions up to 16 * MT (rows of
+// the MMA problem) and 8 * NT (columns); larger blocks use the FP64 kernel.
+template <int PREC, int MT, int NT>
+__global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOut C, DevMat Cin,
+                                                       const void *__restrict__ a_left,
+                                                       const void *__restrict__ b_right,
+                                                       double alpha, double beta, DevWs ws,
+                                                       const DevStatus *st) {
+  if (st->overflow) return;
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t nblk = st->nblk_c;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool exact_out = (alpha == 1.0 && beta == 0.0);
+  for (int64_t gb = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; gb < nblk;
+       gb += nwarp) {
+    const int i = C.blk_row[gb], j = C.col_idx[gb];
+    const int m = C.row_sizes[i], n = C.col_sizes[j];
+    // transpose when that needs fewer 16 x 8 tiles
+    const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
+    const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
+    const bool tr = tiles_t < tiles_n;
+    const int Mp = tr ? n : m, Np = tr ? m : n;
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+        for (int x = 0; x < 4; x++) acc[mt][nt][x] = 0.f;
+    const int64_t p0 = ws.prod_ptr[gb], p1 = ws.prod_ptr[gb + 1];
+    for (int64_t p = p0; p < p1; p++) {
+      const int2 pr = ws.prods[p];
+      const int s = A.col_sizes[A.col_idx[pr.x]];
+      const int64_t aoff = A.blk_off[pr.x], boff = B.blk_off[pr.y];
+      if (PREC == BSM_PREC_SPLIT_BF16X3) {
+        const uint16_t *Al = static_cast<const uint16_t *>(a_left) + 12 * aoff;
+        const uint16_t *Br = static_cast<const uint16_t *>(b_right) + 12 * boff;
+        const int sp = s + (s & 1);
+        const int aplane = (m + (m & 1)) * sp, bplane = sp * (n + (n & 1));
+        if (!tr)
+          bf16_block<MT, NT>(Al, Br, Mp, Np, s, aplane, bplane, acc);
+        else
+          bf16_block<MT, NT>(Br, Al, Mp, Np, s, bplane, aplane, acc);
+      } else {
+        const uint32_t *Al = static_cast<const uint32_t *>(a_left) + 2 * aoff;
+        const uint32_t *Br = static_cast<const uint32_t *>(b_right) + 2 * boff;
+        if (!tr)
+          tf32_block<MT, NT>(Al, Br, Mp, Np, s, m * s, s * n, acc);
+        else
+          tf32_block<MT, NT>(Br, Al, Mp, Np, s, s * n, m * s, acc);
+      }
+    }
+    // epilogue: C_ij = beta * C_in_ij + alpha * S_ij in FP64 (exact copy when
+    // alpha = 1 and beta = 0)
+    const int cin = ws.c_cin[gb];
+    const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+    double *out = C.vals + C.blk_off[gb];
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+          const int rr = mt * 16 + g + ((x >> 1) << 3);
+          const int cc = nt * 8 + 2 * t + (x & 1);
+          if (rr < Mp && cc < Np) {
+            const int row = tr ? cc : rr, col = tr ? rr : cc;
+            const int64_t e = (int64_t)col * m + row;
+            double v = f32_to_f64_exact(acc[mt][nt][x]);
+            if (!exact_out) {
+              v = alpha * v;
+              if (cinv) v = fma(beta, cinv[e], v);
+            }
+            out[e] = v;
+          }
+        }
+  }
+}
+
+cudaError_t launch_numeric_split(int precision, DevMat A, DevMat B, DevOut C, DevMat Cin,
+                                 const void *a_left, const void *b_right, double alpha,
+                                 double beta, DevWs ws, const DevStatus *st, int max_dim, int nsm,
+                                 cudaStream_t stream) {
+  const int grid = nsm * 8;
+  if (precision == BSM_PREC_SPLIT_BF16X3) {
+    if (max_dim <= 16)
+      k_numeric_split<BSM_PREC_SPLIT_BF16X3, 1, 2><<<grid, 128, 0, stream>>>(
+          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st);
+    else
+      k_numeric_split<BSM_PREC_SPLIT_BF16X3, 2, 4><<<grid, 128, 0, stream>>>(
+          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st);
+  } else {
+    if (max_dim <= 16)
+      k_numeric_split<BSM_PREC_SPLIT_TF32X2, 1, 2><<<grid, 128, 0, stream>>>(
+          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st);
+    else
+      k_numeric_split<BSM_PREC_SPLIT_TF32X2, 2, 4><<<grid, 128, 0, stream>>>(
+          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bsm

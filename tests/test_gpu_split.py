@@ -1,0 +1,101 @@
+"""GPU parity of the split-precision paths (BF16x3, TF32x2) against the CPU
+oracle, through the C ABI.
+
+* Small integers (|a| <= 4): every slice after the first is zero, every slice
+  product is exact and all FP32 partial sums stay far below 2^24, so the result
+  must equal the oracle bit for bit.
+* General values: the pattern is bit-exact (same symbolic phase) and every
+  element obeys the bound derived from the slicing:
+      |C - C_ref| <= (u_split + K * 2^-23) * (|A| |B|) + tiny,
+  u_split = 3 * 2^-22 (BF16x3) or 2^-19 (TF32x2), K the inner dimension.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+PRECS = {"bf16x3": 1, "tf32x2": 2}
+U_SPLIT = {"bf16x3": 3 * 2.0 ** -22, "tf32x2": 2.0 ** -19}
+REL_F = {"bf16x3": 2e-6, "tf32x2": 1e-5}  # stated relative Frobenius targets on water
+
+
+def gpu_mult(ctx, A, B, prec, alpha=1.0, beta=0.0, C=None, eps=0.0):
+    dA = ctx.from_blocks(A)
+    dB = dA if B is A else ctx.from_blocks(B)
+    dC = ctx.from_blocks(C) if C is not None else ctx.empty(A.row_sizes, B.col_sizes)
+    st = ctx.multiply(alpha, dA, dB, beta, dC, eps, precision=PRECS[prec], stats=True)
+    r, c = dC.pattern()
+    v = dC.values()
+    for m in {id(dA): dA, id(dB): dB, id(dC): dC}.values():
+        m.destroy()
+    return r, c, v, st
+
+
+@pytest.mark.parametrize("prec", sorted(PRECS))
+@pytest.mark.parametrize("seed", range(3))
+def test_split_integer_exact(gpu_ctx, oracle_mod, prec, seed):
+    rng = np.random.default_rng(700 + seed)
+    sizes = (1, 2, 5, 9, 13, 23, 32)
+    rs, ks, cs = rng.choice(sizes, 7), rng.choice(sizes, 8), rng.choice(sizes, 6)
+    A = synth.random_blocks(rng, rs, ks, 0.5, kind="int", shuffle=True)
+    B = synth.random_blocks(rng, ks, cs, 0.5, kind="int", shuffle=True)
+    ref = oracle_mod.multiply(A, B, eps=0.0)
+    r, c, v, st = gpu_mult(gpu_ctx, A, B, prec)
+    assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+    assert st.kept == ref.kept and st.flops == ref.flops
+    assert np.array_equal(v, ref.values)
+
+
+def _abs(M):
+    return synth.BlockMatrix(M.row_sizes, M.col_sizes, M.blk_row, M.blk_col, np.abs(M.values))
+
+
+@pytest.mark.parametrize("prec", sorted(PRECS))
+def test_split_water_bound(gpu_ctx, oracle_mod, prec):
+    A = synth.water(64, seed=0)
+    eps = 1e-10
+    ref = oracle_mod.multiply(A, A, eps=eps)
+    absref = oracle_mod.multiply(_abs(A), _abs(A), eps=eps)  # same filter: norms ignore signs
+    r, c, v, st = gpu_mult(gpu_ctx, A, A, prec, eps=eps)
+    assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+    K = int(A.row_sizes.sum())
+    bound = (U_SPLIT[prec] + K * 2.0 ** -23) * absref.values + 1e-300
+    assert np.all(np.abs(v - ref.values) <= bound)
+    rel = H.rel_frobenius(v, ref.values)
+    assert rel <= REL_F[prec], rel
+    assert np.max(np.abs(v - ref.values)) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", sorted(PRECS))
+def test_split_mixed_sizes_alpha_beta(gpu_ctx, oracle_mod, prec):
+    """Amorphous-style sizes {5,9,13,23,32}, alpha/beta != (1, 0), filter active."""
+    A = synth.amorphous(80, seed=4, density=0.05, cutoff=6.0)
+    rng = np.random.default_rng(1)
+    C = synth.random_blocks(rng, A.row_sizes, A.col_sizes, 0.2, kind="normal")
+    nA = oracle_mod.norms(A)
+    eps = float(np.percentile(np.outer(nA[:50], nA[:50]), 20))
+    ref = oracle_mod.multiply(A, A, alpha=0.75, beta=-1.25, C=C, eps=eps)
+    absref = oracle_mod.multiply(_abs(A), _abs(A), eps=eps)
+    r, c, v, st = gpu_mult(gpu_ctx, A, A, prec, alpha=0.75, beta=-1.25, C=C, eps=eps)
+    assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+    assert st.dropped == ref.dropped and st.dropped > 0
+    # the product part on the absref pattern: bound on |alpha| |A||B|
+    Rg = H.to_dense(H.result_matrix(type("R", (), dict(blk_row=r, blk_col=c, values=v))(), A.row_sizes, A.col_sizes))
+    Rr = H.to_dense(H.result_matrix(ref, A.row_sizes, A.col_sizes))
+    Ab = H.to_dense(H.result_matrix(absref, A.row_sizes, A.col_sizes))
+    K = int(A.row_sizes.sum())
+    bound = 0.75 * (U_SPLIT[prec] + K * 2.0 ** -23) * Ab + 1e-12 * np.abs(Rr) + 1e-300
+    assert np.all(np.abs(Rg - Rr) <= bound)
+
+
+def test_split_rejects_large_blocks(gpu_ctx, bsm_lib):
+    rs = np.array([40, 3], np.int32)
+    A = gpu_ctx.matrix(rs, rs, [0], [0], np.ones(1600))
+    C = gpu_ctx.empty(rs, rs)
+    with pytest.raises(bsm_lib.BsmError) as e:
+        gpu_ctx.multiply(1.0, A, A, 0.0, C, precision=1)
+    assert e.value.name == "UNSUPPORTED"
+    A.destroy()
+    C.destroy()
