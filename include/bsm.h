@@ -164,6 +164,54 @@ int bsm_ctx_profile(bsm_ctx ctx, int enable);
 /* Totals since the last bsm_ctx_profile(ctx, 1). Synchronises the context. */
 int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free multiply. The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc (a framework whose pool owns
+ * all device memory, a callback that must not block on the allocator, a
+ * process at its allocation limit). The caller passes device buffers for the
+ * inputs and the outputs; everything else the multiply needs lives in one
+ * fixed array of BSM_NOALLOC_SCRATCH_BYTES that the library image carries on
+ * every GPU that loads it, for the life of the process. No context is used.
+ * ------------------------------------------------------------------------- */
+#define BSM_NOALLOC_SCRATCH_BYTES (32ll << 20)
+
+/* A block-sparse matrix in device memory, blocked CSR: blocks of a row sorted
+ * by column, each block's values column-major at vals + blk_off[b]. */
+typedef struct {
+  int32_t nbr, nbc;
+  const int32_t *row_sizes; /* device [nbr] */
+  const int32_t *col_sizes; /* device [nbc] */
+  const int32_t *row_ptr;   /* device [nbr+1] */
+  const int32_t *col_idx;   /* device [nblk] */
+  const int64_t *blk_off;   /* device [nblk] */
+  const double *values;     /* device [nnz] */
+  int64_t nblk;
+} bsm_dev_csr;
+
+/* Caller-owned device buffers that receive the result in the same form. */
+typedef struct {
+  int32_t *row_ptr; /* device [nbr of A + 1] */
+  int32_t *col_idx; /* device [cap_blk] */
+  int64_t *blk_off; /* device [cap_blk] */
+  double *values;   /* device [cap_nnz] */
+  int64_t cap_blk, cap_nnz;
+} bsm_dev_csr_out;
+
+/* C = alpha * A.B with the on-the-fly filter, FP64, the result written into
+ * C's caller buffers; the C pattern and values are the same as bsm_multiply's
+ * with beta = 0. sizes (host, 3 words) receives {C blocks, C values, kept
+ * products}. Calls no cudaMalloc, cudaFree or allocating library routine.
+ * The first call on a device (with that device current) looks up the device
+ * address of the scratch array; make that first call before any stream
+ * capture. Calls share the array: calls that overlap on the GPU race. The
+ * call enqueues on `stream` (a cudaStream_t, NULL = legacy default) and
+ * returns after the work is done. Errors: INVALID_ARG (also when C's
+ * capacities are too small: sizes[] then holds what is needed), DIM_MISMATCH,
+ * UNSUPPORTED (the problem needs more scratch than BSM_NOALLOC_SCRATCH_BYTES),
+ * CUDA. */
+int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bsm_dev_csr *B, double eps,
+                         bsm_dev_csr_out *C, int64_t *sizes, void *stream);
+
 /* Wait for all work of the context and complete every pending result. */
 int bsm_sync(bsm_ctx ctx);
 

@@ -259,3 +259,39 @@ class Matrix:
             self._h = None
             if self in self.ctx._mats:
                 self.ctx._mats.remove(self)
+
+
+# ---------------------------------------------------------------------------
+# Allocation-free multiply (bsm_multiply_noalloc): for callers that cannot
+# allocate device memory. Every pointer here is a device address the caller
+# owns (e.g. torch tensors' data_ptr()); the library adds no allocation.
+# ---------------------------------------------------------------------------
+class DevCsr(ctypes.Structure):
+    _fields_ = [
+        ("nbr", ctypes.c_int32), ("nbc", ctypes.c_int32),
+        ("row_sizes", ctypes.c_void_p), ("col_sizes", ctypes.c_void_p),
+        ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+        ("blk_off", ctypes.c_void_p), ("values", ctypes.c_void_p),
+        ("nblk", ctypes.c_int64),
+    ]
+
+
+class DevCsrOut(ctypes.Structure):
+    _fields_ = [
+        ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+        ("blk_off", ctypes.c_void_p), ("values", ctypes.c_void_p),
+        ("cap_blk", ctypes.c_int64), ("cap_nnz", ctypes.c_int64),
+    ]
+
+
+_SIGS["bsm_multiply_noalloc"] = (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(DevCsr), ctypes.POINTER(DevCsr),
+                                                ctypes.c_double, ctypes.POINTER(DevCsrOut),
+                                                ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p])
+
+
+def multiply_noalloc(alpha: float, A: DevCsr, B: DevCsr, eps: float, C: DevCsrOut, stream=None):
+    """Calls bsm_multiply_noalloc; returns (rc, (C blocks, C values, kept products))."""
+    sizes = (ctypes.c_int64 * 3)()
+    rc = lib().bsm_multiply_noalloc(float(alpha), ctypes.byref(A), ctypes.byref(B), float(eps),
+                                    ctypes.byref(C), sizes, _stream_ptr(stream))
+    return int(rc), (int(sizes[0]), int(sizes[1]), int(sizes[2]))
