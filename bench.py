@@ -39,6 +39,15 @@ WORKLOADS = {
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
 
 
+def measured_peak(key, fallback):
+    """(value, source) from MEASURED_PEAKS.json, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), f"measured ({key}, MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
 def make_workload(name):
     import synth
 
@@ -46,6 +55,24 @@ def make_workload(name):
     if w["kind"] == "water":
         return synth.water(w["n"], seed=w["seed"]), w["eps"]
     return synth.amorphous(w["n"], seed=w["seed"]), w["eps"]
+
+
+def replica_aggregate(local_ms, local_flop, dist=None, device="cpu"):
+    """Replicas only: every rank runs its own multiplies on its own GPU (no
+    data-path collective). The job time is the slowest rank's; the job's
+    throughput is all ranks' FLOPs over that time (GFLOP/s)."""
+    import torch
+
+    t = torch.tensor([local_ms, local_flop], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized():
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        fsum = t[1:].clone()
+        dist.all_reduce(fsum, op=dist.ReduceOp.SUM)
+        ms, flop = float(tmax.item()), float(fsum.item())
+    else:
+        ms, flop = float(local_ms), float(local_flop)
+    return ms, flop / (ms / 1e3) / 1e9
 
 
 def dist_env():
@@ -174,6 +201,102 @@ def run_reference(args, rank, world):
     return 0
 
 
+def serve_bench(args):
+    """Serving: C = A.A for a stream of independent water systems of different
+    sizes (log-uniform 32..1024 molecules), replayed with Poisson arrivals at
+    0.8 x the measured sequential capacity and as a saturating burst, against
+    sequential per-call execution. Prints one JSON line."""
+    import synth
+    from paper_1705_10218_gb300 import Context, Server
+
+    rng = np.random.default_rng(4)
+    eps = 1e-10
+    pool_n = args.serve_pool
+    sizes = np.rint(np.exp(rng.uniform(np.log(32), np.log(1024), pool_n))).astype(int)
+    pool = [synth.water(int(n), seed=1000 + p) for p, n in enumerate(sizes)]
+    pick = rng.integers(0, pool_n, args.requests)
+    gflop = []
+
+    # sequential per-call execution through the C ABI (upload, multiply, read back)
+    ctx = Context(0)
+    lat_seq = []
+    for r in range(min(8, args.requests)):  # warm-up
+        A = pool[pick[r]]
+        dA = ctx.from_blocks(A)
+        dC = ctx.empty(A.row_sizes, A.col_sizes)
+        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, blocking=True)
+        dC.values()
+        dA.destroy()
+        dC.destroy()
+    t0 = time.perf_counter()
+    for r in range(args.requests):
+        A = pool[pick[r]]
+        ts = time.perf_counter()
+        dA = ctx.from_blocks(A)
+        dC = ctx.empty(A.row_sizes, A.col_sizes)
+        st = ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stats=True)
+        dC.values()
+        dA.destroy()
+        dC.destroy()
+        lat_seq.append((time.perf_counter() - ts) * 1e3)
+        gflop.append(st.flops / 1e9)
+    t_seq = time.perf_counter() - t0
+    ctx.close()
+    cap = args.requests / t_seq
+
+    def replay(arrivals):
+        lat, order = [], []
+        with Server(0, slots=args.slots, hbm_budget=int(args.budget_gb * (1 << 30))) as srv:
+            ids = [None] * args.requests
+            nxt, done = 0, 0
+            t0 = time.perf_counter()
+            while done < args.requests:
+                now = time.perf_counter() - t0
+                while nxt < args.requests and arrivals[nxt] <= now:
+                    ids[nxt] = srv.submit(pool[pick[nxt]], eps)
+                    order.append(nxt)
+                    nxt += 1
+                srv.progress()
+                for r in list(order):
+                    state, l_ms, _, _ = srv.poll(ids[r])
+                    if state >= 2:
+                        srv.take(ids[r])  # the result comes back to the host
+                        lat.append(l_ms)
+                        order.remove(r)
+                        done += 1
+            makespan = time.perf_counter() - t0
+            peak = srv.info()["bytes_peak"]
+        return lat, makespan, peak
+
+    lam = 0.8 * cap
+    gaps = rng.exponential(1.0 / lam, args.requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    lat_p, span_p, peak_p = replay(arrivals)
+    lat_b, span_b, peak_b = replay(np.zeros(args.requests))
+
+    def pct(x, q):
+        return round(float(np.percentile(np.asarray(x), q)), 3)
+
+    tot_gflop = float(np.sum(gflop))
+    line = {
+        "metric": "multiplies/s + p50/p99 latency (serving, continuous batching)",
+        "value": round(args.requests / span_b, 3), "unit": "multiplies/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "water requests, 32..1024 molecules log-uniform", "requests": args.requests,
+                   "distinct_systems": pool_n, "slots": args.slots, "budget_gb": args.budget_gb,
+                   "eps": eps, "total_gflop": round(tot_gflop, 2)},
+        "sequential": {"multiplies_per_s": round(cap, 3), "p50_ms": pct(lat_seq, 50),
+                       "p99_ms": pct(lat_seq, 99), "gflop_per_s": round(tot_gflop / t_seq, 2)},
+        "poisson": {"arrival_rate_per_s": round(lam, 3), "multiplies_per_s": round(args.requests / span_p, 3),
+                    "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99), "peak_gb": round(peak_p / 2**30, 3)},
+        "burst": {"multiplies_per_s": round(args.requests / span_b, 3), "p50_ms": pct(lat_b, 50),
+                  "p99_ms": pct(lat_b, 99), "gflop_per_s": round(tot_gflop / span_b, 2),
+                  "peak_gb": round(peak_b / 2**30, 3)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,9 +306,18 @@ def main():
     ap.add_argument("--workload", default="water2048", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--launch", default="persistent", choices=["persistent", "per_stack"])
+    ap.add_argument("--graph", action="store_true", help="replay the multiply as a CUDA graph")
+    ap.add_argument("--autotune", action="store_true", help="tune the FP64 kernel variants first")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="the request-loop benchmark instead")
+    ap.add_argument("--requests", type=int, default=500)
+    ap.add_argument("--serve-pool", type=int, default=48)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=16.0)
     args = ap.parse_args()
+    if args.serve:
+        return serve_bench(args)
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -208,11 +340,13 @@ def main():
     ctx = Context(local)
     dA = ctx.from_blocks(A)
     dC = ctx.empty(A.row_sizes, A.col_sizes)
-    st = ctx.multiply(1.0, dA, dA, 0.0, dC, eps, precision=prec, launch=launch, stats=True)
+    kw = dict(precision=prec, launch=launch, graph=args.graph, autotune=args.autotune)
+    st = ctx.multiply(1.0, dA, dA, 0.0, dC, eps, precision=prec, launch=launch,
+                      autotune=args.autotune, stats=True)
     flops = st.flops
     s = torch.cuda.Stream()
     for _ in range(args.warmup):
-        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, precision=prec, launch=launch, stream=s)
+        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stream=s, **kw)
     s.synchronize()
     ctx.profile(True)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -222,7 +356,7 @@ def main():
     with ClockSampler(local) as clk:
         ev[0].record(s)
         for k in range(args.steps):
-            ctx.multiply(1.0, dA, dA, 0.0, dC, eps, precision=prec, launch=launch, stream=s)
+            ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stream=s, **kw)
             ev[k + 1].record(s)
         s.synchronize()
         torch.cuda.synchronize()
@@ -234,22 +368,42 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     launches = prof.launches
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = flops * args.steps * world / (total_ms / 1e3) / 1e9
+    total_ms, value = replica_aggregate(total_ms, flops * args.steps, dist, device="cuda")
     nb_c, nnz_c = dC.nblocks()
 
-    # dominant kernel: the numeric phase (one launch per multiply)
-    num_ms = prof.ms_numeric / max(prof.multiplies, 1)
-    achieved = flops / (num_ms / 1e3) / 1e9
-    roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
-            "kernel": "k_numeric_fp64", "peak_source": "nominal FP64 FMA rate (1.25 TFLOP/s)",
-            "phase_ms": {"norms": round(prof.ms_norms / max(prof.multiplies, 1), 4),
-                         "symbolic": round(prof.ms_symbolic / max(prof.multiplies, 1), 4),
-                         "numeric": round(num_ms, 4)}}
+    # dominant kernel: the numeric phase (one launch per multiply). In graph
+    # replay the phases are not timed separately: the whole multiply is used.
+    if prof.multiplies > 0:
+        num_ms = prof.ms_numeric / prof.multiplies
+        kname = "k_numeric_fp64_t16" if args.precision == "fp64" else "k_numeric_split"
+    else:
+        num_ms = total_ms / args.steps
+        kname = "whole multiply (CUDA graph replay)"
+    phase = {"norms": round(prof.ms_norms / max(prof.multiplies, 1), 4),
+             "symbolic": round(prof.ms_symbolic / max(prof.multiplies, 1), 4),
+             "numeric": round(num_ms, 4)}
+    if args.precision == "fp64":
+        achieved = flops / (num_ms / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "kernel": kname, "peak_source": "nominal FP64 FMA rate of the GB300 (1.25 TFLOP/s)",
+                "algorithmic": "2*m*n*k over kept products per launch", "phase_ms": phase}
+    else:
+        # compulsory bytes of the numeric kernel: C written once (FP64) and the
+        # operand slices read once (A = B: left and right layouts)
+        rs = A.row_sizes.astype(np.int64)
+        r, c = rs[A.blk_row], A.col_sizes.astype(np.int64)[A.blk_col]
+        if args.precision == "bf16x3":
+            slice_bytes = 2 * 3 * 2 * int(((r + (r & 1)) * (c + (c & 1))).sum())
+        else:
+            slice_bytes = 2 * 2 * 4 * int((r * c).sum())
+        nbytes = 8 * nnz_c + slice_bytes
+        achieved = nbytes / (num_ms / 1e3) / 1e9
+        peak = measured_peak("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak[0], "unit": "GB/s",
+                "frac": round(achieved / peak[0], 4), "traffic": None, "kernel": kname,
+                "peak_source": peak[1], "algorithmic": f"{nbytes} B per launch (C write + operand slices)",
+                "phase_ms": phase}
 
     # end to end through the C ABI with host buffers: create A from pinned host
     # memory, multiply, read C back into pinned host memory, free A.
@@ -302,6 +456,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else args.precision, "data": "synthetic",
             "config": {"workload": args.workload, "atoms": A.nbr, "dimension": int(A.row_sizes.sum()),
                        "eps": eps, "precision": args.precision, "launch": args.launch,
+                       "graph": bool(args.graph), "autotune": bool(args.autotune),
                        "a_blocks": A.nblk, "c_blocks": nb_c, "c_nnz": nnz_c,
                        "kept_products": st.kept, "dropped_products": st.dropped,
                        "gflop_per_multiply": round(flops / 1e9, 4),

@@ -79,8 +79,14 @@ typedef struct {
   int32_t precision; /* BSM_PREC_* */
   int32_t launch;    /* BSM_LAUNCH_* */
   int32_t blocking;  /* 1: return after the result is complete and checked */
-  int32_t autotune;  /* 1: pick per-shape tile variants from the tuner table */
+  int32_t autotune;  /* 1: time the FP64 kernel variants on the real data the first
+                        time a shape class (per-stack) or class mix (persistent) is
+                        met, and use the fastest; the choice is kept per context and,
+                        with BSM_AUTOTUNE_CACHE=<file>, across runs */
   void *stream;      /* cudaStream_t to use instead of the context stream, or NULL */
+  int32_t graph;     /* 1: capture the multiply's launches in a CUDA graph the first
+                        time a given set of arguments is met and replay it after */
+  int32_t reserved;
 } bsm_opts;
 
 /* Counters of one multiply (filled when bsm_stats* is not NULL; this makes
@@ -163,6 +169,59 @@ int bsm_ctx_profile(bsm_ctx ctx, int enable);
 
 /* Totals since the last bsm_ctx_profile(ctx, 1). Synchronises the context. */
 int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
+
+/* ---------------------------------------------------------------------------
+ * Request loop (serving). Independent multiplies C = A.A of square block-sparse
+ * systems of different sizes (the application's repeated multiplies, Sec. 1)
+ * arrive one by one. The server keeps `slots` lanes, each with its own stream
+ * and workspace; a request waits in a FIFO queue until a lane is free and its
+ * device-memory footprint fits the budget beside the requests already held
+ * (an upper bound before its multiply, the exact result size after), then it
+ * is uploaded and runs while the other lanes' requests keep running. Results
+ * stay on the device until taken. Single-threaded: call from one thread.
+ * ------------------------------------------------------------------------- */
+typedef struct bsm_server_s *bsm_server;
+
+typedef struct {
+  int32_t slots;      /* requests on the device at once (default 4, at most 64) */
+  int32_t precision;  /* BSM_PREC_* of every multiply */
+  int64_t hbm_budget; /* device bytes the admitted requests may hold (default 8 GiB) */
+} bsm_server_opts;
+
+typedef struct {
+  int64_t queued, running, completed;
+  int64_t bytes_in_use, bytes_peak, budget;
+} bsm_server_info;
+
+/* Request states reported by bsm_server_poll. */
+enum { BSM_REQ_QUEUED = 0, BSM_REQ_RUNNING = 1, BSM_REQ_DONE = 2, BSM_REQ_FAILED = 3 };
+
+int bsm_server_create(int device, const bsm_server_opts *opts, bsm_server *out);
+int bsm_server_destroy(bsm_server s);
+
+/* Queue C = A.A for a square matrix given as in bsm_mat_create (block sizes
+ * sizes[nbrows] for rows and columns, a block list, column-major values in
+ * list order). The arrays are copied. *id receives the request id. NOMEM if
+ * the request's footprint bound exceeds the whole budget. */
+int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_t nblocks,
+                      const int32_t *blk_row, const int32_t *blk_col, const double *values,
+                      double eps, int64_t *id);
+
+/* Retire finished requests and admit queued ones; never blocks on the device
+ * (an admission uploads its request). *completed: requests finished by this call. */
+int bsm_server_progress(bsm_server s, int32_t *completed);
+
+/* State of a request; latency_ms (submit to completion) once done, and the
+ * result's block and value counts. */
+int bsm_server_poll(bsm_server s, int64_t id, int32_t *state, double *latency_ms,
+                    int64_t *nblocks, int64_t *nnz);
+
+/* Copy a finished request's result (pattern sorted by (row, col), values as
+ * bsm_mat_get_values) to the host and release it. Null arrays skip a part. */
+int bsm_server_take(bsm_server s, int64_t id, int64_t cap_blk, int32_t *blk_row,
+                    int32_t *blk_col, int64_t cap_nnz, double *values);
+
+int bsm_server_get_info(bsm_server s, bsm_server_info *out);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free multiply. The paper has no counterpart: this entry point

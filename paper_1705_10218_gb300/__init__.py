@@ -19,6 +19,7 @@ from .bsm import (  # noqa: F401
     BsmError,
     Context,
     Matrix,
+    Server,
     Stats,
     lib,
     lib_path,

@@ -45,6 +45,8 @@ class _Opts(ctypes.Structure):
         ("blocking", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("graph", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -188,9 +190,9 @@ class Context:
     def multiply(self, alpha, A: "Matrix", B: "Matrix", beta, C: "Matrix", eps: float = 0.0, *,
                  precision: int = BSM_PREC_FP64, launch: int = BSM_LAUNCH_PERSISTENT,
                  blocking: bool = False, autotune: bool = False, stream=None,
-                 stats: bool = False) -> Stats | None:
+                 graph: bool = False, stats: bool = False) -> Stats | None:
         o = _Opts(int(precision), int(launch), int(bool(blocking)), int(bool(autotune)),
-                  _stream_ptr(stream))
+                  _stream_ptr(stream), int(bool(graph)), 0)
         st = _Stats() if stats else None
         rc = lib().bsm_multiply(self._h, float(alpha), A._h, B._h, float(beta), C._h, float(eps),
                                 ctypes.byref(o), ctypes.byref(st) if st is not None else None)
@@ -295,3 +297,89 @@ def multiply_noalloc(alpha: float, A: DevCsr, B: DevCsr, eps: float, C: DevCsrOu
     rc = lib().bsm_multiply_noalloc(float(alpha), ctypes.byref(A), ctypes.byref(B), float(eps),
                                     ctypes.byref(C), sizes, _stream_ptr(stream))
     return int(rc), (int(sizes[0]), int(sizes[1]), int(sizes[2]))
+
+
+# ---------------------------------------------------------------------------
+# Request loop (bsm_server_*): multiplies C = A.A of independent square systems,
+# run with continuous batching on several lanes.
+# ---------------------------------------------------------------------------
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("precision", ctypes.c_int32), ("hbm_budget", ctypes.c_int64)]
+
+
+class _ServerInfo(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("bytes_peak", ctypes.c_int64), ("budget", ctypes.c_int64)]
+
+
+_SIGS.update({
+    "bsm_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_ServerOpts), ctypes.POINTER(_P)]),
+    "bsm_server_destroy": (ctypes.c_int, [_P]),
+    "bsm_server_submit": (ctypes.c_int, [_P, _I32, _P, _I64, _P, _P, _P, _D, ctypes.POINTER(_I64)]),
+    "bsm_server_progress": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "bsm_server_poll": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_D),
+                                       ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "bsm_server_take": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _I64, _P]),
+    "bsm_server_get_info": (ctypes.c_int, [_P, ctypes.POINTER(_ServerInfo)]),
+})
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+class Server:
+    def __init__(self, device: int = 0, slots: int = 4, precision: int = BSM_PREC_FP64,
+                 hbm_budget: int = 8 << 30):
+        h = _P()
+        o = _ServerOpts(int(slots), int(precision), int(hbm_budget))
+        _check(lib().bsm_server_create(int(device), ctypes.byref(o), ctypes.byref(h)), "bsm_server_create")
+        self._h = h
+
+    def submit(self, M, eps: float) -> int:
+        """Queue C = M.M for a square block matrix M (row sizes = column sizes)."""
+        sz = np.ascontiguousarray(M.row_sizes, dtype=np.int32)
+        br = np.ascontiguousarray(M.blk_row, dtype=np.int32)
+        bc = np.ascontiguousarray(M.blk_col, dtype=np.int32)
+        v = np.ascontiguousarray(M.values, dtype=np.float64)
+        rid = _I64()
+        _check(lib().bsm_server_submit(self._h, len(sz), _vp(sz), len(br), _vp(br), _vp(bc), _vp(v),
+                                       float(eps), ctypes.byref(rid)), "bsm_server_submit")
+        return int(rid.value)
+
+    def progress(self) -> int:
+        n = _I32()
+        _check(lib().bsm_server_progress(self._h, ctypes.byref(n)), "bsm_server_progress")
+        return int(n.value)
+
+    def poll(self, rid: int):
+        st, lat, nb, nz = _I32(), _D(), _I64(), _I64()
+        rc = lib().bsm_server_poll(self._h, int(rid), ctypes.byref(st), ctypes.byref(lat),
+                                   ctypes.byref(nb), ctypes.byref(nz))
+        if rc != BSM_OK and st.value != REQ_FAILED:
+            raise BsmError(rc, "bsm_server_poll")
+        return int(st.value), float(lat.value), int(nb.value), int(nz.value)
+
+    def take(self, rid: int):
+        st, _, nb, nz = self.poll(rid)
+        if st != REQ_DONE:
+            raise BsmError(-1, "bsm_server_take")
+        r = np.empty(nb, np.int32)
+        c = np.empty(nb, np.int32)
+        v = np.empty(nz, np.float64)
+        _check(lib().bsm_server_take(self._h, int(rid), nb, _vp(r), _vp(c), nz, _vp(v)), "bsm_server_take")
+        return r, c, v
+
+    def info(self) -> dict:
+        i = _ServerInfo()
+        _check(lib().bsm_server_get_info(self._h, ctypes.byref(i)), "bsm_server_get_info")
+        return {k: int(getattr(i, k)) for k, _ in _ServerInfo._fields_}
+
+    def close(self):
+        if self._h:
+            lib().bsm_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -14,8 +14,11 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -97,6 +100,10 @@ struct bsm_mat_s {
   int32_t nbr = 0, nbc = 0;
   std::vector<int32_t> h_row_sizes, h_col_sizes;
   int32_t max_row = 0, max_col = 0;  // largest block row / column size
+  // shape kinds: the distinct block row / column sizes (at most 32; more are
+  // folded into one kind) and each block row's / column's kind index
+  std::vector<int32_t> row_kinds, col_kinds;
+  int32_t *row_cls = nullptr, *col_cls = nullptr;
   // slices of the values for the split precisions (left / right operand layouts)
   void *split_left = nullptr, *split_right = nullptr;
   int64_t cap_left = 0, cap_right = 0;  // bytes
@@ -132,7 +139,27 @@ struct bsm_ctx_s {
   bsm_profile prof_tot{};
   int64_t launches = 0;
   int64_t launches_at_enable = 0;
+  // shape-class grouping (per-stack launches)
+  int32_t *cls_items = nullptr;  // [cap_cblk]
+  int32_t *cls_counts = nullptr, *cls_cursor = nullptr;  // [kMaxClasses]
+  int64_t *cls_segs = nullptr;   // [2 * kMaxClasses]
+  // captured multiplies (opts.graph), keyed by every kernel argument
+  struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+    uint64_t used = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  // autotuner: key -> FP64 variant
+  std::map<std::string, int> tune;
+  std::string tune_path;
+  uint64_t tune_version = 0;
 };
+
+constexpr int kMaxKinds = 32;
+constexpr int kMaxGraphs = 8;
 
 // Add the phase times of slot s to the totals (once per recorded multiply).
 static int prof_collect(bsm_ctx ctx, int s) {
@@ -192,10 +219,11 @@ static int ws_grow(bsm_ctx ctx, int64_t nblk_c, int64_t nprod) {
     dev_free(w.cnt);
     dev_free(w.c_cin);
     dev_free(w.prod_ptr);
+    dev_free(ctx->cls_items);
     const int64_t n = nblk_c + nblk_c / 8 + 1024;
     int rc;
     if ((rc = dev_alloc(&w.cnt, n)) || (rc = dev_alloc(&w.c_cin, n)) ||
-        (rc = dev_alloc(&w.prod_ptr, n + 1))) {
+        (rc = dev_alloc(&w.prod_ptr, n + 1)) || (rc = dev_alloc(&ctx->cls_items, n))) {
       ctx->cap_cblk = -1;
       return rc;
     }
@@ -335,97 +363,352 @@ static int take_slot(bsm_ctx ctx, bsm_mat owner) {
   return s;
 }
 
+// ---------------------------------------------------------------------------
+// autotuner: FP64 numeric variants per shape class (per-stack launches) or for
+// the whole class mix (one persistent launch), timed on the real data the first
+// time a key is met and kept in a text file (BSM_AUTOTUNE_CACHE) across runs.
+// ---------------------------------------------------------------------------
+static std::string tune_key_class(int m, int n) {
+  return "fp64/class/" + std::to_string(m) + "x" + std::to_string(n);
+}
+
+static std::string tune_key_all(bsm_mat A, bsm_mat B) {
+  std::string k = "fp64/all/";
+  for (int32_t r : A->row_kinds) k += std::to_string(r) + ",";
+  k += "|";
+  for (int32_t c : A->col_kinds) k += std::to_string(c) + ",";
+  k += "|";
+  for (int32_t c : B->col_kinds) k += std::to_string(c) + ",";
+  return k;
+}
+
+static void tune_load(bsm_ctx ctx) {
+  const char *p = getenv("BSM_AUTOTUNE_CACHE");
+  if (!p || !*p) return;
+  ctx->tune_path = p;
+  FILE *f = fopen(p, "r");
+  if (!f) return;
+  char key[512];
+  int v;
+  double ms;
+  while (fscanf(f, "%511s %d %lf", key, &v, &ms) == 3)
+    if (v >= 0 && v < kFp64NumVariants) ctx->tune[key] = v;
+  fclose(f);
+}
+
+static void tune_save(bsm_ctx ctx, const std::string &key, int v, double ms) {
+  ctx->tune[key] = v;
+  ctx->tune_version++;
+  if (ctx->tune_path.empty()) return;
+  FILE *f = fopen(ctx->tune_path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "%s %d %.6f\n", key.c_str(), v, ms);
+  fclose(f);
+}
+
+static bool needs_tuning(bsm_ctx ctx, bsm_mat A, bsm_mat B, const bsm_opts &o) {
+  if (!o.autotune || o.precision != BSM_PREC_FP64) return false;
+  if (o.launch != BSM_LAUNCH_PER_STACK) return !ctx->tune.count(tune_key_all(A, B));
+  for (int32_t m : A->row_kinds)
+    for (int32_t n : B->col_kinds)
+      if (!ctx->tune.count(tune_key_class(m, n))) return true;
+  return false;
+}
+
+static int variant_or_default(bsm_ctx ctx, const std::string &key) {
+  auto it = ctx->tune.find(key);
+  return it == ctx->tune.end() ? kFp64T16B2 : it->second;
+}
+
+struct Launch {
+  bsm_ctx ctx;
+  bsm_mat A, B, C;
+  double alpha, beta, eps;
+  bsm_opts o;
+  int slot;
+  cudaStream_t s;
+  bool use_cin, split, prof;
+  DevMat dA, dB, dC;
+  DevWs ws;
+  DevOut out;
+};
+
+// norms, operand slices, symbolic count and scan
+static int stage_a(Launch &L, bool record) {
+  bsm_ctx ctx = L.ctx;
+  int rc;
+  if (L.prof && record) CK(cudaEventRecord(ctx->prof_ev[L.slot][0], L.s));
+  if ((rc = enqueue_norms(ctx, L.A, L.s))) return rc;
+  ctx->launches++;
+  if (L.B != L.A) {
+    if ((rc = enqueue_norms(ctx, L.B, L.s))) return rc;
+    ctx->launches++;
+  }
+  if (L.split) {  // operand slices for the tensor-core products
+    const int grid = ctx->nsm * 16;
+    bsm_mat A = L.A, B = L.B;
+    CK(launch_split(L.o.precision, A->row_sizes, A->col_sizes, A->front.blk_row, A->front.col_idx,
+                    A->front.blk_off, A->front.vals, A->front.hdr, A->split_left,
+                    B == A ? A->split_right : nullptr, grid, L.s));
+    ctx->launches++;
+    if (B != A) {
+      CK(launch_split(L.o.precision, B->row_sizes, B->col_sizes, B->front.blk_row,
+                      B->front.col_idx, B->front.blk_off, B->front.vals, B->front.hdr, nullptr,
+                      B->split_right, grid, L.s));
+      ctx->launches++;
+    }
+  }
+  if (L.prof && record) CK(cudaEventRecord(ctx->prof_ev[L.slot][1], L.s));
+  CK(launch_symbolic_count(L.dA, L.dB, L.dC, L.use_cin ? 1 : 0, L.eps, L.ws, ctx->nsm * 6, L.s));
+  ctx->launches++;
+  CK(launch_symbolic_scan(L.A->nbr, L.ws, L.out, ctx->d_status, L.s));
+  ctx->launches++;
+  return BSM_OK;
+}
+
+// max_m, max_n: the largest C block row / column size the launch can meet
+// (they pick the split-precision tile paths).
+static int launch_numeric(Launch &L, int variant, const int32_t *items, const int64_t *seg,
+                          int max_m, int max_n) {
+  bsm_ctx ctx = L.ctx;
+  if (L.split) {
+    if (max_m <= 16 && max_n <= 16) {
+      CK(launch_numeric_split(L.o.precision, 0, L.dA, L.dB, L.out, L.dC, L.A->split_left,
+                              L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
+                              ctx->nsm * 4, L.s));
+    } else {
+      CK(launch_numeric_split(L.o.precision, 1, L.dA, L.dB, L.out, L.dC, L.A->split_left,
+                              L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
+                              ctx->nsm * 4, L.s));
+      ctx->launches++;
+      CK(launch_numeric_split(L.o.precision, 2, L.dA, L.dB, L.out, L.dC, L.A->split_left,
+                              L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
+                              ctx->nsm * 2, L.s));
+    }
+  } else
+    CK(launch_numeric_fp64(variant, L.dA, L.dB, L.out, L.dC, L.alpha, L.beta, L.ws,
+                           ctx->d_status, items, seg,
+                           ctx->nsm * fp64_variant_blocks_per_sm(variant), L.s));
+  ctx->launches++;
+  return BSM_OK;
+}
+
+// Time `variant` over a work range (blocking; only while tuning).
+static int time_variant(Launch &L, int variant, const int32_t *items, const int64_t *seg,
+                        int max_m, int max_n, double *ms_out) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e30;
+  int rc = BSM_OK;
+  for (int rep = 0; rep < 3 && rc == BSM_OK; rep++) {
+    cudaEventRecord(e0, L.s);
+    rc = launch_numeric(L, variant, items, seg, max_m, max_n);
+    cudaEventRecord(e1, L.s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = BSM_ERR_CUDA;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, (double)ms);  // the first run warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = best;
+  return rc;
+}
+
+// fill, shape-class grouping (per-stack), numeric
+static int stage_b(Launch &L, bool record, bool may_tune) {
+  bsm_ctx ctx = L.ctx;
+  int rc;
+  CK(launch_symbolic_fill(L.dA, L.dB, L.dC, L.use_cin ? 1 : 0, L.eps, L.ws, L.out, ctx->d_status,
+                          ctx->nsm * 6, L.s));
+  ctx->launches++;
+  if (L.prof && record) CK(cudaEventRecord(ctx->prof_ev[L.slot][2], L.s));
+  if (L.o.launch == BSM_LAUNCH_PER_STACK) {
+    const int ncc = (int)L.B->col_kinds.size();
+    const int ncls = (int)L.A->row_kinds.size() * ncc;
+    CK(launch_class_sort(L.out, L.A->row_cls, L.B->col_cls, ncc, ncls, ctx->d_status,
+                         ctx->cls_counts, ctx->cls_cursor, ctx->cls_segs, ctx->cls_items, ctx->nsm,
+                         L.s));
+    ctx->launches += 3;
+    for (int c = 0; c < ncls; c++) {
+      const int m = L.A->row_kinds[c / ncc], n = L.B->col_kinds[c % ncc];
+      const std::string key = tune_key_class(m, n);
+      const int64_t *seg = ctx->cls_segs + 2 * c;
+      if (may_tune && L.o.autotune && !L.split && !ctx->tune.count(key)) {
+        int best = kFp64T16B2;
+        double best_ms = 1e30;
+        for (int v = 0; v < kFp64NumVariants; v++) {
+          double ms;
+          if ((rc = time_variant(L, v, ctx->cls_items, seg, m, n, &ms))) return rc;
+          if (ms < best_ms) best_ms = ms, best = v;
+        }
+        tune_save(ctx, key, best, best_ms);
+      }
+      if ((rc = launch_numeric(L, variant_or_default(ctx, key), ctx->cls_items, seg, m, n)))
+        return rc;
+    }
+  } else {
+    const std::string key = tune_key_all(L.A, L.B);
+    if (may_tune && L.o.autotune && !L.split && !ctx->tune.count(key)) {
+      int best = kFp64T16B2;
+      double best_ms = 1e30;
+      for (int v = 0; v < kFp64NumVariants; v++) {
+        double ms;
+        if ((rc = time_variant(L, v, nullptr, nullptr, L.A->max_row, L.B->max_col, &ms)))
+          return rc;
+        if (ms < best_ms) best_ms = ms, best = v;
+      }
+      tune_save(ctx, key, best, best_ms);
+    }
+    if ((rc = launch_numeric(L, variant_or_default(ctx, key), nullptr, nullptr, L.A->max_row,
+                             L.B->max_col)))
+      return rc;
+  }
+  if (L.prof && record) {
+    CK(cudaEventRecord(ctx->prof_ev[L.slot][3], L.s));
+    ctx->prof_pending[L.slot] = true;
+  }
+  return BSM_OK;
+}
+
+static void graph_key(const Launch &L, std::vector<uint64_t> &k) {
+  auto put = [&](const void *p) { k.push_back((uint64_t)(uintptr_t)p); };
+  auto num = [&](int64_t v) { k.push_back((uint64_t)v); };
+  auto dbl = [&](double v) {
+    uint64_t u;
+    memcpy(&u, &v, 8);
+    k.push_back(u);
+  };
+  for (bsm_mat M : {L.A, L.B, L.C}) {
+    const Buf *bs[2] = {&M->front, &M->back};
+    for (const Buf *b : bs) {
+      put(b->row_ptr), put(b->col_idx), put(b->blk_row), put(b->blk_off), put(b->norms);
+      put(b->vals), put(b->hdr), num(b->cap_blk), num(b->cap_nnz);
+    }
+    put(M->split_left), put(M->split_right), put(M->row_sizes), put(M->col_sizes);
+    put(M->row_cls), put(M->col_cls), num(M->nbr), num(M->nbc);
+  }
+  const DevWs &w = L.ws;
+  put(w.row_cblk), put(w.row_prod), put(w.row_nnz), put(w.row_cand), put(w.row_flops);
+  put(w.prod_off), put(w.nnz_off), put(w.cnt), put(w.c_cin), put(w.prod_ptr), put(w.prods);
+  num(w.cap_prod), num(L.out.cap_blk), num(L.out.cap_nnz);
+  put(L.ctx->cls_items), put(L.s);
+  dbl(L.alpha), dbl(L.beta), dbl(L.eps);
+  num(L.o.precision), num(L.o.launch), num((int64_t)L.ctx->tune_version);
+}
+
 // Enqueue one multiply. sync_sizes: read the totals back after the scan and
 // size the buffers exactly before the fill and numeric passes.
 static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, bsm_mat C,
                         double eps, const bsm_opts &o, bool sync_sizes, int slot,
                         bsm_stats *stats) {
-  cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->stream;
-  if (s != ctx->stream) CK(cudaStreamWaitEvent(s, ctx->ev_last, 0));
-  const bool use_cin = (beta != 0.0);
+  Launch L{};
+  L.ctx = ctx;
+  L.A = A, L.B = B, L.C = C;
+  L.alpha = alpha, L.beta = beta, L.eps = eps;
+  L.o = o;
+  L.slot = slot;
+  L.s = o.stream ? (cudaStream_t)o.stream : ctx->stream;
+  L.use_cin = (beta != 0.0);
+  L.split = o.precision != BSM_PREC_FP64;
+  if (L.s != ctx->stream) CK(cudaStreamWaitEvent(L.s, ctx->ev_last, 0));
   int rc;
   if ((rc = ws_rows(ctx, A->nbr))) return rc;
   if ((rc = buf_grow(C, C->back, 0, 0, true))) return rc;
   if (ctx->cap_cblk < 0 && (rc = ws_grow(ctx, 0, 0))) return rc;
-  if (stats) CK(cudaEventRecord(ctx->ev_t0, s));
-  const bool prof = ctx->prof;
-  if (prof) CK(cudaEventRecord(ctx->prof_ev[slot][0], s));
-
-  if ((rc = enqueue_norms(ctx, A, s))) return rc;
-  ctx->launches++;
-  if (B != A) {
-    if ((rc = enqueue_norms(ctx, B, s))) return rc;
-    ctx->launches++;
-  }
-  const bool split = o.precision != BSM_PREC_FP64;
-  if (split) {  // operand slices for the tensor-core products
+  if (L.split) {
     if ((rc = split_buffers(A, o.precision, true, B == A))) return rc;
     if (B != A && (rc = split_buffers(B, o.precision, false, true))) return rc;
-    const int grid = ctx->nsm * 16;
-    CK(launch_split(o.precision, A->row_sizes, A->col_sizes, A->front.blk_row, A->front.col_idx,
-                    A->front.blk_off, A->front.vals, A->front.hdr, A->split_left,
-                    B == A ? A->split_right : nullptr, grid, s));
-    ctx->launches++;
-    if (B != A) {
-      CK(launch_split(o.precision, B->row_sizes, B->col_sizes, B->front.blk_row, B->front.col_idx,
-                      B->front.blk_off, B->front.vals, B->front.hdr, nullptr, B->split_right,
-                      grid, s));
-      ctx->launches++;
+  }
+  L.dA = dev_view(A), L.dB = dev_view(B), L.dC = dev_view(C);
+  auto make_out = [&]() {
+    L.ws = ctx->ws;
+    L.out = dev_out(C, C->back);
+    // capacities of the per-C-block scratch cap the block count as well
+    L.out.cap_blk = std::min<int64_t>(L.out.cap_blk, std::max<int64_t>(ctx->cap_cblk - 1, 0));
+  };
+  make_out();
+  const bool use_graph = o.graph && !sync_sizes;
+  L.prof = ctx->prof && !use_graph;
+  if (stats) CK(cudaEventRecord(ctx->ev_t0, L.s));
+
+  if (use_graph) {
+    std::vector<uint64_t> key;
+    graph_key(L, key);
+    bsm_ctx_s::GraphEntry *hit = nullptr;
+    for (auto &g : ctx->graphs)
+      if (g.key == key) hit = &g;
+    if (!hit) {
+      // a multiply with new arguments: capture it once (tuning already done)
+      if (needs_tuning(ctx, A, B, o)) {
+        // run uncaptured first so that the missing tuner entries are filled
+        if ((rc = stage_a(L, false)) || (rc = stage_b(L, false, true))) return rc;
+        graph_key(L, key);  // the tuner may have changed the table version
+        for (auto &g : ctx->graphs)
+          if (g.key == key) hit = &g;
+      }
     }
-  }
-  if (prof) CK(cudaEventRecord(ctx->prof_ev[slot][1], s));
-
-  DevMat dA = dev_view(A), dB = dev_view(B), dC = dev_view(C);
-  const int sym_grid = ctx->nsm * 6;
-  CK(launch_symbolic_count(dA, dB, dC, use_cin ? 1 : 0, eps, ctx->ws, sym_grid, s));
-  ctx->launches++;
-
-  DevWs ws = ctx->ws;
-  ws.cap_prod = ctx->ws.cap_prod;
-  DevOut out = dev_out(C, C->back);
-  // capacities of the per-C-block scratch cap the block count as well
-  out.cap_blk = std::min<int64_t>(out.cap_blk, std::max<int64_t>(ctx->cap_cblk - 1, 0));
-  CK(launch_symbolic_scan(A->nbr, ws, out, ctx->d_status, s));
-  ctx->launches++;
-
-  if (sync_sizes) {
-    DevStatus h{};
-    CK(cudaMemcpyAsync(&h, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    C->hint_blk = h.nblk_c;
-    C->hint_nnz = h.nnz_c;
-    ctx->hint_prod = std::max(ctx->hint_prod, h.nprod);
-    if (h.overflow) {
-      if (h.nblk_c >= (int64_t)INT32_MAX) return BSM_ERR_UNSUPPORTED;
-      if ((rc = buf_grow(C, C->back, h.nblk_c, h.nnz_c, false))) return rc;
-      if ((rc = ws_grow(ctx, h.nblk_c, h.nprod))) return rc;
-      ws = ctx->ws;
-      out = dev_out(C, C->back);
-      out.cap_blk = std::min<int64_t>(out.cap_blk, std::max<int64_t>(ctx->cap_cblk - 1, 0));
-      CK(launch_symbolic_scan(A->nbr, ws, out, ctx->d_status, s));
-      ctx->launches++;
+    if (!hit) {
+      const int64_t l0 = ctx->launches;
+      CK(cudaStreamBeginCapture(L.s, cudaStreamCaptureModeThreadLocal));
+      rc = stage_a(L, false);
+      if (rc == BSM_OK) rc = stage_b(L, false, false);
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(L.s, &graph);
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+      cudaGraphExec_t exec = nullptr;
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+      if ((int)ctx->graphs.size() >= kMaxGraphs) {  // evict the least recently used
+        auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                    [](const bsm_ctx_s::GraphEntry &a,
+                                       const bsm_ctx_s::GraphEntry &b) { return a.used < b.used; });
+        cudaGraphExecDestroy(lru->exec);
+        ctx->graphs.erase(lru);
+      }
+      bsm_ctx_s::GraphEntry e;
+      e.key = key;
+      e.exec = exec;
+      e.launches = (int)(ctx->launches - l0);
+      ctx->launches = l0;  // counted when the graph runs
+      ctx->graphs.push_back(e);
+      hit = &ctx->graphs.back();
     }
+    hit->used = ++ctx->graph_clock;
+    CK(cudaGraphLaunch(hit->exec, L.s));
+    ctx->launches += hit->launches;
+  } else {
+    if ((rc = stage_a(L, true))) return rc;
+    if (sync_sizes) {
+      DevStatus h{};
+      CK(cudaMemcpyAsync(&h, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, L.s));
+      CK(cudaStreamSynchronize(L.s));
+      C->hint_blk = h.nblk_c;
+      C->hint_nnz = h.nnz_c;
+      ctx->hint_prod = std::max(ctx->hint_prod, h.nprod);
+      if (h.overflow) {
+        if (h.nblk_c >= (int64_t)INT32_MAX) return BSM_ERR_UNSUPPORTED;
+        if ((rc = buf_grow(C, C->back, h.nblk_c, h.nnz_c, false))) return rc;
+        if ((rc = ws_grow(ctx, h.nblk_c, h.nprod))) return rc;
+        make_out();
+        CK(launch_symbolic_scan(A->nbr, L.ws, L.out, ctx->d_status, L.s));
+        ctx->launches++;
+      }
+    }
+    if ((rc = stage_b(L, true, true))) return rc;
   }
-  CK(launch_symbolic_fill(dA, dB, dC, use_cin ? 1 : 0, eps, ws, out, ctx->d_status, sym_grid, s));
-  ctx->launches++;
-  if (prof) CK(cudaEventRecord(ctx->prof_ev[slot][2], s));
-  const int max_dim = std::max(A->max_row, std::max(A->max_col, B->max_col));
-  if (split)
-    CK(launch_numeric_split(o.precision, dA, dB, out, dC, A->split_left, B->split_right, alpha,
-                            beta, ws, ctx->d_status, max_dim, ctx->nsm, s));
-  else
-    CK(launch_numeric_fp64(dA, dB, out, dC, alpha, beta, ws, ctx->d_status, max_dim, ctx->nsm, s));
-  ctx->launches++;
-  if (prof) {
-    CK(cudaEventRecord(ctx->prof_ev[slot][3], s));
-    ctx->prof_pending[slot] = true;
-  }
-  if (stats) CK(cudaEventRecord(ctx->ev_t1, s));
+  if (stats) CK(cudaEventRecord(ctx->ev_t1, L.s));
   CK(cudaMemcpyAsync(&ctx->h_slots[slot], ctx->d_status, sizeof(DevStatus),
-                     cudaMemcpyDeviceToHost, s));
-  CK(cudaEventRecord(ctx->slot_ev[slot], s));
-  CK(cudaEventRecord(ctx->ev_last, s));
-  if (s != ctx->stream) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_last, 0));
+                     cudaMemcpyDeviceToHost, L.s));
+  CK(cudaEventRecord(ctx->slot_ev[slot], L.s));
+  CK(cudaEventRecord(ctx->ev_last, L.s));
+  if (L.s != ctx->stream) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_last, 0));
   return BSM_OK;
 }
 
@@ -517,6 +800,15 @@ int bsm_ctx_create(int device, bsm_ctx *out) {
       rc = cuda_fail(e, "cudaEventCreate");
   }
   if (rc == BSM_OK) {
+    if ((e = numeric_fp64_init()) != cudaSuccess) rc = cuda_fail(e, "numeric_fp64_init");
+  }
+  if (rc == BSM_OK) {
+    rc = dev_alloc(&ctx->cls_counts, kMaxClasses);
+    if (rc == BSM_OK) rc = dev_alloc(&ctx->cls_cursor, kMaxClasses);
+    if (rc == BSM_OK) rc = dev_alloc(&ctx->cls_segs, 2 * kMaxClasses);
+  }
+  if (rc == BSM_OK) tune_load(ctx);
+  if (rc == BSM_OK) {
     memset(ctx->h_slots, 0, kSlots * sizeof(DevStatus));
     e = cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -554,6 +846,12 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   dev_free(w.prod_ptr);
   dev_free(w.prods);
   dev_free(ctx->d_status);
+  dev_free(ctx->cls_items);
+  dev_free(ctx->cls_counts);
+  dev_free(ctx->cls_cursor);
+  dev_free(ctx->cls_segs);
+  for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
   if (ctx->h_slots) cudaFreeHost(ctx->h_slots);
   for (int i = 0; i < kSlots; i++) {
     if (ctx->slot_ev[i]) cudaEventDestroy(ctx->slot_ev[i]);
@@ -613,12 +911,31 @@ int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_
   M->h_col_sizes.assign(col_sizes, col_sizes + nbcols);
   for (int32_t v : M->h_row_sizes) M->max_row = std::max(M->max_row, v);
   for (int32_t v : M->h_col_sizes) M->max_col = std::max(M->max_col, v);
+  // shape kinds of the block rows and columns
+  auto kinds = [](const std::vector<int32_t> &sizes, std::vector<int32_t> &kind,
+                  std::vector<int32_t> &cls) {
+    kind = sizes;
+    std::sort(kind.begin(), kind.end());
+    kind.erase(std::unique(kind.begin(), kind.end()), kind.end());
+    cls.resize(sizes.size());
+    if ((int)kind.size() > kMaxKinds) {  // too many sizes: one kind, keyed by the largest
+      kind = {kind.back()};
+      std::fill(cls.begin(), cls.end(), 0);
+      return;
+    }
+    for (size_t i = 0; i < sizes.size(); i++)
+      cls[i] = (int32_t)(std::lower_bound(kind.begin(), kind.end(), sizes[i]) - kind.begin());
+  };
+  std::vector<int32_t> h_row_cls, h_col_cls;
+  kinds(M->h_row_sizes, M->row_kinds, h_row_cls);
+  kinds(M->h_col_sizes, M->col_kinds, h_col_cls);
   ctx->mats.push_back(M);
   auto fail = [&](int code) {
     bsm_mat_destroy(M);
     return code;
   };
-  if ((rc = dev_alloc(&M->row_sizes, nbrows)) || (rc = dev_alloc(&M->col_sizes, nbcols)))
+  if ((rc = dev_alloc(&M->row_sizes, nbrows)) || (rc = dev_alloc(&M->col_sizes, nbcols)) ||
+      (rc = dev_alloc(&M->row_cls, nbrows)) || (rc = dev_alloc(&M->col_cls, nbcols)))
     return fail(rc);
   if ((rc = buf_grow(M, M->front, nblocks, nnz, true))) return fail(rc);
   // host-side CSR arrays in sorted order
@@ -648,6 +965,8 @@ int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_
   cudaError_t e;
   if ((e = cp(M->row_sizes, row_sizes, (size_t)nbrows * 4)) != cudaSuccess ||
       (e = cp(M->col_sizes, col_sizes, (size_t)nbcols * 4)) != cudaSuccess ||
+      (e = cp(M->row_cls, h_row_cls.data(), (size_t)nbrows * 4)) != cudaSuccess ||
+      (e = cp(M->col_cls, h_col_cls.data(), (size_t)nbcols * 4)) != cudaSuccess ||
       (e = cp(M->front.row_ptr, h_row_ptr.data(), ((size_t)nbrows + 1) * 4)) != cudaSuccess ||
       (e = cp(M->front.col_idx, h_col.data(), (size_t)nblocks * 4)) != cudaSuccess ||
       (e = cp(M->front.blk_row, h_row.data(), (size_t)nblocks * 4)) != cudaSuccess ||
@@ -685,6 +1004,11 @@ int bsm_mat_destroy(bsm_mat m) {
   if (m->split_right) cudaFree(m->split_right);
   dev_free(m->row_sizes);
   dev_free(m->col_sizes);
+  dev_free(m->row_cls);
+  dev_free(m->col_cls);
+  // captured multiplies may name this matrix's buffers
+  for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
   auto &v = ctx->mats;
   v.erase(std::remove(v.begin(), v.end(), m), v.end());
   delete m;

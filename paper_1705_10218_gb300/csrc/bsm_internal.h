@@ -90,11 +90,26 @@ cudaError_t launch_symbolic_fill(DevMat A, DevMat B, DevMat Cin, int use_cin, do
                                  DevWs ws, DevOut C, const DevStatus *st, int grid,
                                  cudaStream_t stream);
 
-// max_dim: the largest block dimension (rows of A, columns of A and of B)
-// that can occur; it selects the kernel variant.
-cudaError_t launch_numeric_fp64(DevMat A, DevMat B, DevOut C, DevMat Cin, double alpha,
-                                double beta, DevWs ws, const DevStatus *st, int max_dim,
-                                int nsm, cudaStream_t stream);
+// FP64 numeric kernel variants (k_numeric_fp64.cu).
+enum { kFp64T16B2 = 0, kFp64T16B3 = 1, kFp64T32 = 2, kFp64NumVariants = 3 };
+int fp64_variant_blocks_per_sm(int variant);
+// Per-device kernel attributes (call with the device current, outside capture).
+cudaError_t numeric_fp64_init();
+
+// items: optional work list of C block indices; seg: optional device [begin,
+// end) into it (default: all C blocks of the multiply, in row order).
+cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMat Cin,
+                                double alpha, double beta, DevWs ws, const DevStatus *st,
+                                const int32_t *items, const int64_t *seg, int grid,
+                                cudaStream_t stream);
+
+// Shape classes (k_classes.cu): class of C block g = row_cls[row] * ncc +
+// col_cls[col]; items receives the C blocks grouped by class, segs[2c..2c+1]
+// the [begin, end) of class c. counts/cursor: ncls int32 of scratch.
+constexpr int kMaxClasses = 1024;
+cudaError_t launch_class_sort(DevOut C, const int32_t *row_cls, const int32_t *col_cls, int ncc,
+                              int ncls, const DevStatus *st, int32_t *counts, int32_t *cursor,
+                              int64_t *segs, int32_t *items, int nsm, cudaStream_t stream);
 
 // Split precision (k_split.cu). left/right: slice layouts of the operand as a
 // left (row-major) or right (column-major) MMA operand; either may be null.
@@ -103,10 +118,12 @@ cudaError_t launch_split(int precision, const int32_t *row_sizes, const int32_t 
                          const double *vals, const int64_t *hdr, void *left, void *right,
                          int grid, cudaStream_t stream);
 
-cudaError_t launch_numeric_split(int precision, DevMat A, DevMat B, DevOut C, DevMat Cin,
-                                 const void *a_left, const void *b_right, double alpha,
-                                 double beta, DevWs ws, const DevStatus *st, int max_dim, int nsm,
-                                 cudaStream_t stream);
+// sizes: 0 = every block's MMA problem fits 16 x 16 (one launch covers all);
+// 1 = only the blocks that fit 16 x 16; 2 = only the larger ones (<= 32 x 32).
+cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, DevOut C,
+                                 DevMat Cin, const void *a_left, const void *b_right, double alpha,
+                                 double beta, DevWs ws, const DevStatus *st, const int32_t *items,
+                                 const int64_t *seg, int grid, cudaStream_t stream);
 
 // Bytes of slice storage per FP64 value of an operand (bf16x3: padded planes
 // at 12 halfwords per value; tf32x2: 2 words per value).

@@ -114,6 +114,9 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) return noalloc_cuda_fail(e);
+      // the numeric kernel's shared-memory size attribute, also once per device
+      e = numeric_fp64_init();
+      if (e != cudaSuccess) return noalloc_cuda_fail(e);
       g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
     }
     scratch = g_noalloc_ptr[dev];
@@ -205,8 +208,9 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
     return noalloc_cuda_fail(e);
   if ((e = launch_symbolic_fill(dA, dB, none, 0, eps, ws, out, st, nsm * 6, s)) != cudaSuccess)
     return noalloc_cuda_fail(e);
-  // block sizes live on the device only: take the variant that handles any size
-  if ((e = launch_numeric_fp64(dA, dB, out, none, alpha, 0.0, ws, st, 1 << 30, nsm, s)) != cudaSuccess)
+  // block sizes live on the device only: the 32 x 32 tile variant handles any size
+  if ((e = launch_numeric_fp64(kFp64T32, dA, dB, out, none, alpha, 0.0, ws, st, nullptr, nullptr,
+                                nsm * 3, s)) != cudaSuccess)
     return noalloc_cuda_fail(e);
 
   DevStatus h{};

@@ -215,218 +215,338 @@ __device__ __forceinline__ double f32_to_f64_exact(float f) {
 }
 
 // ---------------------------------------------------------------------------
-// Numeric kernel, BF16x3. One warp per C block; the C block (or its transpose,
-// whichever needs fewer MMA tiles) is covered by MT x NT tiles of 16 x 8; each
-// product contributes k-steps of 16 (and a final step of 8 when at most 8
-// remain) with six slice products per tile and step.
+// Numeric kernel. One warp per C block; the C block (or its transpose,
+// whichever needs fewer MMA tiles) is covered by MT x NT tiles of 16 x 8.
+// A "step" is one k-step of one product: 16 (BF16; 8 for a final step with at
+// most 8 left) or 8 (TF32) values of k, with all slice products of every tile.
 //
-// Operands: L (M' x s) is read from a left layout (row-major, stride sp), R
-// (s x N') from a right layout (column-major, stride sp), where sp = s rounded
-// up to even. Not transposed: L = A_ik (A's left layout), R = B_kj (B's right
-// layout). Transposed (C^T = B^T A^T): L = B_kj^T = B's right layout read as
-// row-major, R = A_ik^T = A's left layout read as column-major.
+// Operands: L (M' x s) is read from a left layout (row-major), R (s x N')
+// from a right layout (column-major). Not transposed: L = A_ik (A's left
+// layout), R = B_kj (B's right layout). Transposed (C^T = B^T A^T): L = B_kj^T
+// = B's right layout read as row-major, R = A_ik^T = A's left layout read as
+// column-major.
+//
+// Accumulation: every product is summed in a fresh FP32 accumulator by the
+// tensor cores (at most a few MMAs deep), then added to a running sum kept as
+// an unevaluated pair hi + lo of FP32 numbers (TwoSum, error-free), so the
+// long sum over the products of a C block loses no more than FP32 rounding of
+// each product; hi + lo is formed in FP64 at the end.
 // ---------------------------------------------------------------------------
+template <int NSL, int MT, int NT>
+struct Frag {
+  uint32_t a[NSL][MT][4];
+  uint32_t b[NSL][NT][2];
+};
+
+// Fragments of one BF16 step (k values kk..kk+15, or kk..kk+7 when k8).
 template <int MT, int NT>
-__device__ __forceinline__ void bf16_block(const uint16_t *__restrict__ Lb,
-                                           const uint16_t *__restrict__ Rb, int Mp, int Np,
-                                           int s, int lplane, int rplane,
-                                           float (&acc)[MT][NT][4]) {
+__device__ __forceinline__ void load_bf16(Frag<3, MT, NT> &f, const uint16_t *__restrict__ Lb,
+                                          const uint16_t *__restrict__ Rb, int Mp, int Np, int sp,
+                                          int kk, bool k8, int lplane, int rplane) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
-  const int sp = s + (s & 1);
-  for (int kk = 0; kk < s; kk += 16) {
-    const bool k8 = (s - kk) <= 8;
-    // fragments of L: rows g (+8) of each M tile, k pairs 2t (+8)
-    uint32_t a[3][MT][4];
+  const int k0 = kk + 2 * t, k1 = k0 + 8;
 #pragma unroll
-    for (int q = 0; q < 3; q++)
+  for (int q = 0; q < 3; q++) {
+    const uint32_t *P = reinterpret_cast<const uint32_t *>(Lb + (int64_t)q * lplane);
 #pragma unroll
-      for (int mt = 0; mt < MT; mt++) {
-        const int r0 = mt * 16 + g, r1 = r0 + 8;
-        const int k0 = kk + 2 * t, k1 = k0 + 8;
-        const uint32_t *P = reinterpret_cast<const uint32_t *>(Lb + (int64_t)q * lplane);
-        a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + ((r0 * sp + k0) >> 1)) : 0u;
-        a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + ((r1 * sp + k0) >> 1)) : 0u;
-        a[q][mt][2] = (!k8 && r0 < Mp && k1 < sp) ? __ldg(P + ((r0 * sp + k1) >> 1)) : 0u;
-        a[q][mt][3] = (!k8 && r1 < Mp && k1 < sp) ? __ldg(P + ((r1 * sp + k1) >> 1)) : 0u;
+    for (int mt = 0; mt < MT; mt++) {
+      const int r0 = mt * 16 + g, r1 = r0 + 8;
+      f.a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + ((r0 * sp + k0) >> 1)) : 0u;
+      f.a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + ((r1 * sp + k0) >> 1)) : 0u;
+      f.a[q][mt][2] = (!k8 && r0 < Mp && k1 < sp) ? __ldg(P + ((r0 * sp + k1) >> 1)) : 0u;
+      f.a[q][mt][3] = (!k8 && r1 < Mp && k1 < sp) ? __ldg(P + ((r1 * sp + k1) >> 1)) : 0u;
+    }
+    const uint32_t *Q = reinterpret_cast<const uint32_t *>(Rb + (int64_t)q * rplane);
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      const int c = nt * 8 + g;
+      f.b[q][nt][0] = (c < Np && k0 < sp) ? __ldg(Q + ((c * sp + k0) >> 1)) : 0u;
+      f.b[q][nt][1] = (!k8 && c < Np && k1 < sp) ? __ldg(Q + ((c * sp + k1) >> 1)) : 0u;
+    }
+  }
+}
+
+template <int MT, int NT>
+__device__ __forceinline__ void mma_bf16(float (&acc)[MT][NT][4], const Frag<3, MT, NT> &f,
+                                         bool k8, int Mp, int Np) {
+  // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
+  constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
+  constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      if (mt * 16 >= Mp || nt * 8 >= Np) continue;
+#pragma unroll
+      for (int pq = 0; pq < 6; pq++) {
+        if (k8)
+          mma_bf16_k8(acc[mt][nt], f.a[PA[pq]][mt][0], f.a[PA[pq]][mt][1], f.b[PB[pq]][nt][0]);
+        else
+          mma_bf16_k16(acc[mt][nt], f.a[PA[pq]][mt], f.b[PB[pq]][nt][0], f.b[PB[pq]][nt][1]);
       }
-    uint32_t bb[3][NT][2];
+    }
+}
+
+// Fragments of one TF32 step (k values kk..kk+7).
+template <int MT, int NT>
+__device__ __forceinline__ void load_tf32(Frag<2, MT, NT> &f, const uint32_t *__restrict__ Lb,
+                                          const uint32_t *__restrict__ Rb, int Mp, int Np, int s,
+                                          int kk, int lplane, int rplane) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int k0 = kk + t, k1 = k0 + 4;
 #pragma unroll
-    for (int q = 0; q < 3; q++)
+  for (int q = 0; q < 2; q++) {
+    const uint32_t *P = Lb + (int64_t)q * lplane;
 #pragma unroll
-      for (int nt = 0; nt < NT; nt++) {
-        const int c = nt * 8 + g;
-        const int k0 = kk + 2 * t, k1 = k0 + 8;
-        const uint32_t *P = reinterpret_cast<const uint32_t *>(Rb + (int64_t)q * rplane);
-        bb[q][nt][0] = (c < Np && k0 < sp) ? __ldg(P + ((c * sp + k0) >> 1)) : 0u;
-        bb[q][nt][1] = (!k8 && c < Np && k1 < sp) ? __ldg(P + ((c * sp + k1) >> 1)) : 0u;
+    for (int mt = 0; mt < MT; mt++) {
+      const int r0 = mt * 16 + g, r1 = r0 + 8;
+      f.a[q][mt][0] = (r0 < Mp && k0 < s) ? __ldg(P + r0 * s + k0) : 0u;
+      f.a[q][mt][1] = (r1 < Mp && k0 < s) ? __ldg(P + r1 * s + k0) : 0u;
+      f.a[q][mt][2] = (r0 < Mp && k1 < s) ? __ldg(P + r0 * s + k1) : 0u;
+      f.a[q][mt][3] = (r1 < Mp && k1 < s) ? __ldg(P + r1 * s + k1) : 0u;
+    }
+    const uint32_t *Q = Rb + (int64_t)q * rplane;
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      const int c = nt * 8 + g;
+      f.b[q][nt][0] = (c < Np && k0 < s) ? __ldg(Q + c * s + k0) : 0u;
+      f.b[q][nt][1] = (c < Np && k1 < s) ? __ldg(Q + c * s + k1) : 0u;
+    }
+  }
+}
+
+template <int MT, int NT>
+__device__ __forceinline__ void mma_tf32(float (&acc)[MT][NT][4], const Frag<2, MT, NT> &f,
+                                         int Mp, int Np) {
+  // (2,1) (1,2) (1,1)
+  constexpr int PA[3] = {1, 0, 0};
+  constexpr int PB[3] = {0, 1, 0};
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      if (mt * 16 >= Mp || nt * 8 >= Np) continue;
+#pragma unroll
+      for (int pq = 0; pq < 3; pq++)
+        mma_tf32_k8(acc[mt][nt], f.a[PA[pq]][mt], f.b[PB[pq]][nt][0], f.b[PB[pq]][nt][1]);
+    }
+}
+
+// hi + lo += x, exactly (Knuth's TwoSum in FP32, no fused operations).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+// One C block by one warp: the MMA problem M' x N' in MT x NT tiles. The
+// (A offset, B offset, k) of up to 32 products are read at once, one per lane;
+// with PREFETCH the next step's fragments are loaded while the current step
+// multiplies (twice the fragment registers).
+template <int PREC, int MT, int NT, bool PREFETCH>
+__device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, const DevOut &C,
+                                             const DevMat &Cin, const void *__restrict__ a_left,
+                                             const void *__restrict__ b_right, double alpha,
+                                             double beta, const DevWs &ws, int64_t gb, int m,
+                                             int n, bool tr, int Mp, int Np) {
+  constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
+  constexpr int NSL = BF ? 3 : 2;
+  constexpr int KSTEP = BF ? 16 : 8;
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  float hi[MT][NT][4], lo[MT][NT][4], acc[MT][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+      for (int x = 0; x < 4; x++) hi[mt][nt][x] = lo[mt][nt][x] = acc[mt][nt][x] = 0.f;
+  const int mp2 = m + (m & 1), np2 = n + (n & 1);
+
+  // operand pointers and planes of product (aoff, boff, s) for this block
+  auto operands = [&](int64_t aoff, int64_t boff, int s, const void *&L, const void *&R,
+                      int &lplane, int &rplane) {
+    if (BF) {
+      const uint16_t *Al = static_cast<const uint16_t *>(a_left) + 12 * aoff;
+      const uint16_t *Br = static_cast<const uint16_t *>(b_right) + 12 * boff;
+      const int sp = s + (s & 1);
+      const int ap = mp2 * sp, bpl = sp * np2;
+      L = tr ? (const void *)Br : (const void *)Al;
+      R = tr ? (const void *)Al : (const void *)Br;
+      lplane = tr ? bpl : ap;
+      rplane = tr ? ap : bpl;
+    } else {
+      const uint32_t *Al = static_cast<const uint32_t *>(a_left) + 2 * aoff;
+      const uint32_t *Br = static_cast<const uint32_t *>(b_right) + 2 * boff;
+      L = tr ? (const void *)Br : (const void *)Al;
+      R = tr ? (const void *)Al : (const void *)Br;
+      lplane = tr ? s * n : m * s;
+      rplane = tr ? m * s : s * n;
+    }
+  };
+  auto load = [&](Frag<NSL, MT, NT> &f, const void *L, const void *R, int lplane, int rplane,
+                  int s, int kk) {
+    if constexpr (BF)
+      load_bf16<MT, NT>(f, static_cast<const uint16_t *>(L), static_cast<const uint16_t *>(R), Mp,
+                        Np, s + (s & 1), kk, (s - kk) <= 8, lplane, rplane);
+    else
+      load_tf32<MT, NT>(f, static_cast<const uint32_t *>(L), static_cast<const uint32_t *>(R), Mp,
+                        Np, s, kk, lplane, rplane);
+  };
+
+  const int64_t p0 = ws.prod_ptr[gb], p1 = ws.prod_ptr[gb + 1];
+  for (int64_t pb = p0; pb < p1; pb += 32) {
+    const int nb = (p1 - pb < 32) ? (int)(p1 - pb) : 32;
+    int64_t my_a = 0, my_b = 0;
+    int my_s = 1;
+    if (lane < nb) {
+      const int2 pr = ws.prods[pb + lane];
+      my_a = A.blk_off[pr.x];
+      my_b = B.blk_off[pr.y];
+      my_s = A.col_sizes[A.col_idx[pr.x]];
+    }
+    Frag<NSL, MT, NT> cur, nxt;
+    int q = 0, kk = 0;
+    int s = __shfl_sync(0xffffffffu, my_s, 0);
+    const void *L, *R;
+    int lplane, rplane;
+    operands(__shfl_sync(0xffffffffu, my_a, 0), __shfl_sync(0xffffffffu, my_b, 0), s, L, R,
+             lplane, rplane);
+    load(cur, L, R, lplane, rplane, s, 0);
+    while (q < nb) {
+      // the next step: the next k-step of this product, or the next product
+      int nq = q, nkk = kk + KSTEP;
+      if (nkk >= s) {
+        nq = q + 1;
+        nkk = 0;
       }
-    // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
-    constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
-    constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+      const int src = nq < nb ? nq : 0;
+      const int ns = __shfl_sync(0xffffffffu, my_s, src);
+      const int64_t na = __shfl_sync(0xffffffffu, my_a, src);
+      const int64_t nbo = __shfl_sync(0xffffffffu, my_b, src);
+      const void *nL = L, *nR = R;
+      int nlp = lplane, nrp = rplane;
+      if (nq < nb && nq != q) operands(na, nbo, ns, nL, nR, nlp, nrp);
+      if (PREFETCH && nq < nb) load(nxt, nL, nR, nlp, nrp, ns, nkk);
+      if constexpr (BF)
+        mma_bf16<MT, NT>(acc, cur, (s - kk) <= 8, Mp, Np);
+      else
+        mma_tf32<MT, NT>(acc, cur, Mp, Np);
+      if (!PREFETCH && nq < nb) load(nxt, nL, nR, nlp, nrp, ns, nkk);
+      if (nq != q) {  // product done: fold it into the running sum
 #pragma unroll
-    for (int mt = 0; mt < MT; mt++)
+        for (int mt = 0; mt < MT; mt++)
 #pragma unroll
-      for (int nt = 0; nt < NT; nt++) {
-        if (mt * 16 >= Mp || nt * 8 >= Np) continue;
+          for (int nt = 0; nt < NT; nt++)
 #pragma unroll
-        for (int pq = 0; pq < 6; pq++) {
-          if (k8)
-            mma_bf16_k8(acc[mt][nt], a[PA[pq]][mt][0], a[PA[pq]][mt][1], bb[PB[pq]][nt][0]);
-          else
-            mma_bf16_k16(acc[mt][nt], a[PA[pq]][mt], bb[PB[pq]][nt][0], bb[PB[pq]][nt][1]);
+            for (int x = 0; x < 4; x++) {
+              two_sum_acc(hi[mt][nt][x], lo[mt][nt][x], acc[mt][nt][x]);
+              acc[mt][nt][x] = 0.f;
+            }
+      }
+      cur = nxt;
+      q = nq;
+      kk = nkk;
+      s = ns;
+      L = nL, R = nR, lplane = nlp, rplane = nrp;
+    }
+  }
+  // epilogue: C_ij = beta * C_in_ij + alpha * (hi + lo), formed in FP64
+  const bool plain = (alpha == 1.0 && beta == 0.0);
+  const int cin = ws.c_cin[gb];
+  const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+  double *out = C.vals + C.blk_off[gb];
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int rr = mt * 16 + g + ((x >> 1) << 3);
+        const int cc = nt * 8 + 2 * t + (x & 1);
+        if (rr < Mp && cc < Np) {
+          const int row = tr ? cc : rr, col = tr ? rr : cc;
+          const int64_t e = (int64_t)col * m + row;
+          double v = f32_to_f64_exact(hi[mt][nt][x]) + f32_to_f64_exact(lo[mt][nt][x]);
+          if (!plain) {
+            v = alpha * v;
+            if (cinv) v = fma(beta, cinv[e], v);
+          }
+          out[e] = v;
         }
       }
-  }
 }
 
-template <int MT, int NT>
-__device__ __forceinline__ void tf32_block(const uint32_t *__restrict__ Lb,
-                                           const uint32_t *__restrict__ Rb, int Mp, int Np,
-                                           int s, int lplane, int rplane,
-                                           float (&acc)[MT][NT][4]) {
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  for (int kk = 0; kk < s; kk += 8) {
-    uint32_t a[2][MT][4];
-#pragma unroll
-    for (int q = 0; q < 2; q++)
-#pragma unroll
-      for (int mt = 0; mt < MT; mt++) {
-        const int r0 = mt * 16 + g, r1 = r0 + 8;
-        const int k0 = kk + t, k1 = k0 + 4;
-        const uint32_t *P = Lb + (int64_t)q * lplane;
-        a[q][mt][0] = (r0 < Mp && k0 < s) ? __ldg(P + r0 * s + k0) : 0u;
-        a[q][mt][1] = (r1 < Mp && k0 < s) ? __ldg(P + r1 * s + k0) : 0u;
-        a[q][mt][2] = (r0 < Mp && k1 < s) ? __ldg(P + r0 * s + k1) : 0u;
-        a[q][mt][3] = (r1 < Mp && k1 < s) ? __ldg(P + r1 * s + k1) : 0u;
-      }
-    uint32_t bb[2][NT][2];
-#pragma unroll
-    for (int q = 0; q < 2; q++)
-#pragma unroll
-      for (int nt = 0; nt < NT; nt++) {
-        const int c = nt * 8 + g;
-        const int k0 = kk + t, k1 = k0 + 4;
-        const uint32_t *P = Rb + (int64_t)q * rplane;
-        bb[q][nt][0] = (c < Np && k0 < s) ? __ldg(P + c * s + k0) : 0u;
-        bb[q][nt][1] = (c < Np && k1 < s) ? __ldg(P + c * s + k1) : 0u;
-      }
-    // (2,1) (1,2) (1,1)
-    constexpr int PA[3] = {1, 0, 0};
-    constexpr int PB[3] = {0, 1, 0};
-#pragma unroll
-    for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-      for (int nt = 0; nt < NT; nt++) {
-        if (mt * 16 >= Mp || nt * 8 >= Np) continue;
-#pragma unroll
-        for (int pq = 0; pq < 3; pq++)
-          mma_tf32_k8(acc[mt][nt], a[PA[pq]][mt], bb[PB[pq]][nt][0], bb[PB[pq]][nt][1]);
-      }
-  }
-}
-
-// One warp per C block (grid-stride). Block dimensions up to 16 * MT (rows of
-// the MMA problem) and 8 * NT (columns); larger blocks use the FP64 kernel.
-template <int PREC, int MT, int NT>
+// One warp per C block (grid-stride over the work list). SIZES selects the
+// blocks a launch takes: 0 all (every MMA problem fits 16 x 16), 1 those that
+// fit 16 x 16, 2 the others (up to 32 x 32). Small blocks use 1 x 2 tiles with
+// prefetching; large ones 2 x 4 tiles without (register budget).
+template <int PREC, int SIZES>
 __global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOut C, DevMat Cin,
                                                        const void *__restrict__ a_left,
                                                        const void *__restrict__ b_right,
                                                        double alpha, double beta, DevWs ws,
-                                                       const DevStatus *st) {
+                                                       const DevStatus *st,
+                                                       const int32_t *__restrict__ items,
+                                                       const int64_t *__restrict__ seg) {
   if (st->overflow) return;
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int64_t nblk = st->nblk_c;
+  int64_t wb = 0, we = st->nblk_c;
+  if (seg) {
+    wb = seg[0];
+    we = seg[1];
+  }
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const bool exact_out = (alpha == 1.0 && beta == 0.0);
-  for (int64_t gb = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; gb < nblk;
-       gb += nwarp) {
+  for (int64_t w = wb + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); w < we;
+       w += nwarp) {
+    const int64_t gb = items ? items[w] : w;
     const int i = C.blk_row[gb], j = C.col_idx[gb];
     const int m = C.row_sizes[i], n = C.col_sizes[j];
-    // transpose when that needs fewer 16 x 8 tiles
     const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
     const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
     const bool tr = tiles_t < tiles_n;
     const int Mp = tr ? n : m, Np = tr ? m : n;
-    float acc[MT][NT][4];
-#pragma unroll
-    for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-      for (int nt = 0; nt < NT; nt++)
-#pragma unroll
-        for (int x = 0; x < 4; x++) acc[mt][nt][x] = 0.f;
-    const int64_t p0 = ws.prod_ptr[gb], p1 = ws.prod_ptr[gb + 1];
-    for (int64_t p = p0; p < p1; p++) {
-      const int2 pr = ws.prods[p];
-      const int s = A.col_sizes[A.col_idx[pr.x]];
-      const int64_t aoff = A.blk_off[pr.x], boff = B.blk_off[pr.y];
-      if (PREC == BSM_PREC_SPLIT_BF16X3) {
-        const uint16_t *Al = static_cast<const uint16_t *>(a_left) + 12 * aoff;
-        const uint16_t *Br = static_cast<const uint16_t *>(b_right) + 12 * boff;
-        const int sp = s + (s & 1);
-        const int aplane = (m + (m & 1)) * sp, bplane = sp * (n + (n & 1));
-        if (!tr)
-          bf16_block<MT, NT>(Al, Br, Mp, Np, s, aplane, bplane, acc);
-        else
-          bf16_block<MT, NT>(Br, Al, Mp, Np, s, bplane, aplane, acc);
-      } else {
-        const uint32_t *Al = static_cast<const uint32_t *>(a_left) + 2 * aoff;
-        const uint32_t *Br = static_cast<const uint32_t *>(b_right) + 2 * boff;
-        if (!tr)
-          tf32_block<MT, NT>(Al, Br, Mp, Np, s, m * s, s * n, acc);
-        else
-          tf32_block<MT, NT>(Br, Al, Mp, Np, s, s * n, m * s, acc);
-      }
+    const bool small = (Mp <= 16 && Np <= 16);
+    if (SIZES == 2) {
+      if (!small)
+        split_cblock<PREC, 2, 4, false>(A, B, C, Cin, a_left, b_right, alpha, beta, ws, gb, m, n,
+                                        tr, Mp, Np);
+    } else if (SIZES == 0 || small) {
+      split_cblock<PREC, 1, 2, true>(A, B, C, Cin, a_left, b_right, alpha, beta, ws, gb, m, n, tr,
+                                     Mp, Np);
     }
-    // epilogue: C_ij = beta * C_in_ij + alpha * S_ij in FP64 (exact copy when
-    // alpha = 1 and beta = 0)
-    const int cin = ws.c_cin[gb];
-    const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
-    double *out = C.vals + C.blk_off[gb];
-#pragma unroll
-    for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-      for (int nt = 0; nt < NT; nt++)
-#pragma unroll
-        for (int x = 0; x < 4; x++) {
-          const int rr = mt * 16 + g + ((x >> 1) << 3);
-          const int cc = nt * 8 + 2 * t + (x & 1);
-          if (rr < Mp && cc < Np) {
-            const int row = tr ? cc : rr, col = tr ? rr : cc;
-            const int64_t e = (int64_t)col * m + row;
-            double v = f32_to_f64_exact(acc[mt][nt][x]);
-            if (!exact_out) {
-              v = alpha * v;
-              if (cinv) v = fma(beta, cinv[e], v);
-            }
-            out[e] = v;
-          }
-        }
   }
 }
 
-cudaError_t launch_numeric_split(int precision, DevMat A, DevMat B, DevOut C, DevMat Cin,
-                                 const void *a_left, const void *b_right, double alpha,
-                                 double beta, DevWs ws, const DevStatus *st, int max_dim, int nsm,
-                                 cudaStream_t stream) {
-  const int grid = nsm * 8;
-  if (precision == BSM_PREC_SPLIT_BF16X3) {
-    if (max_dim <= 16)
-      k_numeric_split<BSM_PREC_SPLIT_BF16X3, 1, 2><<<grid, 128, 0, stream>>>(
-          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st);
-    else
-      k_numeric_split<BSM_PREC_SPLIT_BF16X3, 2, 4><<<grid, 128, 0, stream>>>(
-          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st);
-  } else {
-    if (max_dim <= 16)
-      k_numeric_split<BSM_PREC_SPLIT_TF32X2, 1, 2><<<grid, 128, 0, stream>>>(
-          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st);
-    else
-      k_numeric_split<BSM_PREC_SPLIT_TF32X2, 2, 4><<<grid, 128, 0, stream>>>(
-          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st);
-  }
+template <int PREC>
+static void launch_split_sizes(int sizes, int grid, cudaStream_t stream, DevMat A, DevMat B,
+                               DevOut C, DevMat Cin, const void *a_left, const void *b_right,
+                               double alpha, double beta, DevWs ws, const DevStatus *st,
+                               const int32_t *items, const int64_t *seg) {
+  if (sizes == 0)
+    k_numeric_split<PREC, 0><<<grid, 128, 0, stream>>>(A, B, C, Cin, a_left, b_right, alpha, beta,
+                                                       ws, st, items, seg);
+  else if (sizes == 1)
+    k_numeric_split<PREC, 1><<<grid, 128, 0, stream>>>(A, B, C, Cin, a_left, b_right, alpha, beta,
+                                                       ws, st, items, seg);
+  else
+    k_numeric_split<PREC, 2><<<grid, 128, 0, stream>>>(A, B, C, Cin, a_left, b_right, alpha, beta,
+                                                       ws, st, items, seg);
+}
+
+cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, DevOut C,
+                                 DevMat Cin, const void *a_left, const void *b_right, double alpha,
+                                 double beta, DevWs ws, const DevStatus *st, const int32_t *items,
+                                 const int64_t *seg, int grid, cudaStream_t stream) {
+  if (precision == BSM_PREC_SPLIT_BF16X3)
+    launch_split_sizes<BSM_PREC_SPLIT_BF16X3>(sizes, grid, stream, A, B, C, Cin, a_left, b_right,
+                                              alpha, beta, ws, st, items, seg);
+  else
+    launch_split_sizes<BSM_PREC_SPLIT_TF32X2>(sizes, grid, stream, A, B, C, Cin, a_left, b_right,
+                                              alpha, beta, ws, st, items, seg);
   return cudaGetLastError();
 }
 

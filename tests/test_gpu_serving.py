@@ -1,0 +1,80 @@
+"""The request loop (continuous batching) on the GPU: requests of different
+sizes submitted while others run give, each, the same result as the request
+run alone through bsm_multiply (bit for bit: the same kernels on the same data)
+and the oracle's pattern and values."""
+import numpy as np
+import pytest
+
+import synth
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def alone(bsm_lib, A, eps):
+    with bsm_lib.Context(0) as ctx:
+        dA = ctx.from_blocks(A)
+        dC = ctx.empty(A.row_sizes, A.col_sizes)
+        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, blocking=True)
+        r, c = dC.pattern()
+        return r, c, dC.values()
+
+
+def drain(srv, ids, limit=100000):
+    for _ in range(limit):
+        srv.progress()
+        if all(srv.poll(i)[0] >= 2 for i in ids):
+            return
+    raise AssertionError("requests did not finish")
+
+
+def test_alone_vs_mix(bsm_lib, oracle_mod):
+    eps = 1e-10
+    sizes = [8, 40, 16, 64, 24, 8, 32, 12]
+    systems = [synth.water(n, seed=1000 + r) for r, n in enumerate(sizes)]
+    with bsm_lib.Server(0, slots=3, hbm_budget=2 << 30) as srv:
+        ids = [srv.submit(systems[0], eps), srv.submit(systems[1], eps)]
+        srv.progress()  # the first two start; the rest arrive while they run
+        for A in systems[2:]:
+            ids.append(srv.submit(A, eps))
+            srv.progress()
+        drain(srv, ids)
+        info = srv.info()
+        assert info["completed"] == len(systems) and info["bytes_peak"] <= 2 << 30
+        results = [srv.take(i) for i in ids]
+    for A, (r, c, v) in zip(systems, results):
+        ra, ca, va = alone(bsm_lib, A, eps)
+        assert np.array_equal(r, ra) and np.array_equal(c, ca)
+        assert np.array_equal(v, va)  # same kernels, same data: identical
+        ref = oracle_mod.multiply(A, A, eps=eps)
+        assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+        assert H.rel_frobenius(v, ref.values) <= 1e-12
+
+
+def test_budget_admission_and_fifo(bsm_lib):
+    """A small budget forces requests to wait for memory: never more held than
+    the budget, every request completes, and a request larger than the whole
+    budget is refused at submission."""
+    eps = 1e-10
+    systems = [synth.water(24, seed=2000 + r) for r in range(4)]
+    # the footprint bound of one such request, as the server accounts it
+    with bsm_lib.Server(0, slots=1, hbm_budget=8 << 30) as srv:
+        i0 = srv.submit(systems[0], eps)
+        srv.progress()
+        F = srv.info()["bytes_in_use"]
+        drain(srv, [i0])
+        srv.take(i0)
+    budget = int(2.5 * F)  # room for two requests at a time
+    with bsm_lib.Server(0, slots=4, hbm_budget=budget) as srv:
+        ids = [srv.submit(A, eps) for A in systems]
+        srv.progress()
+        info = srv.info()
+        assert info["running"] <= 2 and info["queued"] >= 2  # memory, not lanes, limits
+        drain(srv, ids)
+        assert srv.info()["bytes_peak"] <= budget
+        with pytest.raises(bsm_lib.BsmError) as e:
+            srv.submit(synth.water(96, seed=1), eps)
+        assert e.value.name == "NOMEM"
+        for i in ids:
+            srv.take(i)
+        assert srv.info()["bytes_in_use"] == 0

@@ -18,7 +18,7 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 PRECS = {"bf16x3": 1, "tf32x2": 2}
 U_SPLIT = {"bf16x3": 3 * 2.0 ** -22, "tf32x2": 2.0 ** -19}
-REL_F = {"bf16x3": 2e-6, "tf32x2": 1e-5}  # stated relative Frobenius targets on water
+REL_F = {"bf16x3": 2e-6, "tf32x2": 1e-5}  # stated relative Frobenius bounds on water
 
 
 def gpu_mult(ctx, A, B, prec, alpha=1.0, beta=0.0, C=None, eps=0.0):
@@ -65,7 +65,8 @@ def test_split_water_bound(gpu_ctx, oracle_mod, prec):
     assert np.all(np.abs(v - ref.values) <= bound)
     rel = H.rel_frobenius(v, ref.values)
     assert rel <= REL_F[prec], rel
-    assert np.max(np.abs(v - ref.values)) <= 1e-4
+    # the largest error, relative to the largest element
+    assert np.max(np.abs(v - ref.values)) <= REL_F[prec] * np.max(np.abs(ref.values))
 
 
 @pytest.mark.parametrize("prec", sorted(PRECS))
