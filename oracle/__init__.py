@@ -111,6 +111,11 @@ def _load():
         ]
         lib.bsmo_norms.restype = ctypes.c_int
         lib.bsmo_norms.argtypes = [ctypes.POINTER(_Mat), ctypes.c_void_p]
+        lib.bsmo_post_filter.restype = ctypes.c_int
+        lib.bsmo_post_filter.argtypes = [ctypes.POINTER(_Mat), ctypes.c_double, ctypes.POINTER(_Res)]
+        lib.bsmo_add.restype = ctypes.c_int
+        lib.bsmo_add.argtypes = [ctypes.POINTER(_Mat), ctypes.POINTER(_Mat), ctypes.c_double,
+                                 ctypes.c_double, ctypes.POINTER(_Res)]
         lib.bsmo_max_threads.restype = ctypes.c_int
         lib.bsmo_max_threads.argtypes = []
         _lib = lib
@@ -230,3 +235,44 @@ def blocks(A, B, pairs, alpha: float = 1.0, beta: float = 0.0, C=None, eps: floa
     if rc:
         raise OracleError(rc)
     return present.astype(bool), [out[o:o + n].copy() for o, n in zip(offs, lens)]
+
+
+def _result(lib, res, pattern_only=False) -> Result:
+    try:
+        nb, nnz = int(res.nblk), int(res.nnz)
+        br = np.ctypeslib.as_array(res.blk_row, (nb,)).copy() if nb else np.zeros(0, np.int32)
+        bc = np.ctypeslib.as_array(res.blk_col, (nb,)).copy() if nb else np.zeros(0, np.int32)
+        bo = np.ctypeslib.as_array(res.blk_off, (nb,)).copy() if nb else np.zeros(0, np.int64)
+        vals = None
+        if not pattern_only:
+            vals = np.ctypeslib.as_array(res.values, (nnz,)).copy() if nnz else np.zeros(0)
+        return Result(br, bc, bo, vals, nnz, int(res.candidates), int(res.kept),
+                      int(res.dropped), float(res.flops))
+    finally:
+        lib.bsmo_free_result(ctypes.byref(res))
+
+
+def post_filter(M, eps: float) -> Result:
+    """Blocks of M whose canonical norm is not below eps (Sec. 1 and 2: the
+    filter applied after the multiplication), sorted by (row, col)."""
+    lib = _load()
+    h = _Held(M)
+    res = _Res()
+    rc = lib.bsmo_post_filter(ctypes.byref(h.s), float(eps), ctypes.byref(res))
+    if rc:
+        raise OracleError(rc)
+    return _result(lib, res)
+
+
+def add(alpha: float, A, beta: float = 0.0, C=None) -> Result:
+    """C = beta*C_in + alpha*A on the union of the patterns (Algorithm 2's
+    accumulation of partial C panels); beta == 0 ignores C_in."""
+    lib = _load()
+    ha = _Held(A)
+    hc = _Held(C) if C is not None else None
+    res = _Res()
+    rc = lib.bsmo_add(ctypes.byref(ha.s), ctypes.byref(hc.s) if hc else None, float(alpha),
+                      float(beta), ctypes.byref(res))
+    if rc:
+        raise OracleError(rc)
+    return _result(lib, res)

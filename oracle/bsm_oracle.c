@@ -579,3 +579,129 @@ int bsmo_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Post-multiplication filter (Sec. 1: filtering after each multiply;  */
+/* Sec. 2: blocks below the threshold are removed after the multiply). */
+/* A block of M is dropped iff its canonical norm is below eps (a tie  */
+/* and NaN are kept, eps <= 0 drops nothing). The kept blocks keep     */
+/* their values; the result is sorted by (row, col).                   */
+/* ------------------------------------------------------------------ */
+int bsmo_post_filter(const bsmo_matrix *M, double eps, bsmo_result *res) {
+  if (!M || !res) return BSMO_ERR_INVALID_ARG;
+  memset(res, 0, sizeof(*res));
+  rowview v;
+  int err = rowview_build(M, 1, &v);
+  if (err != BSMO_OK) return err;
+  int64_t nb = 0, nnz = 0;
+  for (int64_t p = 0; p < M->nblk; p++) {
+    int64_t b = v.order[p];
+    if (!(v.norm[b] < eps)) {
+      nb++;
+      nnz += (int64_t)M->row_sizes[M->blk_row[b]] * M->col_sizes[M->blk_col[b]];
+    }
+  }
+  res->blk_row = (int32_t *)malloc(((size_t)nb + 1) * sizeof(int32_t));
+  res->blk_col = (int32_t *)malloc(((size_t)nb + 1) * sizeof(int32_t));
+  res->blk_off = (int64_t *)malloc(((size_t)nb + 1) * sizeof(int64_t));
+  res->values = (double *)malloc(((size_t)nnz + 1) * sizeof(double));
+  if (!res->blk_row || !res->blk_col || !res->blk_off || !res->values) {
+    rowview_free(&v);
+    bsmo_free_result(res);
+    return BSMO_ERR_NOMEM;
+  }
+  int64_t q = 0, o = 0;
+  for (int64_t p = 0; p < M->nblk; p++) {
+    int64_t b = v.order[p];
+    if (v.norm[b] < eps) continue;
+    int64_t len = (int64_t)M->row_sizes[M->blk_row[b]] * M->col_sizes[M->blk_col[b]];
+    res->blk_row[q] = M->blk_row[b];
+    res->blk_col[q] = M->blk_col[b];
+    res->blk_off[q] = o;
+    memcpy(res->values + o, M->values + v.off[b], (size_t)len * sizeof(double));
+    o += len;
+    q++;
+  }
+  res->nblk = nb;
+  res->nnz = nnz;
+  rowview_free(&v);
+  return BSMO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Block-sparse accumulation C = beta*C_in + alpha*A (Algorithm 2: the */
+/* partial C panels of the last ticks are summed into the final one).  */
+/* Pattern: A's blocks, plus C_in's when beta != 0 (beta == 0 ignores  */
+/* C_in, as for the multiply).                                         */
+/* ------------------------------------------------------------------ */
+int bsmo_add(const bsmo_matrix *A, const bsmo_matrix *Cin, double alpha, double beta,
+             bsmo_result *res) {
+  if (!A || !res) return BSMO_ERR_INVALID_ARG;
+  memset(res, 0, sizeof(*res));
+  const int use_cin = (Cin != NULL) && (beta != 0.0);
+  rowview a, c;
+  memset(&c, 0, sizeof(c));
+  int err = rowview_build(A, 0, &a);
+  if (err != BSMO_OK) return err;
+  if (use_cin && (err = rowview_build(Cin, 0, &c)) != BSMO_OK) {
+    rowview_free(&a);
+    return err;
+  }
+  if (use_cin) {
+    int bad = Cin->nbr != A->nbr || Cin->nbc != A->nbc;
+    for (int32_t i = 0; !bad && i < A->nbr; i++) bad = Cin->row_sizes[i] != A->row_sizes[i];
+    for (int32_t j = 0; !bad && j < A->nbc; j++) bad = Cin->col_sizes[j] != A->col_sizes[j];
+    if (bad) {
+      rowview_free(&a);
+      rowview_free(&c);
+      return BSMO_ERR_DIM_MISMATCH;
+    }
+  }
+  /* upper bounds, then the merge of the two sorted rows */
+  int64_t cap_b = A->nblk + (use_cin ? Cin->nblk : 0);
+  int64_t cap_v = 0;
+  for (int64_t b = 0; b < A->nblk; b++)
+    cap_v += (int64_t)A->row_sizes[A->blk_row[b]] * A->col_sizes[A->blk_col[b]];
+  if (use_cin)
+    for (int64_t b = 0; b < Cin->nblk; b++)
+      cap_v += (int64_t)Cin->row_sizes[Cin->blk_row[b]] * Cin->col_sizes[Cin->blk_col[b]];
+  res->blk_row = (int32_t *)malloc(((size_t)cap_b + 1) * sizeof(int32_t));
+  res->blk_col = (int32_t *)malloc(((size_t)cap_b + 1) * sizeof(int32_t));
+  res->blk_off = (int64_t *)malloc(((size_t)cap_b + 1) * sizeof(int64_t));
+  res->values = (double *)malloc(((size_t)cap_v + 1) * sizeof(double));
+  if (!res->blk_row || !res->blk_col || !res->blk_off || !res->values) {
+    rowview_free(&a);
+    rowview_free(&c);
+    bsmo_free_result(res);
+    return BSMO_ERR_NOMEM;
+  }
+  int64_t q = 0, o = 0;
+  for (int32_t i = 0; i < A->nbr; i++) {
+    int64_t pa = a.row_start[i], ea = a.row_start[i + 1];
+    int64_t pc = use_cin ? c.row_start[i] : 0, ec = use_cin ? c.row_start[i + 1] : 0;
+    while (pa < ea || pc < ec) {
+      int32_t ja = pa < ea ? A->blk_col[a.order[pa]] : INT32_MAX;
+      int32_t jc = pc < ec ? Cin->blk_col[c.order[pc]] : INT32_MAX;
+      int32_t j = ja < jc ? ja : jc;
+      int64_t len = (int64_t)A->row_sizes[i] * A->col_sizes[j];
+      const double *va = (ja == j) ? A->values + a.off[a.order[pa]] : NULL;
+      const double *vc = (jc == j) ? Cin->values + c.off[c.order[pc]] : NULL;
+      for (int64_t e = 0; e < len; e++) {
+        double base = vc ? beta * vc[e] : 0.0;
+        res->values[o + e] = va ? base + alpha * va[e] : base;
+      }
+      res->blk_row[q] = i;
+      res->blk_col[q] = j;
+      res->blk_off[q] = o;
+      o += len;
+      q++;
+      if (ja == j) pa++;
+      if (jc == j) pc++;
+    }
+  }
+  res->nblk = q;
+  res->nnz = o;
+  rowview_free(&a);
+  rowview_free(&c);
+  return BSMO_OK;
+}
