@@ -152,6 +152,19 @@ int bsm_mat_get_pattern(bsm_mat m, int64_t cap, int32_t *blk_row, int32_t *blk_c
  * column-major, into a host array of capacity cap (>= nnz). Synchronises. */
 int bsm_mat_get_values(bsm_mat m, int64_t cap, double *values);
 
+/* Post-multiplication filter (Sec. 1: filtering also after each
+ * multiplication; Sec. 2: blocks below the threshold are removed after the
+ * multiplication): drop every block of m whose canonical norm is below eps
+ * (a tie and NaN are kept; eps <= 0 drops nothing). Kept blocks keep their
+ * values. Blocking. Errors: INVALID_ARG, NOMEM, CUDA. */
+int bsm_mat_filter(bsm_mat m, double eps);
+
+/* Block-sparse accumulation C = beta*C + alpha*A (Algorithm 2: the partial C
+ * panels of the last ticks are summed into the final panel). A and C have the
+ * same block sizes; the result pattern is A's plus, when beta != 0, C's.
+ * Blocking. Errors: INVALID_ARG, DIM_MISMATCH, ALIAS (A == C), NOMEM, CUDA. */
+int bsm_mat_add(bsm_ctx ctx, double alpha, bsm_mat A, double beta, bsm_mat C);
+
 /* Device-time profile of the multiplies of a context: CUDA events recorded
  * on the launch stream at the phase boundaries of every multiply (block norms
  * | symbolic count, scan and fill | numeric block products). */

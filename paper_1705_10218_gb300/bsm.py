@@ -112,6 +112,8 @@ _SIGS = {
     "bsm_mat_get_values": (ctypes.c_int, [_P, _I64, _P]),
     "bsm_sync": (ctypes.c_int, [_P]),
     "bsm_ctx_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "bsm_mat_filter": (ctypes.c_int, [_P, _D]),
+    "bsm_mat_add": (ctypes.c_int, [_P, _D, _P, _D, _P]),
     "bsm_ctx_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(_Profile)]),
     "bsm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "bsm_last_cuda_error": (ctypes.c_char_p, []),
@@ -205,6 +207,10 @@ class Context:
     def sync(self):
         _check(lib().bsm_sync(self._h), "bsm_sync")
 
+    def add(self, alpha, A: "Matrix", beta, C: "Matrix"):
+        """C = beta*C + alpha*A on the union of the patterns."""
+        _check(lib().bsm_mat_add(self._h, float(alpha), A._h, float(beta), C._h), "bsm_mat_add")
+
     def profile(self, enable: bool = True):
         _check(lib().bsm_ctx_profile(self._h, int(bool(enable))), "bsm_ctx_profile")
 
@@ -254,6 +260,10 @@ class Matrix:
             raise BsmError(-1, "bsm_mat_get_values")
         _check(lib().bsm_mat_get_values(self._h, out.size, _vp(out)), "bsm_mat_get_values")
         return out[:nz]
+
+    def filter(self, eps: float):
+        """Drop the blocks whose canonical norm is below eps."""
+        _check(lib().bsm_mat_filter(self._h, float(eps)), "bsm_mat_filter")
 
     def destroy(self):
         if self._h:

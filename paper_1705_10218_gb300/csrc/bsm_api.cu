@@ -71,6 +71,7 @@ struct Buf {
   int32_t *blk_row = nullptr;  // [cap_blk]
   int64_t *blk_off = nullptr;  // [cap_blk]
   double *norms = nullptr;     // [cap_blk]
+  float *normsf = nullptr;     // [cap_blk] FP32 copies for the filter's fast test
   double *vals = nullptr;      // [cap_nnz]
   int64_t *hdr = nullptr;      // {nblk, nnz}
   int64_t cap_blk = -1, cap_nnz = -1;  // -1: never sized
@@ -81,6 +82,7 @@ struct Buf {
     dev_free(blk_row);
     dev_free(blk_off);
     dev_free(norms);
+    dev_free(normsf);
     dev_free(vals);
     dev_free(hdr);
     cap_blk = cap_nnz = -1;
@@ -258,10 +260,12 @@ static int buf_grow(bsm_mat M, Buf &b, int64_t nblk, int64_t nnz, bool exact) {
     dev_free(b.blk_row);
     dev_free(b.blk_off);
     dev_free(b.norms);
+    dev_free(b.normsf);
     const int64_t n = exact ? nblk : nblk + nblk / 8 + 64;
     int rc;
     if ((rc = dev_alloc(&b.col_idx, n)) || (rc = dev_alloc(&b.blk_row, n)) ||
-        (rc = dev_alloc(&b.blk_off, n)) || (rc = dev_alloc(&b.norms, n))) {
+        (rc = dev_alloc(&b.blk_off, n)) || (rc = dev_alloc(&b.norms, n)) ||
+        (rc = dev_alloc(&b.normsf, n))) {
       b.cap_blk = -1;
       return rc;
     }
@@ -293,6 +297,7 @@ static DevMat dev_view(bsm_mat M) {
   v.blk_off = M->front.blk_off;
   v.vals = M->front.vals;
   v.norms = M->front.norms;
+  v.normsf = M->front.normsf;
   v.hdr = M->front.hdr;
   return v;
 }
@@ -322,7 +327,8 @@ static int resolve(bsm_mat M, bsm_stats *timed = nullptr);
 static int enqueue_norms(bsm_ctx ctx, bsm_mat M, cudaStream_t s) {
   const int grid = ctx->nsm * 8;
   CK(launch_block_norms(M->row_sizes, M->col_sizes, M->front.blk_row, M->front.col_idx,
-                        M->front.blk_off, M->front.vals, M->front.hdr, M->front.norms, grid, s));
+                        M->front.blk_off, M->front.vals, M->front.hdr, M->front.norms,
+                        M->front.normsf, grid, s));
   return BSM_OK;
 }
 
@@ -472,18 +478,19 @@ static int launch_numeric(Launch &L, int variant, const int32_t *items, const in
                           int max_m, int max_n) {
   bsm_ctx ctx = L.ctx;
   if (L.split) {
+    const int smax = L.A->max_col;
     if (max_m <= 16 && max_n <= 16) {
       CK(launch_numeric_split(L.o.precision, 0, L.dA, L.dB, L.out, L.dC, L.A->split_left,
                               L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
-                              ctx->nsm * 4, L.s));
+                              smax, ctx->nsm, L.s));
     } else {
       CK(launch_numeric_split(L.o.precision, 1, L.dA, L.dB, L.out, L.dC, L.A->split_left,
                               L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
-                              ctx->nsm * 4, L.s));
+                              smax, ctx->nsm, L.s));
       ctx->launches++;
       CK(launch_numeric_split(L.o.precision, 2, L.dA, L.dB, L.out, L.dC, L.A->split_left,
                               L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
-                              ctx->nsm * 2, L.s));
+                              smax, ctx->nsm, L.s));
     }
   } else
     CK(launch_numeric_fp64(variant, L.dA, L.dB, L.out, L.dC, L.alpha, L.beta, L.ws,
@@ -584,6 +591,7 @@ static void graph_key(const Launch &L, std::vector<uint64_t> &k) {
     const Buf *bs[2] = {&M->front, &M->back};
     for (const Buf *b : bs) {
       put(b->row_ptr), put(b->col_idx), put(b->blk_row), put(b->blk_off), put(b->norms);
+      put(b->normsf);
       put(b->vals), put(b->hdr), num(b->cap_blk), num(b->cap_nnz);
     }
     put(M->split_left), put(M->split_right), put(M->row_sizes), put(M->col_sizes);
@@ -801,6 +809,7 @@ int bsm_ctx_create(int device, bsm_ctx *out) {
   }
   if (rc == BSM_OK) {
     if ((e = numeric_fp64_init()) != cudaSuccess) rc = cuda_fail(e, "numeric_fp64_init");
+    else if ((e = numeric_split_init()) != cudaSuccess) rc = cuda_fail(e, "numeric_split_init");
   }
   if (rc == BSM_OK) {
     rc = dev_alloc(&ctx->cls_counts, kMaxClasses);
@@ -1112,6 +1121,71 @@ int bsm_mat_get_values(bsm_mat m, int64_t cap, double *values) {
   cudaStream_t s = m->ctx->stream;
   CK(cudaMemcpyAsync(values, m->front.vals, (size_t)m->nnz * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return BSM_OK;
+}
+
+int bsm_mat_filter(bsm_mat M, double eps) {
+  if (!M) return BSM_ERR_INVALID_ARG;
+  bsm_ctx ctx = M->ctx;
+  int rc = ctx_set_device(ctx);
+  if (rc || (rc = resolve(M))) return rc;
+  cudaStream_t s = ctx->stream;
+  if ((rc = ws_rows(ctx, M->nbr)) || (rc = buf_grow(M, M->back, M->nblk, M->nnz, false)))
+    return rc;
+  if ((rc = enqueue_norms(ctx, M, s))) return rc;
+  DevMat dM = dev_view(M);
+  DevWs ws = ctx->ws;
+  DevOut out = dev_out(M, M->back);
+  CK(launch_filter_count(dM, eps, ws, ctx->nsm, s));
+  CK(launch_symbolic_scan(M->nbr, ws, out, ctx->d_status, s));
+  CK(launch_filter_fill(dM, eps, ws, out, ctx->d_status, ctx->nsm, s));
+  ctx->launches += 4;
+  DevStatus h{};
+  CK(cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h.overflow) return BSM_ERR_NOMEM;  // cannot happen: the back buffer holds all blocks
+  std::swap(M->front, M->back);
+  M->nblk = h.nblk_c;
+  M->nnz = h.nnz_c;
+  return BSM_OK;
+}
+
+int bsm_mat_add(bsm_ctx ctx, double alpha, bsm_mat A, double beta, bsm_mat C) {
+  if (!ctx || !A || !C || A->ctx != ctx || C->ctx != ctx) return BSM_ERR_INVALID_ARG;
+  if (A == C) return BSM_ERR_ALIAS;
+  if (A->h_row_sizes != C->h_row_sizes || A->h_col_sizes != C->h_col_sizes)
+    return BSM_ERR_DIM_MISMATCH;
+  int rc = ctx_set_device(ctx);
+  if (rc || (rc = resolve(A))) return rc;
+  const bool use_cin = beta != 0.0;
+  if (use_cin) {
+    if ((rc = resolve(C))) return rc;
+  } else {
+    C->pend.active = false;
+  }
+  const int64_t nb = A->nblk + (use_cin ? C->nblk : 0);
+  const int64_t nz = A->nnz + (use_cin ? C->nnz : 0);
+  cudaStream_t s = ctx->stream;
+  if ((rc = ws_rows(ctx, A->nbr)) || (rc = buf_grow(C, C->back, nb, nz, false)) ||
+      (rc = ws_grow(ctx, nb, 0)))
+    return rc;
+  DevMat dA = dev_view(A), dC = dev_view(C);
+  DevWs ws = ctx->ws;
+  DevOut out = dev_out(C, C->back);
+  CK(launch_add(0, dA, dC, use_cin, alpha, beta, ws, out, ctx->d_status, ctx->nsm, s));
+  CK(launch_symbolic_scan(A->nbr, ws, out, ctx->d_status, s));
+  CK(launch_add(1, dA, dC, use_cin, alpha, beta, ws, out, ctx->d_status, ctx->nsm, s));
+  CK(launch_add(2, dA, dC, use_cin, alpha, beta, ws, out, ctx->d_status, ctx->nsm, s));
+  ctx->launches += 4;
+  DevStatus h{};
+  CK(cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h.overflow) return BSM_ERR_NOMEM;
+  std::swap(C->front, C->back);
+  C->nblk = h.nblk_c;
+  C->nnz = h.nnz_c;
+  C->hint_blk = std::max(C->hint_blk, h.nblk_c);
+  C->hint_nnz = std::max(C->hint_nnz, h.nnz_c);
   return BSM_OK;
 }
 

@@ -28,6 +28,7 @@ struct DevMat {
   const int64_t *blk_off;    // [nblk]
   const double *vals;        // [nnz]
   const double *norms;       // [nblk] canonical block norms
+  const float *normsf;       // [nblk] FP32 copies for the filter's fast test (NaN: none)
   const int64_t *hdr;        // device header {nblk, nnz}
 };
 
@@ -78,7 +79,7 @@ struct DevStatus {
 cudaError_t launch_block_norms(const int32_t *row_sizes, const int32_t *col_sizes,
                                const int32_t *blk_row, const int32_t *col_idx,
                                const int64_t *blk_off, const double *vals, const int64_t *hdr,
-                               double *norms, int grid, cudaStream_t stream);
+                               double *norms, float *normsf, int grid, cudaStream_t stream);
 
 cudaError_t launch_symbolic_count(DevMat A, DevMat B, DevMat Cin, int use_cin, double eps,
                                   DevWs ws, int grid, cudaStream_t stream);
@@ -120,15 +121,31 @@ cudaError_t launch_split(int precision, const int32_t *row_sizes, const int32_t 
 
 // sizes: 0 = every block's MMA problem fits 16 x 16 (one launch covers all);
 // 1 = only the blocks that fit 16 x 16; 2 = only the larger ones (<= 32 x 32).
+// smax: the largest k (column size of A) the launch can meet, at most 32.
 cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, DevOut C,
                                  DevMat Cin, const void *a_left, const void *b_right, double alpha,
                                  double beta, DevWs ws, const DevStatus *st, const int32_t *items,
-                                 const int64_t *seg, int grid, cudaStream_t stream);
+                                 const int64_t *seg, int smax, int nsm, cudaStream_t stream);
+// Post filter and block-sparse add (k_extra.cu).
+cudaError_t launch_filter_count(DevMat M, double eps, DevWs ws, int nsm, cudaStream_t stream);
+cudaError_t launch_filter_fill(DevMat M, double eps, DevWs ws, DevOut O, const DevStatus *st,
+                               int nsm, cudaStream_t stream);
+// stage 0: per-row union counts; 1: union pattern and sources; 2: values
+cudaError_t launch_add(int stage, DevMat A, DevMat Cin, int use_cin, double alpha, double beta,
+                       DevWs ws, DevOut O, const DevStatus *st, int nsm, cudaStream_t stream);
 
-// Bytes of slice storage per FP64 value of an operand (bf16x3: padded planes
-// at 12 halfwords per value; tf32x2: 2 words per value).
+// Per-device kernel attributes of the split kernels (outside capture).
+cudaError_t numeric_split_init();
+
+// Slice storage of an operand block b starts at a fixed multiple of its FP64
+// offset blk_off[b], 16-byte aligned so whole blocks can be copied with
+// 16-byte asynchronous copies: BF16x3 at halfword 16*blk_off (32 bytes per
+// value; the 3 padded planes take at most 24), TF32x2 at word 4*blk_off (16
+// bytes per value; the 2 planes take 8).
+constexpr int64_t kBf16HalfwordsPerValue = 16;
+constexpr int64_t kTf32WordsPerValue = 4;
 inline int64_t split_bytes_per_value(int precision) {
-  return precision == BSM_PREC_SPLIT_BF16X3 ? 24 : 8;
+  return precision == BSM_PREC_SPLIT_BF16X3 ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue;
 }
 
 }  // namespace bsm

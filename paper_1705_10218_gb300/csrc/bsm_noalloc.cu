@@ -127,9 +127,11 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
   Carve cv{scratch};
   DevStatus *st = cv.take<DevStatus>(1);
   double *norms_a = cv.take<double>(A->nblk);
+  float *normsf_a = cv.take<float>(A->nblk);
   int32_t *brow_a = cv.take<int32_t>(A->nblk);
   int64_t *hdr_a = cv.take<int64_t>(2);
   double *norms_b = same ? norms_a : cv.take<double>(B->nblk);
+  float *normsf_b = same ? normsf_a : cv.take<float>(B->nblk);
   int32_t *brow_b = same ? brow_a : cv.take<int32_t>(B->nblk);
   int64_t *hdr_b = same ? hdr_a : cv.take<int64_t>(2);
   const int64_t rows = (int64_t)A->nbr + 1;
@@ -163,7 +165,7 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
   if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_cuda_fail(e);
 
   auto view = [](const bsm_dev_csr *m, const int32_t *brow, const double *norms,
-                 const int64_t *hdr) {
+                 const float *normsf, const int64_t *hdr) {
     DevMat v{};
     v.nbr = m->nbr;
     v.nbc = m->nbc;
@@ -175,11 +177,12 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
     v.blk_off = m->blk_off;
     v.vals = m->values;
     v.norms = norms;
+    v.normsf = normsf;
     v.hdr = hdr;
     return v;
   };
-  DevMat dA = view(A, brow_a, norms_a, hdr_a);
-  DevMat dB = view(B, brow_b, norms_b, hdr_b);
+  DevMat dA = view(A, brow_a, norms_a, normsf_a, hdr_a);
+  DevMat dB = view(B, brow_b, norms_b, normsf_b, hdr_b);
   DevMat none{};
   DevOut out{};
   out.nbr = A->nbr;
@@ -196,10 +199,11 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
   out.cap_nnz = C->cap_nnz;
 
   if ((e = launch_block_norms(A->row_sizes, A->col_sizes, brow_a, A->col_idx, A->blk_off,
-                              A->values, hdr_a, norms_a, nsm * 8, s)) != cudaSuccess)
+                              A->values, hdr_a, norms_a, normsf_a, nsm * 8, s)) != cudaSuccess)
     return noalloc_cuda_fail(e);
   if (!same && (e = launch_block_norms(B->row_sizes, B->col_sizes, brow_b, B->col_idx,
-                                       B->blk_off, B->values, hdr_b, norms_b, nsm * 8, s)) !=
+                                       B->blk_off, B->values, hdr_b, norms_b, normsf_b, nsm * 8,
+                                       s)) !=
                    cudaSuccess)
     return noalloc_cuda_fail(e);
   if ((e = launch_symbolic_count(dA, dB, none, 0, eps, ws, nsm * 6, s)) != cudaSuccess)

@@ -19,12 +19,12 @@
 // the slices live at a fixed multiple of the FP64 offset, so no extra offset
 // table is needed:
 //   BF16: 3 planes of rp x cp elements (rp, cp = r, c rounded up to even;
-//         padding is zero) at 16-bit index 12*blk_off[b] (rp*cp <= 4*r*c);
+//         padding is zero) at 16-bit index 16*blk_off[b] (rp*cp <= 4*r*c);
 //         "left" layout (the block as a left operand) is row-major with
 //         stride cp, "right" layout (as a right operand) column-major with
 //         stride rp, so the two k-adjacent values of an MMA fragment register
 //         are one aligned 32-bit word.
-//   TF32: 2 planes of r x c 32-bit elements at 32-bit index 2*blk_off[b];
+//   TF32: 2 planes of r x c 32-bit elements at 32-bit index 4*blk_off[b];
 //         left row-major, right column-major.
 #include <cstdint>
 
@@ -106,7 +106,7 @@ __global__ void k_split_bf16x3(const int32_t *__restrict__ row_sizes,
     const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
     const int rp = r + (r & 1), cp = c + (c & 1);
     const int plane = rp * cp;
-    const int64_t base = 12 * blk_off[b];
+    const int64_t base = kBf16HalfwordsPerValue * blk_off[b];
     const double *x = vals + blk_off[b];
     for (int e = lane; e < plane; e += 32) {
       // position (row xr, col yc) in the padded rp x cp block, column-major order
@@ -136,7 +136,7 @@ __global__ void k_split_tf32x2(const int32_t *__restrict__ row_sizes,
   for (int64_t b = w0; b < nblk; b += nw) {
     const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
     const int plane = r * c;
-    const int64_t base = 2 * blk_off[b];
+    const int64_t base = kTf32WordsPerValue * blk_off[b];
     const double *x = vals + blk_off[b];
     for (int e = lane; e < plane; e += 32) {
       const int xr = e % r, yc = e / r;
@@ -371,8 +371,8 @@ __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, c
   auto operands = [&](int64_t aoff, int64_t boff, int s, const void *&L, const void *&R,
                       int &lplane, int &rplane) {
     if (BF) {
-      const uint16_t *Al = static_cast<const uint16_t *>(a_left) + 12 * aoff;
-      const uint16_t *Br = static_cast<const uint16_t *>(b_right) + 12 * boff;
+      const uint16_t *Al = static_cast<const uint16_t *>(a_left) + kBf16HalfwordsPerValue * aoff;
+      const uint16_t *Br = static_cast<const uint16_t *>(b_right) + kBf16HalfwordsPerValue * boff;
       const int sp = s + (s & 1);
       const int ap = mp2 * sp, bpl = sp * np2;
       L = tr ? (const void *)Br : (const void *)Al;
@@ -380,8 +380,8 @@ __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, c
       lplane = tr ? bpl : ap;
       rplane = tr ? ap : bpl;
     } else {
-      const uint32_t *Al = static_cast<const uint32_t *>(a_left) + 2 * aoff;
-      const uint32_t *Br = static_cast<const uint32_t *>(b_right) + 2 * boff;
+      const uint32_t *Al = static_cast<const uint32_t *>(a_left) + kTf32WordsPerValue * aoff;
+      const uint32_t *Br = static_cast<const uint32_t *>(b_right) + kTf32WordsPerValue * boff;
       L = tr ? (const void *)Br : (const void *)Al;
       R = tr ? (const void *)Al : (const void *)Br;
       lplane = tr ? s * n : m * s;
@@ -481,6 +481,234 @@ __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, c
       }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined kernel for blocks whose MMA problem fits 16 x 16 (the water and
+// small-block case). Each warp streams the slices of its C block's products
+// through a ring of kStages shared-memory slots with 16-byte asynchronous
+// copies (cp.async), kStages - 1 products ahead of the tensor-core work, so the
+// L2 latency of a product's operands is hidden behind the products before it.
+// The (A offset, B offset, k) of the products are read 32 at a time into a
+// per-warp table in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 4;
+constexpr int kPipeWarps = 4;
+constexpr int kMetaEntries = 64;
+constexpr int kMetaBytes = kMetaEntries * (8 + 8 + 4);
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gptr) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gptr) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(saddr));
+  return v;
+}
+
+// Bytes of one operand slot: BF16 3 planes of at most 16 x sp halfwords, TF32
+// 2 planes of at most 16 x s words (multiples of 16 bytes).
+__host__ __device__ __forceinline__ int pipe_operand_bytes(int precision, int smax) {
+  return precision == BSM_PREC_SPLIT_BF16X3 ? 96 * (smax + (smax & 1)) : 128 * smax;
+}
+__host__ __device__ __forceinline__ int pipe_warp_bytes(int precision, int smax) {
+  return kStages * 2 * pipe_operand_bytes(precision, smax) + kMetaBytes;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kPipeWarps * 32)
+    k_numeric_split_pipe(DevMat A, DevMat B, DevOut C, DevMat Cin, const void *__restrict__ a_left,
+                         const void *__restrict__ b_right, double alpha, double beta, DevWs ws,
+                         const DevStatus *st, const int32_t *__restrict__ items,
+                         const int64_t *__restrict__ seg, int smax, int only_small) {
+  if (st->overflow) return;
+  constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
+  constexpr int KSTEP = BF ? 16 : 8;
+  extern __shared__ __align__(16) unsigned char smem_pipe[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int opb = pipe_operand_bytes(PREC, smax);
+  unsigned char *wbase = smem_pipe + warp * pipe_warp_bytes(PREC, smax);
+  int64_t *meta_a = reinterpret_cast<int64_t *>(wbase + kStages * 2 * opb);
+  int64_t *meta_b = meta_a + kMetaEntries;
+  int *meta_s = reinterpret_cast<int *>(meta_b + kMetaEntries);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(wbase);
+
+  int64_t wb = 0, we = st->nblk_c;
+  if (seg) {
+    wb = seg[0];
+    we = seg[1];
+  }
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool plain = (alpha == 1.0 && beta == 0.0);
+  for (int64_t w = wb + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); w < we;
+       w += nwarp) {
+    const int64_t gb = items ? items[w] : w;
+    const int i = C.blk_row[gb], j = C.col_idx[gb];
+    const int m = C.row_sizes[i], n = C.col_sizes[j];
+    const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
+    const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
+    const bool tr = tiles_t < tiles_n;
+    const int Mp = tr ? n : m, Np = tr ? m : n;
+    if (only_small && !(Mp <= 16 && Np <= 16)) continue;
+    const int mp2 = m + (m & 1), np2 = n + (n & 1);
+    const int64_t p0 = ws.prod_ptr[gb];
+    const int np = (int)(ws.prod_ptr[gb + 1] - p0);
+
+    float hi[2][4], lo[2][4], acc[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+      for (int x = 0; x < 4; x++) hi[nt][x] = lo[nt][x] = acc[nt][x] = 0.f;
+
+    // copies of product q into slot q % kStages; always commits one group
+    auto issue = [&](int q) {
+      if (q < np) {
+        if ((q & 31) == 0) {  // the next 32 products' offsets and k
+          const int qq = q + lane;
+          if (qq < np) {
+            const int2 pr = ws.prods[p0 + qq];
+            meta_a[qq & (kMetaEntries - 1)] = A.blk_off[pr.x];
+            meta_b[qq & (kMetaEntries - 1)] = B.blk_off[pr.y];
+            meta_s[qq & (kMetaEntries - 1)] = A.col_sizes[A.col_idx[pr.x]];
+          }
+          __syncwarp();
+        }
+        const int s = meta_s[q & (kMetaEntries - 1)];
+        const int sp = s + (s & 1);
+        const unsigned char *srcA = static_cast<const unsigned char *>(a_left) +
+                                    (BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue) *
+                                        meta_a[q & (kMetaEntries - 1)];
+        const unsigned char *srcB = static_cast<const unsigned char *>(b_right) +
+                                    (BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue) *
+                                        meta_b[q & (kMetaEntries - 1)];
+        const int bytesA = BF ? 6 * mp2 * sp : 8 * m * s;
+        const int bytesB = BF ? 6 * sp * np2 : 8 * s * n;
+        const uint32_t dst = sbase + (uint32_t)((q % kStages) * 2 * opb);
+        for (int c = lane; c < (bytesA + 15) >> 4; c += 32) cp_async16(dst + 16 * c, srcA + 16 * c);
+        for (int c = lane; c < (bytesB + 15) >> 4; c += 32)
+          cp_async16(dst + opb + 16 * c, srcB + 16 * c);
+      }
+      cp_async_commit();
+    };
+
+#pragma unroll
+    for (int q = 0; q < kStages - 1; q++) issue(q);
+    for (int q = 0; q < np; q++) {
+      cp_async_wait<kStages - 2>();
+      __syncwarp();
+      issue(q + kStages - 1);  // into the slot consumed by the previous product
+      const int s = meta_s[q & (kMetaEntries - 1)];
+      const int sp = s + (s & 1);
+      const uint32_t sA = sbase + (uint32_t)((q % kStages) * 2 * opb), sB = sA + opb;
+      // L (M' x s, row-major) and R (s x N', column-major) in the slot
+      const uint32_t sL = tr ? sB : sA, sR = tr ? sA : sB;
+      if (BF) {
+        const int lplane = 2 * (tr ? sp * np2 : mp2 * sp), rplane = 2 * (tr ? mp2 * sp : sp * np2);
+        for (int kk = 0; kk < s; kk += KSTEP) {
+          const bool k8 = (s - kk) <= 8;
+          const int k0 = kk + 2 * t, k1 = k0 + 8;
+          const int r0 = g, r1 = g + 8;
+          uint32_t a[3][4], b[3][2][2];
+#pragma unroll
+          for (int q3 = 0; q3 < 3; q3++) {
+            const uint32_t P = sL + q3 * lplane, Q = sR + q3 * rplane;
+            a[q3][0] = (r0 < Mp && k0 < sp) ? lds32(P + 2 * (r0 * sp + k0)) : 0u;
+            a[q3][1] = (r1 < Mp && k0 < sp) ? lds32(P + 2 * (r1 * sp + k0)) : 0u;
+            a[q3][2] = (!k8 && r0 < Mp && k1 < sp) ? lds32(P + 2 * (r0 * sp + k1)) : 0u;
+            a[q3][3] = (!k8 && r1 < Mp && k1 < sp) ? lds32(P + 2 * (r1 * sp + k1)) : 0u;
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+              const int c = nt * 8 + g;
+              b[q3][nt][0] = (c < Np && k0 < sp) ? lds32(Q + 2 * (c * sp + k0)) : 0u;
+              b[q3][nt][1] = (!k8 && c < Np && k1 < sp) ? lds32(Q + 2 * (c * sp + k1)) : 0u;
+            }
+          }
+          constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
+          constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+          for (int nt = 0; nt < 2; nt++) {
+            if (nt * 8 >= Np) continue;
+#pragma unroll
+            for (int pq = 0; pq < 6; pq++) {
+              if (k8)
+                mma_bf16_k8(acc[nt], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][nt][0]);
+              else
+                mma_bf16_k16(acc[nt], a[PA[pq]], b[PB[pq]][nt][0], b[PB[pq]][nt][1]);
+            }
+          }
+        }
+      } else {
+        const int lplane = 4 * (tr ? s * n : m * s), rplane = 4 * (tr ? m * s : s * n);
+        for (int kk = 0; kk < s; kk += KSTEP) {
+          const int k0 = kk + t, k1 = k0 + 4;
+          const int r0 = g, r1 = g + 8;
+          uint32_t a[2][4], b[2][2][2];
+#pragma unroll
+          for (int q2 = 0; q2 < 2; q2++) {
+            const uint32_t P = sL + q2 * lplane, Q = sR + q2 * rplane;
+            a[q2][0] = (r0 < Mp && k0 < s) ? lds32(P + 4 * (r0 * s + k0)) : 0u;
+            a[q2][1] = (r1 < Mp && k0 < s) ? lds32(P + 4 * (r1 * s + k0)) : 0u;
+            a[q2][2] = (r0 < Mp && k1 < s) ? lds32(P + 4 * (r0 * s + k1)) : 0u;
+            a[q2][3] = (r1 < Mp && k1 < s) ? lds32(P + 4 * (r1 * s + k1)) : 0u;
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+              const int c = nt * 8 + g;
+              b[q2][nt][0] = (c < Np && k0 < s) ? lds32(Q + 4 * (c * s + k0)) : 0u;
+              b[q2][nt][1] = (c < Np && k1 < s) ? lds32(Q + 4 * (c * s + k1)) : 0u;
+            }
+          }
+          constexpr int PA[3] = {1, 0, 0};
+          constexpr int PB[3] = {0, 1, 0};
+#pragma unroll
+          for (int nt = 0; nt < 2; nt++) {
+            if (nt * 8 >= Np) continue;
+#pragma unroll
+            for (int pq = 0; pq < 3; pq++)
+              mma_tf32_k8(acc[nt], a[PA[pq]], b[PB[pq]][nt][0], b[PB[pq]][nt][1]);
+          }
+        }
+      }
+      // product done: fold it into the running sum
+#pragma unroll
+      for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+          two_sum_acc(hi[nt][x], lo[nt][x], acc[nt][x]);
+          acc[nt][x] = 0.f;
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+
+    const int cin = ws.c_cin[gb];
+    const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+    double *out = C.vals + C.blk_off[gb];
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int rr = g + ((x >> 1) << 3);
+        const int cc = nt * 8 + 2 * t + (x & 1);
+        if (rr < Mp && cc < Np) {
+          const int row = tr ? cc : rr, col = tr ? rr : cc;
+          const int64_t e = (int64_t)col * m + row;
+          double v = f32_to_f64_exact(hi[nt][x]) + f32_to_f64_exact(lo[nt][x]);
+          if (!plain) {
+            v = alpha * v;
+            if (cinv) v = fma(beta, cinv[e], v);
+          }
+          out[e] = v;
+        }
+      }
+  }
+}
+
 // One warp per C block (grid-stride over the work list). SIZES selects the
 // blocks a launch takes: 0 all (every MMA problem fits 16 x 16), 1 those that
 // fit 16 x 16, 2 the others (up to 32 x 32). Small blocks use 1 x 2 tiles with
@@ -521,33 +749,49 @@ __global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOu
   }
 }
 
-template <int PREC>
-static void launch_split_sizes(int sizes, int grid, cudaStream_t stream, DevMat A, DevMat B,
-                               DevOut C, DevMat Cin, const void *a_left, const void *b_right,
-                               double alpha, double beta, DevWs ws, const DevStatus *st,
-                               const int32_t *items, const int64_t *seg) {
-  if (sizes == 0)
-    k_numeric_split<PREC, 0><<<grid, 128, 0, stream>>>(A, B, C, Cin, a_left, b_right, alpha, beta,
-                                                       ws, st, items, seg);
-  else if (sizes == 1)
-    k_numeric_split<PREC, 1><<<grid, 128, 0, stream>>>(A, B, C, Cin, a_left, b_right, alpha, beta,
-                                                       ws, st, items, seg);
-  else
-    k_numeric_split<PREC, 2><<<grid, 128, 0, stream>>>(A, B, C, Cin, a_left, b_right, alpha, beta,
-                                                       ws, st, items, seg);
-}
-
 cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, DevOut C,
                                  DevMat Cin, const void *a_left, const void *b_right, double alpha,
                                  double beta, DevWs ws, const DevStatus *st, const int32_t *items,
-                                 const int64_t *seg, int grid, cudaStream_t stream) {
+                                 const int64_t *seg, int smax, int nsm, cudaStream_t stream) {
+  if (sizes == 2) {  // blocks beyond 16 x 16: direct fragment loads, 2 x 4 tiles
+    const int grid = nsm * 2;
+    if (precision == BSM_PREC_SPLIT_BF16X3)
+      k_numeric_split<BSM_PREC_SPLIT_BF16X3, 2><<<grid, 128, 0, stream>>>(
+          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg);
+    else
+      k_numeric_split<BSM_PREC_SPLIT_TF32X2, 2><<<grid, 128, 0, stream>>>(
+          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg);
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t)kPipeWarps * pipe_warp_bytes(precision, smax);
+  int per_sm = 1;
+  cudaError_t e;
   if (precision == BSM_PREC_SPLIT_BF16X3)
-    launch_split_sizes<BSM_PREC_SPLIT_BF16X3>(sizes, grid, stream, A, B, C, Cin, a_left, b_right,
-                                              alpha, beta, ws, st, items, seg);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3>, kPipeWarps * 32, smem);
   else
-    launch_split_sizes<BSM_PREC_SPLIT_TF32X2>(sizes, grid, stream, A, B, C, Cin, a_left, b_right,
-                                              alpha, beta, ws, st, items, seg);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2>, kPipeWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = nsm * (per_sm > 0 ? per_sm : 1);
+  if (precision == BSM_PREC_SPLIT_BF16X3)
+    k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3><<<grid, kPipeWarps * 32, smem, stream>>>(
+        A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sizes == 1);
+  else
+    k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2><<<grid, kPipeWarps * 32, smem, stream>>>(
+        A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sizes == 1);
   return cudaGetLastError();
+}
+
+cudaError_t numeric_split_init() {
+  // the largest slot layout: k up to 32
+  const int bf = kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_BF16X3, 32);
+  const int tf = kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, 32);
+  cudaError_t e = cudaFuncSetAttribute(k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bf);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, tf);
 }
 
 }  // namespace bsm

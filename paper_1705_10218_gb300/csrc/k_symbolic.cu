@@ -16,9 +16,46 @@
 
 namespace bsm {
 
-// The filter of Sec. 2: drop iff nrm(A_ik)*nrm(B_kj) < eps (a tie and NaN are kept).
+// The filter of Sec. 2: drop iff nrm(A_ik)*nrm(B_kj) < eps (a tie and NaN are kept),
+// decided exactly as FP64 decides it.
 __device__ __forceinline__ bool keep_product(double na, double nb, double eps) {
   return !(__dmul_rn(na, nb) < eps);
+}
+
+// The same decision with FP32 arithmetic for all but the near-ties. The FP32
+// copies of the norms are within 2^-24 (relative) of the FP64 norms and lie in
+// [2^-60, 2^60] (else NaN), so their FP32 product is within 3*2^-24 of the
+// exact product; it is compared with eps widened by 2^-20 either way (lo, hi),
+// and only a product inside that band (or a NaN) takes the FP64 test.
+struct EpsBand {
+  float lo, hi;
+};
+
+__device__ __forceinline__ EpsBand eps_band(double eps) {
+  EpsBand b;
+  if (!(eps > 0.0)) {  // eps <= 0 (or NaN eps): every non-NaN product is kept
+    b.lo = -INFINITY;
+    b.hi = -INFINITY;
+  } else if (eps >= 0x1p-100 && eps <= 0x1p100) {
+    b.lo = __double2float_rd(eps * (1.0 - 0x1p-20));
+    b.hi = __double2float_ru(eps * (1.0 + 0x1p-20));
+  } else {  // out of the fast test's range: always the FP64 test
+    b.lo = -INFINITY;
+    b.hi = INFINITY;
+  }
+  if (eps != eps) {
+    b.lo = -INFINITY;
+    b.hi = INFINITY;
+  }
+  return b;
+}
+
+__device__ __forceinline__ bool keep_fast(float fa, float fb, double na, double nb, double eps,
+                                          const EpsBand &band) {
+  const float x = fa * fb;
+  if (x >= band.hi) return true;
+  if (x < band.lo) return false;
+  return keep_product(na, nb, eps);
 }
 
 __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int lo, int hi, int key) {
@@ -41,7 +78,7 @@ __global__ void k_block_norms(const int32_t *__restrict__ row_sizes,
                               const int32_t *__restrict__ col_idx,
                               const int64_t *__restrict__ blk_off,
                               const double *__restrict__ vals, const int64_t *__restrict__ hdr,
-                              double *__restrict__ norms) {
+                              double *__restrict__ norms, float *__restrict__ normsf) {
   const int64_t nblk = hdr[0];
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk;
        b += (int64_t)gridDim.x * blockDim.x) {
@@ -52,16 +89,18 @@ __global__ void k_block_norms(const int32_t *__restrict__ row_sizes,
       const double v = __ldg(x + e);
       s = __dadd_rn(s, __dmul_rn(v, v));
     }
-    norms[b] = __dsqrt_rn(s);
+    const double nrm = __dsqrt_rn(s);
+    norms[b] = nrm;
+    normsf[b] = (nrm >= 0x1p-60 && nrm <= 0x1p60) ? __double2float_rn(nrm) : NAN;
   }
 }
 
 cudaError_t launch_block_norms(const int32_t *row_sizes, const int32_t *col_sizes,
                                const int32_t *blk_row, const int32_t *col_idx,
                                const int64_t *blk_off, const double *vals, const int64_t *hdr,
-                               double *norms, int grid, cudaStream_t stream) {
+                               double *norms, float *normsf, int grid, cudaStream_t stream) {
   k_block_norms<<<grid, 256, 0, stream>>>(row_sizes, col_sizes, blk_row, col_idx, blk_off, vals,
-                                          hdr, norms);
+                                          hdr, norms, normsf);
   return cudaGetLastError();
 }
 
@@ -117,9 +156,11 @@ __device__ void row_bitmap(const DevMat &A, const DevMat &B, const DevMat &Cin, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int m = A.row_sizes[i];
   const int p0 = A.row_ptr[i], p1 = A.row_ptr[i + 1];
+  const EpsBand band = eps_band(eps);
   for (int p = p0 + warp; p < p1; p += nwarps) {
     const int k = A.col_idx[p];
     const double na = A.norms[p];
+    const float fa = A.normsf[p];
     int q0 = B.row_ptr[k], q1 = B.row_ptr[k + 1];
     if (!whole) {
       q0 = lower_bound_i32(B.col_idx, q0, q1, w0);
@@ -129,7 +170,7 @@ __device__ void row_bitmap(const DevMat &A, const DevMat &B, const DevMat &Cin, 
     for (int q = q0 + lane; q < q1; q += 32) {
       const int j = B.col_idx[q];
       if (COUNT) cand++;
-      if (keep_product(na, B.norms[q], eps)) {
+      if (keep_fast(fa, B.normsf[q], na, B.norms[q], eps, band)) {
         const int jj = j - w0;
         atomicOr(&bitmap[jj >> 5], 1u << (jj & 31));
         if (COUNT) {
@@ -281,6 +322,9 @@ __device__ int word_prefix(const uint32_t *bitmap, int32_t *wpre, int nwords) {
   return (int)total;
 }
 
+// Words of the per-row (C block x A block) bit matrix of the fill pass.
+constexpr int kMaskWords = 8192;
+
 // Rank of column offset jj inside the window among the set bits.
 __device__ __forceinline__ int bit_rank(const uint32_t *bitmap, const int32_t *wpre, int jj) {
   return wpre[jj >> 5] + __popc(bitmap[jj >> 5] & ((1u << (jj & 31)) - 1u));
@@ -302,11 +346,98 @@ __global__ void __launch_bounds__(kSymThreads) k_symbolic_fill(DevMat A, DevMat 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int64_t dummy0 = 0, dummy1 = 0, dummy2 = 0;
 
+  uint32_t *mask = smem_bits + 2 * nwords_max;  // kMaskWords words, see below
+  const EpsBand band = eps_band(eps);
+
   for (int i = blockIdx.x; i < A.nbr; i += gridDim.x) {
     const int g0 = C.row_ptr[i], g1 = C.row_ptr[i + 1];
     if (g0 == g1) continue;
     const int m = A.row_sizes[i];
     const int p0 = A.row_ptr[i], p1 = A.row_ptr[i + 1];
+
+    // Fast path (one column window, small enough row): a bit matrix in shared
+    // memory with one bit per (C block of the row, A block of the row) says
+    // which kept products exist; a product's place in its C block's list
+    // (ascending k) is then the popcount of the bits before it, so every
+    // product is placed at once, without a pass per A block.
+    const int wps = (p1 - p0 + 31) >> 5;  // mask words per C block
+    if (whole && (int64_t)(g1 - g0) * wps <= kMaskWords) {
+      const int nwords = (nbc + 31) >> 5;
+      row_bitmap<false>(A, B, Cin, use_cin, eps, i, 0, nbc, true, bitmap, nwords, dummy0, dummy1,
+                        dummy2);
+      word_prefix(bitmap, wpre, nwords);
+      for (int t = threadIdx.x; t < nwords; t += blockDim.x) {
+        uint32_t bits = bitmap[t];
+        int g = g0 + wpre[t];
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1;
+          C.col_idx[g] = 32 * t + b;
+          C.blk_row[g] = i;
+          ws.c_cin[g] = -1;
+          g++;
+        }
+      }
+      for (int t = threadIdx.x; t < (g1 - g0) * wps; t += blockDim.x) mask[t] = 0u;
+      __syncthreads();
+      for (int p = p0 + warp; p < p1; p += nwarps) {
+        const int k = A.col_idx[p];
+        const double na = A.norms[p];
+        const float fa = A.normsf[p];
+        const uint32_t bit = 1u << ((p - p0) & 31);
+        const int wofs = (p - p0) >> 5;
+        for (int q = B.row_ptr[k] + lane; q < B.row_ptr[k + 1]; q += 32) {
+          if (keep_fast(fa, B.normsf[q], na, B.norms[q], eps, band)) {
+            const int sl = bit_rank(bitmap, wpre, B.col_idx[q]);
+            atomicOr(&mask[sl * wps + wofs], bit);
+          }
+        }
+      }
+      if (use_cin) {
+        for (int c = Cin.row_ptr[i] + threadIdx.x; c < Cin.row_ptr[i + 1]; c += blockDim.x)
+          ws.c_cin[g0 + bit_rank(bitmap, wpre, Cin.col_idx[c])] = c;
+      }
+      __syncthreads();
+      // product ranges and value offsets of the row's C blocks
+      int64_t carry_p = ws.prod_off[i], carry_v = ws.nnz_off[i];
+      for (int base = g0; base < g1; base += blockDim.x) {
+        const int g = base + threadIdx.x;
+        const bool in = g < g1;
+        int64_t cp = 0;
+        if (in)
+          for (int w = 0; w < wps; w++) cp += __popc(mask[(g - g0) * wps + w]);
+        const int64_t cv = in ? (int64_t)m * C.col_sizes[C.col_idx[g]] : 0;
+        int64_t tp, tv;
+        const int64_t ep = block_exclusive_scan(cp, &tp);
+        const int64_t ev = block_exclusive_scan(cv, &tv);
+        if (in) {
+          ws.prod_ptr[g] = carry_p + ep;
+          C.blk_off[g] = carry_v + ev;
+        }
+        carry_p += tp;
+        carry_v += tv;
+      }
+      __syncthreads();
+      // every kept product straight to its place
+      for (int p = p0 + warp; p < p1; p += nwarps) {
+        const int k = A.col_idx[p];
+        const double na = A.norms[p];
+        const float fa = A.normsf[p];
+        const int pi = p - p0;
+        const uint32_t below = (1u << (pi & 31)) - 1u;
+        for (int q = B.row_ptr[k] + lane; q < B.row_ptr[k + 1]; q += 32) {
+          if (keep_fast(fa, B.normsf[q], na, B.norms[q], eps, band)) {
+            const int sl = bit_rank(bitmap, wpre, B.col_idx[q]);
+            const uint32_t *mk = mask + sl * wps;
+            int pos = __popc(mk[pi >> 5] & below);
+            for (int w = 0; w < (pi >> 5); w++) pos += __popc(mk[w]);
+            ws.prods[ws.prod_ptr[g0 + sl] + pos] = make_int2(p, q);
+          }
+        }
+      }
+      __syncthreads();
+      continue;
+    }
 
     // pass 1: C blocks of the row, per-block product counts, C_in map
     int slot_base = 0;
@@ -333,13 +464,14 @@ __global__ void __launch_bounds__(kSymThreads) k_symbolic_fill(DevMat A, DevMat 
       for (int p = p0 + warp; p < p1; p += nwarps) {
         const int k = A.col_idx[p];
         const double na = A.norms[p];
+        const float fa = A.normsf[p];
         int q0 = B.row_ptr[k], q1 = B.row_ptr[k + 1];
         if (!whole) {
           q0 = lower_bound_i32(B.col_idx, q0, q1, w0);
           q1 = lower_bound_i32(B.col_idx, q0, q1, w0 + wn);
         }
         for (int q = q0 + lane; q < q1; q += 32) {
-          if (keep_product(na, B.norms[q], eps)) {
+          if (keep_fast(fa, B.normsf[q], na, B.norms[q], eps, band)) {
             const int g = g0 + slot_base + bit_rank(bitmap, wpre, B.col_idx[q] - w0);
             atomicAdd(&ws.cnt[g], 1);
           }
@@ -398,13 +530,14 @@ __global__ void __launch_bounds__(kSymThreads) k_symbolic_fill(DevMat A, DevMat 
       for (int p = p0; p < p1; p++) {
         const int k = A.col_idx[p];
         const double na = A.norms[p];
+        const float fa = A.normsf[p];
         int q0 = B.row_ptr[k], q1 = B.row_ptr[k + 1];
         if (!whole) {
           q0 = lower_bound_i32(B.col_idx, q0, q1, w0);
           q1 = lower_bound_i32(B.col_idx, q0, q1, w0 + wn);
         }
         for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-          if (keep_product(na, B.norms[q], eps)) {
+          if (keep_fast(fa, B.normsf[q], na, B.norms[q], eps, band)) {
             const int g = g0 + slot_base + bit_rank(bitmap, wpre, B.col_idx[q] - w0);
             const int c = ws.cnt[g];
             ws.cnt[g] = c + 1;
@@ -422,7 +555,7 @@ cudaError_t launch_symbolic_fill(DevMat A, DevMat B, DevMat Cin, int use_cin, do
                                  DevWs ws, DevOut C, const DevStatus *st, int grid,
                                  cudaStream_t stream) {
   const int nwords = (min(B.nbc, kWindowCols) + 31) / 32;
-  const size_t smem = (size_t)max(nwords, 1) * 2 * sizeof(uint32_t);
+  const size_t smem = ((size_t)max(nwords, 1) * 2 + kMaskWords) * sizeof(uint32_t);
   k_symbolic_fill<<<grid, kSymThreads, smem, stream>>>(A, B, Cin, use_cin, eps, ws, C, st);
   return cudaGetLastError();
 }

@@ -227,3 +227,37 @@ def paper_workload(name: str) -> BlockMatrix:
     if name == "amorphous4096":
         return amorphous(4096, seed=2)
     raise KeyError(name)
+
+
+def dense_blocks(nb: int, bs: int, seed: int) -> BlockMatrix:
+    """Fully occupied symmetric matrix of nb x nb blocks of bs x bs (the Dense
+    benchmark of Table 1, block 32, scaled to one GPU)."""
+    rng = np.random.default_rng(seed)
+    n = nb * bs
+    X = rng.standard_normal((n, n))
+    D = (X + X.T) / np.sqrt(2.0 * n) + 5.0 * np.eye(n) / np.sqrt(n)
+    rows, cols = np.divmod(np.arange(nb * nb, dtype=np.int64), nb)
+    blocks = D.reshape(nb, bs, nb, bs).transpose(0, 2, 3, 1)  # [i, j, col, row]: column-major
+    sizes = np.full(nb, bs, np.int32)
+    return BlockMatrix(sizes, sizes.copy(), rows.astype(np.int32), cols.astype(np.int32),
+                       np.ascontiguousarray(blocks).reshape(-1))
+
+
+def sparse_random(nb: int, bs: int, occupancy: float, seed: int) -> BlockMatrix:
+    """Symmetric random block pattern with the given block occupancy (off
+    diagonal) plus the diagonal, blocks bs x bs (the S-E benchmark of Table 1:
+    block 6, occupancy about 0.05%, scaled to one GPU). Entries N(0,1)*0.3,
+    diagonal blocks symmetric with +5 on the diagonal."""
+    rng = np.random.default_rng(seed)
+    npairs = int(round(occupancy * nb * (nb - 1) / 2))
+    I = rng.integers(0, nb, 2 * npairs + 16)
+    J = rng.integers(0, nb, 2 * npairs + 16)
+    keep = I < J
+    key = np.unique(I[keep].astype(np.int64) * nb + J[keep])[:npairs]
+    I, J = np.divmod(key, nb)
+    I = np.concatenate([I, np.arange(nb)])
+    J = np.concatenate([J, np.arange(nb)])
+    order = np.lexsort((J, I))
+    I, J = I[order], J[order]
+    R = np.full(len(I), -np.log(0.3) / 0.5)  # entries scaled by exp(-0.5 r) = 0.3
+    return _symmetric_matrix(np.full(nb, bs, np.int32), I, J, R, 0.5, 5.0, rng)
