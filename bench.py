@@ -82,6 +82,25 @@ def replica_aggregate(local_ms, local_flop, dist=None, device="cpu"):
     return ms, flop / (ms / 1e3) / 1e9
 
 
+def norm_product_percentile(A, pct, sample=2_000_000, seed=0):
+    """eps at a percentile of the candidate norm products nrm(A_ik) nrm(A_kj)
+    (numpy Frobenius norms over a random sample of candidates): a threshold
+    that makes the filter drop about pct percent of the products."""
+    off = np.zeros(A.nblk + 1, np.int64)
+    lens = A.row_sizes.astype(np.int64)[A.blk_row] * A.col_sizes.astype(np.int64)[A.blk_col]
+    np.cumsum(lens, out=off[1:])
+    sq = np.add.reduceat(A.values * A.values, off[:-1]) if A.nblk else np.zeros(0)
+    nrm = np.sqrt(sq)
+    rng = np.random.default_rng(seed)
+    row_start = np.searchsorted(A.blk_row, np.arange(A.nbr + 1))
+    a = rng.integers(0, A.nblk, sample)
+    k = A.blk_col[a]
+    cnt = row_start[k + 1] - row_start[k]
+    ok = cnt > 0
+    b = row_start[k[ok]] + (rng.random(int(ok.sum())) * cnt[ok]).astype(np.int64)
+    return float(np.percentile(nrm[a[ok]] * nrm[b], pct))
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -313,6 +332,9 @@ def main():
     ap.add_argument("--workload", default="water2048", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--launch", default="persistent", choices=["persistent", "per_stack"])
+    ap.add_argument("--eps", type=float, default=None, help="filter threshold (default: the workload's)")
+    ap.add_argument("--eps-percentile", type=float, default=None,
+                    help="filter threshold at this percentile of the candidate norm products")
     ap.add_argument("--graph", action="store_true", help="replay the multiply as a CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="tune the FP64 kernel variants first")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -342,6 +364,10 @@ def main():
     from paper_1705_10218_gb300 import Context
 
     A, eps = make_workload(args.workload)
+    if args.eps is not None:
+        eps = args.eps
+    if args.eps_percentile is not None:
+        eps = norm_product_percentile(A, args.eps_percentile)
     prec = PRECISIONS[args.precision]
     launch = 0 if args.launch == "persistent" else 1
     ctx = Context(local)
