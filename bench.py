@@ -408,7 +408,7 @@ def main():
     # replay the phases are not timed separately: the whole multiply is used.
     if prof.multiplies > 0:
         num_ms = prof.ms_numeric / prof.multiplies
-        kname = "k_numeric_fp64_t16" if args.precision == "fp64" else "k_numeric_split"
+        kname = "k_numeric_fp64_t16" if args.precision == "fp64" else "k_numeric_split_pipe"
     else:
         num_ms = total_ms / args.steps
         kname = "whole multiply (CUDA graph replay)"

@@ -139,12 +139,13 @@ cudaError_t numeric_split_init();
 
 // Slice storage of an operand block b starts at a fixed multiple of its FP64
 // offset blk_off[b], 16-byte aligned so whole blocks can be copied with
-// 16-byte asynchronous copies: BF16x3 at 48 bytes per value, TF32x2 at 64
-// (both bound the k-padded fragment-order layouts of k_split.cu).
-constexpr int64_t kBf16BytesPerValue = 48;
-constexpr int64_t kTf32BytesPerValue = 64;
+// 16-byte asynchronous copies: BF16x3 at halfword 16*blk_off (32 bytes per
+// value; the 3 padded planes take at most 24), TF32x2 at word 4*blk_off (16
+// bytes per value; the 2 planes take 8).
+constexpr int64_t kBf16HalfwordsPerValue = 16;
+constexpr int64_t kTf32WordsPerValue = 4;
 inline int64_t split_bytes_per_value(int precision) {
-  return precision == BSM_PREC_SPLIT_BF16X3 ? kBf16BytesPerValue : kTf32BytesPerValue;
+  return precision == BSM_PREC_SPLIT_BF16X3 ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue;
 }
 
 }  // namespace bsm

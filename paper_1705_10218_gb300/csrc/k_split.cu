@@ -15,46 +15,22 @@
 // previous slices left), so no FP64 arithmetic is spent on splitting; the
 // filter and the norms stay in FP64 (k_symbolic.cu).
 //
-// Slice layout ("fragment order"). An operand block enters an MMA either as
-// the left factor (its rows are M rows, its columns the k dimension) or as the
-// right factor (its rows the k dimension, its columns N columns). Each layout
-// stores, per M row (left) or per N column (right), the k values of that row
-// or column padded to kpad(k) and permuted inside every k-step so that one
-// lane's fragment registers of a step are one aligned 8-byte (k16 / tf32 k8)
-// or 4-byte (bf16 k8 tail) word:
-//   BF16: k-steps of 16, and a final step of 8 when at most 8 remain; inside a
-//         16-step, lane t's values k = 2t, 2t+1, 2t+8, 2t+9 sit at 4t..4t+3;
-//         an 8-step keeps natural order (lane t reads 2t, 2t+1).
-//   TF32: k-steps of 8; lane t's values k = t, t+4 sit at 2t, 2t+1.
-// Padding is zero, so fragment loads need no predicates on k. Per block the
-// layout starts at a fixed multiple of its FP64 offset blk_off[b] (48 bytes per
-// value for BF16, 64 for TF32; both bound the padded size), 16-byte aligned.
+// Slice layout. For every block b of r x c values (FP64 offset blk_off[b]),
+// the slices live at a fixed multiple of the FP64 offset, so no extra offset
+// table is needed:
+//   BF16: 3 planes of rp x cp elements (rp, cp = r, c rounded up to even;
+//         padding is zero) at 16-bit index 16*blk_off[b] (rp*cp <= 4*r*c);
+//         "left" layout (the block as a left operand) is row-major with
+//         stride cp, "right" layout (as a right operand) column-major with
+//         stride rp, so the two k-adjacent values of an MMA fragment register
+//         are one aligned 32-bit word.
+//   TF32: 2 planes of r x c 32-bit elements at 32-bit index 4*blk_off[b];
+//         left row-major, right column-major.
 #include <cstdint>
 
 #include "bsm_internal.h"
 
 namespace bsm {
-
-// Padded k extent.
-__host__ __device__ __forceinline__ int kpad_bf16(int k) {
-  const int r = k & 15;
-  return (k & ~15) + (r == 0 ? 0 : (r <= 8 ? 8 : 16));
-}
-__host__ __device__ __forceinline__ int kpad_tf32(int k) { return (k + 7) & ~7; }
-
-// The k index stored at position pos (inside the padded extent of k values).
-__device__ __forceinline__ int bf16_k_at(int pos, int k) {
-  const int base = pos & ~15;
-  const int in = pos & 15;
-  if (k - base <= 8) return pos;  // the final 8-step: natural order
-  const int t = in >> 2, w = in & 3;
-  return base + ((w < 2) ? (2 * t + w) : (2 * t + 8 + (w - 2)));
-}
-__device__ __forceinline__ int tf32_k_at(int pos) {
-  const int base = pos & ~7;
-  const int in = pos & 7;
-  return base + ((in & 1) ? (in >> 1) + 4 : (in >> 1));
-}
 
 // ---------------------------------------------------------------------------
 // Splitting an FP64 value into slices of BITS significant bits (truncation).
@@ -112,8 +88,8 @@ __device__ __forceinline__ Slices<NS, BITS> split_value(double x) {
 }
 
 // ---------------------------------------------------------------------------
-// Split every block of a matrix into the left and/or right layouts. One warp
-// per block (grid-stride), lanes over the padded positions of a layout.
+// Split every block of a matrix into the left and/or right slice layouts.
+// One warp per block (grid-stride), lanes over the padded positions.
 // ---------------------------------------------------------------------------
 __global__ void k_split_bf16x3(const int32_t *__restrict__ row_sizes,
                                const int32_t *__restrict__ col_sizes,
@@ -128,28 +104,19 @@ __global__ void k_split_bf16x3(const int32_t *__restrict__ row_sizes,
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = w0; b < nblk; b += nw) {
     const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
-    const int64_t base = (kBf16BytesPerValue / 2) * blk_off[b];
+    const int rp = r + (r & 1), cp = c + (c & 1);
+    const int plane = rp * cp;
+    const int64_t base = kBf16HalfwordsPerValue * blk_off[b];
     const double *x = vals + blk_off[b];
-    if (left) {  // r rows of kpad(c), k = column index
-      const int kp = kpad_bf16(c);
-      const int plane = r * kp;
-      for (int e = lane; e < plane; e += 32) {
-        const int row = e / kp, pos = e - row * kp;
-        const int k = bf16_k_at(pos, c);
-        const Slices<3, 8> sl = split_value<3, 8>(k < c ? x[row + (int64_t)k * r] : 0.0);
+    for (int e = lane; e < plane; e += 32) {
+      // position (row xr, col yc) in the padded rp x cp block, column-major order
+      const int xr = e % rp, yc = e / rp;
+      const double v = (xr < r && yc < c) ? x[xr + (int64_t)yc * r] : 0.0;
+      const Slices<3, 8> sl = split_value<3, 8>(v);
 #pragma unroll
-        for (int q = 0; q < 3; q++) left[base + (int64_t)q * plane + e] = (uint16_t)sl.s[q];
-      }
-    }
-    if (right) {  // c columns of kpad(r), k = row index
-      const int kp = kpad_bf16(r);
-      const int plane = c * kp;
-      for (int e = lane; e < plane; e += 32) {
-        const int col = e / kp, pos = e - col * kp;
-        const int k = bf16_k_at(pos, r);
-        const Slices<3, 8> sl = split_value<3, 8>(k < r ? x[k + (int64_t)col * r] : 0.0);
-#pragma unroll
-        for (int q = 0; q < 3; q++) right[base + (int64_t)q * plane + e] = (uint16_t)sl.s[q];
+      for (int q = 0; q < 3; q++) {
+        if (left) left[base + (int64_t)q * plane + xr * cp + yc] = (uint16_t)sl.s[q];
+        if (right) right[base + (int64_t)q * plane + yc * rp + xr] = (uint16_t)sl.s[q];
       }
     }
   }
@@ -168,28 +135,16 @@ __global__ void k_split_tf32x2(const int32_t *__restrict__ row_sizes,
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = w0; b < nblk; b += nw) {
     const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
-    const int64_t base = (kTf32BytesPerValue / 4) * blk_off[b];
+    const int plane = r * c;
+    const int64_t base = kTf32WordsPerValue * blk_off[b];
     const double *x = vals + blk_off[b];
-    if (left) {
-      const int kp = kpad_tf32(c);
-      const int plane = r * kp;
-      for (int e = lane; e < plane; e += 32) {
-        const int row = e / kp, pos = e - row * kp;
-        const int k = tf32_k_at(pos);
-        const Slices<2, 11> sl = split_value<2, 11>(k < c ? x[row + (int64_t)k * r] : 0.0);
+    for (int e = lane; e < plane; e += 32) {
+      const int xr = e % r, yc = e / r;
+      const Slices<2, 11> sl = split_value<2, 11>(x[e]);
 #pragma unroll
-        for (int q = 0; q < 2; q++) left[base + (int64_t)q * plane + e] = sl.s[q];
-      }
-    }
-    if (right) {
-      const int kp = kpad_tf32(r);
-      const int plane = c * kp;
-      for (int e = lane; e < plane; e += 32) {
-        const int col = e / kp, pos = e - col * kp;
-        const int k = tf32_k_at(pos);
-        const Slices<2, 11> sl = split_value<2, 11>(k < r ? x[k + (int64_t)col * r] : 0.0);
-#pragma unroll
-        for (int q = 0; q < 2; q++) right[base + (int64_t)q * plane + e] = sl.s[q];
+      for (int q = 0; q < 2; q++) {
+        if (left) left[base + (int64_t)q * plane + xr * c + yc] = sl.s[q];
+        if (right) right[base + (int64_t)q * plane + e] = sl.s[q];
       }
     }
   }
@@ -211,13 +166,13 @@ cudaError_t launch_split(int precision, const int32_t *row_sizes, const int32_t 
 // ---------------------------------------------------------------------------
 // Tensor-core fragments (mma.sync, FP32 accumulation).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_bf16_k16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                             uint32_t a3, uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void mma_bf16_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                             uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
       "{%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 __device__ __forceinline__ void mma_bf16_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
@@ -228,13 +183,13 @@ __device__ __forceinline__ void mma_bf16_k8(float (&d)[4], uint32_t a0, uint32_t
       : "r"(a0), "r"(a1), "r"(b0));
 }
 
-__device__ __forceinline__ void mma_tf32_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                            uint32_t a3, uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void mma_tf32_k8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                            uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
       "{%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // Exact FP32 -> FP64 conversion with integer operations only.
@@ -259,6 +214,126 @@ __device__ __forceinline__ double f32_to_f64_exact(float f) {
   return __longlong_as_double((long long)bits);
 }
 
+// ---------------------------------------------------------------------------
+// Numeric kernel. One warp per C block; the C block (or its transpose,
+// whichever needs fewer MMA tiles) is covered by MT x NT tiles of 16 x 8.
+// A "step" is one k-step of one product: 16 (BF16; 8 for a final step with at
+// most 8 left) or 8 (TF32) values of k, with all slice products of every tile.
+//
+// Operands: L (M' x s) is read from a left layout (row-major), R (s x N')
+// from a right layout (column-major). Not transposed: L = A_ik (A's left
+// layout), R = B_kj (B's right layout). Transposed (C^T = B^T A^T): L = B_kj^T
+// = B's right layout read as row-major, R = A_ik^T = A's left layout read as
+// column-major.
+//
+// Accumulation: every product is summed in a fresh FP32 accumulator by the
+// tensor cores (at most a few MMAs deep), then added to a running sum kept as
+// an unevaluated pair hi + lo of FP32 numbers (TwoSum, error-free), so the
+// long sum over the products of a C block loses no more than FP32 rounding of
+// each product; hi + lo is formed in FP64 at the end.
+// ---------------------------------------------------------------------------
+template <int NSL, int MT, int NT>
+struct Frag {
+  uint32_t a[NSL][MT][4];
+  uint32_t b[NSL][NT][2];
+};
+
+// Fragments of one BF16 step (k values kk..kk+15, or kk..kk+7 when k8).
+template <int MT, int NT>
+__device__ __forceinline__ void load_bf16(Frag<3, MT, NT> &f, const uint16_t *__restrict__ Lb,
+                                          const uint16_t *__restrict__ Rb, int Mp, int Np, int sp,
+                                          int kk, bool k8, int lplane, int rplane) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int k0 = kk + 2 * t, k1 = k0 + 8;
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    const uint32_t *P = reinterpret_cast<const uint32_t *>(Lb + (int64_t)q * lplane);
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++) {
+      const int r0 = mt * 16 + g, r1 = r0 + 8;
+      f.a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + ((r0 * sp + k0) >> 1)) : 0u;
+      f.a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + ((r1 * sp + k0) >> 1)) : 0u;
+      f.a[q][mt][2] = (!k8 && r0 < Mp && k1 < sp) ? __ldg(P + ((r0 * sp + k1) >> 1)) : 0u;
+      f.a[q][mt][3] = (!k8 && r1 < Mp && k1 < sp) ? __ldg(P + ((r1 * sp + k1) >> 1)) : 0u;
+    }
+    const uint32_t *Q = reinterpret_cast<const uint32_t *>(Rb + (int64_t)q * rplane);
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      const int c = nt * 8 + g;
+      f.b[q][nt][0] = (c < Np && k0 < sp) ? __ldg(Q + ((c * sp + k0) >> 1)) : 0u;
+      f.b[q][nt][1] = (!k8 && c < Np && k1 < sp) ? __ldg(Q + ((c * sp + k1) >> 1)) : 0u;
+    }
+  }
+}
+
+template <int MT, int NT>
+__device__ __forceinline__ void mma_bf16(float (&acc)[MT][NT][4], const Frag<3, MT, NT> &f,
+                                         bool k8, int Mp, int Np) {
+  // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
+  constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
+  constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      if (mt * 16 >= Mp || nt * 8 >= Np) continue;
+#pragma unroll
+      for (int pq = 0; pq < 6; pq++) {
+        if (k8)
+          mma_bf16_k8(acc[mt][nt], f.a[PA[pq]][mt][0], f.a[PA[pq]][mt][1], f.b[PB[pq]][nt][0]);
+        else
+          mma_bf16_k16(acc[mt][nt], f.a[PA[pq]][mt], f.b[PB[pq]][nt][0], f.b[PB[pq]][nt][1]);
+      }
+    }
+}
+
+// Fragments of one TF32 step (k values kk..kk+7).
+template <int MT, int NT>
+__device__ __forceinline__ void load_tf32(Frag<2, MT, NT> &f, const uint32_t *__restrict__ Lb,
+                                          const uint32_t *__restrict__ Rb, int Mp, int Np, int s,
+                                          int kk, int lplane, int rplane) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int k0 = kk + t, k1 = k0 + 4;
+#pragma unroll
+  for (int q = 0; q < 2; q++) {
+    const uint32_t *P = Lb + (int64_t)q * lplane;
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++) {
+      const int r0 = mt * 16 + g, r1 = r0 + 8;
+      f.a[q][mt][0] = (r0 < Mp && k0 < s) ? __ldg(P + r0 * s + k0) : 0u;
+      f.a[q][mt][1] = (r1 < Mp && k0 < s) ? __ldg(P + r1 * s + k0) : 0u;
+      f.a[q][mt][2] = (r0 < Mp && k1 < s) ? __ldg(P + r0 * s + k1) : 0u;
+      f.a[q][mt][3] = (r1 < Mp && k1 < s) ? __ldg(P + r1 * s + k1) : 0u;
+    }
+    const uint32_t *Q = Rb + (int64_t)q * rplane;
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      const int c = nt * 8 + g;
+      f.b[q][nt][0] = (c < Np && k0 < s) ? __ldg(Q + c * s + k0) : 0u;
+      f.b[q][nt][1] = (c < Np && k1 < s) ? __ldg(Q + c * s + k1) : 0u;
+    }
+  }
+}
+
+template <int MT, int NT>
+__device__ __forceinline__ void mma_tf32(float (&acc)[MT][NT][4], const Frag<2, MT, NT> &f,
+                                         int Mp, int Np) {
+  // (2,1) (1,2) (1,1)
+  constexpr int PA[3] = {1, 0, 0};
+  constexpr int PB[3] = {0, 1, 0};
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      if (mt * 16 >= Mp || nt * 8 >= Np) continue;
+#pragma unroll
+      for (int pq = 0; pq < 3; pq++)
+        mma_tf32_k8(acc[mt][nt], f.a[PA[pq]][mt], f.b[PB[pq]][nt][0], f.b[PB[pq]][nt][1]);
+    }
+}
+
 // hi + lo += x, exactly (Knuth's TwoSum in FP32, no fused operations).
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   const float s = __fadd_rn(hi, x);
@@ -268,151 +343,123 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   lo = __fadd_rn(lo, err);
 }
 
-// ---------------------------------------------------------------------------
-// Loads of fragment words. `Sh` selects shared (32-bit addresses) or global.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t lds32(uint32_t a) {
-  uint32_t v;
-  asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ uint2 lds64(uint32_t a) {
-  uint2 v;
-  asm volatile("ld.shared.v2.b32 {%0,%1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "r"(a));
-  return v;
-}
-
-// One k-step of all slice products of a warp's MT x NT tiles.
-//   L: left operand base (rows of the MMA problem, stride lstride bytes),
-//   R: right operand base (columns, stride rstride bytes), plane strides in
-//   bytes, kk: position of the step, k8: an 8-wide BF16 tail step. Rows /
-//   columns past Mp / Np read nothing and use zero fragments.
-template <int PREC, int MT, int NT, bool SH>
-__device__ __forceinline__ void split_step(float (&acc)[MT][NT][4], const unsigned char *Lg,
-                                           const unsigned char *Rg, uint32_t Ls, uint32_t Rs,
-                                           int lstride, int rstride, int lplane, int rplane,
-                                           int kk, bool k8, int Mp, int Np) {
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
+// One C block by one warp: the MMA problem M' x N' in MT x NT tiles. The
+// (A offset, B offset, k) of up to 32 products are read at once, one per lane;
+// with PREFETCH the next step's fragments are loaded while the current step
+// multiplies (twice the fragment registers).
+template <int PREC, int MT, int NT, bool PREFETCH>
+__device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, const DevOut &C,
+                                             const DevMat &Cin, const void *__restrict__ a_left,
+                                             const void *__restrict__ b_right, double alpha,
+                                             double beta, const DevWs &ws, int64_t gb, int m,
+                                             int n, bool tr, int Mp, int Np) {
   constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
   constexpr int NSL = BF ? 3 : 2;
-  constexpr int ES = BF ? 2 : 4;  // bytes per element
-  // byte offset of lane's word inside a row / column of the step
-  const int wofs = BF ? (k8 ? (kk + 2 * t) * ES : (kk + 4 * t) * ES) : (kk + 2 * t) * ES;
-  uint32_t a[NSL][MT][4], b[NSL][NT][2];
-#pragma unroll
-  for (int q = 0; q < NSL; q++) {
-#pragma unroll
-    for (int mt = 0; mt < MT; mt++) {
-      const int r0 = mt * 16 + g, r1 = r0 + 8;
-      const int o0 = q * lplane + r0 * lstride + wofs, o1 = q * lplane + r1 * lstride + wofs;
-      uint2 v0 = make_uint2(0u, 0u), v1 = make_uint2(0u, 0u);
-      if (BF && k8) {
-        if (r0 < Mp) v0.x = SH ? lds32(Ls + o0) : __ldg(reinterpret_cast<const uint32_t *>(Lg + o0));
-        if (r1 < Mp) v1.x = SH ? lds32(Ls + o1) : __ldg(reinterpret_cast<const uint32_t *>(Lg + o1));
-      } else {
-        if (r0 < Mp) v0 = SH ? lds64(Ls + o0) : __ldg(reinterpret_cast<const uint2 *>(Lg + o0));
-        if (r1 < Mp) v1 = SH ? lds64(Ls + o1) : __ldg(reinterpret_cast<const uint2 *>(Lg + o1));
-      }
-      // bf16 k16: {k 2t..2t+1, k 2t+8..2t+9}; tf32: {k t, k t+4}
-      a[q][mt][0] = v0.x;
-      a[q][mt][1] = v1.x;
-      a[q][mt][2] = v0.y;
-      a[q][mt][3] = v1.y;
-    }
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++) {
-      const int c = nt * 8 + g;
-      const int o = q * rplane + c * rstride + wofs;
-      uint2 v = make_uint2(0u, 0u);
-      if (c < Np) {
-        if (BF && k8)
-          v.x = SH ? lds32(Rs + o) : __ldg(reinterpret_cast<const uint32_t *>(Rg + o));
-        else
-          v = SH ? lds64(Rs + o) : __ldg(reinterpret_cast<const uint2 *>(Rg + o));
-      }
-      b[q][nt][0] = v.x;
-      b[q][nt][1] = v.y;
-    }
-  }
-  if (BF) {
-    // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
-    constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
-    constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
-#pragma unroll
-    for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-      for (int nt = 0; nt < NT; nt++) {
-        if (mt * 16 >= Mp || nt * 8 >= Np) continue;
-#pragma unroll
-        for (int pq = 0; pq < 6; pq++) {
-          const uint32_t *aa = a[PA[pq]][mt];
-          if (k8)
-            mma_bf16_k8(acc[mt][nt], aa[0], aa[1], b[PB[pq]][nt][0]);
-          else
-            mma_bf16_k16(acc[mt][nt], aa[0], aa[1], aa[2], aa[3], b[PB[pq]][nt][0],
-                         b[PB[pq]][nt][1]);
-        }
-      }
-  } else {
-    // (2,1) (1,2) (1,1)
-    constexpr int PA[3] = {1, 0, 0};
-    constexpr int PB[3] = {0, 1, 0};
-#pragma unroll
-    for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-      for (int nt = 0; nt < NT; nt++) {
-        if (mt * 16 >= Mp || nt * 8 >= Np) continue;
-#pragma unroll
-        for (int pq = 0; pq < 3; pq++) {
-          const uint32_t *aa = a[PA[pq]][mt];
-          mma_tf32_k8(acc[mt][nt], aa[0], aa[1], aa[2], aa[3], b[PB[pq]][nt][0],
-                      b[PB[pq]][nt][1]);
-        }
-      }
-  }
-}
-
-// The geometry of one product's operands in the layouts: byte size of a layout
-// block with `rows` rows (or columns) and k values, its row stride, plane size.
-template <int PREC>
-__device__ __forceinline__ void layout_dims(int rows, int k, int &stride, int &plane) {
-  if (PREC == BSM_PREC_SPLIT_BF16X3) {
-    stride = 2 * kpad_bf16(k);
-    plane = rows * stride;
-  } else {
-    stride = 4 * kpad_tf32(k);
-    plane = rows * stride;
-  }
-}
-
-template <int PREC>
-__device__ __forceinline__ void run_steps_prologue(int s, int &nsteps) {
-  nsteps = (PREC == BSM_PREC_SPLIT_BF16X3) ? (kpad_bf16(s) + 15) / 16 : kpad_tf32(s) / 8;
-}
-
-// Position of step st of a product with k = s: (kk, k8).
-template <int PREC>
-__device__ __forceinline__ void step_pos(int st, int s, int &kk, bool &k8) {
-  if (PREC == BSM_PREC_SPLIT_BF16X3) {
-    kk = 16 * st;
-    k8 = (s - kk) <= 8;
-  } else {
-    kk = 8 * st;
-    k8 = false;
-  }
-}
-
-// Epilogue of a C block: C_ij = beta * C_in_ij + alpha * (hi + lo) in FP64 (an
-// exact copy of hi + lo when alpha = 1 and beta = 0).
-template <int MT, int NT>
-__device__ __forceinline__ void split_epilogue(const float (&hi)[MT][NT][4],
-                                               const float (&lo)[MT][NT][4], double alpha,
-                                               double beta, const double *cinv, double *out,
-                                               int m, bool tr, int Mp, int Np) {
+  constexpr int KSTEP = BF ? 16 : 8;
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
+  float hi[MT][NT][4], lo[MT][NT][4], acc[MT][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+      for (int x = 0; x < 4; x++) hi[mt][nt][x] = lo[mt][nt][x] = acc[mt][nt][x] = 0.f;
+  const int mp2 = m + (m & 1), np2 = n + (n & 1);
+
+  // operand pointers and planes of product (aoff, boff, s) for this block
+  auto operands = [&](int64_t aoff, int64_t boff, int s, const void *&L, const void *&R,
+                      int &lplane, int &rplane) {
+    if (BF) {
+      const uint16_t *Al = static_cast<const uint16_t *>(a_left) + kBf16HalfwordsPerValue * aoff;
+      const uint16_t *Br = static_cast<const uint16_t *>(b_right) + kBf16HalfwordsPerValue * boff;
+      const int sp = s + (s & 1);
+      const int ap = mp2 * sp, bpl = sp * np2;
+      L = tr ? (const void *)Br : (const void *)Al;
+      R = tr ? (const void *)Al : (const void *)Br;
+      lplane = tr ? bpl : ap;
+      rplane = tr ? ap : bpl;
+    } else {
+      const uint32_t *Al = static_cast<const uint32_t *>(a_left) + kTf32WordsPerValue * aoff;
+      const uint32_t *Br = static_cast<const uint32_t *>(b_right) + kTf32WordsPerValue * boff;
+      L = tr ? (const void *)Br : (const void *)Al;
+      R = tr ? (const void *)Al : (const void *)Br;
+      lplane = tr ? s * n : m * s;
+      rplane = tr ? m * s : s * n;
+    }
+  };
+  auto load = [&](Frag<NSL, MT, NT> &f, const void *L, const void *R, int lplane, int rplane,
+                  int s, int kk) {
+    if constexpr (BF)
+      load_bf16<MT, NT>(f, static_cast<const uint16_t *>(L), static_cast<const uint16_t *>(R), Mp,
+                        Np, s + (s & 1), kk, (s - kk) <= 8, lplane, rplane);
+    else
+      load_tf32<MT, NT>(f, static_cast<const uint32_t *>(L), static_cast<const uint32_t *>(R), Mp,
+                        Np, s, kk, lplane, rplane);
+  };
+
+  const int64_t p0 = ws.prod_ptr[gb], p1 = ws.prod_ptr[gb + 1];
+  for (int64_t pb = p0; pb < p1; pb += 32) {
+    const int nb = (p1 - pb < 32) ? (int)(p1 - pb) : 32;
+    int64_t my_a = 0, my_b = 0;
+    int my_s = 1;
+    if (lane < nb) {
+      const int2 pr = ws.prods[pb + lane];
+      my_a = A.blk_off[pr.x];
+      my_b = B.blk_off[pr.y];
+      my_s = A.col_sizes[A.col_idx[pr.x]];
+    }
+    Frag<NSL, MT, NT> cur, nxt;
+    int q = 0, kk = 0;
+    int s = __shfl_sync(0xffffffffu, my_s, 0);
+    const void *L, *R;
+    int lplane, rplane;
+    operands(__shfl_sync(0xffffffffu, my_a, 0), __shfl_sync(0xffffffffu, my_b, 0), s, L, R,
+             lplane, rplane);
+    load(cur, L, R, lplane, rplane, s, 0);
+    while (q < nb) {
+      // the next step: the next k-step of this product, or the next product
+      int nq = q, nkk = kk + KSTEP;
+      if (nkk >= s) {
+        nq = q + 1;
+        nkk = 0;
+      }
+      const int src = nq < nb ? nq : 0;
+      const int ns = __shfl_sync(0xffffffffu, my_s, src);
+      const int64_t na = __shfl_sync(0xffffffffu, my_a, src);
+      const int64_t nbo = __shfl_sync(0xffffffffu, my_b, src);
+      const void *nL = L, *nR = R;
+      int nlp = lplane, nrp = rplane;
+      if (nq < nb && nq != q) operands(na, nbo, ns, nL, nR, nlp, nrp);
+      if (PREFETCH && nq < nb) load(nxt, nL, nR, nlp, nrp, ns, nkk);
+      if constexpr (BF)
+        mma_bf16<MT, NT>(acc, cur, (s - kk) <= 8, Mp, Np);
+      else
+        mma_tf32<MT, NT>(acc, cur, Mp, Np);
+      if (!PREFETCH && nq < nb) load(nxt, nL, nR, nlp, nrp, ns, nkk);
+      if (nq != q) {  // product done: fold it into the running sum
+#pragma unroll
+        for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+          for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+            for (int x = 0; x < 4; x++) {
+              two_sum_acc(hi[mt][nt][x], lo[mt][nt][x], acc[mt][nt][x]);
+              acc[mt][nt][x] = 0.f;
+            }
+      }
+      cur = nxt;
+      q = nq;
+      kk = nkk;
+      s = ns;
+      L = nL, R = nR, lplane = nlp, rplane = nrp;
+    }
+  }
+  // epilogue: C_ij = beta * C_in_ij + alpha * (hi + lo), formed in FP64
   const bool plain = (alpha == 1.0 && beta == 0.0);
+  const int cin = ws.c_cin[gb];
+  const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+  double *out = C.vals + C.blk_off[gb];
 #pragma unroll
   for (int mt = 0; mt < MT; mt++)
 #pragma unroll
@@ -434,103 +481,23 @@ __device__ __forceinline__ void split_epilogue(const float (&hi)[MT][NT][4],
       }
 }
 
-// The MMA problem of C block (m x n): the block or its transpose, whichever
-// needs fewer 16 x 8 tiles.
-__device__ __forceinline__ void mma_problem(int m, int n, bool &tr, int &Mp, int &Np) {
-  const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
-  const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
-  tr = tiles_t < tiles_n;
-  Mp = tr ? n : m;
-  Np = tr ? m : n;
-}
-
 // ---------------------------------------------------------------------------
-// Large blocks (an MMA problem beyond 16 x 16, up to 32 x 32): fragments
-// straight from global memory, 2 x 4 tiles.
-// ---------------------------------------------------------------------------
-template <int PREC>
-__global__ void __launch_bounds__(128) k_numeric_split_large(DevMat A, DevMat B, DevOut C,
-                                                             DevMat Cin,
-                                                             const void *__restrict__ a_left,
-                                                             const void *__restrict__ b_right,
-                                                             double alpha, double beta, DevWs ws,
-                                                             const DevStatus *st,
-                                                             const int32_t *__restrict__ items,
-                                                             const int64_t *__restrict__ seg) {
-  if (st->overflow) return;
-  constexpr int BPV = (PREC == BSM_PREC_SPLIT_BF16X3) ? kBf16BytesPerValue : kTf32BytesPerValue;
-  int64_t wb = 0, we = st->nblk_c;
-  if (seg) {
-    wb = seg[0];
-    we = seg[1];
-  }
-  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = wb + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); w < we;
-       w += nwarp) {
-    const int64_t gb = items ? items[w] : w;
-    const int i = C.blk_row[gb], j = C.col_idx[gb];
-    const int m = C.row_sizes[i], n = C.col_sizes[j];
-    bool tr;
-    int Mp, Np;
-    mma_problem(m, n, tr, Mp, Np);
-    if (Mp <= 16 && Np <= 16) continue;  // the pipelined kernel takes these
-    float hi[2][4][4], lo[2][4][4], acc[2][4][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-      for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-        for (int x = 0; x < 4; x++) hi[mt][nt][x] = lo[mt][nt][x] = acc[mt][nt][x] = 0.f;
-    const int64_t p0 = ws.prod_ptr[gb], p1 = ws.prod_ptr[gb + 1];
-    for (int64_t p = p0; p < p1; p++) {
-      const int2 pr = ws.prods[p];
-      const int s = A.col_sizes[A.col_idx[pr.x]];
-      const unsigned char *Al = static_cast<const unsigned char *>(a_left) + BPV * A.blk_off[pr.x];
-      const unsigned char *Br = static_cast<const unsigned char *>(b_right) + BPV * B.blk_off[pr.y];
-      int str, apl, bpl;
-      layout_dims<PREC>(m, s, str, apl);
-      layout_dims<PREC>(n, s, str, bpl);
-      const unsigned char *Lg = tr ? Br : Al, *Rg = tr ? Al : Br;
-      const int lplane = tr ? bpl : apl, rplane = tr ? apl : bpl;
-      int nsteps;
-      run_steps_prologue<PREC>(s, nsteps);
-      for (int stp = 0; stp < nsteps; stp++) {
-        int kk;
-        bool k8;
-        step_pos<PREC>(stp, s, kk, k8);
-        split_step<PREC, 2, 4, false>(acc, Lg, Rg, 0u, 0u, str, str, lplane, rplane, kk, k8, Mp,
-                                      Np);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-        for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-          for (int x = 0; x < 4; x++) {
-            two_sum_acc(hi[mt][nt][x], lo[mt][nt][x], acc[mt][nt][x]);
-            acc[mt][nt][x] = 0.f;
-          }
-    }
-    const int cin = ws.c_cin[gb];
-    split_epilogue<2, 4>(hi, lo, alpha, beta, (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr,
-                         C.vals + C.blk_off[gb], m, tr, Mp, Np);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Blocks whose MMA problem fits 16 x 16 (the water and small-block case). Each
-// warp streams the layouts of its C block's products through a ring of
-// kStages shared-memory slots with 16-byte asynchronous copies (cp.async),
-// kStages - 1 products ahead of the tensor-core work. The (A offset, B offset,
-// k) of the products are read 32 at a time into a per-warp table in shared
-// memory. The FP32 partial sum is folded into the compensated running sum
-// every kFold products.
+// Pipelined kernel for blocks whose MMA problem fits 16 x 16 (the water and
+// small-block case). Each warp streams the slices of its C block's products
+// through a ring of kStages shared-memory slots with 16-byte asynchronous
+// copies (cp.async), kStages - 1 products ahead of the tensor-core work, so the
+// L2 latency of a product's operands is hidden behind the products before it.
+// The (A offset, B offset, k) of the products are read 32 at a time into a
+// per-warp table in shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kStages = 4;
 constexpr int kPipeWarps = 4;
+// Products summed plainly in FP32 before each compensated fold: a partial sum
+// of kFold products carries kFold times the rounding of one, still far below
+// the slice truncation error, and the fold costs 6 FP32 operations per value.
+constexpr int kFold = 4;
 constexpr int kMetaEntries = 64;
 constexpr int kMetaBytes = kMetaEntries * (8 + 8 + 4);
-constexpr int kFold = 4;
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gptr) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gptr) : "memory");
@@ -542,11 +509,16 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+__device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(saddr));
+  return v;
+}
 
-// Bytes of one operand slot: 16 rows (or columns) of the padded largest k.
+// Bytes of one operand slot: BF16 3 planes of at most 16 x sp halfwords, TF32
+// 2 planes of at most 16 x s words (multiples of 16 bytes).
 __host__ __device__ __forceinline__ int pipe_operand_bytes(int precision, int smax) {
-  return precision == BSM_PREC_SPLIT_BF16X3 ? 3 * 16 * 2 * kpad_bf16(smax)
-                                            : 2 * 16 * 4 * kpad_tf32(smax);
+  return precision == BSM_PREC_SPLIT_BF16X3 ? 96 * (smax + (smax & 1)) : 128 * smax;
 }
 __host__ __device__ __forceinline__ int pipe_warp_bytes(int precision, int smax) {
   return kStages * 2 * pipe_operand_bytes(precision, smax) + kMetaBytes;
@@ -559,9 +531,11 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
                          const DevStatus *st, const int32_t *__restrict__ items,
                          const int64_t *__restrict__ seg, int smax, int only_small) {
   if (st->overflow) return;
-  constexpr int BPV = (PREC == BSM_PREC_SPLIT_BF16X3) ? kBf16BytesPerValue : kTf32BytesPerValue;
+  constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
+  constexpr int KSTEP = BF ? 16 : 8;
   extern __shared__ __align__(16) unsigned char smem_pipe[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
   const int opb = pipe_operand_bytes(PREC, smax);
   unsigned char *wbase = smem_pipe + warp * pipe_warp_bytes(PREC, smax);
   int64_t *meta_a = reinterpret_cast<int64_t *>(wbase + kStages * 2 * opb);
@@ -575,23 +549,26 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
     we = seg[1];
   }
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool plain = (alpha == 1.0 && beta == 0.0);
   for (int64_t w = wb + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); w < we;
        w += nwarp) {
     const int64_t gb = items ? items[w] : w;
     const int i = C.blk_row[gb], j = C.col_idx[gb];
     const int m = C.row_sizes[i], n = C.col_sizes[j];
-    bool tr;
-    int Mp, Np;
-    mma_problem(m, n, tr, Mp, Np);
+    const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
+    const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
+    const bool tr = tiles_t < tiles_n;
+    const int Mp = tr ? n : m, Np = tr ? m : n;
     if (only_small && !(Mp <= 16 && Np <= 16)) continue;
+    const int mp2 = m + (m & 1), np2 = n + (n & 1);
     const int64_t p0 = ws.prod_ptr[gb];
     const int np = (int)(ws.prod_ptr[gb + 1] - p0);
 
-    float hi[1][2][4], lo[1][2][4], acc[1][2][4];
+    float hi[2][4], lo[2][4], acc[2][4];
 #pragma unroll
     for (int nt = 0; nt < 2; nt++)
 #pragma unroll
-      for (int x = 0; x < 4; x++) hi[0][nt][x] = lo[0][nt][x] = acc[0][nt][x] = 0.f;
+      for (int x = 0; x < 4; x++) hi[nt][x] = lo[nt][x] = acc[nt][x] = 0.f;
 
     // copies of product q into slot q % kStages; always commits one group
     auto issue = [&](int q) {
@@ -607,15 +584,15 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
           __syncwarp();
         }
         const int s = meta_s[q & (kMetaEntries - 1)];
-        int str, apl, bpl;
-        layout_dims<PREC>(m, s, str, apl);
-        layout_dims<PREC>(n, s, str, bpl);
-        const unsigned char *srcA =
-            static_cast<const unsigned char *>(a_left) + BPV * meta_a[q & (kMetaEntries - 1)];
-        const unsigned char *srcB =
-            static_cast<const unsigned char *>(b_right) + BPV * meta_b[q & (kMetaEntries - 1)];
-        const int bytesA = ((PREC == BSM_PREC_SPLIT_BF16X3) ? 3 : 2) * apl;
-        const int bytesB = ((PREC == BSM_PREC_SPLIT_BF16X3) ? 3 : 2) * bpl;
+        const int sp = s + (s & 1);
+        const unsigned char *srcA = static_cast<const unsigned char *>(a_left) +
+                                    (BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue) *
+                                        meta_a[q & (kMetaEntries - 1)];
+        const unsigned char *srcB = static_cast<const unsigned char *>(b_right) +
+                                    (BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue) *
+                                        meta_b[q & (kMetaEntries - 1)];
+        const int bytesA = BF ? 6 * mp2 * sp : 8 * m * s;
+        const int bytesB = BF ? 6 * sp * np2 : 8 * s * n;
         const uint32_t dst = sbase + (uint32_t)((q % kStages) * 2 * opb);
         for (int c = lane; c < (bytesA + 15) >> 4; c += 32) cp_async16(dst + 16 * c, srcA + 16 * c);
         for (int c = lane; c < (bytesB + 15) >> 4; c += 32)
@@ -631,36 +608,151 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
       __syncwarp();
       issue(q + kStages - 1);  // into the slot consumed by the previous product
       const int s = meta_s[q & (kMetaEntries - 1)];
-      int str, apl, bpl;
-      layout_dims<PREC>(m, s, str, apl);
-      layout_dims<PREC>(n, s, str, bpl);
+      const int sp = s + (s & 1);
       const uint32_t sA = sbase + (uint32_t)((q % kStages) * 2 * opb), sB = sA + opb;
+      // L (M' x s, row-major) and R (s x N', column-major) in the slot
       const uint32_t sL = tr ? sB : sA, sR = tr ? sA : sB;
-      const int lplane = tr ? bpl : apl, rplane = tr ? apl : bpl;
-      int nsteps;
-      run_steps_prologue<PREC>(s, nsteps);
-      for (int stp = 0; stp < nsteps; stp++) {
-        int kk;
-        bool k8;
-        step_pos<PREC>(stp, s, kk, k8);
-        split_step<PREC, 1, 2, true>(acc, nullptr, nullptr, sL, sR, str, str, lplane, rplane, kk,
-                                     k8, Mp, Np);
+      if (BF) {
+        const int lplane = 2 * (tr ? sp * np2 : mp2 * sp), rplane = 2 * (tr ? mp2 * sp : sp * np2);
+        for (int kk = 0; kk < s; kk += KSTEP) {
+          const bool k8 = (s - kk) <= 8;
+          const int k0 = kk + 2 * t, k1 = k0 + 8;
+          const int r0 = g, r1 = g + 8;
+          uint32_t a[3][4], b[3][2][2];
+#pragma unroll
+          for (int q3 = 0; q3 < 3; q3++) {
+            const uint32_t P = sL + q3 * lplane, Q = sR + q3 * rplane;
+            a[q3][0] = (r0 < Mp && k0 < sp) ? lds32(P + 2 * (r0 * sp + k0)) : 0u;
+            a[q3][1] = (r1 < Mp && k0 < sp) ? lds32(P + 2 * (r1 * sp + k0)) : 0u;
+            a[q3][2] = (!k8 && r0 < Mp && k1 < sp) ? lds32(P + 2 * (r0 * sp + k1)) : 0u;
+            a[q3][3] = (!k8 && r1 < Mp && k1 < sp) ? lds32(P + 2 * (r1 * sp + k1)) : 0u;
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+              const int c = nt * 8 + g;
+              b[q3][nt][0] = (c < Np && k0 < sp) ? lds32(Q + 2 * (c * sp + k0)) : 0u;
+              b[q3][nt][1] = (!k8 && c < Np && k1 < sp) ? lds32(Q + 2 * (c * sp + k1)) : 0u;
+            }
+          }
+          constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
+          constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+          for (int nt = 0; nt < 2; nt++) {
+            if (nt * 8 >= Np) continue;
+#pragma unroll
+            for (int pq = 0; pq < 6; pq++) {
+              if (k8)
+                mma_bf16_k8(acc[nt], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][nt][0]);
+              else
+                mma_bf16_k16(acc[nt], a[PA[pq]], b[PB[pq]][nt][0], b[PB[pq]][nt][1]);
+            }
+          }
+        }
+      } else {
+        const int lplane = 4 * (tr ? s * n : m * s), rplane = 4 * (tr ? m * s : s * n);
+        for (int kk = 0; kk < s; kk += KSTEP) {
+          const int k0 = kk + t, k1 = k0 + 4;
+          const int r0 = g, r1 = g + 8;
+          uint32_t a[2][4], b[2][2][2];
+#pragma unroll
+          for (int q2 = 0; q2 < 2; q2++) {
+            const uint32_t P = sL + q2 * lplane, Q = sR + q2 * rplane;
+            a[q2][0] = (r0 < Mp && k0 < s) ? lds32(P + 4 * (r0 * s + k0)) : 0u;
+            a[q2][1] = (r1 < Mp && k0 < s) ? lds32(P + 4 * (r1 * s + k0)) : 0u;
+            a[q2][2] = (r0 < Mp && k1 < s) ? lds32(P + 4 * (r0 * s + k1)) : 0u;
+            a[q2][3] = (r1 < Mp && k1 < s) ? lds32(P + 4 * (r1 * s + k1)) : 0u;
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++) {
+              const int c = nt * 8 + g;
+              b[q2][nt][0] = (c < Np && k0 < s) ? lds32(Q + 4 * (c * s + k0)) : 0u;
+              b[q2][nt][1] = (c < Np && k1 < s) ? lds32(Q + 4 * (c * s + k1)) : 0u;
+            }
+          }
+          constexpr int PA[3] = {1, 0, 0};
+          constexpr int PB[3] = {0, 1, 0};
+#pragma unroll
+          for (int nt = 0; nt < 2; nt++) {
+            if (nt * 8 >= Np) continue;
+#pragma unroll
+            for (int pq = 0; pq < 3; pq++)
+              mma_tf32_k8(acc[nt], a[PA[pq]], b[PB[pq]][nt][0], b[PB[pq]][nt][1]);
+          }
+        }
       }
+      // every kFold products (and after the last): fold the FP32 partial sum
+      // into the compensated running sum
       if ((q % kFold) == kFold - 1 || q == np - 1) {
 #pragma unroll
         for (int nt = 0; nt < 2; nt++)
 #pragma unroll
           for (int x = 0; x < 4; x++) {
-            two_sum_acc(hi[0][nt][x], lo[0][nt][x], acc[0][nt][x]);
-            acc[0][nt][x] = 0.f;
+            two_sum_acc(hi[nt][x], lo[nt][x], acc[nt][x]);
+            acc[nt][x] = 0.f;
           }
       }
     }
     cp_async_wait<0>();
     __syncwarp();
+
     const int cin = ws.c_cin[gb];
-    split_epilogue<1, 2>(hi, lo, alpha, beta, (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr,
-                         C.vals + C.blk_off[gb], m, tr, Mp, Np);
+    const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+    double *out = C.vals + C.blk_off[gb];
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int rr = g + ((x >> 1) << 3);
+        const int cc = nt * 8 + 2 * t + (x & 1);
+        if (rr < Mp && cc < Np) {
+          const int row = tr ? cc : rr, col = tr ? rr : cc;
+          const int64_t e = (int64_t)col * m + row;
+          double v = f32_to_f64_exact(hi[nt][x]) + f32_to_f64_exact(lo[nt][x]);
+          if (!plain) {
+            v = alpha * v;
+            if (cinv) v = fma(beta, cinv[e], v);
+          }
+          out[e] = v;
+        }
+      }
+  }
+}
+
+// One warp per C block (grid-stride over the work list). SIZES selects the
+// blocks a launch takes: 0 all (every MMA problem fits 16 x 16), 1 those that
+// fit 16 x 16, 2 the others (up to 32 x 32). Small blocks use 1 x 2 tiles with
+// prefetching; large ones 2 x 4 tiles without (register budget).
+template <int PREC, int SIZES>
+__global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOut C, DevMat Cin,
+                                                       const void *__restrict__ a_left,
+                                                       const void *__restrict__ b_right,
+                                                       double alpha, double beta, DevWs ws,
+                                                       const DevStatus *st,
+                                                       const int32_t *__restrict__ items,
+                                                       const int64_t *__restrict__ seg) {
+  if (st->overflow) return;
+  int64_t wb = 0, we = st->nblk_c;
+  if (seg) {
+    wb = seg[0];
+    we = seg[1];
+  }
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = wb + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); w < we;
+       w += nwarp) {
+    const int64_t gb = items ? items[w] : w;
+    const int i = C.blk_row[gb], j = C.col_idx[gb];
+    const int m = C.row_sizes[i], n = C.col_sizes[j];
+    const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
+    const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
+    const bool tr = tiles_t < tiles_n;
+    const int Mp = tr ? n : m, Np = tr ? m : n;
+    const bool small = (Mp <= 16 && Np <= 16);
+    if (SIZES == 2) {
+      if (!small)
+        split_cblock<PREC, 2, 4, false>(A, B, C, Cin, a_left, b_right, alpha, beta, ws, gb, m, n,
+                                        tr, Mp, Np);
+    } else if (SIZES == 0 || small) {
+      split_cblock<PREC, 1, 2, true>(A, B, C, Cin, a_left, b_right, alpha, beta, ws, gb, m, n, tr,
+                                     Mp, Np);
+    }
   }
 }
 
@@ -668,13 +760,13 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
                                  DevMat Cin, const void *a_left, const void *b_right, double alpha,
                                  double beta, DevWs ws, const DevStatus *st, const int32_t *items,
                                  const int64_t *seg, int smax, int nsm, cudaStream_t stream) {
-  if (sizes == 2) {  // blocks beyond 16 x 16
+  if (sizes == 2) {  // blocks beyond 16 x 16: direct fragment loads, 2 x 4 tiles
     const int grid = nsm * 2;
     if (precision == BSM_PREC_SPLIT_BF16X3)
-      k_numeric_split_large<BSM_PREC_SPLIT_BF16X3><<<grid, 128, 0, stream>>>(
+      k_numeric_split<BSM_PREC_SPLIT_BF16X3, 2><<<grid, 128, 0, stream>>>(
           A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg);
     else
-      k_numeric_split_large<BSM_PREC_SPLIT_TF32X2><<<grid, 128, 0, stream>>>(
+      k_numeric_split<BSM_PREC_SPLIT_TF32X2, 2><<<grid, 128, 0, stream>>>(
           A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg);
     return cudaGetLastError();
   }
