@@ -40,6 +40,11 @@ WORKLOADS = {
     "se40000": dict(kind="sparse", n=40000, bs=6, occ=5e-4, seed=5, eps=1e-10),
 }
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
+# FP64 numeric kernels (BSM_FP64_*): name -> (number, kernel symbol)
+FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64_t16"),
+                "t32": (2, "k_numeric_fp64_t32"), "pkb2": (3, "k_numeric_fp64_pk"),
+                "pkb3": (4, "k_numeric_fp64_pk")}
+FP64_BY_NUMBER = {v[0]: k for k, v in FP64_KERNELS.items()}
 
 
 def measured_peak(key, fallback):
@@ -337,6 +342,8 @@ def main():
                     help="filter threshold at this percentile of the candidate norm products")
     ap.add_argument("--graph", action="store_true", help="replay the multiply as a CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="tune the FP64 kernel variants first")
+    ap.add_argument("--fp64-kernel", default=None, choices=sorted(FP64_KERNELS),
+                    help="force one FP64 numeric kernel (default: the library's choice)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true", help="the request-loop benchmark instead")
@@ -373,9 +380,10 @@ def main():
     ctx = Context(local)
     dA = ctx.from_blocks(A)
     dC = ctx.empty(A.row_sizes, A.col_sizes)
-    kw = dict(precision=prec, launch=launch, graph=args.graph, autotune=args.autotune)
+    fk = None if args.fp64_kernel is None else FP64_KERNELS[args.fp64_kernel][0]
+    kw = dict(precision=prec, launch=launch, graph=args.graph, autotune=args.autotune, fp64_kernel=fk)
     st = ctx.multiply(1.0, dA, dA, 0.0, dC, eps, precision=prec, launch=launch,
-                      autotune=args.autotune, stats=True)
+                      autotune=args.autotune, fp64_kernel=fk, stats=True)
     flops = st.flops
     s = torch.cuda.Stream()
     for _ in range(args.warmup):
@@ -408,7 +416,8 @@ def main():
     # replay the phases are not timed separately: the whole multiply is used.
     if prof.multiplies > 0:
         num_ms = prof.ms_numeric / prof.multiplies
-        kname = "k_numeric_fp64_t16" if args.precision == "fp64" else "k_numeric_split_pipe"
+        kname = (FP64_KERNELS[FP64_BY_NUMBER[prof.last_fp64_kernel]][1] if args.precision == "fp64"
+                 else "k_numeric_split_pipe")
     else:
         num_ms = total_ms / args.steps
         kname = "whole multiply (CUDA graph replay)"
@@ -449,14 +458,14 @@ def main():
         Ce = ctx.empty(rs, cs)
         for _ in range(2):
             Ae = ctx.matrix(rs, cs, br, bc, pin_vals)
-            ctx.multiply(1.0, Ae, Ae, 0.0, Ce, eps, precision=prec, launch=launch)
+            ctx.multiply(1.0, Ae, Ae, 0.0, Ce, eps, precision=prec, launch=launch, fp64_kernel=fk)
             Ce.values(out=pin_out)
             Ae.destroy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             Ae = ctx.matrix(rs, cs, br, bc, pin_vals)
-            ctx.multiply(1.0, Ae, Ae, 0.0, Ce, eps, precision=prec, launch=launch)
+            ctx.multiply(1.0, Ae, Ae, 0.0, Ce, eps, precision=prec, launch=launch, fp64_kernel=fk)
             Ce.values(out=pin_out)
             Ae.destroy()
         dt = time.perf_counter() - t0
@@ -490,6 +499,8 @@ def main():
             "config": {"workload": args.workload, "atoms": A.nbr, "dimension": int(A.row_sizes.sum()),
                        "eps": eps, "precision": args.precision, "launch": args.launch,
                        "graph": bool(args.graph), "autotune": bool(args.autotune),
+                       "fp64_kernel": (FP64_BY_NUMBER.get(prof.last_fp64_kernel)
+                                       if args.precision == "fp64" else None),
                        "a_blocks": A.nblk, "c_blocks": nb_c, "c_nnz": nnz_c,
                        "kept_products": st.kept, "dropped_products": st.dropped,
                        "gflop_per_multiply": round(flops / 1e9, 4),

@@ -65,6 +65,25 @@ enum {
   BSM_PREC_SPLIT_TF32X2 = 2  /* 2 TF32 slices per operand, 3 slice products, FP32 sums */
 };
 
+/* FP64 numeric kernels. bsm_opts.fp64_kernel = 1 + one of these forces that
+ * kernel for every shape class (no autotuning); 0 leaves the choice to the
+ * library: the tuned one with autotune, else PK_B2, or T16_B2 when the last
+ * multiply into the same C had fewer than 4 block products per C block (there
+ * the per-block setup of PK costs more than its fuller lanes save).
+ *   T16: one output element per lane slot, 16 x 16 tiles, 2 or 3 blocks/SM;
+ *   T32: 32 x 32 tiles, synchronous staging;
+ *   PK:  packed lane slots (output element, k-group) over the products of a C
+ *        block concatenated along k, 16 x 16 tiles, 2 or 3 blocks/SM.
+ * All give the same result up to the order of the FP64 additions. */
+enum {
+  BSM_FP64_T16_B2 = 0,
+  BSM_FP64_T16_B3 = 1,
+  BSM_FP64_T32 = 2,
+  BSM_FP64_PK_B2 = 3,
+  BSM_FP64_PK_B3 = 4,
+  BSM_FP64_NUM_KERNELS = 5
+};
+
 /* How the numeric stacks are launched. */
 enum {
   BSM_LAUNCH_PERSISTENT = 0, /* one persistent launch over all shape classes */
@@ -86,7 +105,8 @@ typedef struct {
   void *stream;      /* cudaStream_t to use instead of the context stream, or NULL */
   int32_t graph;     /* 1: capture the multiply's launches in a CUDA graph the first
                         time a given set of arguments is met and replay it after */
-  int32_t reserved;
+  int32_t fp64_kernel; /* 0, or 1 + BSM_FP64_* to force that FP64 kernel (ignored by
+                          the split precisions); out of range: BSM_ERR_INVALID_ARG */
 } bsm_opts;
 
 /* Counters of one multiply (filled when bsm_stats* is not NULL; this makes
@@ -175,6 +195,9 @@ typedef struct {
   double ms_total;     /* ... of whole multiplies */
   int64_t multiplies;  /* multiplies profiled */
   int64_t launches;    /* kernels launched by this context since profiling started */
+  int32_t last_fp64_kernel; /* BSM_FP64_* of the last FP64 numeric launch enqueued by the
+                               context (forced, tuned or default), -1 if none */
+  int32_t reserved;
 } bsm_profile;
 
 /* enable != 0: start profiling (totals reset); enable == 0: stop. */

@@ -11,6 +11,12 @@ by every tick of Algorithms 1 and 2. Every step runs in the CUDA kernels of
 marshals arguments (see :mod:`paper_1705_10218_gb300.bsm`).
 """
 from .bsm import (  # noqa: F401
+    BSM_FP64_NUM_KERNELS,
+    BSM_FP64_PK_B2,
+    BSM_FP64_PK_B3,
+    BSM_FP64_T16_B2,
+    BSM_FP64_T16_B3,
+    BSM_FP64_T32,
     BSM_LAUNCH_PER_STACK,
     BSM_LAUNCH_PERSISTENT,
     BSM_PREC_FP64,

@@ -25,6 +25,12 @@ BSM_PREC_SPLIT_BF16X3 = 1
 BSM_PREC_SPLIT_TF32X2 = 2
 BSM_LAUNCH_PERSISTENT = 0
 BSM_LAUNCH_PER_STACK = 1
+BSM_FP64_T16_B2 = 0
+BSM_FP64_T16_B3 = 1
+BSM_FP64_T32 = 2
+BSM_FP64_PK_B2 = 3
+BSM_FP64_PK_B3 = 4
+BSM_FP64_NUM_KERNELS = 5
 
 
 class BsmError(RuntimeError):
@@ -46,7 +52,7 @@ class _Opts(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("graph", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("fp64_kernel", ctypes.c_int32),
     ]
 
 
@@ -72,6 +78,8 @@ class _Profile(ctypes.Structure):
         ("ms_total", ctypes.c_double),
         ("multiplies", ctypes.c_int64),
         ("launches", ctypes.c_int64),
+        ("last_fp64_kernel", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -83,6 +91,7 @@ class Profile:
     ms_total: float
     multiplies: int
     launches: int
+    last_fp64_kernel: int  # BSM_FP64_* of the last FP64 numeric launch, -1 if none
 
 
 @dataclass
@@ -192,9 +201,12 @@ class Context:
     def multiply(self, alpha, A: "Matrix", B: "Matrix", beta, C: "Matrix", eps: float = 0.0, *,
                  precision: int = BSM_PREC_FP64, launch: int = BSM_LAUNCH_PERSISTENT,
                  blocking: bool = False, autotune: bool = False, stream=None,
-                 graph: bool = False, stats: bool = False) -> Stats | None:
+                 graph: bool = False, stats: bool = False, fp64_kernel: int | None = None) -> Stats | None:
+        """fp64_kernel: one of BSM_FP64_* to force that FP64 kernel, None for the
+        library's choice."""
         o = _Opts(int(precision), int(launch), int(bool(blocking)), int(bool(autotune)),
-                  _stream_ptr(stream), int(bool(graph)), 0)
+                  _stream_ptr(stream), int(bool(graph)),
+                  0 if fp64_kernel is None else int(fp64_kernel) + 1)
         st = _Stats() if stats else None
         rc = lib().bsm_multiply(self._h, float(alpha), A._h, B._h, float(beta), C._h, float(eps),
                                 ctypes.byref(o), ctypes.byref(st) if st is not None else None)
@@ -217,7 +229,8 @@ class Context:
     def profile_read(self) -> Profile:
         p = _Profile()
         _check(lib().bsm_ctx_profile_read(self._h, ctypes.byref(p)), "bsm_ctx_profile_read")
-        return Profile(p.ms_norms, p.ms_symbolic, p.ms_numeric, p.ms_total, p.multiplies, p.launches)
+        return Profile(p.ms_norms, p.ms_symbolic, p.ms_numeric, p.ms_total, p.multiplies, p.launches,
+                       p.last_fp64_kernel)
 
     def close(self):
         if self._h:

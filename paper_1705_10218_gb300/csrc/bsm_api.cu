@@ -125,6 +125,7 @@ struct bsm_ctx_s {
   cudaEvent_t ev_last = nullptr;   // last work of this context (any stream)
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
   DevStatus *d_status = nullptr;
+  unsigned long long *d_work = nullptr;  // work counter of the dynamically scheduled kernels
   DevStatus *h_slots = nullptr;    // pinned ring of status copies
   cudaEvent_t slot_ev[kSlots] = {};
   bsm_mat slot_owner[kSlots] = {};
@@ -139,6 +140,7 @@ struct bsm_ctx_s {
   cudaEvent_t prof_ev[kSlots][4] = {};
   bool prof_pending[kSlots] = {};
   bsm_profile prof_tot{};
+  int last_fp64 = -1;  // BSM_FP64_* of the last FP64 numeric launch
   int64_t launches = 0;
   int64_t launches_at_enable = 0;
   // shape-class grouping (per-stack launches)
@@ -413,7 +415,7 @@ static void tune_save(bsm_ctx ctx, const std::string &key, int v, double ms) {
 }
 
 static bool needs_tuning(bsm_ctx ctx, bsm_mat A, bsm_mat B, const bsm_opts &o) {
-  if (!o.autotune || o.precision != BSM_PREC_FP64) return false;
+  if (!o.autotune || o.precision != BSM_PREC_FP64 || o.fp64_kernel) return false;
   if (o.launch != BSM_LAUNCH_PER_STACK) return !ctx->tune.count(tune_key_all(A, B));
   for (int32_t m : A->row_kinds)
     for (int32_t n : B->col_kinds)
@@ -421,9 +423,25 @@ static bool needs_tuning(bsm_ctx ctx, bsm_mat A, bsm_mat B, const bsm_opts &o) {
   return false;
 }
 
-static int variant_or_default(bsm_ctx ctx, const std::string &key) {
+static_assert(kFp64T16B2 == BSM_FP64_T16_B2 && kFp64T16B3 == BSM_FP64_T16_B3 &&
+                  kFp64T32 == BSM_FP64_T32 && kFp64PkB2 == BSM_FP64_PK_B2 &&
+                  kFp64PkB3 == BSM_FP64_PK_B3 && kFp64NumVariants == BSM_FP64_NUM_KERNELS,
+              "public and internal FP64 kernel numbers differ");
+
+// The default FP64 kernel for a result C: the packed kernel, unless the last
+// multiply into C had fewer than 4 block products per C block (the sizes of
+// the previous result, or of this one once the symbolic totals were read).
+static int fp64_default(bsm_ctx ctx, bsm_mat C) {
+  if (C->hint_blk > 0 && ctx->hint_prod < 4 * C->hint_blk) return kFp64T16B2;
+  return kFp64PkB2;
+}
+
+// The forced kernel, else the tuned one, else the default.
+static int variant_or_default(bsm_ctx ctx, bsm_mat C, const bsm_opts &o,
+                              const std::string &key) {
+  if (o.fp64_kernel > 0) return o.fp64_kernel - 1;
   auto it = ctx->tune.find(key);
-  return it == ctx->tune.end() ? kFp64T16B2 : it->second;
+  return it == ctx->tune.end() ? fp64_default(ctx, C) : it->second;
 }
 
 struct Launch {
@@ -492,10 +510,14 @@ static int launch_numeric(Launch &L, int variant, const int32_t *items, const in
                               L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
                               smax, ctx->nsm, L.s));
     }
-  } else
+  } else {
+    if (fp64_variant_uses_work(variant))
+      CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
+    ctx->last_fp64 = variant;
     CK(launch_numeric_fp64(variant, L.dA, L.dB, L.out, L.dC, L.alpha, L.beta, L.ws,
                            ctx->d_status, items, seg,
-                           ctx->nsm * fp64_variant_blocks_per_sm(variant), L.s));
+                           ctx->nsm * fp64_variant_blocks_per_sm(variant), ctx->d_work, L.s));
+  }
   ctx->launches++;
   return BSM_OK;
 }
@@ -542,8 +564,8 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
       const int m = L.A->row_kinds[c / ncc], n = L.B->col_kinds[c % ncc];
       const std::string key = tune_key_class(m, n);
       const int64_t *seg = ctx->cls_segs + 2 * c;
-      if (may_tune && L.o.autotune && !L.split && !ctx->tune.count(key)) {
-        int best = kFp64T16B2;
+      if (may_tune && L.o.autotune && !L.o.fp64_kernel && !L.split && !ctx->tune.count(key)) {
+        int best = fp64_default(ctx, L.C);
         double best_ms = 1e30;
         for (int v = 0; v < kFp64NumVariants; v++) {
           double ms;
@@ -552,13 +574,13 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
         }
         tune_save(ctx, key, best, best_ms);
       }
-      if ((rc = launch_numeric(L, variant_or_default(ctx, key), ctx->cls_items, seg, m, n)))
+      if ((rc = launch_numeric(L, variant_or_default(ctx, L.C, L.o, key), ctx->cls_items, seg, m, n)))
         return rc;
     }
   } else {
     const std::string key = tune_key_all(L.A, L.B);
-    if (may_tune && L.o.autotune && !L.split && !ctx->tune.count(key)) {
-      int best = kFp64T16B2;
+    if (may_tune && L.o.autotune && !L.o.fp64_kernel && !L.split && !ctx->tune.count(key)) {
+      int best = fp64_default(ctx, L.C);
       double best_ms = 1e30;
       for (int v = 0; v < kFp64NumVariants; v++) {
         double ms;
@@ -568,7 +590,7 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
       }
       tune_save(ctx, key, best, best_ms);
     }
-    if ((rc = launch_numeric(L, variant_or_default(ctx, key), nullptr, nullptr, L.A->max_row,
+    if ((rc = launch_numeric(L, variant_or_default(ctx, L.C, L.o, key), nullptr, nullptr, L.A->max_row,
                              L.B->max_col)))
       return rc;
   }
@@ -603,7 +625,8 @@ static void graph_key(const Launch &L, std::vector<uint64_t> &k) {
   num(w.cap_prod), num(L.out.cap_blk), num(L.out.cap_nnz);
   put(L.ctx->cls_items), put(L.s);
   dbl(L.alpha), dbl(L.beta), dbl(L.eps);
-  num(L.o.precision), num(L.o.launch), num((int64_t)L.ctx->tune_version);
+  num(L.o.precision), num(L.o.launch), num(L.o.fp64_kernel), num((int64_t)L.ctx->tune_version);
+  num(fp64_default(L.ctx, L.C));
 }
 
 // Enqueue one multiply. sync_sizes: read the totals back after the scan and
@@ -800,6 +823,7 @@ int bsm_ctx_create(int device, bsm_ctx *out) {
       (e = cudaEventCreate(&ctx->ev_t0)) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev_t1)) != cudaSuccess ||
       (e = cudaMalloc((void **)&ctx->d_status, sizeof(DevStatus))) != cudaSuccess ||
+      (e = cudaMalloc((void **)&ctx->d_work, sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMallocHost((void **)&ctx->h_slots, kSlots * sizeof(DevStatus))) != cudaSuccess) {
     rc = cuda_fail(e, "bsm_ctx_create");
   }
@@ -855,6 +879,7 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   dev_free(w.prod_ptr);
   dev_free(w.prods);
   dev_free(ctx->d_status);
+  dev_free(ctx->d_work);
   dev_free(ctx->cls_items);
   dev_free(ctx->cls_counts);
   dev_free(ctx->cls_cursor);
@@ -1036,6 +1061,7 @@ int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, b
     return BSM_ERR_INVALID_ARG;
   if (o.launch != BSM_LAUNCH_PERSISTENT && o.launch != BSM_LAUNCH_PER_STACK)
     return BSM_ERR_INVALID_ARG;
+  if (o.fp64_kernel < 0 || o.fp64_kernel > BSM_FP64_NUM_KERNELS) return BSM_ERR_INVALID_ARG;
   if (A->nbc != B->nbr || A->h_col_sizes != B->h_row_sizes) return BSM_ERR_DIM_MISMATCH;
   if (C->nbr != A->nbr || C->nbc != B->nbc || C->h_row_sizes != A->h_row_sizes ||
       C->h_col_sizes != B->h_col_sizes)
@@ -1214,6 +1240,8 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out) {
     if ((rc = prof_collect(ctx, s))) return rc;
   *out = ctx->prof_tot;
   out->launches = ctx->launches - ctx->launches_at_enable;
+  out->last_fp64_kernel = ctx->last_fp64;
+  out->reserved = 0;
   return BSM_OK;
 }
 

@@ -92,17 +92,29 @@ cudaError_t launch_symbolic_fill(DevMat A, DevMat B, DevMat Cin, int use_cin, do
                                  cudaStream_t stream);
 
 // FP64 numeric kernel variants (k_numeric_fp64.cu).
-enum { kFp64T16B2 = 0, kFp64T16B3 = 1, kFp64T32 = 2, kFp64NumVariants = 3 };
+enum {
+  kFp64T16B2 = 0,
+  kFp64T16B3 = 1,
+  kFp64T32 = 2,
+  kFp64PkB2 = 3,
+  kFp64PkB3 = 4,
+  kFp64NumVariants = 5
+};
 int fp64_variant_blocks_per_sm(int variant);
 // Per-device kernel attributes (call with the device current, outside capture).
 cudaError_t numeric_fp64_init();
 
 // items: optional work list of C block indices; seg: optional device [begin,
 // end) into it (default: all C blocks of the multiply, in row order).
+// work: a device counter that must be zero when the launch starts (used by the
+// pk variants, which hand out C blocks dynamically; may be null for the others).
 cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMat Cin,
                                 double alpha, double beta, DevWs ws, const DevStatus *st,
                                 const int32_t *items, const int64_t *seg, int grid,
-                                cudaStream_t stream);
+                                unsigned long long *work, cudaStream_t stream);
+inline bool fp64_variant_uses_work(int variant) {
+  return variant == kFp64PkB2 || variant == kFp64PkB3;
+}
 
 // Shape classes (k_classes.cu): class of C block g = row_cls[row] * ncc +
 // col_cls[col]; items receives the C blocks grouped by class, segs[2c..2c+1]

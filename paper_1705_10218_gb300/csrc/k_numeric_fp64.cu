@@ -14,7 +14,17 @@
 //        at once, one per lane, and handed out with warp shuffles. Compiled for
 //        2 or 3 thread blocks of 8 warps per SM.
 //   t32: 32 x 32 output tiles, synchronous staging, 4 warps per block.
-// Both take an optional work list (C block indices, e.g. one shape class) and
+//   pk:  "packed" lane slots for tiles of up to 16 x 16: a lane slot is a pair
+//        (output element, k-group), so a tile of te elements is computed by
+//        te * G slots in nT passes of 32 lanes, with nT and G chosen per tile
+//        shape so that te * G nearly fills 32 * nT (13 x 5: 65 elements, 7
+//        groups in 15 passes, 95% of the slots useful, where one element per
+//        slot uses 68%). The products of a C block are concatenated along k
+//        (the C block is one GEMM over the concatenated k), staged in chunks
+//        with 8-byte asynchronous copies, double buffered; group g sums the
+//        k positions congruent to g mod G, and the G partial sums of an
+//        element are added in group order at the end.
+// All take an optional work list (C block indices, e.g. one shape class) and
 // its [begin, end) range in device memory.
 #include <cstdlib>
 
@@ -258,10 +268,307 @@ __global__ void __launch_bounds__(kSWarps * 32, MINB)
   }
 }
 
+// ----------------------------------------------------------------------------
+// pk
+// ----------------------------------------------------------------------------
+constexpr int kPkWarps = 8;          // warps per thread block
+constexpr int kPkTile = 16;          // output tile edge
+constexpr int kPkSlots = 16;         // accumulator slots per lane (largest nT)
+constexpr int kPkMaxG = 8;           // largest number of k-groups
+constexpr int kPkMaxKC = 32;         // largest chunk (k positions)
+// Doubles per stage (two stages per warp): 880 fits 2 blocks of 8 warps per SM,
+// 560 fits 3. A tile of tm x tn takes chunks of KC k positions with
+// KC * tm + tn * (KC + 1) within the stage.
+template <int MINB>
+struct PkStage {
+  static constexpr int kDoubles = MINB >= 3 ? 560 : 880;
+};
+static_assert(32 * kPkSlots <= 560, "the slot sums must fit one stage");
+
+template <int MINB>
+size_t pk_smem_bytes() {
+  return (size_t)kPkWarps * 2 * PkStage<MINB>::kDoubles * sizeof(double);
+}
+
+// Slot shape of a tile of te (1..256) elements: the (nT, G) with nT <= kPkSlots,
+// G <= kPkMaxG and te * G <= 32 * nT that maximises te * G / (32 * nT), the
+// smallest nT among equals.
+struct PkShapes {
+  uint8_t nt[kPkTile * kPkTile + 1], g[kPkTile * kPkTile + 1];
+};
+constexpr PkShapes make_pk_shapes() {
+  PkShapes tab{};
+  for (int te = 1; te <= kPkTile * kPkTile; te++) {
+    int bt = (te + 31) / 32, bg = 1;
+    for (int t = 1; t <= kPkSlots; t++) {
+      int g = (32 * t) / te;
+      if (g > kPkMaxG) g = kPkMaxG;
+      if (g >= 1 && g * bt > bg * t) {
+        bt = t;
+        bg = g;
+      }
+    }
+    tab.nt[te] = (uint8_t)bt;
+    tab.g[te] = (uint8_t)bg;
+  }
+  return tab;
+}
+__constant__ PkShapes c_pk_shapes = make_pk_shapes();
+
+// floor(x / d) as (x * r) >> 16 with r = ceil(2^16 / d): exact while
+// x * (r * d - 2^16) < 2^16, i.e. for d <= 16 and x < 4096 (the error term is
+// below d).
+__device__ __forceinline__ uint32_t rcp16(uint32_t d) { return (65535u + d) / d; }
+__device__ __forceinline__ int div16(int x, uint32_t r) { return (int)(((uint32_t)x * r) >> 16); }
+
+__device__ __forceinline__ void cp_async8(double *sdst, const double *gsrc) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void pk_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void pk_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// C blocks a warp takes from the work counter at a time.
+constexpr int kPkGrab = 1;
+
+// `steps` steps of one chunk for a tile of NT slots per lane: slot t adds
+// sA[ia_t + u * G * tm] * sB[ib_t + u * G] at step u. NT is a compile-time
+// constant, so all loads of a step can be issued ahead of its FMAs; the step
+// loop itself is not unrolled (with 16 instances, unrolled copies overflow the
+// instruction cache on workloads with many tile shapes).
+template <int NT>
+__device__ __forceinline__ void pk_steps(const double *__restrict__ sA,
+                                         const double *__restrict__ sB,
+                                         const uint32_t (&idx)[kPkSlots],
+                                         double (&acc)[kPkSlots], int steps, int gtm, int G) {
+#pragma unroll 1  // one copy of the step body per NT keeps the instruction footprint small
+  for (int u = 0; u < steps; u++) {
+#pragma unroll
+    for (int t = 0; t < NT; t++) acc[t] = fma(sA[idx[t] & 0xFFFFu], sB[idx[t] >> 16], acc[t]);
+    sA += gtm;
+    sB += G;
+  }
+}
+
+// work: a counter that is zero when the launch starts; warps take the next
+// kPkGrab C blocks of the work range from it until the range is exhausted.
+template <int MINB>
+__global__ void __launch_bounds__(kPkWarps * 32, MINB)
+    k_numeric_fp64_pk(DevMat A, DevMat B, DevOut C, DevMat Cin, double alpha, double beta,
+                      DevWs ws, const DevStatus *st, const int32_t *items, const int64_t *seg,
+                      unsigned long long *work) {
+  if (st->overflow) return;
+  constexpr int kStage = PkStage<MINB>::kDoubles;
+  extern __shared__ double smem_pk[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double *wbuf = smem_pk + warp * 2 * kStage;
+  int64_t wb, we;
+  work_range(st, seg, wb, we);
+
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(work, (unsigned long long)kPkGrab);
+    const int64_t w0 = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    if (w0 >= we) break;
+    const int64_t w1 = (w0 + kPkGrab < we) ? w0 + kPkGrab : we;
+    for (int64_t w = w0; w < w1; w++) {
+      const int64_t gblk = items ? items[w] : w;
+      const int i = C.blk_row[gblk], j = C.col_idx[gblk];
+      const int m = C.row_sizes[i], n = C.col_sizes[j];
+      const int64_t p0 = ws.prod_ptr[gblk], p1 = ws.prod_ptr[gblk + 1];
+      const int cin = ws.c_cin[gblk];
+      const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+      double *out = C.vals + C.blk_off[gblk];
+
+      for (int r0 = 0; r0 < m; r0 += kPkTile) {
+        for (int c0 = 0; c0 < n; c0 += kPkTile) {
+          const int tm = min(kPkTile, m - r0), tn = min(kPkTile, n - c0);
+          const int te = tm * tn;
+          const int nT = c_pk_shapes.nt[te], G = c_pk_shapes.g[te];
+          const int used = te * G;
+          const uint32_t rtm = rcp16(tm), rg = rcp16(G);
+          // chunk length: the largest multiple of G with KC * tm + tn * (KC + 1) <= kStage
+          const int kfit = min(kPkMaxKC, (kStage - tn) / (tm + tn));
+          const int KC = G * div16(kfit, rg);
+          const int ldB = KC + 1;  // sB[c * ldB + kk]
+          const int dq_tm = div16(32, rtm), dr_tm = 32 - dq_tm * tm;  // 32 = dq_tm * tm + dr_tm
+          // slot t of this lane: z = lane + 32 t -> group g = z / te, element
+          // e = z % te (row e % tm, column e / tm); its operands at step 0 are
+          // sA[ia] and sB[ib], kept as ia | ib << 16 (both below 2^9)
+          uint32_t idx[kPkSlots];
+          double acc[kPkSlots];
+          {
+            int g = 0, e = lane;
+            while (e >= te) {
+              e -= te;
+              g++;
+            }
+  #pragma unroll
+            for (int t = 0; t < kPkSlots; t++) {
+              idx[t] = 0;  // slots past te * G read valid operands; their sums are discarded
+              if (g < G) {
+                const int c = div16(e, rtm), r = e - c * tm;
+                idx[t] = (uint32_t)(g * tm + r) | ((uint32_t)(c * ldB + g) << 16);
+              }
+              acc[t] = 0.0;
+              e += 32;
+              while (e >= te) {
+                e -= te;
+                g++;
+              }
+            }
+          }
+
+          // product cursor: batch [pb, pb + nb) of metadata, one product per lane
+          int64_t pb = p0;
+          int nb = 0, q = 0, lq = 0;
+          int64_t my_a = 0, my_b = 0;
+          int my_s = 1;
+          auto load_batch = [&]() {
+            nb = (p1 - pb < 32) ? (int)(p1 - pb) : 32;
+            if (lane < nb) {
+              const int2 pr = ws.prods[pb + lane];
+              my_a = A.blk_off[pr.x];
+              my_b = B.blk_off[pr.y];
+              my_s = A.col_sizes[A.col_idx[pr.x]];
+            }
+          };
+          if (pb < p1) load_batch();
+
+          // Copies the next (up to) KC k positions of the concatenated products
+          // into stage `buf`: sA[kk * tm + r] = A(r0 + r, k), sB[c * ldB + kk] =
+          // B(k, c0 + c); zero-fills up to the next multiple of G. Returns the
+          // number of steps (k positions / G) of the chunk.
+          auto fill = [&](int buf) -> int {
+            double *sA = wbuf + buf * kStage;
+            double *sB = sA + KC * tm;
+            int kk = 0;
+            while (kk < KC && pb < p1) {
+              const int s = __shfl_sync(0xffffffffu, my_s, q);
+              const int64_t ao = __shfl_sync(0xffffffffu, my_a, q);
+              const int64_t bo = __shfl_sync(0xffffffffu, my_b, q);
+              const int nc = min(s - lq, KC - kk);
+              const double *Ab = A.vals + ao + (int64_t)lq * m + r0;  // column lq, row r0
+              const double *Bb = B.vals + bo + (int64_t)c0 * s + lq;  // row lq, column c0
+              double *dA = sA + kk * tm;
+              if (tm == m) {  // whole columns: one contiguous range
+                for (int z = lane; z < nc * m; z += 32) cp_async8(dA + z, Ab + z);
+              } else {  // (l, r) = divmod(z, tm), stepped by 32
+                int l = div16(lane, rtm), r = lane - l * tm;
+                for (int z = lane; z < nc * tm; z += 32) {
+                  cp_async8(dA + l * tm + r, Ab + (int64_t)l * m + r);
+                  l += dq_tm;
+                  r += dr_tm;
+                  if (r >= tm) {
+                    r -= tm;
+                    l++;
+                  }
+                }
+              }
+              {  // (c, l) = divmod(z, nc), stepped by 32
+                const uint32_t rnc = rcp16(nc);
+                const int dq = div16(32, rnc), dr = 32 - dq * nc;
+                int c = div16(lane, rnc), l = lane - c * nc;
+                double *dB = sB + kk;
+                for (int z = lane; z < nc * tn; z += 32) {
+                  cp_async8(dB + c * ldB + l, Bb + (int64_t)c * s + l);
+                  c += dq;
+                  l += dr;
+                  if (l >= nc) {
+                    l -= nc;
+                    c++;
+                  }
+                }
+              }
+              kk += nc;
+              lq += nc;
+              if (lq == s) {
+                lq = 0;
+                if (++q == nb) {
+                  pb += nb;
+                  q = 0;
+                  if (pb < p1) load_batch();
+                }
+              }
+            }
+            const int steps = div16(kk + G - 1, rg);
+            const int pad = steps * G - kk;
+            if (pad) {
+              for (int z = lane; z < pad * tm; z += 32) sA[kk * tm + z] = 0.0;
+              for (int z = lane; z < pad * tn; z += 32) {
+                const int c = div16(z, rcp16(pad)), l = z - c * pad;
+                sB[c * ldB + kk + l] = 0.0;
+              }
+            }
+            return steps;
+          };
+
+          int cur = fill(0);  // steps of the current chunk
+          pk_commit();
+          for (int ch = 0;; ch++) {
+            const int buf = ch & 1;
+            const int nxt = (pb < p1) ? fill(buf ^ 1) : 0;
+            pk_commit();
+            pk_wait<1>();  // the current chunk has landed
+            __syncwarp();
+            const double *sA = wbuf + buf * kStage;
+            const double *sB = sA + KC * tm;
+            const int gtm = G * tm;
+            switch (nT) {
+  #define BSM_PK_CASE(N)                              \
+    case N:                                           \
+      pk_steps<N>(sA, sB, idx, acc, cur, gtm, G);     \
+      break;
+              BSM_PK_CASE(1) BSM_PK_CASE(2) BSM_PK_CASE(3) BSM_PK_CASE(4)
+              BSM_PK_CASE(5) BSM_PK_CASE(6) BSM_PK_CASE(7) BSM_PK_CASE(8)
+              BSM_PK_CASE(9) BSM_PK_CASE(10) BSM_PK_CASE(11) BSM_PK_CASE(12)
+              BSM_PK_CASE(13) BSM_PK_CASE(14) BSM_PK_CASE(15) BSM_PK_CASE(16)
+  #undef BSM_PK_CASE
+            }
+            __syncwarp();  // the stage is read before it is filled again
+            if (nxt == 0) break;
+            cur = nxt;
+          }
+          pk_wait<0>();
+          __syncwarp();
+
+          // the G partial sums of each element, added in group order
+          double *red = wbuf;
+  #pragma unroll
+          for (int t = 0; t < kPkSlots; t++) {
+            const int z = lane + 32 * t;
+            if (t < nT && z < used) red[z] = acc[t];
+          }
+          __syncwarp();
+          int c = div16(lane, rtm), r = lane - c * tm;
+          for (int e = lane; e < te; e += 32) {
+            double v = red[e];
+            for (int g = 1; g < G; g++) v += red[g * te + e];
+            const int64_t loc = (int64_t)(c0 + c) * m + r0 + r;
+            v = alpha * v;
+            if (cinv) v = fma(beta, cinv[loc], v);
+            out[loc] = v;
+            c += dq_tm;
+            r += dr_tm;
+            if (r >= tm) {
+              r -= tm;
+              c++;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+}
+
 cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMat Cin,
                                 double alpha, double beta, DevWs ws, const DevStatus *st,
                                 const int32_t *items, const int64_t *seg, int grid,
-                                cudaStream_t stream) {
+                                unsigned long long *work, cudaStream_t stream) {
   switch (variant) {
     case kFp64T16B3:
       k_numeric_fp64_t16<3><<<grid, kSWarps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws, st,
@@ -274,6 +581,14 @@ cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMa
                                                                  st, items, seg);
       break;
     }
+    case kFp64PkB2:
+      k_numeric_fp64_pk<2><<<grid, kPkWarps * 32, pk_smem_bytes<2>(), stream>>>(
+          A, B, C, Cin, alpha, beta, ws, st, items, seg, work);
+      break;
+    case kFp64PkB3:
+      k_numeric_fp64_pk<3><<<grid, kPkWarps * 32, pk_smem_bytes<3>(), stream>>>(
+          A, B, C, Cin, alpha, beta, ws, st, items, seg, work);
+      break;
     default:
       k_numeric_fp64_t16<2><<<grid, kSWarps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws, st,
                                                                items, seg);
@@ -281,12 +596,20 @@ cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMa
   return cudaGetLastError();
 }
 
-int fp64_variant_blocks_per_sm(int variant) { return variant == kFp64T16B2 ? 2 : 3; }
+int fp64_variant_blocks_per_sm(int variant) {
+  return (variant == kFp64T16B2 || variant == kFp64PkB2) ? 2 : 3;
+}
 
 cudaError_t numeric_fp64_init() {
   const size_t smem = (size_t)kNumWarps * kWarpSmem * sizeof(double);
-  return cudaFuncSetAttribute(k_numeric_fp64_t32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_numeric_fp64_t32,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_numeric_fp64_pk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pk_smem_bytes<2>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_numeric_fp64_pk<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pk_smem_bytes<3>());
 }
 
 }  // namespace bsm

@@ -203,3 +203,69 @@ def test_torch_stream(gpu_ctx, oracle_mod):
     A = synth.water(20, seed=3)
     s = torch.cuda.Stream()
     ref, v, _ = check(gpu_ctx, oracle_mod, A, A, eps=1e-10, stream=s)
+
+
+FP64_KERNELS = range(5)  # BSM_FP64_T16_B2 .. BSM_FP64_PK_B3
+
+
+@pytest.mark.parametrize("kern", FP64_KERNELS)
+def test_each_fp64_kernel(gpu_ctx, oracle_mod, kern):
+    """Every FP64 kernel, forced for the whole multiply: integer inputs (exact
+    for any summation order) over tile edges 1..33, water blocks with C blocks
+    of more than 32 products, alpha/beta with C_in, both launch modes."""
+    rng = np.random.default_rng(900 + kern)
+    sizes = (1, 2, 5, 6, 9, 13, 16, 17, 23, 32, 33)
+    rs, ks, cs = rng.choice(sizes, 12), rng.choice(sizes, 14), rng.choice(sizes, 11)
+    A = synth.random_blocks(rng, rs, ks, 0.5, kind="int", shuffle=True)
+    B = synth.random_blocks(rng, ks, cs, 0.5, kind="int", shuffle=True)
+    C = synth.random_blocks(rng, rs, cs, 0.4, kind="int", shuffle=True)
+    for launch in (0, 1):
+        check(gpu_ctx, oracle_mod, A, B, 2.0, -1.0, C, eps=0.0, exact=True, fp64_kernel=kern,
+              launch=launch)
+    W = synth.water(40, seed=11)
+    ref, _, st = check(gpu_ctx, oracle_mod, W, W, eps=1e-10, fp64_kernel=kern)
+    assert st.kept > 32 * st.c_blocks // 2  # most C blocks span several product batches
+    CW = synth.random_blocks(np.random.default_rng(3), W.row_sizes, W.col_sizes, 0.3, kind="normal")
+    for launch in (0, 1):
+        check(gpu_ctx, oracle_mod, W, W, -0.5, 2.0, CW, eps=1e-6, fp64_kernel=kern, launch=launch)
+
+
+@pytest.mark.parametrize("kern", FP64_KERNELS)
+def test_each_fp64_kernel_nan_and_single(gpu_ctx, oracle_mod, kern):
+    def single(v):
+        return BlockMatrix(np.array([1], np.int32), np.array([1], np.int32), np.array([0], np.int32),
+                           np.array([0], np.int32), np.array([v], np.float64))
+    _, _, v, st = run_gpu(gpu_ctx, single(np.nan), single(3.0), eps=1e300, fp64_kernel=kern)
+    assert st.kept == 1 and np.isnan(v[0])
+    _, _, v, _ = run_gpu(gpu_ctx, single(1.5), single(-2.0), fp64_kernel=kern)
+    assert v[0] == -3.0
+
+
+def test_fp64_kernel_out_of_range(gpu_ctx, bsm_lib):
+    rs = np.array([2, 3], np.int32)
+    A = gpu_ctx.matrix(rs, rs, [0, 1], [0, 1], np.ones(13))
+    C = gpu_ctx.empty(rs, rs)
+    for bad in (5, -2):
+        with pytest.raises(bsm_lib.BsmError) as e:
+            gpu_ctx.multiply(1.0, A, A, 0.0, C, fp64_kernel=bad)
+        assert e.value.name == "INVALID_ARG"
+    A.destroy()
+    C.destroy()
+
+
+def test_default_fp64_kernel(bsm_lib, oracle_mod):
+    """Without a forced or tuned kernel: the packed kernel where C blocks have
+    many products (water), t16 where they have about one (a sparse random
+    pattern); both results equal the oracle's. Fresh contexts: the product
+    count hint is kept per context."""
+    W = synth.water(16, seed=2)
+    S = synth.sparse_random(3000, 6, 5e-4, seed=1)
+    for M, want in ((W, bsm_lib.BSM_FP64_PK_B2), (S, bsm_lib.BSM_FP64_T16_B2)):
+        ctx = bsm_lib.Context(0)
+        try:
+            ctx.profile(True)
+            ref, _, st = check(ctx, oracle_mod, M, M, eps=1e-10)
+            assert ctx.profile_read().last_fp64_kernel == want
+            assert (st.kept >= 4 * st.c_blocks) == (want == bsm_lib.BSM_FP64_PK_B2)
+        finally:
+            ctx.close()
