@@ -45,6 +45,32 @@ FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64
                 "t32": (2, "k_numeric_fp64_t32"), "pkb2": (3, "k_numeric_fp64_pk"),
                 "pkb3": (4, "k_numeric_fp64_pk")}
 FP64_BY_NUMBER = {v[0]: k for k, v in FP64_KERNELS.items()}
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/): valid only while
+# the kernel's source file is unchanged (its SHA-256) and for that workload.
+MEASURED_TRAFFIC = {
+    ("k_numeric_fp64_pk", "water2048", "fp64"): dict(
+        source="paper_1705_10218_gb300/csrc/k_numeric_fp64.cu",
+        sha256="078c3db56a2515fefbe4e60a50ea50c082b2e8eef4eeb1c4baa4c7ddad2c79e2",
+        bytes=8.87e9 + 1.59e9),
+}
+
+
+def measured_traffic(kernel, workload, precision):
+    """DRAM bytes per launch from the ncu capture, or None when there is none
+    for this kernel and workload or the kernel's source changed since."""
+    import hashlib
+
+    m = MEASURED_TRAFFIC.get((kernel, workload, precision))
+    if m is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, m["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != m["sha256"]:
+                return None
+    except OSError:
+        return None
+    return m["bytes"]
 
 
 def measured_peak(key, fallback):
@@ -427,7 +453,9 @@ def main():
     if args.precision == "fp64":
         achieved = flops / (num_ms / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                "traffic": measured_traffic(kname, args.workload, args.precision),
+                "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + write.sum)",
                 "kernel": kname, "peak_source": "nominal FP64 FMA rate of the GB300 (1.25 TFLOP/s)",
                 "algorithmic": "2*m*n*k over kept products per launch", "phase_ms": phase}
     else:
