@@ -216,8 +216,32 @@ def cpu_baseline(A, eps, budget_s=12.0, nthreads=None, ref_rows=None):
     gflops = r.flops / dt / 1e9
     info = {"value": round(gflops, 3), "unit": "GFLOP/s", "cores": nthreads, "kind": "oracle",
             "sample": f"C block rows 0..{nrows} of {A.nbr} ({r.flops / 1e9:.2f} GFLOP, {dt:.1f} s, "
-                      f"OpenMP over block rows)"}
+                      f"OpenMP over block rows)", "cpu_model": cpu_model()}
+    # one thread on a sample of about 3 s
+    probe1 = max(1, min(A.nbr, 16))
+    t0 = time.perf_counter()
+    oracle.multiply(A, A, eps=eps, rows=(0, probe1), nthreads=1)
+    rows1 = int(min(A.nbr, max(probe1, probe1 / max(time.perf_counter() - t0, 1e-3) * 3.0)))
+    t0 = time.perf_counter()
+    r1 = oracle.multiply(A, A, eps=eps, rows=(0, rows1), nthreads=1)
+    dt1 = time.perf_counter() - t0
+    info["single_thread"] = {"value": round(r1.flops / dt1 / 1e9, 3), "unit": "GFLOP/s",
+                             "sample": f"C block rows 0..{rows1} ({r1.flops / 1e9:.2f} GFLOP, {dt1:.1f} s)"}
     return info, nrows, r
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.machine()
 
 
 def run_reference(args, rank, world):
@@ -357,7 +381,7 @@ def serve_bench(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water2048", choices=sorted(WORKLOADS))
@@ -450,6 +474,14 @@ def main():
     phase = {"norms": round(prof.ms_norms / max(prof.multiplies, 1), 4),
              "symbolic": round(prof.ms_symbolic / max(prof.multiplies, 1), 4),
              "numeric": round(num_ms, 4)}
+    # the integer / streaming phases against their own units: the norms read A's
+    # values once (A = B); the symbolic phase (count, scan, fill) visits every
+    # candidate product
+    phase_rates = None
+    if prof.multiplies > 0 and args.precision == "fp64":
+        phase_rates = {
+            "norms_gb_per_s": round(8 * len(A.values) / (phase["norms"] / 1e3) / 1e9, 1),
+            "symbolic_gcandidates_per_s": round(st.candidates / (phase["symbolic"] / 1e3) / 1e9, 2)}
     if args.precision == "fp64":
         achieved = flops / (num_ms / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
@@ -457,7 +489,8 @@ def main():
                 "traffic": measured_traffic(kname, args.workload, args.precision),
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + write.sum)",
                 "kernel": kname, "peak_source": "nominal FP64 FMA rate of the GB300 (1.25 TFLOP/s)",
-                "algorithmic": "2*m*n*k over kept products per launch", "phase_ms": phase}
+                "algorithmic": "2*m*n*k over kept products per launch", "phase_ms": phase,
+                "phase_rates": phase_rates}
     else:
         # compulsory bytes of the numeric kernel: C written once (FP64) and the
         # operand slices read once (A = B: left and right layouts)
@@ -535,7 +568,8 @@ def main():
                        "l2": "inputs larger than L2 (A 272 MB, C 1.6 GB); no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "multiplies_per_s": round(1e3 * args.steps * world / total_ms, 3),
-            "latency_ms": {"p50": round(statistics.median(per_step), 4), "p99": round(p99, 4)},
+            "latency_ms": {"p50": round(statistics.median(per_step), 4), "p99": round(p99, 4),
+                           "min": round(min(per_step), 4), "max": round(max(per_step), 4)},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -73,3 +73,15 @@ def rel_frobenius(x, y):
     y = np.asarray(y, np.float64)
     den = np.linalg.norm(y)
     return float(np.linalg.norm(x - y) / (den if den > 0 else 1.0))
+
+
+def select_blocks(M, keep):
+    """The blocks of M where the boolean array keep (one entry per block) is set,
+    in their list order, with their values."""
+    keep = np.asarray(keep, bool)
+    bo = block_list_offsets(M)
+    parts = [np.asarray(M.values[bo[b]:bo[b + 1]]) for b in np.nonzero(keep)[0]]
+    v = np.concatenate(parts) if parts else np.zeros(0)
+    return BlockMatrix(np.asarray(M.row_sizes, np.int32), np.asarray(M.col_sizes, np.int32),
+                       np.asarray(M.blk_row, np.int32)[keep].copy(),
+                       np.asarray(M.blk_col, np.int32)[keep].copy(), v)

@@ -100,3 +100,28 @@ def test_sign_iteration_converges_to_sign(oracle_mod):
     assert np.linalg.norm(H.to_dense(X) - sign) / np.linalg.norm(sign) < 1e-9
     ev = np.linalg.eigvalsh(H.to_dense(X))
     assert np.allclose(np.abs(ev), 1.0, atol=1e-9)
+
+
+def test_partial_panels_sum_to_full_product(oracle_mod):
+    """Algorithms 1 and 2: the products over L disjoint k ranges (the partial C
+    panels of one process), summed with the block-sparse add, or accumulated
+    tick by tick with beta = 1, give the full product: same pattern, and, for
+    integer inputs, the same values exactly (dense integer product)."""
+    rng = np.random.default_rng(31)
+    rs, ks, cs = rng.choice([1, 2, 3, 5], 10), rng.choice([1, 2, 3, 5], 12), rng.choice([1, 2, 3, 5], 9)
+    A = synth.random_blocks(rng, rs, ks, 0.5, kind="int", shuffle=True)
+    B = synth.random_blocks(rng, ks, cs, 0.5, kind="int", shuffle=True)
+    grp = rng.integers(0, 3, len(ks))
+    acc = tick = None
+    for g in range(3):
+        Ag = H.select_blocks(A, grp[A.blk_col] == g)
+        Bg = H.select_blocks(B, grp[B.blk_row] == g)
+        P = H.result_matrix(oracle_mod.multiply(Ag, Bg), rs, cs)
+        acc = P if acc is None else H.result_matrix(oracle_mod.add(1.0, P, 1.0, acc), rs, cs)
+        T = oracle_mod.multiply(Ag, Bg, beta=1.0 if tick is not None else 0.0, C=tick)
+        tick = H.result_matrix(T, rs, cs)
+    full = oracle_mod.multiply(A, B)
+    D = H.to_dense(A) @ H.to_dense(B)
+    for M in (acc, tick):
+        assert np.array_equal(M.blk_row, full.blk_row) and np.array_equal(M.blk_col, full.blk_col)
+        assert np.array_equal(H.to_dense(M), D)
