@@ -107,6 +107,17 @@ typedef struct {
                         time a given set of arguments is met and replay it after */
   int32_t fp64_kernel; /* 0, or 1 + BSM_FP64_* to force that FP64 kernel (ignored by
                           the split precisions); out of range: BSM_ERR_INVALID_ARG */
+  double *host_values; /* NULL, or page-locked host memory (cudaHostAlloc /
+                          cudaHostRegister, device-mapped) of host_cap doubles that also
+                          receives the result's values, in bsm_mat_get_values order,
+                          written by the device while the multiply runs (the packed FP64
+                          kernel stores each C block there as it completes it; the other
+                          kernels are followed by a device copy). Written only if the
+                          result has at most host_cap values (bsm_mat_nblocks tells); valid
+                          once the result is complete (a getter, bsm_sync or a blocking
+                          multiply). Memory that is not device-mapped: BSM_ERR_INVALID_ARG.
+                          The caller keeps ownership and must not free it before then. */
+  int64_t host_cap;
 } bsm_opts;
 
 /* Counters of one multiply (filled when bsm_stats* is not NULL; this makes

@@ -53,6 +53,8 @@ class _Opts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("graph", ctypes.c_int32),
         ("fp64_kernel", ctypes.c_int32),
+        ("host_values", ctypes.c_void_p),
+        ("host_cap", ctypes.c_int64),
     ]
 
 
@@ -201,12 +203,20 @@ class Context:
     def multiply(self, alpha, A: "Matrix", B: "Matrix", beta, C: "Matrix", eps: float = 0.0, *,
                  precision: int = BSM_PREC_FP64, launch: int = BSM_LAUNCH_PERSISTENT,
                  blocking: bool = False, autotune: bool = False, stream=None,
-                 graph: bool = False, stats: bool = False, fp64_kernel: int | None = None) -> Stats | None:
+                 graph: bool = False, stats: bool = False, fp64_kernel: int | None = None,
+                 host_out: np.ndarray | None = None) -> Stats | None:
         """fp64_kernel: one of BSM_FP64_* to force that FP64 kernel, None for the
-        library's choice."""
+        library's choice. host_out: a float64 array in page-locked host memory
+        that also receives C's values (bsm_mat_get_values order) while the
+        multiply runs, when they fit; valid once the result is complete."""
+        hv, hcap = None, 0
+        if host_out is not None:
+            if host_out.dtype != np.float64 or not host_out.flags.c_contiguous:
+                raise ValueError("host_out must be a contiguous float64 array")
+            hv, hcap = host_out.ctypes.data, host_out.size
         o = _Opts(int(precision), int(launch), int(bool(blocking)), int(bool(autotune)),
                   _stream_ptr(stream), int(bool(graph)),
-                  0 if fp64_kernel is None else int(fp64_kernel) + 1)
+                  0 if fp64_kernel is None else int(fp64_kernel) + 1, hv, hcap)
         st = _Stats() if stats else None
         rc = lib().bsm_multiply(self._h, float(alpha), A._h, B._h, float(beta), C._h, float(eps),
                                 ctypes.byref(o), ctypes.byref(st) if st is not None else None)

@@ -452,6 +452,7 @@ struct Launch {
   int slot;
   cudaStream_t s;
   bool use_cin, split, prof;
+  bool host_written;  // every numeric launch so far stored the host copy itself
   DevMat dA, dB, dC;
   DevWs ws;
   DevOut out;
@@ -514,6 +515,7 @@ static int launch_numeric(Launch &L, int variant, const int32_t *items, const in
     if (fp64_variant_uses_work(variant))
       CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
     ctx->last_fp64 = variant;
+    L.host_written = L.host_written && fp64_variant_writes_host(variant);
     CK(launch_numeric_fp64(variant, L.dA, L.dB, L.out, L.dC, L.alpha, L.beta, L.ws,
                            ctx->d_status, items, seg,
                            ctx->nsm * fp64_variant_blocks_per_sm(variant), ctx->d_work, L.s));
@@ -549,6 +551,7 @@ static int time_variant(Launch &L, int variant, const int32_t *items, const int6
 static int stage_b(Launch &L, bool record, bool may_tune) {
   bsm_ctx ctx = L.ctx;
   int rc;
+  L.host_written = true;  // the split kernels store it; FP64 launches update this
   CK(launch_symbolic_fill(L.dA, L.dB, L.dC, L.use_cin ? 1 : 0, L.eps, L.ws, L.out, ctx->d_status,
                           ctx->nsm * 6, L.s));
   ctx->launches++;
@@ -594,6 +597,11 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
                              L.B->max_col)))
       return rc;
   }
+  // the host copy of the values, where a numeric kernel did not store it
+  if (L.out.host_vals && !L.host_written) {
+    CK(launch_copy_out(L.out, ctx->d_status, ctx->nsm, L.s));
+    ctx->launches++;
+  }
   if (L.prof && record) {
     CK(cudaEventRecord(ctx->prof_ev[L.slot][3], L.s));
     ctx->prof_pending[L.slot] = true;
@@ -626,6 +634,7 @@ static void graph_key(const Launch &L, std::vector<uint64_t> &k) {
   put(L.ctx->cls_items), put(L.s);
   dbl(L.alpha), dbl(L.beta), dbl(L.eps);
   num(L.o.precision), num(L.o.launch), num(L.o.fp64_kernel), num((int64_t)L.ctx->tune_version);
+  put(L.out.host_vals), num(L.out.host_cap);
   num(fp64_default(L.ctx, L.C));
 }
 
@@ -653,9 +662,17 @@ static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double 
     if (B != A && (rc = split_buffers(B, o.precision, false, true))) return rc;
   }
   L.dA = dev_view(A), L.dB = dev_view(B), L.dC = dev_view(C);
+  double *host_dev = nullptr;  // device address of o.host_values
+  if (o.host_values) {
+    cudaPointerAttributes pa{};
+    CK(cudaPointerGetAttributes(&pa, o.host_values));
+    host_dev = static_cast<double *>(pa.devicePointer);
+  }
   auto make_out = [&]() {
     L.ws = ctx->ws;
     L.out = dev_out(C, C->back);
+    L.out.host_vals = host_dev;
+    L.out.host_cap = o.host_values ? o.host_cap : 0;
     // capacities of the per-C-block scratch cap the block count as well
     L.out.cap_blk = std::min<int64_t>(L.out.cap_blk, std::max<int64_t>(ctx->cap_cblk - 1, 0));
   };
@@ -1062,6 +1079,15 @@ int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, b
   if (o.launch != BSM_LAUNCH_PERSISTENT && o.launch != BSM_LAUNCH_PER_STACK)
     return BSM_ERR_INVALID_ARG;
   if (o.fp64_kernel < 0 || o.fp64_kernel > BSM_FP64_NUM_KERNELS) return BSM_ERR_INVALID_ARG;
+  if (o.host_values) {  // must be device-mapped page-locked host memory
+    if (o.host_cap < 0) return BSM_ERR_INVALID_ARG;
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, o.host_values) != cudaSuccess ||
+        pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
+      cudaGetLastError();
+      return BSM_ERR_INVALID_ARG;
+    }
+  }
   if (A->nbc != B->nbr || A->h_col_sizes != B->h_row_sizes) return BSM_ERR_DIM_MISMATCH;
   if (C->nbr != A->nbr || C->nbc != B->nbc || C->h_row_sizes != A->h_row_sizes ||
       C->h_col_sizes != B->h_col_sizes)

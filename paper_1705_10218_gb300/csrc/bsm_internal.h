@@ -44,6 +44,10 @@ struct DevOut {
   double *vals;      // [cap_nnz]
   int64_t *hdr;      // {nblk, nnz}
   int64_t cap_blk, cap_nnz;
+  // optional second destination of the values: pinned host memory (its device
+  // address) of host_cap doubles, written only when the result fits
+  double *host_vals;
+  int64_t host_cap;
 };
 
 // Per-context scratch of one multiply.
@@ -143,6 +147,13 @@ cudaError_t launch_filter_count(DevMat M, double eps, DevWs ws, int nsm, cudaStr
 cudaError_t launch_filter_fill(DevMat M, double eps, DevWs ws, DevOut O, const DevStatus *st,
                                int nsm, cudaStream_t stream);
 // stage 0: per-row union counts; 1: union pattern and sources; 2: values
+// Copies C's values (nnz from the status) to O.host_vals when they fit host_cap
+// and the multiply did not overflow.
+cudaError_t launch_copy_out(DevOut O, const DevStatus *st, int nsm, cudaStream_t stream);
+inline bool fp64_variant_writes_host(int variant) {
+  return variant == kFp64PkB2 || variant == kFp64PkB3;
+}
+
 cudaError_t launch_add(int stage, DevMat A, DevMat Cin, int use_cin, double alpha, double beta,
                        DevWs ws, DevOut O, const DevStatus *st, int nsm, cudaStream_t stream);
 

@@ -179,6 +179,24 @@ __global__ void k_add_values(DevMat A, DevMat Cin, double alpha, double beta, De
   }
 }
 
+// ---------------------------------------------------------------------------
+// Values of the result to host memory (pinned, device-mapped): C's values are
+// contiguous in block order, [0, nnz).
+// ---------------------------------------------------------------------------
+__global__ void k_copy_out(DevOut O, const DevStatus *st) {
+  if (st->overflow) return;
+  const int64_t n = st->nnz_c;
+  if (n > O.host_cap) return;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = t0; e < n; e += nt) O.host_vals[e] = O.vals[e];
+}
+
+cudaError_t launch_copy_out(DevOut O, const DevStatus *st, int nsm, cudaStream_t stream) {
+  k_copy_out<<<nsm * 8, 256, 0, stream>>>(O, st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add(int stage, DevMat A, DevMat Cin, int use_cin, double alpha, double beta,
                        DevWs ws, DevOut O, const DevStatus *st, int nsm, cudaStream_t stream) {
   if (stage == 0)

@@ -367,6 +367,8 @@ __global__ void __launch_bounds__(kPkWarps * 32, MINB)
   double *wbuf = smem_pk + warp * 2 * kStage;
   int64_t wb, we;
   work_range(st, seg, wb, we);
+  // the second destination (host memory) when the whole result fits it
+  double *hout = (C.host_vals && st->nnz_c <= C.host_cap) ? C.host_vals : nullptr;
 
   for (;;) {
     unsigned long long got = 0;
@@ -382,6 +384,7 @@ __global__ void __launch_bounds__(kPkWarps * 32, MINB)
       const int cin = ws.c_cin[gblk];
       const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
       double *out = C.vals + C.blk_off[gblk];
+      double *hblk = hout ? hout + C.blk_off[gblk] : nullptr;
 
       for (int r0 = 0; r0 < m; r0 += kPkTile) {
         for (int c0 = 0; c0 < n; c0 += kPkTile) {
@@ -551,6 +554,7 @@ __global__ void __launch_bounds__(kPkWarps * 32, MINB)
             v = alpha * v;
             if (cinv) v = fma(beta, cinv[loc], v);
             out[loc] = v;
+            if (hblk) hblk[loc] = v;
             c += dq_tm;
             r += dr_tm;
             if (r >= tm) {

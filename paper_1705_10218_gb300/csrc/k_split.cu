@@ -346,13 +346,14 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 // One C block by one warp: the MMA problem M' x N' in MT x NT tiles. The
 // (A offset, B offset, k) of up to 32 products are read at once, one per lane;
 // with PREFETCH the next step's fragments are loaded while the current step
-// multiplies (twice the fragment registers).
+// multiplies (twice the fragment registers). st_nnz: the result's value count
+// (the host copy is written when it fits C.host_cap).
 template <int PREC, int MT, int NT, bool PREFETCH>
 __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, const DevOut &C,
                                              const DevMat &Cin, const void *__restrict__ a_left,
                                              const void *__restrict__ b_right, double alpha,
                                              double beta, const DevWs &ws, int64_t gb, int m,
-                                             int n, bool tr, int Mp, int Np) {
+                                             int n, bool tr, int Mp, int Np, int64_t st_nnz) {
   constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
   constexpr int NSL = BF ? 3 : 2;
   constexpr int KSTEP = BF ? 16 : 8;
@@ -460,6 +461,8 @@ __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, c
   const int cin = ws.c_cin[gb];
   const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
   double *out = C.vals + C.blk_off[gb];
+  // the second destination (host memory) when the whole result fits it
+  double *hblk = (C.host_vals && st_nnz <= C.host_cap) ? C.host_vals + C.blk_off[gb] : nullptr;
 #pragma unroll
   for (int mt = 0; mt < MT; mt++)
 #pragma unroll
@@ -477,6 +480,7 @@ __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, c
             if (cinv) v = fma(beta, cinv[e], v);
           }
           out[e] = v;
+          if (hblk) hblk[e] = v;
         }
       }
 }
@@ -696,6 +700,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
     const int cin = ws.c_cin[gb];
     const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
     double *out = C.vals + C.blk_off[gb];
+    double *hblk = (C.host_vals && st->nnz_c <= C.host_cap) ? C.host_vals + C.blk_off[gb] : nullptr;
 #pragma unroll
     for (int nt = 0; nt < 2; nt++)
 #pragma unroll
@@ -711,6 +716,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
             if (cinv) v = fma(beta, cinv[e], v);
           }
           out[e] = v;
+          if (hblk) hblk[e] = v;
         }
       }
   }
@@ -748,10 +754,10 @@ __global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOu
     if (SIZES == 2) {
       if (!small)
         split_cblock<PREC, 2, 4, false>(A, B, C, Cin, a_left, b_right, alpha, beta, ws, gb, m, n,
-                                        tr, Mp, Np);
+                                        tr, Mp, Np, st->nnz_c);
     } else if (SIZES == 0 || small) {
       split_cblock<PREC, 1, 2, true>(A, B, C, Cin, a_left, b_right, alpha, beta, ws, gb, m, n, tr,
-                                     Mp, Np);
+                                     Mp, Np, st->nnz_c);
     }
   }
 }

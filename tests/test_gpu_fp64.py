@@ -269,3 +269,51 @@ def test_default_fp64_kernel(bsm_lib, oracle_mod):
             assert (st.kept >= 4 * st.c_blocks) == (want == bsm_lib.BSM_FP64_PK_B2)
         finally:
             ctx.close()
+
+
+def _pinned(n, fill=0.0):
+    import torch
+
+    a = torch.empty(max(n, 1), dtype=torch.float64, pin_memory=True).numpy()
+    a[:] = fill
+    return a
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(fp64_kernel=0), dict(launch=1), dict(precision=1),
+                                dict(graph=True)])
+def test_host_values(gpu_ctx, oracle_mod, kw):
+    """opts.host_values: the device stores the result's values in page-locked
+    host memory while the multiply runs (packed kernel epilogue) or right after
+    (copy kernel); they equal bsm_mat_get_values bit for bit."""
+    A = synth.water(20, seed=6)
+    ref = oracle_mod.multiply(A, A, eps=1e-10)
+    dA = gpu_ctx.from_blocks(A)
+    dC = gpu_ctx.empty(A.row_sizes, A.col_sizes)
+    host = _pinned(ref.nnz + 7, np.nan)
+    for _ in range(3 if kw.get("graph") else 1):  # graph: capture, then replays
+        host[:] = np.nan
+        gpu_ctx.multiply(1.0, dA, dA, 0.0, dC, 1e-10, host_out=host, **kw)
+        v = dC.values()
+        assert len(v) == ref.nnz
+        assert np.array_equal(host[:ref.nnz], v)
+        assert np.isnan(host[ref.nnz:]).all()
+    tol = 2e-6 if kw.get("precision") else TOL
+    assert H.rel_frobenius(v, ref.values) <= tol
+    dA.destroy()
+    dC.destroy()
+
+
+def test_host_values_small_or_pageable(gpu_ctx, bsm_lib, oracle_mod):
+    A = synth.water(8, seed=1)
+    ref = oracle_mod.multiply(A, A, eps=1e-10)
+    dA = gpu_ctx.from_blocks(A)
+    dC = gpu_ctx.empty(A.row_sizes, A.col_sizes)
+    small = _pinned(ref.nnz - 1, -7.0)
+    gpu_ctx.multiply(1.0, dA, dA, 0.0, dC, 1e-10, host_out=small, blocking=True)
+    assert (small == -7.0).all()  # the result does not fit: nothing written
+    assert H.rel_frobenius(dC.values(), ref.values) <= TOL
+    with pytest.raises(bsm_lib.BsmError) as e:
+        gpu_ctx.multiply(1.0, dA, dA, 0.0, dC, 1e-10, host_out=np.zeros(ref.nnz))
+    assert e.value.name == "INVALID_ARG"
+    dA.destroy()
+    dC.destroy()
