@@ -159,6 +159,18 @@ int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_
 /* Free a matrix (after the work that uses it has finished). */
 int bsm_mat_destroy(bsm_mat m);
 
+/* Replaces the pattern and values of m with a new block list over the same
+ * block row / column sizes (arguments as in bsm_mat_create; values NULL =
+ * zeros). m's device buffers are reused and grown only when too small, so a
+ * stream of inputs of similar size costs no device allocation. Work that reads
+ * m is finished first; a pending result computed into m is dropped. Inputs are
+ * copied before the call returns. Errors: BSM_ERR_OUT_OF_RANGE,
+ * BSM_ERR_DUPLICATE_BLOCK, BSM_ERR_INVALID_ARG, BSM_ERR_UNSUPPORTED leave m
+ * unchanged; BSM_ERR_NOMEM / BSM_ERR_CUDA leave m empty (no blocks).
+ * The paper has no counterpart (there the operands are given to each multiply). */
+int bsm_mat_assign(bsm_mat m, int64_t nblocks, const int32_t *blk_row, const int32_t *blk_col,
+                   const double *values);
+
 /* C = beta*C + alpha*A.B with the on-the-fly filter (Sec. 2, Algorithm 1's
  * local step C_ij = C_ij + A_comp . B_comp).
  *   A: r x s blocks, B: s x c blocks (A's column sizes must equal B's row

@@ -124,6 +124,7 @@ _SIGS = {
     "bsm_sync": (ctypes.c_int, [_P]),
     "bsm_ctx_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "bsm_mat_filter": (ctypes.c_int, [_P, _D]),
+    "bsm_mat_assign": (ctypes.c_int, [_P, _I64, _P, _P, _P]),
     "bsm_mat_add": (ctypes.c_int, [_P, _D, _P, _D, _P]),
     "bsm_ctx_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(_Profile)]),
     "bsm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -287,6 +288,16 @@ class Matrix:
     def filter(self, eps: float):
         """Drop the blocks whose canonical norm is below eps."""
         _check(lib().bsm_mat_filter(self._h, float(eps)), "bsm_mat_filter")
+
+    def assign(self, blk_row, blk_col, values=None):
+        """Replace the block list and values (same block sizes), reusing the
+        device buffers."""
+        br = np.ascontiguousarray(blk_row, dtype=np.int32)
+        bc = np.ascontiguousarray(blk_col, dtype=np.int32)
+        if br.shape != bc.shape:
+            raise BsmError(-1, "bsm_mat_assign")
+        v = None if values is None else np.ascontiguousarray(values, dtype=np.float64)
+        _check(lib().bsm_mat_assign(self._h, len(br), _vp(br), _vp(bc), _vp(v)), "bsm_mat_assign")
 
     def destroy(self):
         if self._h:

@@ -127,6 +127,8 @@ struct bsm_ctx_s {
   DevStatus *d_status = nullptr;
   unsigned long long *d_work = nullptr;  // work counter of the dynamically scheduled kernels
   DevStatus *h_slots = nullptr;    // pinned ring of status copies
+  unsigned char *h_stage = nullptr;  // pinned staging of uploaded index arrays
+  size_t h_stage_cap = 0;
   cudaEvent_t slot_ev[kSlots] = {};
   bsm_mat slot_owner[kSlots] = {};
   int next_slot = 0;
@@ -904,6 +906,7 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   ctx->graphs.clear();
   if (ctx->h_slots) cudaFreeHost(ctx->h_slots);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   for (int i = 0; i < kSlots; i++) {
     if (ctx->slot_ev[i]) cudaEventDestroy(ctx->slot_ev[i]);
     for (int e = 0; e < 4; e++)
@@ -917,6 +920,131 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   return BSM_OK;
 }
 
+}  // extern "C"
+
+// Validates a block list against M's block sizes, builds the blocked CSR
+// arrays (sorted by row, then column) in the context's pinned staging memory
+// and uploads them with the values into M's front buffers (grown when they are
+// too small). Synchronises the context stream before returning, so the
+// caller's arrays may be reused at once.
+static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
+                           const int32_t *blk_col, const double *values, bool exact) {
+  bsm_ctx ctx = M->ctx;
+  const int32_t nbrows = M->nbr, nbcols = M->nbc;
+  const int32_t *row_sizes = M->h_row_sizes.data(), *col_sizes = M->h_col_sizes.data();
+  if (nblocks < 0 || (nblocks > 0 && (!blk_row || !blk_col))) return BSM_ERR_INVALID_ARG;
+  if (nblocks >= (int64_t)INT32_MAX) return BSM_ERR_UNSUPPORTED;
+  // pinned staging: row_ptr | col | row | off (16-byte aligned parts)
+  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t b_ptr = al(((size_t)nbrows + 1) * 4), b_col = al((size_t)nblocks * 4);
+  const size_t b_off = al(((size_t)nblocks + 1) * 8), need = b_ptr + 2 * b_col + b_off;
+  CK(cudaStreamSynchronize(ctx->stream));  // the staging may still feed an earlier upload
+  if (ctx->h_stage_cap < need) {
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_cap = 0;
+    const size_t cap = need + need / 4 + 4096;
+    if (cudaMallocHost((void **)&ctx->h_stage, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return BSM_ERR_NOMEM;
+    }
+    ctx->h_stage_cap = cap;
+  }
+  int32_t *h_row_ptr = reinterpret_cast<int32_t *>(ctx->h_stage);
+  int32_t *h_col = reinterpret_cast<int32_t *>(ctx->h_stage + b_ptr);
+  int32_t *h_row = reinterpret_cast<int32_t *>(ctx->h_stage + b_ptr + b_col);
+  int64_t *h_off = reinterpret_cast<int64_t *>(ctx->h_stage + b_ptr + 2 * b_col);
+  // one pass: range check, sortedness, offsets of the blocks in list order
+  bool sorted = true;
+  h_off[0] = 0;
+  for (int64_t b = 0; b < nblocks; b++) {
+    const int32_t i = blk_row[b], j = blk_col[b];
+    if (i < 0 || i >= nbrows || j < 0 || j >= nbcols) return BSM_ERR_OUT_OF_RANGE;
+    h_off[b + 1] = h_off[b] + (int64_t)row_sizes[i] * col_sizes[j];
+    if (b > 0 && (blk_row[b - 1] > i || (blk_row[b - 1] == i && blk_col[b - 1] >= j)))
+      sorted = false;
+  }
+  const int64_t nnz = h_off[nblocks];
+  std::vector<int64_t> order, list_off;
+  if (!sorted) {
+    order.resize(nblocks);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+      return blk_row[a] != blk_row[b] ? blk_row[a] < blk_row[b] : blk_col[a] < blk_col[b];
+    });
+    for (int64_t p = 1; p < nblocks; p++)
+      if (blk_row[order[p]] == blk_row[order[p - 1]] && blk_col[order[p]] == blk_col[order[p - 1]])
+        return BSM_ERR_DUPLICATE_BLOCK;
+    list_off.assign(h_off, h_off + nblocks + 1);
+  }
+  int rc;
+  if ((rc = buf_grow(M, M->front, nblocks, nnz, exact))) return rc;
+  cudaStream_t st = ctx->stream;
+  auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  cudaError_t e;
+  // values in sorted order: start their copy now, it runs while the index
+  // arrays are staged
+  if (sorted && values && (e = cp(M->front.vals, values, (size_t)nnz * 8)) != cudaSuccess)
+    return cuda_fail(e, "matrix upload values");
+  std::vector<double> staged;
+  if (sorted) {
+    memcpy(h_row, blk_row, (size_t)nblocks * 4);
+    memcpy(h_col, blk_col, (size_t)nblocks * 4);
+    memset(h_row_ptr, 0, ((size_t)nbrows + 1) * 4);
+    for (int64_t b = 0; b < nblocks; b++) h_row_ptr[blk_row[b] + 1]++;
+  } else {
+    memset(h_row_ptr, 0, ((size_t)nbrows + 1) * 4);
+    if (values) staged.resize((size_t)nnz);
+    int64_t acc = 0;
+    for (int64_t p = 0; p < nblocks; p++) {
+      const int64_t b = order[p];
+      h_row[p] = blk_row[b];
+      h_col[p] = blk_col[b];
+      h_off[p] = acc;
+      const int64_t len = list_off[b + 1] - list_off[b];
+      if (values) memcpy(&staged[acc], values + list_off[b], (size_t)len * sizeof(double));
+      acc += len;
+      h_row_ptr[blk_row[b] + 1]++;
+    }
+  }
+  for (int32_t i = 0; i < nbrows; i++) h_row_ptr[i + 1] += h_row_ptr[i];
+  int64_t hdr[2] = {nblocks, nnz};
+  if ((e = cp(M->front.row_ptr, h_row_ptr, ((size_t)nbrows + 1) * 4)) != cudaSuccess ||
+      (e = cp(M->front.col_idx, h_col, (size_t)nblocks * 4)) != cudaSuccess ||
+      (e = cp(M->front.blk_row, h_row, (size_t)nblocks * 4)) != cudaSuccess ||
+      (e = cp(M->front.blk_off, h_off, (size_t)nblocks * 8)) != cudaSuccess ||
+      (e = cp(M->front.hdr, hdr, sizeof(hdr))) != cudaSuccess)
+    return cuda_fail(e, "matrix upload");
+  if (!sorted && values) {
+    if ((e = cp(M->front.vals, staged.data(), (size_t)nnz * 8)) != cudaSuccess)
+      return cuda_fail(e, "matrix upload values");
+  } else if (!values && nnz > 0) {
+    if ((e = cudaMemsetAsync(M->front.vals, 0, (size_t)nnz * 8, st)) != cudaSuccess)
+      return cuda_fail(e, "matrix upload zero");
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "matrix upload sync");
+  M->nblk = nblocks;
+  M->nnz = nnz;
+  return BSM_OK;
+}
+
+// Work that reads M as an input, or writes it, must be finished (and any
+// recompute that would read M done) before M's contents change.
+static int quiesce(bsm_mat m) {
+  bsm_ctx ctx = m->ctx;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (bsm_mat o : std::vector<bsm_mat>(ctx->mats))
+    if (o != m && o->pend.active && (o->pend.A == m || o->pend.B == m)) {
+      int rc = resolve(o);
+      if (rc) return rc;
+    }
+  return BSM_OK;
+}
+
+extern "C" {
+
 int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_t nbcols,
                    const int32_t *col_sizes, int64_t nblocks, const int32_t *blk_row,
                    const int32_t *blk_col, const double *values, bsm_mat *out) {
@@ -929,28 +1057,6 @@ int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_
     if (row_sizes[i] <= 0) return BSM_ERR_INVALID_ARG;
   for (int32_t j = 0; j < nbcols; j++)
     if (col_sizes[j] <= 0) return BSM_ERR_INVALID_ARG;
-  // list offsets, range check, CSR order
-  std::vector<int64_t> list_off((size_t)nblocks + 1, 0);
-  bool sorted = true;
-  for (int64_t b = 0; b < nblocks; b++) {
-    const int32_t i = blk_row[b], j = blk_col[b];
-    if (i < 0 || i >= nbrows || j < 0 || j >= nbcols) return BSM_ERR_OUT_OF_RANGE;
-    list_off[b + 1] = list_off[b] + (int64_t)row_sizes[i] * col_sizes[j];
-    if (b > 0 && (blk_row[b - 1] > i || (blk_row[b - 1] == i && blk_col[b - 1] >= j)))
-      sorted = false;
-  }
-  const int64_t nnz = list_off[nblocks];
-  std::vector<int64_t> order;
-  if (!sorted) {
-    order.resize(nblocks);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-      return blk_row[a] != blk_row[b] ? blk_row[a] < blk_row[b] : blk_col[a] < blk_col[b];
-    });
-    for (int64_t p = 1; p < nblocks; p++)
-      if (blk_row[order[p]] == blk_row[order[p - 1]] && blk_col[order[p]] == blk_col[order[p - 1]])
-        return BSM_ERR_DUPLICATE_BLOCK;
-  }
   int rc = ctx_set_device(ctx);
   if (rc) return rc;
   bsm_mat M = new (std::nothrow) bsm_mat_s();
@@ -988,28 +1094,7 @@ int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_
   if ((rc = dev_alloc(&M->row_sizes, nbrows)) || (rc = dev_alloc(&M->col_sizes, nbcols)) ||
       (rc = dev_alloc(&M->row_cls, nbrows)) || (rc = dev_alloc(&M->col_cls, nbcols)))
     return fail(rc);
-  if ((rc = buf_grow(M, M->front, nblocks, nnz, true))) return fail(rc);
-  // host-side CSR arrays in sorted order
-  std::vector<int32_t> h_row_ptr((size_t)nbrows + 1, 0), h_col((size_t)nblocks), h_row((size_t)nblocks);
-  std::vector<int64_t> h_off((size_t)nblocks);
-  std::vector<double> staged;
-  const double *vsrc = values;
-  if (!sorted && values) staged.resize((size_t)nnz);
-  int64_t acc = 0;
-  for (int64_t p = 0; p < nblocks; p++) {
-    const int64_t b = sorted ? p : order[p];
-    h_row[p] = blk_row[b];
-    h_col[p] = blk_col[b];
-    h_off[p] = acc;
-    const int64_t len = list_off[b + 1] - list_off[b];
-    if (!sorted && values) memcpy(&staged[acc], values + list_off[b], (size_t)len * sizeof(double));
-    acc += len;
-    h_row_ptr[blk_row[b] + 1]++;
-  }
-  for (int32_t i = 0; i < nbrows; i++) h_row_ptr[i + 1] += h_row_ptr[i];
-  if (!sorted && values) vsrc = staged.data();
   cudaStream_t s = ctx->stream;
-  int64_t hdr[2] = {nblocks, nnz};
   auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
     return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
   };
@@ -1017,26 +1102,36 @@ int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_
   if ((e = cp(M->row_sizes, row_sizes, (size_t)nbrows * 4)) != cudaSuccess ||
       (e = cp(M->col_sizes, col_sizes, (size_t)nbcols * 4)) != cudaSuccess ||
       (e = cp(M->row_cls, h_row_cls.data(), (size_t)nbrows * 4)) != cudaSuccess ||
-      (e = cp(M->col_cls, h_col_cls.data(), (size_t)nbcols * 4)) != cudaSuccess ||
-      (e = cp(M->front.row_ptr, h_row_ptr.data(), ((size_t)nbrows + 1) * 4)) != cudaSuccess ||
-      (e = cp(M->front.col_idx, h_col.data(), (size_t)nblocks * 4)) != cudaSuccess ||
-      (e = cp(M->front.blk_row, h_row.data(), (size_t)nblocks * 4)) != cudaSuccess ||
-      (e = cp(M->front.blk_off, h_off.data(), (size_t)nblocks * 8)) != cudaSuccess ||
-      (e = cp(M->front.hdr, hdr, sizeof(hdr))) != cudaSuccess) {
+      (e = cp(M->col_cls, h_col_cls.data(), (size_t)nbcols * 4)) != cudaSuccess)
     return fail(cuda_fail(e, "bsm_mat_create copy"));
-  }
-  if (vsrc) {
-    if ((e = cp(M->front.vals, vsrc, (size_t)nnz * 8)) != cudaSuccess)
-      return fail(cuda_fail(e, "bsm_mat_create values"));
-  } else if (nnz > 0) {
-    if ((e = cudaMemsetAsync(M->front.vals, 0, (size_t)nnz * 8, s)) != cudaSuccess)
-      return fail(cuda_fail(e, "bsm_mat_create zero"));
-  }
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "bsm_mat_create sync"));
-  M->nblk = nblocks;
-  M->nnz = nnz;
+  if ((rc = upload_contents(M, nblocks, blk_row, blk_col, values, true))) return fail(rc);
   *out = M;
   return BSM_OK;
+}
+
+int bsm_mat_assign(bsm_mat m, int64_t nblocks, const int32_t *blk_row, const int32_t *blk_col,
+                   const double *values) {
+  if (!m) return BSM_ERR_INVALID_ARG;
+  int rc = ctx_set_device(m->ctx);
+  if (rc || (rc = quiesce(m))) return rc;
+  m->pend.active = false;  // a result computed into m is replaced, not read
+  const void *before[2] = {m->front.col_idx, m->front.vals};
+  rc = upload_contents(m, nblocks, blk_row, blk_col, values, false);
+  if (before[0] != m->front.col_idx || before[1] != m->front.vals) {
+    // captured multiplies may name the old buffers
+    for (auto &g : m->ctx->graphs) cudaGraphExecDestroy(g.exec);
+    m->ctx->graphs.clear();
+  }
+  const bool validation = rc == BSM_ERR_INVALID_ARG || rc == BSM_ERR_OUT_OF_RANGE ||
+                          rc == BSM_ERR_DUPLICATE_BLOCK || rc == BSM_ERR_UNSUPPORTED;
+  if (rc && !validation) {  // the old contents may be partly overwritten: leave m empty
+    m->nblk = m->nnz = 0;
+    int64_t z[2] = {0, 0};
+    if (m->front.hdr) cudaMemcpy(m->front.hdr, z, sizeof(z), cudaMemcpyHostToDevice);
+    if (m->front.row_ptr)
+      cudaMemset(m->front.row_ptr, 0, ((size_t)m->nbr + 1) * sizeof(int32_t));
+  }
+  return rc;
 }
 
 int bsm_mat_destroy(bsm_mat m) {

@@ -317,3 +317,35 @@ def test_host_values_small_or_pageable(gpu_ctx, bsm_lib, oracle_mod):
     assert e.value.name == "INVALID_ARG"
     dA.destroy()
     dC.destroy()
+
+
+def test_assign_reuses_matrix(gpu_ctx, bsm_lib, oracle_mod):
+    """bsm_mat_assign: a new block list (smaller, then larger than the buffers)
+    in the same handle; multiplies (also graph replays) see the new contents;
+    a bad block list leaves the handle unchanged."""
+    rng = np.random.default_rng(77)
+    rs = rng.choice([1, 5, 13], 30)
+    big = synth.random_blocks(rng, rs, rs, 0.5, kind="int")
+    small = synth.random_blocks(rng, rs, rs, 0.1, kind="int")
+    mid = synth.random_blocks(rng, rs, rs, 0.3, kind="normal", shuffle=True)
+    dA = gpu_ctx.from_blocks(mid)
+    dC = gpu_ctx.empty(rs, rs)
+    for M, graph in ((small, False), (big, True), (mid, True), (small, True)):
+        dA.assign(M.blk_row, M.blk_col, M.values)
+        for _ in range(2):
+            gpu_ctx.multiply(1.0, dA, dA, 0.0, dC, 0.0, graph=graph)
+            ref = oracle_mod.multiply(M, M)
+            r, c = dC.pattern()
+            assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+            assert H.rel_frobenius(dC.values(), ref.values) <= TOL
+    with pytest.raises(bsm_lib.BsmError) as e:
+        dA.assign([0, 0], [1, 1], np.zeros(2 * int(rs[0]) * int(rs[1])))
+    assert e.value.name == "DUPLICATE_BLOCK"
+    with pytest.raises(bsm_lib.BsmError) as e:
+        dA.assign([len(rs)], [0], np.zeros(int(rs[0])))
+    assert e.value.name == "OUT_OF_RANGE"
+    r, c = dA.pattern()  # still `small`
+    assert np.array_equal(r, small.blk_row) and np.array_equal(c, small.blk_col)
+    assert np.array_equal(dA.values(), small.values)
+    dA.destroy()
+    dC.destroy()
