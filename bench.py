@@ -378,6 +378,119 @@ def serve_bench(args):
     return 0
 
 
+def next_bench(args):
+    """The next items beside the multiply, on the device, one JSON line:
+    the post-multiplication filter and the block-sparse add on the water2048
+    result, and the sign iteration of Eq. 3 (Newton-Schulz, two filtered
+    multiplies per iteration plus the post filter) on water512."""
+    import torch
+
+    import synth
+    from paper_1705_10218_gb300 import Context
+    from paper_1705_10218_gb300.sign import block_identity
+
+    torch.cuda.set_device(0)
+    ctx = Context(0)
+    out = {"metric": "next items: post filter, block-sparse add (GB/s), sign iteration (GFLOP/s)",
+           "n_gpus": 1, "dtype": "f64", "data": "synthetic", "impl": "ours"}
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    # post filter and add on C = A.A (water2048)
+    A, eps = make_workload("water2048")
+    dA = ctx.from_blocks(A)
+    dC = ctx.empty(A.row_sizes, A.col_sizes)
+    ctx.multiply(1.0, dA, dA, 0.0, dC, eps, blocking=True)
+    nb0, nnz0 = dC.nblocks()
+    r, c = dC.pattern()
+    v = dC.values()
+    lens = A.row_sizes.astype(np.int64)[r] * A.col_sizes.astype(np.int64)[c]
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    nrm = np.sqrt(np.add.reduceat(v * v, off[:-1]))
+    feps = float(np.percentile(nrm, 30))
+    times, kept = [], 0
+    for k in range(args.warmup + args.steps):
+        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, blocking=True)
+        dt = wall(lambda: dC.filter(feps))
+        if k >= args.warmup:
+            times.append(dt)
+    nb1, nnz1 = dC.nblocks()
+    fbytes = 8 * nnz0 + 16 * nnz1  # norms read every value; kept values read and written
+    ms = 1e3 * statistics.median(times)
+    out["post_filter"] = {"workload": "water2048 C = A.A", "eps": feps, "blocks_before": nb0,
+                          "blocks_after": nb1, "ms": round(ms, 3),
+                          "gb_per_s": round(fbytes / (ms / 1e3) / 1e9, 1),
+                          "algorithmic": "8 B per value (norms) + 16 B per kept value (copy)"}
+    times = []
+    ctx.multiply(1.0, dA, dA, 0.0, dC, eps, blocking=True)
+    for k in range(args.warmup + args.steps):
+        dt = wall(lambda: ctx.add(1.0, dA, 1.0, dC))
+        if k >= args.warmup:
+            times.append(dt)
+    nb2, nnz2 = dC.nblocks()
+    abytes = 8 * (len(A.values) + nnz0 + nnz2)
+    ms = 1e3 * statistics.median(times)
+    out["add"] = {"workload": "water2048: C = C + A", "ms": round(ms, 3),
+                  "gb_per_s": round(abytes / (ms / 1e3) / 1e9, 1),
+                  "algorithmic": "A and C read once, the sum written once"}
+    dA.destroy()
+    dC.destroy()
+
+    # sign iteration on water512: X0 = (A - mu I) / ||A - mu I||_F
+    S = synth.water(512, seed=1)
+    vals = S.values.copy()
+    lens = S.row_sizes.astype(np.int64)[S.blk_row] * S.col_sizes.astype(np.int64)[S.blk_col]
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    diag = []
+    for b in np.nonzero(S.blk_row == S.blk_col)[0]:
+        n = int(S.row_sizes[S.blk_row[b]])
+        diag.append(off[b] + np.arange(n) * (n + 1))
+    diag = np.concatenate(diag)
+    mu = float(vals[diag].mean())
+    vals[diag] -= mu
+    vals /= np.linalg.norm(vals)
+    sizes = S.row_sizes
+    X = ctx.matrix(sizes, sizes, S.blk_row, S.blk_col, vals)
+    eps_s, feps_s = 1e-8, 1e-6
+    its = []
+    for it in range(8):
+        T = block_identity(ctx, sizes, 3.0)
+        s1 = ctx.multiply(-1.0, X, X, 1.0, T, eps_s, stats=True)  # 3I - X^2
+        Xn = ctx.empty(sizes, sizes)
+        s2 = ctx.multiply(0.5, X, T, 0.0, Xn, eps_s, stats=True)  # X (3I - X^2) / 2
+        tf = wall(lambda: Xn.filter(feps_s))
+        T.destroy()
+        X.destroy()
+        X = Xn
+        nb, nz = X.nblocks()
+        ms = s1.ms_total + s2.ms_total
+        its.append({"iter": it + 1, "gflop": round((s1.flops + s2.flops) / 1e9, 2),
+                    "multiply_ms": round(ms, 2), "filter_ms": round(1e3 * tf, 2),
+                    "gflop_per_s": round((s1.flops + s2.flops) / (ms / 1e3) / 1e9, 1),
+                    "x_blocks": nb, "x_block_occupancy": round(nb / (S.nbr * S.nbr), 4),
+                    "dropped_products": s1.dropped + s2.dropped})
+    # convergence: || X^2 - I ||_F / sqrt(N)
+    Y = ctx.empty(sizes, sizes)
+    ctx.multiply(1.0, X, X, 0.0, Y, 0.0, blocking=True)
+    ctx.add(-1.0, block_identity(ctx, sizes), 1.0, Y)
+    idem = float(np.linalg.norm(Y.values()) / np.sqrt(sizes.sum()))
+    tot_f = sum(i["gflop"] for i in its)
+    tot_ms = sum(i["multiply_ms"] for i in its)
+    out["sign_iteration"] = {"workload": "water512 (N = 11776), X0 = (A - mu I)/||A - mu I||_F",
+                             "eps": eps_s, "post_filter_eps": feps_s, "iterations": its,
+                             "gflop_per_s": round(tot_f / (tot_ms / 1e3), 1),
+                             "idempotency_error": idem}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,6 +510,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true", help="the request-loop benchmark instead")
+    ap.add_argument("--next", action="store_true",
+                    help="post filter, block-sparse add and sign iteration instead")
     ap.add_argument("--requests", type=int, default=500)
     ap.add_argument("--serve-pool", type=int, default=48)
     ap.add_argument("--slots", type=int, default=4)
@@ -404,6 +519,8 @@ def main():
     args = ap.parse_args()
     if args.serve:
         return serve_bench(args)
+    if args.next:
+        return next_bench(args)
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
     if args.impl == "reference":

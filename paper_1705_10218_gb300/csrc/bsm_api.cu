@@ -1277,7 +1277,8 @@ int bsm_mat_filter(bsm_mat M, double eps) {
   int rc = ctx_set_device(ctx);
   if (rc || (rc = resolve(M))) return rc;
   cudaStream_t s = ctx->stream;
-  if ((rc = ws_rows(ctx, M->nbr)) || (rc = buf_grow(M, M->back, M->nblk, M->nnz, false)))
+  if ((rc = ws_rows(ctx, M->nbr)) || (rc = buf_grow(M, M->back, M->nblk, M->nnz, false)) ||
+      (rc = ws_grow(ctx, M->nblk, 0)))
     return rc;
   if ((rc = enqueue_norms(ctx, M, s))) return rc;
   DevMat dM = dev_view(M);
@@ -1286,7 +1287,7 @@ int bsm_mat_filter(bsm_mat M, double eps) {
   CK(launch_filter_count(dM, eps, ws, ctx->nsm, s));
   CK(launch_symbolic_scan(M->nbr, ws, out, ctx->d_status, s));
   CK(launch_filter_fill(dM, eps, ws, out, ctx->d_status, ctx->nsm, s));
-  ctx->launches += 4;
+  ctx->launches += 5;
   DevStatus h{};
   CK(cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

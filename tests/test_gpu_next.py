@@ -120,3 +120,22 @@ def test_partial_panels_on_device(gpu_ctx, oracle_mod):
         assert H.rel_frobenius(M.values(), ref.values) <= 1e-12
     for m in owned:
         m.destroy()
+
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 1.0), (-0.3, 0.7), (1.7, 0.0)])
+def test_add_parity_float_bit_exact(gpu_ctx, oracle_mod, alpha, beta):
+    """The device add rounds beta*C and alpha*A separately and then their sum,
+    as the oracle does: bit-identical values on normal data, including
+    many-block rows that span several 32-block copy steps."""
+    rng = np.random.default_rng(23)
+    rs, cs = rng.choice([1, 5, 13, 32], 60), rng.choice([1, 5, 13], 200)
+    A = synth.random_blocks(rng, rs, cs, 0.4, kind="normal", shuffle=True)
+    C = synth.random_blocks(rng, rs, cs, 0.4, kind="normal", shuffle=True)
+    ref = oracle_mod.add(alpha, A, beta, C)
+    dA, dC = gpu_ctx.from_blocks(A), gpu_ctx.from_blocks(C)
+    gpu_ctx.add(alpha, dA, beta, dC)
+    r, c = dC.pattern()
+    assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+    assert np.array_equal(dC.values(), ref.values)
+    dA.destroy()
+    dC.destroy()
