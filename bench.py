@@ -678,6 +678,9 @@ def main():
         err = float(np.linalg.norm(gv[:nv] - r.values) / np.linalg.norm(r.values)) if same else None
         cpu["gpu_pattern_equal_on_sample"] = bool(same)
         cpu["gpu_rel_err_on_sample"] = err
+        if same and nv:
+            cpu["gpu_max_abs_err_on_sample"] = float(np.max(np.abs(gv[:nv] - r.values)))
+            cpu["max_abs_value_on_sample"] = float(np.max(np.abs(r.values)))
 
     if rank == 0:
         srt = sorted(per_step)
