@@ -42,8 +42,8 @@ WORKLOADS = {
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
 # FP64 numeric kernels (BSM_FP64_*): name -> (number, kernel symbol)
 FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64_t16"),
-                "t32": (2, "k_numeric_fp64_t32"), "pkb2": (3, "k_numeric_fp64_pk"),
-                "pkb3": (4, "k_numeric_fp64_pk")}
+                "t32": (2, "k_numeric_fp64_t32"), "pk12": (3, "k_numeric_fp64_pk"),
+                "pk16": (4, "k_numeric_fp64_pk")}
 FP64_BY_NUMBER = {v[0]: k for k, v in FP64_KERNELS.items()}
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/): valid only while
@@ -51,7 +51,7 @@ FP64_BY_NUMBER = {v[0]: k for k, v in FP64_KERNELS.items()}
 MEASURED_TRAFFIC = {
     ("k_numeric_fp64_pk", "water2048", "fp64"): dict(
         source="paper_1705_10218_gb300/csrc/k_numeric_fp64.cu",
-        sha256="9d144530ff1eeb916b0337555faec222e98f011e592e378fb8fe00d085ba542c",
+        sha256="b4cd9822b6591929bb012e0c8d57a3bca77bb275188bd079efc781abbde75392",
         bytes=8.87e9 + 1.59e9),
 }
 

@@ -67,20 +67,21 @@ enum {
 
 /* FP64 numeric kernels. bsm_opts.fp64_kernel = 1 + one of these forces that
  * kernel for every shape class (no autotuning); 0 leaves the choice to the
- * library: the tuned one with autotune, else PK_B2, or T16_B2 when the last
+ * library: the tuned one with autotune, else PK12, or T16_B2 when the last
  * multiply into the same C had fewer than 4 block products per C block (there
  * the per-block setup of PK costs more than its fuller lanes save).
  *   T16: one output element per lane slot, 16 x 16 tiles, 2 or 3 blocks/SM;
  *   T32: 32 x 32 tiles, synchronous staging;
- *   PK:  packed lane slots (output element, k-group) over the products of a C
- *        block concatenated along k, 16 x 16 tiles, 2 or 3 blocks/SM.
+ *   PK12, PK16: packed lane slots (output element, k-group) over the products
+ *        of a C block concatenated along k, 16 x 16 tiles, 12 or 16 slots per
+ *        lane, 2 blocks/SM.
  * All give the same result up to the order of the FP64 additions. */
 enum {
   BSM_FP64_T16_B2 = 0,
   BSM_FP64_T16_B3 = 1,
   BSM_FP64_T32 = 2,
-  BSM_FP64_PK_B2 = 3,
-  BSM_FP64_PK_B3 = 4,
+  BSM_FP64_PK12 = 3,
+  BSM_FP64_PK16 = 4,
   BSM_FP64_NUM_KERNELS = 5
 };
 

@@ -12,8 +12,8 @@ marshals arguments (see :mod:`paper_1705_10218_gb300.bsm`).
 """
 from .bsm import (  # noqa: F401
     BSM_FP64_NUM_KERNELS,
-    BSM_FP64_PK_B2,
-    BSM_FP64_PK_B3,
+    BSM_FP64_PK12,
+    BSM_FP64_PK16,
     BSM_FP64_T16_B2,
     BSM_FP64_T16_B3,
     BSM_FP64_T32,

@@ -28,8 +28,8 @@ BSM_LAUNCH_PER_STACK = 1
 BSM_FP64_T16_B2 = 0
 BSM_FP64_T16_B3 = 1
 BSM_FP64_T32 = 2
-BSM_FP64_PK_B2 = 3
-BSM_FP64_PK_B3 = 4
+BSM_FP64_PK12 = 3
+BSM_FP64_PK16 = 4
 BSM_FP64_NUM_KERNELS = 5
 
 

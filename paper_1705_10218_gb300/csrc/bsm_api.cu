@@ -426,8 +426,8 @@ static bool needs_tuning(bsm_ctx ctx, bsm_mat A, bsm_mat B, const bsm_opts &o) {
 }
 
 static_assert(kFp64T16B2 == BSM_FP64_T16_B2 && kFp64T16B3 == BSM_FP64_T16_B3 &&
-                  kFp64T32 == BSM_FP64_T32 && kFp64PkB2 == BSM_FP64_PK_B2 &&
-                  kFp64PkB3 == BSM_FP64_PK_B3 && kFp64NumVariants == BSM_FP64_NUM_KERNELS,
+                  kFp64T32 == BSM_FP64_T32 && kFp64Pk12 == BSM_FP64_PK12 &&
+                  kFp64Pk16 == BSM_FP64_PK16 && kFp64NumVariants == BSM_FP64_NUM_KERNELS,
               "public and internal FP64 kernel numbers differ");
 
 // The default FP64 kernel for a result C: the packed kernel, unless the last
@@ -435,7 +435,7 @@ static_assert(kFp64T16B2 == BSM_FP64_T16_B2 && kFp64T16B3 == BSM_FP64_T16_B3 &&
 // the previous result, or of this one once the symbolic totals were read).
 static int fp64_default(bsm_ctx ctx, bsm_mat C) {
   if (C->hint_blk > 0 && ctx->hint_prod < 4 * C->hint_blk) return kFp64T16B2;
-  return kFp64PkB2;
+  return kFp64Pk12;
 }
 
 // The forced kernel, else the tuned one, else the default.

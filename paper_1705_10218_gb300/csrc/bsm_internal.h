@@ -100,8 +100,8 @@ enum {
   kFp64T16B2 = 0,
   kFp64T16B3 = 1,
   kFp64T32 = 2,
-  kFp64PkB2 = 3,
-  kFp64PkB3 = 4,
+  kFp64Pk12 = 3,
+  kFp64Pk16 = 4,
   kFp64NumVariants = 5
 };
 int fp64_variant_blocks_per_sm(int variant);
@@ -117,7 +117,7 @@ cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMa
                                 const int32_t *items, const int64_t *seg, int grid,
                                 unsigned long long *work, cudaStream_t stream);
 inline bool fp64_variant_uses_work(int variant) {
-  return variant == kFp64PkB2 || variant == kFp64PkB3;
+  return variant == kFp64Pk12 || variant == kFp64Pk16;
 }
 
 // Shape classes (k_classes.cu): class of C block g = row_cls[row] * ncc +
@@ -151,7 +151,7 @@ cudaError_t launch_filter_fill(DevMat M, double eps, DevWs ws, DevOut O, const D
 // and the multiply did not overflow.
 cudaError_t launch_copy_out(DevOut O, const DevStatus *st, int nsm, cudaStream_t stream);
 inline bool fp64_variant_writes_host(int variant) {
-  return variant == kFp64PkB2 || variant == kFp64PkB3;
+  return variant == kFp64Pk12 || variant == kFp64Pk16;
 }
 
 cudaError_t launch_add(int stage, DevMat A, DevMat Cin, int use_cin, double alpha, double beta,

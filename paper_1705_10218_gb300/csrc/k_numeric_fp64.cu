@@ -271,36 +271,30 @@ __global__ void __launch_bounds__(kSWarps * 32, MINB)
 // ----------------------------------------------------------------------------
 // pk
 // ----------------------------------------------------------------------------
-constexpr int kPkWarps = 8;          // warps per thread block
+constexpr int kPkWarps = 8;          // warps per thread block (2 blocks per SM)
 constexpr int kPkTile = 16;          // output tile edge
-constexpr int kPkSlots = 16;         // accumulator slots per lane (largest nT)
+constexpr int kPkMaxSlots = 16;      // accumulator slots per lane (largest nT) of the pk16 variant
 constexpr int kPkMaxG = 8;           // largest number of k-groups
 constexpr int kPkMaxKC = 32;         // largest chunk (k positions)
-// Doubles per stage (two stages per warp): 880 fits 2 blocks of 8 warps per SM,
-// 560 fits 3. A tile of tm x tn takes chunks of KC k positions with
-// KC * tm + tn * (KC + 1) within the stage.
-template <int MINB>
-struct PkStage {
-  static constexpr int kDoubles = MINB >= 3 ? 560 : 880;
-};
-static_assert(32 * kPkSlots <= 560, "the slot sums must fit one stage");
+// Doubles per stage (two stages per warp; 2 blocks of 8 warps fit an SM). A
+// tile of tm x tn takes chunks of KC k positions with KC * tm + tn * (KC + 1)
+// within the stage.
+constexpr int kPkStage = 880;
+static_assert(32 * kPkMaxSlots <= kPkStage, "the slot sums must fit one stage");
 
-template <int MINB>
-size_t pk_smem_bytes() {
-  return (size_t)kPkWarps * 2 * PkStage<MINB>::kDoubles * sizeof(double);
-}
+size_t pk_smem_bytes() { return (size_t)kPkWarps * 2 * kPkStage * sizeof(double); }
 
-// Slot shape of a tile of te (1..256) elements: the (nT, G) with nT <= kPkSlots,
-// G <= kPkMaxG and te * G <= 32 * nT that maximises te * G / (32 * nT), the
-// smallest nT among equals.
+// Slot shape of a tile of te (1..256) elements with at most `slots` slots per
+// lane: the (nT, G) with nT <= slots, G <= kPkMaxG and te * G <= 32 * nT that
+// maximises te * G / (32 * nT), the smallest nT among equals.
 struct PkShapes {
   uint8_t nt[kPkTile * kPkTile + 1], g[kPkTile * kPkTile + 1];
 };
-constexpr PkShapes make_pk_shapes() {
+constexpr PkShapes make_pk_shapes(int slots) {
   PkShapes tab{};
   for (int te = 1; te <= kPkTile * kPkTile; te++) {
     int bt = (te + 31) / 32, bg = 1;
-    for (int t = 1; t <= kPkSlots; t++) {
+    for (int t = 1; t <= slots; t++) {
       int g = (32 * t) / te;
       if (g > kPkMaxG) g = kPkMaxG;
       if (g >= 1 && g * bt > bg * t) {
@@ -313,7 +307,8 @@ constexpr PkShapes make_pk_shapes() {
   }
   return tab;
 }
-__constant__ PkShapes c_pk_shapes = make_pk_shapes();
+__constant__ PkShapes c_pk_shapes12 = make_pk_shapes(12);
+__constant__ PkShapes c_pk_shapes16 = make_pk_shapes(16);
 
 // floor(x / d) as (x * r) >> 16 with r = ceil(2^16 / d): exact while
 // x * (r * d - 2^16) < 2^16, i.e. for d <= 16 and x < 4096 (the error term is
@@ -339,11 +334,11 @@ constexpr int kPkGrab = 1;
 // constant, so all loads of a step can be issued ahead of its FMAs; the step
 // loop itself is not unrolled (with 16 instances, unrolled copies overflow the
 // instruction cache on workloads with many tile shapes).
-template <int NT>
+template <int NT, int SLOTS>
 __device__ __forceinline__ void pk_steps(const double *__restrict__ sA,
                                          const double *__restrict__ sB,
-                                         const uint32_t (&idx)[kPkSlots],
-                                         double (&acc)[kPkSlots], int steps, int gtm, int G) {
+                                         const uint32_t (&idx)[SLOTS],
+                                         double (&acc)[SLOTS], int steps, int gtm, int G) {
 #pragma unroll 1  // one copy of the step body per NT keeps the instruction footprint small
   for (int u = 0; u < steps; u++) {
 #pragma unroll
@@ -355,13 +350,17 @@ __device__ __forceinline__ void pk_steps(const double *__restrict__ sA,
 
 // work: a counter that is zero when the launch starts; warps take the next
 // kPkGrab C blocks of the work range from it until the range is exhausted.
-template <int MINB>
-__global__ void __launch_bounds__(kPkWarps * 32, MINB)
+// SLOTS: accumulator slots per lane (12 or 16). Fewer slots lower the lane use
+// of some tile shapes (13 x 13: 96% instead of 99%) but shorten the per-tile
+// code; which wins depends on the block mix (the autotuner measures it).
+template <int SLOTS>
+__global__ void __launch_bounds__(kPkWarps * 32, 2)
     k_numeric_fp64_pk(DevMat A, DevMat B, DevOut C, DevMat Cin, double alpha, double beta,
                       DevWs ws, const DevStatus *st, const int32_t *items, const int64_t *seg,
                       unsigned long long *work) {
   if (st->overflow) return;
-  constexpr int kStage = PkStage<MINB>::kDoubles;
+  constexpr int kStage = kPkStage;
+  const PkShapes &shapes = (SLOTS == 12) ? c_pk_shapes12 : c_pk_shapes16;
   extern __shared__ double smem_pk[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double *wbuf = smem_pk + warp * 2 * kStage;
@@ -390,7 +389,7 @@ __global__ void __launch_bounds__(kPkWarps * 32, MINB)
         for (int c0 = 0; c0 < n; c0 += kPkTile) {
           const int tm = min(kPkTile, m - r0), tn = min(kPkTile, n - c0);
           const int te = tm * tn;
-          const int nT = c_pk_shapes.nt[te], G = c_pk_shapes.g[te];
+          const int nT = shapes.nt[te], G = shapes.g[te];
           const int used = te * G;
           const uint32_t rtm = rcp16(tm), rg = rcp16(G);
           // chunk length: the largest multiple of G with KC * tm + tn * (KC + 1) <= kStage
@@ -401,16 +400,16 @@ __global__ void __launch_bounds__(kPkWarps * 32, MINB)
           // slot t of this lane: z = lane + 32 t -> group g = z / te, element
           // e = z % te (row e % tm, column e / tm); its operands at step 0 are
           // sA[ia] and sB[ib], kept as ia | ib << 16 (both below 2^9)
-          uint32_t idx[kPkSlots];
-          double acc[kPkSlots];
+          uint32_t idx[SLOTS];
+          double acc[SLOTS];
           {
             int g = 0, e = lane;
             while (e >= te) {
               e -= te;
               g++;
             }
-  #pragma unroll
-            for (int t = 0; t < kPkSlots; t++) {
+#pragma unroll
+            for (int t = 0; t < SLOTS; t++) {
               idx[t] = 0;  // slots past te * G read valid operands; their sums are discarded
               if (g < G) {
                 const int c = div16(e, rtm), r = e - c * tm;
@@ -521,15 +520,15 @@ __global__ void __launch_bounds__(kPkWarps * 32, MINB)
             const double *sB = sA + KC * tm;
             const int gtm = G * tm;
             switch (nT) {
-  #define BSM_PK_CASE(N)                              \
-    case N:                                           \
-      pk_steps<N>(sA, sB, idx, acc, cur, gtm, G);     \
-      break;
+#define BSM_PK_CASE(N)                                                                 \
+  case N:                                                                              \
+    if (N <= SLOTS) pk_steps<(N <= SLOTS ? N : 1), SLOTS>(sA, sB, idx, acc, cur, gtm, G); \
+    break;
               BSM_PK_CASE(1) BSM_PK_CASE(2) BSM_PK_CASE(3) BSM_PK_CASE(4)
               BSM_PK_CASE(5) BSM_PK_CASE(6) BSM_PK_CASE(7) BSM_PK_CASE(8)
               BSM_PK_CASE(9) BSM_PK_CASE(10) BSM_PK_CASE(11) BSM_PK_CASE(12)
               BSM_PK_CASE(13) BSM_PK_CASE(14) BSM_PK_CASE(15) BSM_PK_CASE(16)
-  #undef BSM_PK_CASE
+#undef BSM_PK_CASE
             }
             __syncwarp();  // the stage is read before it is filled again
             if (nxt == 0) break;
@@ -540,8 +539,8 @@ __global__ void __launch_bounds__(kPkWarps * 32, MINB)
 
           // the G partial sums of each element, added in group order
           double *red = wbuf;
-  #pragma unroll
-          for (int t = 0; t < kPkSlots; t++) {
+#pragma unroll
+          for (int t = 0; t < SLOTS; t++) {
             const int z = lane + 32 * t;
             if (t < nT && z < used) red[z] = acc[t];
           }
@@ -585,12 +584,12 @@ cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMa
                                                                  st, items, seg);
       break;
     }
-    case kFp64PkB2:
-      k_numeric_fp64_pk<2><<<grid, kPkWarps * 32, pk_smem_bytes<2>(), stream>>>(
+    case kFp64Pk12:
+      k_numeric_fp64_pk<12><<<grid, kPkWarps * 32, pk_smem_bytes(), stream>>>(
           A, B, C, Cin, alpha, beta, ws, st, items, seg, work);
       break;
-    case kFp64PkB3:
-      k_numeric_fp64_pk<3><<<grid, kPkWarps * 32, pk_smem_bytes<3>(), stream>>>(
+    case kFp64Pk16:
+      k_numeric_fp64_pk<16><<<grid, kPkWarps * 32, pk_smem_bytes(), stream>>>(
           A, B, C, Cin, alpha, beta, ws, st, items, seg, work);
       break;
     default:
@@ -601,7 +600,7 @@ cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMa
 }
 
 int fp64_variant_blocks_per_sm(int variant) {
-  return (variant == kFp64T16B2 || variant == kFp64PkB2) ? 2 : 3;
+  return (variant == kFp64T16B3 || variant == kFp64T32) ? 3 : 2;
 }
 
 cudaError_t numeric_fp64_init() {
@@ -609,11 +608,11 @@ cudaError_t numeric_fp64_init() {
   cudaError_t e = cudaFuncSetAttribute(k_numeric_fp64_t32,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_numeric_fp64_pk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)pk_smem_bytes<2>());
+  e = cudaFuncSetAttribute(k_numeric_fp64_pk<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pk_smem_bytes());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_numeric_fp64_pk<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)pk_smem_bytes<3>());
+  return cudaFuncSetAttribute(k_numeric_fp64_pk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pk_smem_bytes());
 }
 
 }  // namespace bsm

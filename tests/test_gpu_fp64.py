@@ -205,7 +205,7 @@ def test_torch_stream(gpu_ctx, oracle_mod):
     ref, v, _ = check(gpu_ctx, oracle_mod, A, A, eps=1e-10, stream=s)
 
 
-FP64_KERNELS = range(5)  # BSM_FP64_T16_B2 .. BSM_FP64_PK_B3
+FP64_KERNELS = range(5)  # BSM_FP64_T16_B2 .. BSM_FP64_PK16
 
 
 @pytest.mark.parametrize("kern", FP64_KERNELS)
@@ -260,13 +260,13 @@ def test_default_fp64_kernel(bsm_lib, oracle_mod):
     count hint is kept per context."""
     W = synth.water(16, seed=2)
     S = synth.sparse_random(3000, 6, 5e-4, seed=1)
-    for M, want in ((W, bsm_lib.BSM_FP64_PK_B2), (S, bsm_lib.BSM_FP64_T16_B2)):
+    for M, want in ((W, bsm_lib.BSM_FP64_PK12), (S, bsm_lib.BSM_FP64_T16_B2)):
         ctx = bsm_lib.Context(0)
         try:
             ctx.profile(True)
             ref, _, st = check(ctx, oracle_mod, M, M, eps=1e-10)
             assert ctx.profile_read().last_fp64_kernel == want
-            assert (st.kept >= 4 * st.c_blocks) == (want == bsm_lib.BSM_FP64_PK_B2)
+            assert (st.kept >= 4 * st.c_blocks) == (want == bsm_lib.BSM_FP64_PK12)
         finally:
             ctx.close()
 
