@@ -501,17 +501,20 @@ static int launch_numeric(Launch &L, int variant, const int32_t *items, const in
   if (L.split) {
     const int smax = L.A->max_col;
     if (max_m <= 16 && max_n <= 16) {
+      CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
       CK(launch_numeric_split(L.o.precision, 0, L.dA, L.dB, L.out, L.dC, L.A->split_left,
                               L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
-                              smax, ctx->nsm, L.s));
+                              smax, ctx->nsm, ctx->d_work, L.s));
     } else {
+      CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
       CK(launch_numeric_split(L.o.precision, 1, L.dA, L.dB, L.out, L.dC, L.A->split_left,
                               L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
-                              smax, ctx->nsm, L.s));
+                              smax, ctx->nsm, ctx->d_work, L.s));
       ctx->launches++;
+      CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
       CK(launch_numeric_split(L.o.precision, 2, L.dA, L.dB, L.out, L.dC, L.A->split_left,
                               L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items, seg,
-                              smax, ctx->nsm, L.s));
+                              smax, ctx->nsm, ctx->d_work, L.s));
     }
   } else {
     if (fp64_variant_uses_work(variant))

@@ -141,7 +141,8 @@ cudaError_t launch_split(int precision, const int32_t *row_sizes, const int32_t 
 cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, DevOut C,
                                  DevMat Cin, const void *a_left, const void *b_right, double alpha,
                                  double beta, DevWs ws, const DevStatus *st, const int32_t *items,
-                                 const int64_t *seg, int smax, int nsm, cudaStream_t stream);
+                                 const int64_t *seg, int smax, int nsm, unsigned long long *work,
+                                 cudaStream_t stream);
 // Post filter and block-sparse add (k_extra.cu).
 cudaError_t launch_filter_count(DevMat M, double eps, DevWs ws, int nsm, cudaStream_t stream);
 cudaError_t launch_filter_fill(DevMat M, double eps, DevWs ws, DevOut O, const DevStatus *st,

@@ -533,7 +533,8 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
     k_numeric_split_pipe(DevMat A, DevMat B, DevOut C, DevMat Cin, const void *__restrict__ a_left,
                          const void *__restrict__ b_right, double alpha, double beta, DevWs ws,
                          const DevStatus *st, const int32_t *__restrict__ items,
-                         const int64_t *__restrict__ seg, int smax, int only_small) {
+                         const int64_t *__restrict__ seg, int smax, int only_small,
+                         unsigned long long *work) {
   if (st->overflow) return;
   constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
   constexpr int KSTEP = BF ? 16 : 8;
@@ -552,10 +553,13 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
     wb = seg[0];
     we = seg[1];
   }
-  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool plain = (alpha == 1.0 && beta == 0.0);
-  for (int64_t w = wb + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); w < we;
-       w += nwarp) {
+  // C blocks come one at a time from the work counter (zero at launch)
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(work, 1ull);
+    const int64_t w = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    if (w >= we) break;
     const int64_t gb = items ? items[w] : w;
     const int i = C.blk_row[gb], j = C.col_idx[gb];
     const int m = C.row_sizes[i], n = C.col_sizes[j];
@@ -722,7 +726,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
   }
 }
 
-// One warp per C block (grid-stride over the work list). SIZES selects the
+// One warp per C block (dynamically assigned). SIZES selects the
 // blocks a launch takes: 0 all (every MMA problem fits 16 x 16), 1 those that
 // fit 16 x 16, 2 the others (up to 32 x 32). Small blocks use 1 x 2 tiles with
 // prefetching; large ones 2 x 4 tiles without (register budget).
@@ -733,16 +737,21 @@ __global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOu
                                                        double alpha, double beta, DevWs ws,
                                                        const DevStatus *st,
                                                        const int32_t *__restrict__ items,
-                                                       const int64_t *__restrict__ seg) {
+                                                       const int64_t *__restrict__ seg,
+                                                       unsigned long long *work) {
   if (st->overflow) return;
+  const int lane = threadIdx.x & 31;
   int64_t wb = 0, we = st->nblk_c;
   if (seg) {
     wb = seg[0];
     we = seg[1];
   }
-  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = wb + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); w < we;
-       w += nwarp) {
+  // C blocks come one at a time from the work counter (zero at launch)
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(work, 1ull);
+    const int64_t w = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    if (w >= we) break;
     const int64_t gb = items ? items[w] : w;
     const int i = C.blk_row[gb], j = C.col_idx[gb];
     const int m = C.row_sizes[i], n = C.col_sizes[j];
@@ -765,15 +774,16 @@ __global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOu
 cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, DevOut C,
                                  DevMat Cin, const void *a_left, const void *b_right, double alpha,
                                  double beta, DevWs ws, const DevStatus *st, const int32_t *items,
-                                 const int64_t *seg, int smax, int nsm, cudaStream_t stream) {
+                                 const int64_t *seg, int smax, int nsm, unsigned long long *work,
+                                 cudaStream_t stream) {
   if (sizes == 2) {  // blocks beyond 16 x 16: direct fragment loads, 2 x 4 tiles
     const int grid = nsm * 2;
     if (precision == BSM_PREC_SPLIT_BF16X3)
       k_numeric_split<BSM_PREC_SPLIT_BF16X3, 2><<<grid, 128, 0, stream>>>(
-          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg);
+          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, work);
     else
       k_numeric_split<BSM_PREC_SPLIT_TF32X2, 2><<<grid, 128, 0, stream>>>(
-          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg);
+          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, work);
     return cudaGetLastError();
   }
   const size_t smem = (size_t)kPipeWarps * pipe_warp_bytes(precision, smax);
@@ -789,10 +799,10 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
   const int grid = nsm * (per_sm > 0 ? per_sm : 1);
   if (precision == BSM_PREC_SPLIT_BF16X3)
     k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3><<<grid, kPipeWarps * 32, smem, stream>>>(
-        A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sizes == 1);
+        A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sizes == 1, work);
   else
     k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2><<<grid, kPipeWarps * 32, smem, stream>>>(
-        A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sizes == 1);
+        A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sizes == 1, work);
   return cudaGetLastError();
 }
 
