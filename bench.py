@@ -51,24 +51,34 @@ FP64_BY_NUMBER = {v[0]: k for k, v in FP64_KERNELS.items()}
 MEASURED_TRAFFIC = {
     ("k_numeric_fp64_pk", "water2048", "fp64"): dict(
         source="paper_1705_10218_gb300/csrc/k_numeric_fp64.cu",
-        sha256="b4cd9822b6591929bb012e0c8d57a3bca77bb275188bd079efc781abbde75392",
+        section=("// pk\n", "cudaError_t launch_numeric_fp64("),
+        sha256="5f1515463fae6160a66f2e243ed0e2d5428949629604d79648e44370236cad79",
         bytes=8.87e9 + 1.59e9),
 }
+
+
+def kernel_source_sha(source, section):
+    """SHA-256 of the part of a source file between two markers (the kernel's
+    own code), or None when the file or a marker is missing."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, source)) as f:
+            text = f.read()
+    except OSError:
+        return None
+    a = text.find(section[0])
+    b = text.find(section[1], a + 1) if a >= 0 else -1
+    if a < 0 or b < 0:
+        return None
+    return hashlib.sha256(text[a:b].encode()).hexdigest()
 
 
 def measured_traffic(kernel, workload, precision):
     """DRAM bytes per launch from the ncu capture, or None when there is none
     for this kernel and workload or the kernel's source changed since."""
-    import hashlib
-
     m = MEASURED_TRAFFIC.get((kernel, workload, precision))
-    if m is None:
-        return None
-    try:
-        with open(os.path.join(ROOT, m["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != m["sha256"]:
-                return None
-    except OSError:
+    if m is None or kernel_source_sha(m["source"], m["section"]) != m["sha256"]:
         return None
     return m["bytes"]
 

@@ -110,15 +110,13 @@ cudaError_t numeric_fp64_init();
 
 // items: optional work list of C block indices; seg: optional device [begin,
 // end) into it (default: all C blocks of the multiply, in row order).
-// work: a device counter that must be zero when the launch starts (used by the
-// pk variants, which hand out C blocks dynamically; may be null for the others).
+// work: a device counter that must be zero when the launch starts (the t16 and
+// pk variants hand out C blocks dynamically; may be null for t32).
 cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMat Cin,
                                 double alpha, double beta, DevWs ws, const DevStatus *st,
                                 const int32_t *items, const int64_t *seg, int grid,
                                 unsigned long long *work, cudaStream_t stream);
-inline bool fp64_variant_uses_work(int variant) {
-  return variant == kFp64Pk12 || variant == kFp64Pk16;
-}
+inline bool fp64_variant_uses_work(int variant) { return variant != kFp64T32; }
 
 // Shape classes (k_classes.cu): class of C block g = row_cls[row] * ncc +
 // col_cls[col]; items receives the C blocks grouped by class, segs[2c..2c+1]

@@ -12,7 +12,8 @@
 //        operands are already in flight in registers while the current one is
 //        multiplied. The (A offset, B offset, k) of up to 32 products are read
 //        at once, one per lane, and handed out with warp shuffles. Compiled for
-//        2 or 3 thread blocks of 8 warps per SM.
+//        2 or 3 thread blocks of 8 warps per SM; C blocks are taken one at a
+//        time from a work counter.
 //   t32: 32 x 32 output tiles, synchronous staging, 4 warps per block.
 //   pk:  "packed" lane slots for tiles of up to 16 x 16: a lane slot is a pair
 //        (output element, k-group), so a tile of te elements is computed by
@@ -170,7 +171,8 @@ __device__ __forceinline__ void t16_load(const double *__restrict__ Ab,
 template <int MINB>
 __global__ void __launch_bounds__(kSWarps * 32, MINB)
     k_numeric_fp64_t16(DevMat A, DevMat B, DevOut C, DevMat Cin, double alpha, double beta,
-                       DevWs ws, const DevStatus *st, const int32_t *items, const int64_t *seg) {
+                       DevWs ws, const DevStatus *st, const int32_t *items, const int64_t *seg,
+                       unsigned long long *work) {
   if (st->overflow) return;
   __shared__ double smem_t16[kSWarps][2 * kS * kS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -178,89 +180,100 @@ __global__ void __launch_bounds__(kSWarps * 32, MINB)
   double *sB = sA + kS * kS;
   int64_t wb, we;
   work_range(st, seg, wb, we);
-  const int64_t nwarp = (int64_t)gridDim.x * kSWarps;
 
-  for (int64_t w = wb + (int64_t)blockIdx.x * kSWarps + warp; w < we; w += nwarp) {
-    const int64_t g = items ? items[w] : w;
-    const int i = C.blk_row[g], j = C.col_idx[g];
-    const int m = C.row_sizes[i], n = C.col_sizes[j];
-    const int64_t p0 = ws.prod_ptr[g], p1 = ws.prod_ptr[g + 1];
-    const int cin = ws.c_cin[g];
-    const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
-    double *out = C.vals + C.blk_off[g];
+  // C blocks come from the work counter (zero at launch), `grab` at a time:
+  // one when there are few per warp, up to 8 when there are many (tiny C
+  // blocks would otherwise queue on the counter)
+  const int64_t per_warp = (we - wb) / ((int64_t)gridDim.x * kSWarps * 64);
+  const int grab = per_warp < 1 ? 1 : (per_warp > 8 ? 8 : (int)per_warp);
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(work, (unsigned long long)grab);
+    const int64_t w0 = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    if (w0 >= we) break;
+    const int64_t w1 = (w0 + grab < we) ? w0 + grab : we;
+    for (int64_t w = w0; w < w1; w++) {
+      const int64_t g = items ? items[w] : w;
+      const int i = C.blk_row[g], j = C.col_idx[g];
+      const int m = C.row_sizes[i], n = C.col_sizes[j];
+      const int64_t p0 = ws.prod_ptr[g], p1 = ws.prod_ptr[g + 1];
+      const int cin = ws.c_cin[g];
+      const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+      double *out = C.vals + C.blk_off[g];
 
-    for (int r0 = 0; r0 < m; r0 += kS) {
-      for (int c0 = 0; c0 < n; c0 += kS) {
-        const int tm = min(kS, m - r0), tn = min(kS, n - c0);
-        const int te = tm * tn;
-        const int nT = (te + 31) >> 5;
-        int rc[kSElems];  // (row, col) in the tile of the lane's t-th output, r | c << 8
-        double acc[kSElems];
+      for (int r0 = 0; r0 < m; r0 += kS) {
+        for (int c0 = 0; c0 < n; c0 += kS) {
+          const int tm = min(kS, m - r0), tn = min(kS, n - c0);
+          const int te = tm * tn;
+          const int nT = (te + 31) >> 5;
+          int rc[kSElems];  // (row, col) in the tile of the lane's t-th output, r | c << 8
+          double acc[kSElems];
 #pragma unroll
-        for (int t = 0; t < kSElems; t++) {
-          const int e = lane + 32 * t;
-          rc[t] = (e < te) ? (e % tm) | ((e / tm) << 8) : 0;  // past the tile: a valid dummy
-          acc[t] = 0.0;
-        }
-        for (int64_t pb = p0; pb < p1; pb += 32) {
-          const int nb = (p1 - pb < 32) ? (int)(p1 - pb) : 32;
-          int64_t my_a = 0, my_b = 0;
-          int my_s = 1;
-          if (lane < nb) {
-            const int2 pr = ws.prods[pb + lane];
-            my_a = A.blk_off[pr.x];
-            my_b = B.blk_off[pr.y];
-            my_s = A.col_sizes[A.col_idx[pr.x]];
+          for (int t = 0; t < kSElems; t++) {
+            const int e = lane + 32 * t;
+            rc[t] = (e < te) ? (e % tm) | ((e / tm) << 8) : 0;  // past the tile: a valid dummy
+            acc[t] = 0.0;
           }
-          double ra[kSElems], rb[kSElems];
-          int q = 0, l0 = 0;
-          int s = __shfl_sync(0xffffffffu, my_s, 0);
-          t16_load(A.vals + __shfl_sync(0xffffffffu, my_a, 0),
-                   B.vals + __shfl_sync(0xffffffffu, my_b, 0), m, s, r0, c0, 0, tm, tn,
-                   min(kS, s), lane, ra, rb);
-          while (q < nb) {
-            __syncwarp();
-#pragma unroll
-            for (int u = 0; u < kSElems; u++) {
-              sA[lane + 32 * u] = ra[u];
-              sB[lane + 32 * u] = rb[u];
+          for (int64_t pb = p0; pb < p1; pb += 32) {
+            const int nb = (p1 - pb < 32) ? (int)(p1 - pb) : 32;
+            int64_t my_a = 0, my_b = 0;
+            int my_s = 1;
+            if (lane < nb) {
+              const int2 pr = ws.prods[pb + lane];
+              my_a = A.blk_off[pr.x];
+              my_b = B.blk_off[pr.y];
+              my_s = A.col_sizes[A.col_idx[pr.x]];
             }
-            __syncwarp();
-            const int kc = min(kS, s - l0);
-            // the next step: the next k-chunk of this product, or the next product
-            int nq = q, nl0 = l0 + kS;
-            if (nl0 >= s) {
-              nq = q + 1;
-              nl0 = 0;
-            }
-            // warp-uniform: every lane evaluates the same (nq, nl0)
-            const int ns = __shfl_sync(0xffffffffu, my_s, nq < nb ? nq : 0);
-            const int64_t na = __shfl_sync(0xffffffffu, my_a, nq < nb ? nq : 0);
-            const int64_t nbo = __shfl_sync(0xffffffffu, my_b, nq < nb ? nq : 0);
-            if (nq < nb)
-              t16_load(A.vals + na, B.vals + nbo, m, ns, r0, c0, nl0, tm, tn, min(kS, ns - nl0),
-                       lane, ra, rb);
-            for (int l = 0; l < kc; l++) {
+            double ra[kSElems], rb[kSElems];
+            int q = 0, l0 = 0;
+            int s = __shfl_sync(0xffffffffu, my_s, 0);
+            t16_load(A.vals + __shfl_sync(0xffffffffu, my_a, 0),
+                     B.vals + __shfl_sync(0xffffffffu, my_b, 0), m, s, r0, c0, 0, tm, tn,
+                     min(kS, s), lane, ra, rb);
+            while (q < nb) {
+              __syncwarp();
 #pragma unroll
-              for (int t = 0; t < kSElems; t++) {
-                if (t >= nT) break;
-                acc[t] = fma(sA[(rc[t] & 255) + l * tm], sB[(rc[t] >> 8) * kc + l], acc[t]);
+              for (int u = 0; u < kSElems; u++) {
+                sA[lane + 32 * u] = ra[u];
+                sB[lane + 32 * u] = rb[u];
               }
-            }
-            q = nq;
-            l0 = nl0;
-            s = ns;
-          }
-        }
-        // epilogue: C_ij = beta * C_in_ij + alpha * S_ij
+              __syncwarp();
+              const int kc = min(kS, s - l0);
+              // the next step: the next k-chunk of this product, or the next product
+              int nq = q, nl0 = l0 + kS;
+              if (nl0 >= s) {
+                nq = q + 1;
+                nl0 = 0;
+              }
+              // warp-uniform: every lane evaluates the same (nq, nl0)
+              const int ns = __shfl_sync(0xffffffffu, my_s, nq < nb ? nq : 0);
+              const int64_t na = __shfl_sync(0xffffffffu, my_a, nq < nb ? nq : 0);
+              const int64_t nbo = __shfl_sync(0xffffffffu, my_b, nq < nb ? nq : 0);
+              if (nq < nb)
+                t16_load(A.vals + na, B.vals + nbo, m, ns, r0, c0, nl0, tm, tn, min(kS, ns - nl0),
+                         lane, ra, rb);
+              for (int l = 0; l < kc; l++) {
 #pragma unroll
-        for (int t = 0; t < kSElems; t++) {
-          const int e = lane + 32 * t;
-          if (t < nT && e < te) {
-            const int64_t loc = (int64_t)(c0 + (rc[t] >> 8)) * m + r0 + (rc[t] & 255);
-            double v = alpha * acc[t];
-            if (cinv) v = fma(beta, cinv[loc], v);
-            out[loc] = v;
+                for (int t = 0; t < kSElems; t++) {
+                  if (t >= nT) break;
+                  acc[t] = fma(sA[(rc[t] & 255) + l * tm], sB[(rc[t] >> 8) * kc + l], acc[t]);
+                }
+              }
+              q = nq;
+              l0 = nl0;
+              s = ns;
+            }
+          }
+          // epilogue: C_ij = beta * C_in_ij + alpha * S_ij
+#pragma unroll
+          for (int t = 0; t < kSElems; t++) {
+            const int e = lane + 32 * t;
+            if (t < nT && e < te) {
+              const int64_t loc = (int64_t)(c0 + (rc[t] >> 8)) * m + r0 + (rc[t] & 255);
+              double v = alpha * acc[t];
+              if (cinv) v = fma(beta, cinv[loc], v);
+              out[loc] = v;
+            }
           }
         }
       }
@@ -575,7 +588,7 @@ cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMa
   switch (variant) {
     case kFp64T16B3:
       k_numeric_fp64_t16<3><<<grid, kSWarps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws, st,
-                                                               items, seg);
+                                                               items, seg, work);
       break;
     case kFp64T32: {
       // the shared-memory attribute is set once per device by numeric_fp64_init
@@ -594,7 +607,7 @@ cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMa
       break;
     default:
       k_numeric_fp64_t16<2><<<grid, kSWarps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws, st,
-                                                               items, seg);
+                                                               items, seg, work);
   }
   return cudaGetLastError();
 }
