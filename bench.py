@@ -52,7 +52,7 @@ MEASURED_TRAFFIC = {
     ("k_numeric_fp64_pk", "water2048", "fp64"): dict(
         source="paper_1705_10218_gb300/csrc/k_numeric_fp64.cu",
         section=("// pk\n", "cudaError_t launch_numeric_fp64("),
-        sha256="5f1515463fae6160a66f2e243ed0e2d5428949629604d79648e44370236cad79",
+        sha256="06626473816c4d2631726748450de2df93e9ce80562b03e8b56c1e7bfbdfdf1f",
         bytes=8.87e9 + 1.59e9),
 }
 

@@ -288,7 +288,7 @@ constexpr int kPkWarps = 8;          // warps per thread block (2 blocks per SM)
 constexpr int kPkTile = 16;          // output tile edge
 constexpr int kPkMaxSlots = 16;      // accumulator slots per lane (largest nT) of the pk16 variant
 constexpr int kPkMaxG = 8;           // largest number of k-groups
-constexpr int kPkMaxKC = 32;         // largest chunk (k positions)
+constexpr int kPkMaxKC = 64;         // largest chunk (k positions)
 // Doubles per stage (two stages per warp; 2 blocks of 8 warps fit an SM). A
 // tile of tm x tn takes chunks of KC k positions with KC * tm + tn * (KC + 1)
 // within the stage.
