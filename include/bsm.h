@@ -55,7 +55,7 @@ enum {
   BSM_ERR_NOMEM = -6,           /* device or pinned host allocation failed */
   BSM_ERR_CUDA = -7,            /* a CUDA runtime error (details: bsm_last_cuda_error) */
   BSM_ERR_TIMEOUT = -8,         /* a bounded device-side wait gave up */
-  BSM_ERR_UNSUPPORTED = -9      /* valid request this build does not handle */
+  BSM_ERR_UNSUPPORTED = -9      /* valid request the library does not handle */
 };
 
 /* Arithmetic of the block products (C accumulation is always FP64). */

@@ -5,9 +5,13 @@ oracle, through the C ABI.
   product is exact and all FP32 partial sums stay far below 2^24, so the result
   must equal the oracle bit for bit.
 * General values: the pattern is bit-exact (same symbolic phase) and every
-  element obeys the bound derived from the slicing:
+  element obeys the bound that follows from the slicing and the FP32 sums:
       |C - C_ref| <= (u_split + K * 2^-23) * (|A| |B|) + tiny,
-  u_split = 3 * 2^-22 (BF16x3) or 2^-19 (TF32x2), K the inner dimension.
+  u_split = 3 * 2^-22 (BF16x3: each operand is represented within 2^-23 of
+  its value by its three slices and the dropped slice products are below
+  2^-22) or 2^-19 (TF32x2: the dropped a2*b2 term is below 2^-20 and each
+  operand's representation error below 2^-21), K the inner dimension (one
+  FP32 rounding per accumulated term).
 """
 import numpy as np
 import pytest
