@@ -488,13 +488,16 @@ __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, c
 // ---------------------------------------------------------------------------
 // Pipelined kernel for blocks whose MMA problem fits 16 x 16 (the water and
 // small-block case). Each warp streams the slices of its C block's products
-// through a ring of kStages shared-memory slots with 16-byte asynchronous
-// copies (cp.async), kStages - 1 products ahead of the tensor-core work, so the
+// through a ring of STAGES shared-memory slots with 16-byte asynchronous
+// copies (cp.async), STAGES - 1 products ahead of the tensor-core work, so the
 // L2 latency of a product's operands is hidden behind the products before it.
 // The (A offset, B offset, k) of the products are read 32 at a time into a
 // per-warp table in shared memory.
 // ---------------------------------------------------------------------------
-constexpr int kStages = 4;
+// STAGES is chosen per launch from the largest block size: deeper rings hide
+// more latency, shallower ones leave room for more warps per SM, and warps
+// count more once the slots are large (3 stages up to 16 x 16 blocks, else 2).
+inline int pipe_stages(int smax) { return smax <= 16 ? 3 : 2; }
 constexpr int kPipeWarps = 4;
 // Products summed plainly in FP32 before each compensated fold: a partial sum
 // of kFold products carries kFold times the rounding of one, still far below
@@ -524,11 +527,11 @@ __device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
 __host__ __device__ __forceinline__ int pipe_operand_bytes(int precision, int smax) {
   return precision == BSM_PREC_SPLIT_BF16X3 ? 96 * (smax + (smax & 1)) : 128 * smax;
 }
-__host__ __device__ __forceinline__ int pipe_warp_bytes(int precision, int smax) {
-  return kStages * 2 * pipe_operand_bytes(precision, smax) + kMetaBytes;
+__host__ __device__ __forceinline__ int pipe_warp_bytes(int precision, int smax, int stages) {
+  return stages * 2 * pipe_operand_bytes(precision, smax) + kMetaBytes;
 }
 
-template <int PREC>
+template <int PREC, int STAGES>
 __global__ void __launch_bounds__(kPipeWarps * 32)
     k_numeric_split_pipe(DevMat A, DevMat B, DevOut C, DevMat Cin, const void *__restrict__ a_left,
                          const void *__restrict__ b_right, double alpha, double beta, DevWs ws,
@@ -542,8 +545,8 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int opb = pipe_operand_bytes(PREC, smax);
-  unsigned char *wbase = smem_pipe + warp * pipe_warp_bytes(PREC, smax);
-  int64_t *meta_a = reinterpret_cast<int64_t *>(wbase + kStages * 2 * opb);
+  unsigned char *wbase = smem_pipe + warp * pipe_warp_bytes(PREC, smax, STAGES);
+  int64_t *meta_a = reinterpret_cast<int64_t *>(wbase + STAGES * 2 * opb);
   int64_t *meta_b = meta_a + kMetaEntries;
   int *meta_s = reinterpret_cast<int *>(meta_b + kMetaEntries);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(wbase);
@@ -578,7 +581,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
 #pragma unroll
       for (int x = 0; x < 4; x++) hi[nt][x] = lo[nt][x] = acc[nt][x] = 0.f;
 
-    // copies of product q into slot q % kStages; always commits one group
+    // copies of product q into slot q % STAGES; always commits one group
     auto issue = [&](int q) {
       if (q < np) {
         if ((q & 31) == 0) {  // the next 32 products' offsets and k
@@ -601,7 +604,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
                                         meta_b[q & (kMetaEntries - 1)];
         const int bytesA = BF ? 6 * mp2 * sp : 8 * m * s;
         const int bytesB = BF ? 6 * sp * np2 : 8 * s * n;
-        const uint32_t dst = sbase + (uint32_t)((q % kStages) * 2 * opb);
+        const uint32_t dst = sbase + (uint32_t)((q % STAGES) * 2 * opb);
         for (int c = lane; c < (bytesA + 15) >> 4; c += 32) cp_async16(dst + 16 * c, srcA + 16 * c);
         for (int c = lane; c < (bytesB + 15) >> 4; c += 32)
           cp_async16(dst + opb + 16 * c, srcB + 16 * c);
@@ -610,14 +613,14 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
     };
 
 #pragma unroll
-    for (int q = 0; q < kStages - 1; q++) issue(q);
+    for (int q = 0; q < STAGES - 1; q++) issue(q);
     for (int q = 0; q < np; q++) {
-      cp_async_wait<kStages - 2>();
+      cp_async_wait<STAGES - 2>();
       __syncwarp();
-      issue(q + kStages - 1);  // into the slot consumed by the previous product
+      issue(q + STAGES - 1);  // into the slot consumed by the previous product
       const int s = meta_s[q & (kMetaEntries - 1)];
       const int sp = s + (s & 1);
-      const uint32_t sA = sbase + (uint32_t)((q % kStages) * 2 * opb), sB = sA + opb;
+      const uint32_t sA = sbase + (uint32_t)((q % STAGES) * 2 * opb), sB = sA + opb;
       // L (M' x s, row-major) and R (s x N', column-major) in the slot
       const uint32_t sL = tr ? sB : sA, sR = tr ? sA : sB;
       if (BF) {
@@ -786,35 +789,58 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
           A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, work);
     return cudaGetLastError();
   }
-  const size_t smem = (size_t)kPipeWarps * pipe_warp_bytes(precision, smax);
-  int per_sm = 1;
-  cudaError_t e;
+  const int stages = pipe_stages(smax);
+  const size_t smem = (size_t)kPipeWarps * pipe_warp_bytes(precision, smax, stages);
+  const void *fn;
   if (precision == BSM_PREC_SPLIT_BF16X3)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3>, kPipeWarps * 32, smem);
+    fn = stages == 3 ? (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 3>
+                     : (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2>;
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2>, kPipeWarps * 32, smem);
+    fn = stages == 3 ? (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 3>
+                     : (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2>;
+  int per_sm = 1;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPipeWarps * 32, smem);
   if (e != cudaSuccess) return e;
   const int grid = nsm * (per_sm > 0 ? per_sm : 1);
-  if (precision == BSM_PREC_SPLIT_BF16X3)
-    k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3><<<grid, kPipeWarps * 32, smem, stream>>>(
-        A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sizes == 1, work);
-  else
-    k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2><<<grid, kPipeWarps * 32, smem, stream>>>(
-        A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sizes == 1, work);
+  const int only_small = sizes == 1;
+#define BSM_SPLIT_PIPE(P, S)                                                                \
+  k_numeric_split_pipe<P, S><<<grid, kPipeWarps * 32, smem, stream>>>(                      \
+      A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, only_small, work)
+  if (precision == BSM_PREC_SPLIT_BF16X3) {
+    if (stages == 3)
+      BSM_SPLIT_PIPE(BSM_PREC_SPLIT_BF16X3, 3);
+    else
+      BSM_SPLIT_PIPE(BSM_PREC_SPLIT_BF16X3, 2);
+  } else {
+    if (stages == 3)
+      BSM_SPLIT_PIPE(BSM_PREC_SPLIT_TF32X2, 3);
+    else
+      BSM_SPLIT_PIPE(BSM_PREC_SPLIT_TF32X2, 2);
+  }
+#undef BSM_SPLIT_PIPE
   return cudaGetLastError();
 }
 
 cudaError_t numeric_split_init() {
-  // the largest slot layout: k up to 32
-  const int bf = kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_BF16X3, 32);
-  const int tf = kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, 32);
-  cudaError_t e = cudaFuncSetAttribute(k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bf);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, tf);
+  // the largest slot layout of each instance: k up to 32
+  const struct {
+    const void *fn;
+    int bytes;
+  } inst[4] = {
+      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 3>,
+       kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_BF16X3, 32, 3)},
+      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2>,
+       kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_BF16X3, 32, 2)},
+      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 3>,
+       kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, 32, 3)},
+      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2>,
+       kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, 32, 2)},
+  };
+  for (const auto &x : inst) {
+    cudaError_t e = cudaFuncSetAttribute(x.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, x.bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace bsm
