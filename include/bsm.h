@@ -233,12 +233,14 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
 /* ---------------------------------------------------------------------------
  * Request loop (serving). Independent multiplies C = A.A of square block-sparse
  * systems of different sizes (the application's repeated multiplies, Sec. 1)
- * arrive one by one. The server keeps `slots` lanes, each with its own stream
- * and workspace; a request waits in a FIFO queue until a lane is free and its
- * device-memory footprint fits the budget beside the requests already held
- * (an upper bound before its multiply, the exact result size after), then it
- * is uploaded and runs while the other lanes' requests keep running. Results
- * stay on the device until taken. Single-threaded: call from one thread.
+ * arrive one by one. The server keeps `slots` lanes, each a context with its
+ * own stream, workspace and worker thread; a request waits in a FIFO queue
+ * until a lane is free and its device-memory footprint (an upper bound
+ * computed at submission) fits the budget beside the requests already held,
+ * then its lane uploads it, runs it while the other lanes run theirs, reads
+ * the result back into page-locked host memory and releases the device memory.
+ * Results wait there until taken (copied out) or released after use in place.
+ * The server functions are called from one thread.
  * ------------------------------------------------------------------------- */
 typedef struct bsm_server_s *bsm_server;
 
@@ -277,9 +279,21 @@ int bsm_server_poll(bsm_server s, int64_t id, int32_t *state, double *latency_ms
                     int64_t *nblocks, int64_t *nnz);
 
 /* Copy a finished request's result (pattern sorted by (row, col), values as
- * bsm_mat_get_values) to the host and release it. Null arrays skip a part. */
+ * bsm_mat_get_values) into the caller's arrays and release it. Null arrays skip
+ * a part; capacities below the result's sizes: INVALID_ARG (nothing released). */
 int bsm_server_take(bsm_server s, int64_t id, int64_t cap_blk, int32_t *blk_row,
                     int32_t *blk_col, int64_t cap_nnz, double *values);
+
+/* A finished request's result without a copy: pointers into page-locked host
+ * memory owned by the server (pattern sorted by (row, col), values as
+ * bsm_mat_get_values), valid until bsm_server_release (or bsm_server_take, or
+ * bsm_server_destroy). Null pointer arguments are skipped. INVALID_ARG if the
+ * request is unknown or not done. */
+int bsm_server_result(bsm_server s, int64_t id, const int32_t **blk_row, const int32_t **blk_col,
+                      const double **values, int64_t *nblocks, int64_t *nnz);
+
+/* Forget a finished (done or failed) request and return its result memory. */
+int bsm_server_release(bsm_server s, int64_t id);
 
 int bsm_server_get_info(bsm_server s, bsm_server_info *out);
 

@@ -364,6 +364,9 @@ _SIGS.update({
     "bsm_server_poll": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_D),
                                        ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "bsm_server_take": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _I64, _P]),
+    "bsm_server_result": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                         ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "bsm_server_release": (ctypes.c_int, [_P, _I64]),
     "bsm_server_get_info": (ctypes.c_int, [_P, ctypes.POINTER(_ServerInfo)]),
 })
 
@@ -411,6 +414,27 @@ class Server:
         v = np.empty(nz, np.float64)
         _check(lib().bsm_server_take(self._h, int(rid), nb, _vp(r), _vp(c), nz, _vp(v)), "bsm_server_take")
         return r, c, v
+
+    def result(self, rid: int):
+        """A finished request's (rows, cols, values) as numpy views of the
+        server's page-locked memory, without a copy; valid until release(rid)."""
+        pr, pc, pv, nb, nz = _P(), _P(), _P(), _I64(), _I64()
+        _check(lib().bsm_server_result(self._h, int(rid), ctypes.byref(pr), ctypes.byref(pc),
+                                       ctypes.byref(pv), ctypes.byref(nb), ctypes.byref(nz)),
+               "bsm_server_result")
+
+        def view(ptr, n, ctype, dtype):
+            if n == 0:
+                return np.zeros(0, dtype)
+            return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctype)), (n,))
+
+        return (view(pr.value, nb.value, ctypes.c_int32, np.int32),
+                view(pc.value, nb.value, ctypes.c_int32, np.int32),
+                view(pv.value, nz.value, ctypes.c_double, np.float64))
+
+    def release(self, rid: int):
+        """Forget a finished request; its result views become invalid."""
+        _check(lib().bsm_server_release(self._h, int(rid)), "bsm_server_release")
 
     def info(self) -> dict:
         i = _ServerInfo()

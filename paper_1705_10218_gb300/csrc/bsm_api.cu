@@ -21,6 +21,7 @@
 #include <string>
 #include <new>
 #include <numeric>
+#include <unordered_map>
 #include <vector>
 
 #include "bsm_internal.h"
@@ -43,22 +44,119 @@ int cuda_fail(cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
+// ---------------------------------------------------------------------------
+// Device memory. cudaFree synchronises the whole device (every stream of every
+// context), so the library keeps freed blocks in a per-device cache and
+// reuses them instead. Every caller frees a block only after the work that
+// used it has finished (after synchronising the owning context's stream), so
+// a cached block can go to any context. Sizes are rounded up to classes 1/8
+// of a power of two apart (under 12.5% slack); the cache holds at most
+// kCacheCap bytes per device (beyond that blocks are freed), a failed
+// cudaMalloc empties it and retries, and it is emptied when the last context
+// on the device is destroyed.
+// ---------------------------------------------------------------------------
+constexpr int kCacheDevices = 64;
+constexpr size_t kCacheCap = 16ull << 30;
+
+struct DevCache {
+  std::mutex mu;
+  std::multimap<size_t, void *> free_blocks;     // class -> block
+  std::unordered_map<void *, size_t> block_size;  // every block the cache handed out
+  size_t cached = 0;
+  int contexts = 0;
+};
+DevCache g_cache[kCacheDevices];
+
+size_t size_class(size_t b) {
+  if (b <= 256) return 256;
+  const int p = 63 - __builtin_clzll((unsigned long long)(b - 1));  // 2^p <= b - 1 < 2^(p+1)
+  const size_t step = (size_t)1 << (p - 3);
+  return (b + step - 1) & ~(step - 1);
+}
+
+DevCache *cache_of_current() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCacheDevices) return nullptr;
+  return &g_cache[dev];
+}
+
+// Frees every cached block (the caller holds c.mu).
+void cache_flush_locked(DevCache &c) {
+  for (auto &kv : c.free_blocks) {
+    c.block_size.erase(kv.second);
+    cudaFree(kv.second);
+  }
+  c.free_blocks.clear();
+  c.cached = 0;
+}
+
+cudaError_t cache_alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  DevCache *c = cache_of_current();
+  const size_t cls = size_class(bytes);
+  if (!c) return cudaMalloc(p, cls);
+  std::lock_guard<std::mutex> lock(c->mu);
+  auto it = c->free_blocks.find(cls);
+  if (it != c->free_blocks.end()) {
+    *p = it->second;
+    c->free_blocks.erase(it);
+    c->cached -= cls;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMalloc(p, cls);
+  if (e == cudaErrorMemoryAllocation && c->cached > 0) {  // give the cache back, retry
+    cudaGetLastError();
+    cache_flush_locked(*c);
+    e = cudaMalloc(p, cls);
+  }
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  c->block_size[*p] = cls;
+  return cudaSuccess;
+}
+
+void cache_free(void *p) {
+  if (!p) return;
+  DevCache *c = cache_of_current();
+  if (!c) {
+    cudaFree(p);
+    return;
+  }
+  std::lock_guard<std::mutex> lock(c->mu);
+  auto it = c->block_size.find(p);
+  if (it == c->block_size.end()) {  // not from the cache (another device current): plain free
+    cudaFree(p);
+    return;
+  }
+  const size_t cls = it->second;
+  if (c->cached + cls <= kCacheCap) {
+    c->free_blocks.emplace(cls, p);
+    c->cached += cls;
+  } else {
+    c->block_size.erase(it);
+    cudaFree(p);
+  }
+}
+
 template <class T>
 int dev_alloc(T **p, int64_t n) {
-  *p = nullptr;
   if (n <= 0) n = 1;
-  cudaError_t e = cudaMalloc((void **)p, (size_t)n * sizeof(T));
+  void *q = nullptr;
+  cudaError_t e = cache_alloc(&q, (size_t)n * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
     return cuda_fail(e, "cudaMalloc");
   }
+  *p = static_cast<T *>(q);
   return BSM_OK;
 }
 
 template <class T>
 void dev_free(T *&p) {
-  if (p) cudaFree((void *)p);
+  cache_free((void *)p);
   p = nullptr;
 }
 
@@ -341,10 +439,13 @@ static int split_buffers(bsm_mat M, int precision, bool left, bool right) {
   const int64_t need = std::max<int64_t>(M->nnz, 1) * split_bytes_per_value(precision);
   auto grow = [&](void *&p, int64_t &cap) -> int {
     if (cap >= need) return BSM_OK;
-    if (p) cudaFree(p);
+    if (p) {  // earlier multiplies may still read the slices
+      CK(cudaStreamSynchronize(M->ctx->stream));
+      cache_free(p);
+    }
     p = nullptr;
     cap = 0;
-    cudaError_t e = cudaMalloc(&p, (size_t)need);
+    cudaError_t e = cache_alloc(&p, (size_t)need);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, "cudaMalloc(slices)");
@@ -835,6 +936,10 @@ int bsm_ctx_create(int device, bsm_ctx *out) {
   bsm_ctx ctx = new (std::nothrow) bsm_ctx_s();
   if (!ctx) return BSM_ERR_NOMEM;
   ctx->device = device;
+  if (device < kCacheDevices) {  // the device-memory cache lives while a context does
+    std::lock_guard<std::mutex> lock(g_cache[device].mu);
+    g_cache[device].contexts++;
+  }
   int rc = BSM_OK;
   cudaError_t e;
   if ((e = cudaSetDevice(device)) != cudaSuccess ||
@@ -844,8 +949,8 @@ int bsm_ctx_create(int device, bsm_ctx *out) {
       (e = cudaEventCreateWithFlags(&ctx->ev_last, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev_t0)) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev_t1)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&ctx->d_status, sizeof(DevStatus))) != cudaSuccess ||
-      (e = cudaMalloc((void **)&ctx->d_work, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cache_alloc((void **)&ctx->d_status, sizeof(DevStatus))) != cudaSuccess ||
+      (e = cache_alloc((void **)&ctx->d_work, sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMallocHost((void **)&ctx->h_slots, kSlots * sizeof(DevStatus))) != cudaSuccess) {
     rc = cuda_fail(e, "bsm_ctx_create");
   }
@@ -919,6 +1024,11 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   if (ctx->ev_t0) cudaEventDestroy(ctx->ev_t0);
   if (ctx->ev_t1) cudaEventDestroy(ctx->ev_t1);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->device < kCacheDevices) {
+    DevCache &c = g_cache[ctx->device];
+    std::lock_guard<std::mutex> lock(c.mu);
+    if (--c.contexts == 0) cache_flush_locked(c);
+  }
   delete ctx;
   return BSM_OK;
 }
@@ -1149,8 +1259,8 @@ int bsm_mat_destroy(bsm_mat m) {
     if (ctx->slot_owner[i] == m) ctx->slot_owner[i] = nullptr;
   m->front.release();
   m->back.release();
-  if (m->split_left) cudaFree(m->split_left);
-  if (m->split_right) cudaFree(m->split_right);
+  cache_free(m->split_left);
+  cache_free(m->split_right);
   dev_free(m->row_sizes);
   dev_free(m->col_sizes);
   dev_free(m->row_cls);

@@ -2,24 +2,30 @@
 // multiplies C = A.A of differently sized systems arrive one by one and are run
 // with continuous batching.
 //
-// The server owns `slots` lanes, each a libbsm context with its own stream and
-// workspace. A request waits in a FIFO queue until a lane is free and its
-// device-memory footprint fits the budget next to the requests already held;
-// it is then uploaded and its multiply enqueued on that lane, while the other
-// lanes' multiplies keep running: requests of different sizes overlap on the
-// device, and a request that arrives while others run starts as soon as a lane
-// and memory free up (no waiting for a batch to drain). The footprint is an
-// upper bound before the multiply (A, a dense-or-candidate bound on C, the
-// product records) and the exact result size after it; results stay on the
-// device until taken. Everything goes through the public C ABI, so a request's
-// result is computed by exactly the kernels a lone bsm_multiply uses.
+// The server owns `slots` lanes, each a libbsm context (own stream and
+// workspace) driven by a worker thread of its own. A request waits in a FIFO
+// queue until a lane is free and its device-memory footprint fits the budget
+// next to the requests already held; the lane's worker then uploads it, runs
+// the multiply, copies the result to host memory and releases the device
+// memory, while the other lanes do the same with their requests: requests of
+// different sizes overlap on the device, and a request that arrives while
+// others run starts as soon as a lane and memory free up (no waiting for a
+// batch to drain). Host work of a request (validation, upload, read-back)
+// blocks only its own lane. The footprint is an upper bound computed before
+// the multiply (A, a dense-or-candidate bound on C, the product records), held
+// from admission to completion. Every step goes through the public C ABI, so a
+// request's result is computed by exactly the kernels a lone bsm_multiply uses.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/bsm.h"
@@ -39,23 +45,90 @@ struct Request {
   std::vector<double> vals;
   double eps = 0;
   int64_t footprint = 0;  // bytes held on the device while admitted
-  int state = kQueued;
+  int64_t c_vals_bound = 0;  // upper bound of the result's value count
+  int state = kQueued;    // changed by the caller's thread only
   int err = BSM_OK;
   int slot = -1;
   double t_submit = 0, t_start = 0, t_done = 0;
-  bsm_mat A = nullptr, C = nullptr;
   int64_t nblk = 0, nnz = 0;
+  // the result, once the lane is done: page-locked host blocks of the server's pool
+  int32_t *res_row = nullptr, *res_col = nullptr;
+  double *res_val = nullptr;
 };
 
+// Page-locked host memory for results: the lanes read results back into it at
+// the DMA rate (pageable memory goes through the driver's staging copies), and
+// a result can be handed to the caller without a copy. Freed blocks are kept
+// for reuse (cudaHostAlloc is slow), up to kPinnedCap bytes.
+constexpr size_t kPinnedCap = 16ull << 30;
+constexpr int64_t kHostValuesCap = 128ll << 20;  // values (1 GiB) a lane's multiply stores directly
+
+struct PinnedPool {
+  std::mutex mu;
+  std::multimap<size_t, void *> free_blocks;
+  std::map<void *, size_t> block_size;
+  size_t cached = 0;
+
+  static size_t size_class(size_t b) {
+    if (b <= 4096) return 4096;
+    const int p = 63 - __builtin_clzll((unsigned long long)(b - 1));
+    const size_t step = (size_t)1 << (p - 3);
+    return (b + step - 1) & ~(step - 1);
+  }
+  void *get(size_t bytes) {
+    const size_t cls = size_class(bytes);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = free_blocks.find(cls);
+    if (it != free_blocks.end()) {
+      void *p = it->second;
+      free_blocks.erase(it);
+      cached -= cls;
+      return p;
+    }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, cls, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    block_size[p] = cls;
+    return p;
+  }
+  void put(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = block_size.find(p);
+    if (it == block_size.end()) return;
+    if (cached + it->second <= kPinnedCap) {
+      free_blocks.emplace(it->second, p);
+      cached += it->second;
+    } else {
+      block_size.erase(it);
+      cudaFreeHost(p);
+    }
+  }
+  void clear() {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &kv : block_size) cudaFreeHost(kv.first);
+    block_size.clear();
+    free_blocks.clear();
+    cached = 0;
+  }
+};
+
+// A lane: a context and the worker thread that runs one request at a time on
+// it. `req` is handed over by the caller's thread and returned with `finished`.
 struct Slot {
   bsm_ctx ctx = nullptr;
-  cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;
   Request *req = nullptr;
+  bool finished = false;
+  bool stop = false;
 };
 
 // Upper bound of the device bytes a request C = A.A can hold.
-int64_t footprint_bound(const Request &r) {
+int64_t footprint_bound(const Request &r, int64_t *c_vals_bound) {
   const int64_t nbr = (int64_t)r.sizes.size();
   std::vector<int64_t> row_nblk(nbr, 0), row_cols(nbr, 0);
   for (size_t b = 0; b < r.brow.size(); b++) {
@@ -72,6 +145,7 @@ int64_t footprint_bound(const Request &r) {
   const int64_t a_bytes = 8 * (int64_t)r.vals.size() + 32 * (int64_t)r.brow.size();
   const int64_t c_blocks = std::min<int64_t>(nbr * nbr, cand);
   const int64_t c_vals = std::min<int64_t>(dim * dim, cand_vals);
+  if (c_vals_bound) *c_vals_bound = c_vals;
   // A (+ slices for the split precisions), C twice (front/back), per-block
   // metadata, product records
   return 4 * a_bytes + 2 * (8 * c_vals + 32 * c_blocks) + 8 * cand + 64 * nbr + (1 << 20);
@@ -88,14 +162,81 @@ struct bsm_server_s {
   std::map<int64_t, Request *> reqs;
   int64_t next_id = 1;
   int64_t completed = 0;
+  PinnedPool pinned;
 };
 
-static void release(bsm_server s, Request *r) {
-  if (r->A) bsm_mat_destroy(r->A);
-  if (r->C) bsm_mat_destroy(r->C);
-  r->A = r->C = nullptr;
-  s->in_use -= r->footprint;
-  r->footprint = 0;
+static void drop_result(bsm_server s, Request *r) {
+  s->pinned.put(r->res_row);
+  s->pinned.put(r->res_col);
+  s->pinned.put(r->res_val);
+  r->res_row = r->res_col = nullptr;
+  r->res_val = nullptr;
+}
+
+// One request on a lane, in the lane's worker thread: upload, multiply, result
+// to host memory, device memory released.
+static void run_request(bsm_server s, Slot &sl, Request *r) {
+  bsm_mat A = nullptr, C = nullptr;
+  const int32_t nbr = (int32_t)r->sizes.size();
+  int rc = bsm_mat_create(sl.ctx, nbr, r->sizes.data(), nbr, r->sizes.data(),
+                          (int64_t)r->brow.size(), r->brow.data(), r->bcol.data(), r->vals.data(),
+                          &A);
+  if (rc == BSM_OK)
+    rc = bsm_mat_create(sl.ctx, nbr, r->sizes.data(), nbr, r->sizes.data(), 0, nullptr, nullptr,
+                        nullptr, &C);
+  // the values go straight to page-locked host memory while the multiply runs,
+  // into a block sized by the bound on the result (up to kHostValuesCap values);
+  // a larger result is read back after the multiply
+  const int64_t hv_cap = std::min<int64_t>(std::max<int64_t>(r->c_vals_bound, 1), kHostValuesCap);
+  double *hv = (rc == BSM_OK) ? static_cast<double *>(s->pinned.get(8 * (size_t)hv_cap)) : nullptr;
+  if (rc == BSM_OK) {
+    bsm_opts o{};
+    o.precision = s->precision;
+    o.blocking = 1;
+    o.host_values = hv;
+    o.host_cap = hv ? hv_cap : 0;
+    rc = bsm_multiply(sl.ctx, 1.0, A, A, 0.0, C, r->eps, &o, nullptr);
+  }
+  if (rc == BSM_OK) rc = bsm_mat_nblocks(C, &r->nblk, &r->nnz);
+  if (rc == BSM_OK) {
+    r->res_row = static_cast<int32_t *>(s->pinned.get(4 * (size_t)r->nblk));
+    r->res_col = static_cast<int32_t *>(s->pinned.get(4 * (size_t)r->nblk));
+    const bool direct = hv && r->nnz <= hv_cap;  // the values are already in host memory
+    if (direct) {
+      r->res_val = hv;
+      hv = nullptr;
+    } else {
+      r->res_val = static_cast<double *>(s->pinned.get(8 * (size_t)r->nnz));
+    }
+    if (!r->res_row || !r->res_col || !r->res_val) rc = BSM_ERR_NOMEM;
+    if (rc == BSM_OK) rc = bsm_mat_get_pattern(C, r->nblk, r->res_row, r->res_col);
+    if (rc == BSM_OK && !direct) rc = bsm_mat_get_values(C, r->nnz, r->res_val);
+    if (rc != BSM_OK) drop_result(s, r);
+  }
+  s->pinned.put(hv);
+  if (A) bsm_mat_destroy(A);
+  if (C) bsm_mat_destroy(C);
+  std::vector<double>().swap(r->vals);  // the host copy of the input is no longer needed
+  r->err = rc;
+  r->t_done = now_ms();
+}
+
+static void worker_loop(bsm_server s, Slot *sl) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    Request *r;
+    {
+      std::unique_lock<std::mutex> lk(sl->mu);
+      sl->cv.wait(lk, [&] { return sl->stop || (sl->req && !sl->finished); });
+      if (!sl->req || sl->finished) return;  // stop with nothing to run
+      r = sl->req;
+    }
+    run_request(s, *sl, r);
+    {
+      std::lock_guard<std::mutex> lk(sl->mu);
+      sl->finished = true;
+    }
+  }
 }
 
 extern "C" {
@@ -117,17 +258,15 @@ int bsm_server_create(int device, const bsm_server_opts *opts, bsm_server *out) 
   s->device = device;
   s->precision = o.precision;
   s->budget = o.hbm_budget;
-  s->slots.resize(o.slots);
+  s->slots = std::vector<Slot>(o.slots);
   for (Slot &sl : s->slots) {
     int rc = bsm_ctx_create(device, &sl.ctx);
-    if (rc == BSM_OK && (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-                         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess))
-      rc = BSM_ERR_CUDA;
     if (rc != BSM_OK) {
       bsm_server_destroy(s);
       return rc;
     }
   }
+  for (Slot &sl : s->slots) sl.worker = std::thread(worker_loop, s, &sl);
   *out = s;
   return BSM_OK;
 }
@@ -135,19 +274,22 @@ int bsm_server_create(int device, const bsm_server_opts *opts, bsm_server *out) 
 int bsm_server_destroy(bsm_server s) {
   if (!s) return BSM_ERR_INVALID_ARG;
   cudaSetDevice(s->device);
-  for (Slot &sl : s->slots) {
-    if (sl.stream) cudaStreamSynchronize(sl.stream);
+  for (Slot &sl : s->slots) {  // a running request is finished first
+    {
+      std::lock_guard<std::mutex> lk(sl.mu);
+      sl.stop = true;
+    }
+    sl.cv.notify_one();
+    if (sl.worker.joinable()) sl.worker.join();
   }
   for (auto &kv : s->reqs) {
-    release(s, kv.second);
+    drop_result(s, kv.second);
     delete kv.second;
   }
   s->reqs.clear();
-  for (Slot &sl : s->slots) {
+  for (Slot &sl : s->slots)
     if (sl.ctx) bsm_ctx_destroy(sl.ctx);
-    if (sl.done) cudaEventDestroy(sl.done);
-    if (sl.stream) cudaStreamDestroy(sl.stream);
-  }
+  s->pinned.clear();
   delete s;
   return BSM_OK;
 }
@@ -178,7 +320,7 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
     }
   r->vals.assign(values, values + nv);
   r->eps = eps;
-  r->footprint = footprint_bound(*r);
+  r->footprint = footprint_bound(*r, &r->c_vals_bound);
   if (r->footprint > s->budget) {  // could never be admitted
     delete r;
     return BSM_ERR_NOMEM;
@@ -193,74 +335,45 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
 
 int bsm_server_progress(bsm_server s, int32_t *completed) {
   if (!s) return BSM_ERR_INVALID_ARG;
-  if (cudaSetDevice(s->device) != cudaSuccess) return BSM_ERR_CUDA;
   int32_t done = 0;
-  // 1. retire finished lanes
+  // 1. retire the requests the lanes have finished
   for (Slot &sl : s->slots) {
-    Request *r = sl.req;
+    Request *r = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(sl.mu);
+      if (sl.req && sl.finished) {
+        r = sl.req;
+        sl.req = nullptr;
+        sl.finished = false;
+      }
+    }
     if (!r) continue;
-    const cudaError_t q = cudaEventQuery(sl.done);
-    if (q == cudaErrorNotReady) continue;
-    if (q != cudaSuccess) {
-      r->err = BSM_ERR_CUDA;
-    } else {
-      r->err = bsm_mat_nblocks(r->C, &r->nblk, &r->nnz);  // completes the result
-    }
-    r->t_done = now_ms();
     r->state = r->err == BSM_OK ? kDone : kFailed;
-    if (r->A) bsm_mat_destroy(r->A);
-    r->A = nullptr;
-    // from the bound to what the result really holds (front and back buffers)
-    const int64_t held = r->err == BSM_OK ? 2 * (8 * r->nnz + 32 * r->nblk) : 0;
-    s->in_use += held - r->footprint;
-    r->footprint = held;
-    if (r->err != BSM_OK && r->C) {
-      bsm_mat_destroy(r->C);
-      r->C = nullptr;
-      s->in_use -= r->footprint;
-      r->footprint = 0;
-    }
-    sl.req = nullptr;
+    s->in_use -= r->footprint;  // the lane released the request's device memory
+    r->footprint = 0;
     s->completed++;
     done++;
   }
   // 2. admit from the head of the queue while a lane and memory are free
   for (Slot &sl : s->slots) {
-    if (sl.req || s->queue.empty()) continue;
+    if (s->queue.empty()) break;
+    {
+      std::lock_guard<std::mutex> lk(sl.mu);
+      if (sl.req) continue;
+    }
     Request *r = s->queue.front();
     if (s->in_use + r->footprint > s->budget) break;  // FIFO: wait for memory
     s->queue.pop_front();
     s->in_use += r->footprint;
     s->peak = std::max(s->peak, s->in_use);
-    const int32_t nbr = (int32_t)r->sizes.size();
-    int rc = bsm_mat_create(sl.ctx, nbr, r->sizes.data(), nbr, r->sizes.data(),
-                            (int64_t)r->brow.size(), r->brow.data(), r->bcol.data(),
-                            r->vals.data(), &r->A);
-    if (rc == BSM_OK)
-      rc = bsm_mat_create(sl.ctx, nbr, r->sizes.data(), nbr, r->sizes.data(), 0, nullptr, nullptr,
-                          nullptr, &r->C);
-    if (rc == BSM_OK) {
-      bsm_opts o{};
-      o.precision = s->precision;
-      o.stream = sl.stream;
-      rc = bsm_multiply(sl.ctx, 1.0, r->A, r->A, 0.0, r->C, r->eps, &o, nullptr);
-    }
-    if (rc == BSM_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = BSM_ERR_CUDA;
-    r->t_start = now_ms();
-    r->slot = (int)(&sl - s->slots.data());
-    if (rc != BSM_OK) {
-      r->err = rc;
-      r->state = kFailed;
-      r->t_done = r->t_start;
-      release(s, r);
-      s->completed++;
-      done++;
-      continue;
-    }
     r->state = kRunning;
-    sl.req = r;
-    // the host copies are no longer needed
-    std::vector<double>().swap(r->vals);
+    r->slot = (int)(&sl - s->slots.data());
+    r->t_start = now_ms();
+    {
+      std::lock_guard<std::mutex> lk(sl.mu);
+      sl.req = r;
+    }
+    sl.cv.notify_one();
   }
   if (completed) *completed = done;
   return BSM_OK;
@@ -288,17 +401,43 @@ int bsm_server_take(bsm_server s, int64_t id, int64_t cap_blk, int32_t *blk_row,
   if (r->state == kFailed) {
     const int err = r->err;
     s->reqs.erase(it);
-    release(s, r);
+    drop_result(s, r);
     delete r;
     return err;
   }
   if (r->state != kDone) return BSM_ERR_INVALID_ARG;
-  int rc = BSM_OK;
-  if (blk_row || blk_col) rc = bsm_mat_get_pattern(r->C, cap_blk, blk_row, blk_col);
-  if (rc == BSM_OK && values) rc = bsm_mat_get_values(r->C, cap_nnz, values);
-  if (rc != BSM_OK) return rc;  // e.g. a small cap: the result stays until taken
+  if (((blk_row || blk_col) && cap_blk < r->nblk) || (values && cap_nnz < r->nnz))
+    return BSM_ERR_INVALID_ARG;  // the result stays until taken
+  if (blk_row) std::copy(r->res_row, r->res_row + r->nblk, blk_row);
+  if (blk_col) std::copy(r->res_col, r->res_col + r->nblk, blk_col);
+  if (values) std::copy(r->res_val, r->res_val + r->nnz, values);
   s->reqs.erase(it);
-  release(s, r);
+  drop_result(s, r);
+  delete r;
+  return BSM_OK;
+}
+
+int bsm_server_result(bsm_server s, int64_t id, const int32_t **blk_row, const int32_t **blk_col,
+                      const double **values, int64_t *nblocks, int64_t *nnz) {
+  if (!s) return BSM_ERR_INVALID_ARG;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end() || it->second->state != kDone) return BSM_ERR_INVALID_ARG;
+  const Request *r = it->second;
+  if (blk_row) *blk_row = r->res_row;
+  if (blk_col) *blk_col = r->res_col;
+  if (values) *values = r->res_val;
+  if (nblocks) *nblocks = r->nblk;
+  if (nnz) *nnz = r->nnz;
+  return BSM_OK;
+}
+
+int bsm_server_release(bsm_server s, int64_t id) {
+  if (!s) return BSM_ERR_INVALID_ARG;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end() || it->second->state < kDone) return BSM_ERR_INVALID_ARG;
+  Request *r = it->second;
+  s->reqs.erase(it);
+  drop_result(s, r);
   delete r;
   return BSM_OK;
 }

@@ -78,3 +78,21 @@ def test_budget_admission_and_fifo(bsm_lib):
         for i in ids:
             srv.take(i)
         assert srv.info()["bytes_in_use"] == 0
+
+
+def test_result_views_and_release(bsm_lib, oracle_mod):
+    """bsm_server_result hands out the result in place (page-locked host memory)
+    and bsm_server_release returns it; the views equal a lone multiply's result."""
+    eps = 1e-10
+    systems = [synth.water(n, seed=3000 + n) for n in (12, 30, 20)]
+    with bsm_lib.Server(0, slots=2, hbm_budget=2 << 30) as srv:
+        ids = [srv.submit(A, eps) for A in systems]
+        drain(srv, ids)
+        for A, i in zip(systems, ids):
+            r, c, v = srv.result(i)
+            ra, ca, va = alone(bsm_lib, A, eps)
+            assert np.array_equal(r, ra) and np.array_equal(c, ca) and np.array_equal(v, va)
+            srv.release(i)
+            with pytest.raises(bsm_lib.BsmError):
+                srv.result(i)
+        assert srv.info()["bytes_in_use"] == 0
