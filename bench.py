@@ -47,9 +47,10 @@ FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64
 FP64_BY_NUMBER = {v[0]: k for k, v in FP64_KERNELS.items()}
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/): valid only while
-# the kernel's source file is unchanged (its SHA-256) and for that workload.
+# the kernel's source section is unchanged (its SHA-256), for that variant
+# (fp64 kernel name or split precision) and workload at its default eps.
 MEASURED_TRAFFIC = {
-    ("k_numeric_fp64_pk", "water2048", "fp64"): dict(
+    ("pk12", "water2048"): dict(
         source="paper_1705_10218_gb300/csrc/k_numeric_fp64.cu",
         section=("// pk\n", "cudaError_t launch_numeric_fp64("),
         sha256="06626473816c4d2631726748450de2df93e9ce80562b03e8b56c1e7bfbdfdf1f",
@@ -74,10 +75,10 @@ def kernel_source_sha(source, section):
     return hashlib.sha256(text[a:b].encode()).hexdigest()
 
 
-def measured_traffic(kernel, workload, precision):
+def measured_traffic(variant, workload):
     """DRAM bytes per launch from the ncu capture, or None when there is none
-    for this kernel and workload or the kernel's source changed since."""
-    m = MEASURED_TRAFFIC.get((kernel, workload, precision))
+    for this variant and workload or the kernel's source changed since."""
+    m = MEASURED_TRAFFIC.get((variant, workload))
     if m is None or kernel_source_sha(m["source"], m["section"]) != m["sha256"]:
         return None
     return m["bytes"]
@@ -649,7 +650,8 @@ def main():
         achieved = flops / (num_ms / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-                "traffic": measured_traffic(kname, args.workload, args.precision),
+                "traffic": (measured_traffic(FP64_BY_NUMBER[prof.last_fp64_kernel], args.workload)
+                            if prof.multiplies > 0 and args.eps_percentile is None else None),
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + write.sum)",
                 "kernel": kname, "peak_source": "nominal FP64 FMA rate of the GB300 (1.25 TFLOP/s)",
                 "algorithmic": "2*m*n*k over kept products per launch", "phase_ms": phase,

@@ -234,13 +234,14 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * Request loop (serving). Independent multiplies C = A.A of square block-sparse
  * systems of different sizes (the application's repeated multiplies, Sec. 1)
  * arrive one by one. The server keeps `slots` lanes, each a context with its
- * own stream, workspace and worker thread; a request waits in a FIFO queue
- * until a lane is free and its device-memory footprint (an upper bound
- * computed at submission) fits the budget beside the requests already held,
- * then its lane uploads it, runs it while the other lanes run theirs, reads
- * the result back into page-locked host memory and releases the device memory.
- * Results wait there until taken (copied out) or released after use in place.
- * The server functions are called from one thread.
+ * own stream, workspace and worker thread. Requests wait in a FIFO queue; a
+ * free lane takes the head as soon as its device-memory footprint (an upper
+ * bound computed at submission) fits the budget beside the requests already
+ * held, uploads it, runs it while the other lanes run theirs, leaves the result
+ * in page-locked host memory and releases the device memory. Admission needs
+ * no call from the caller. Results wait until taken (copied out) or released
+ * after use in place. The server functions may be called from any thread;
+ * bsm_server_destroy only once every other call on the server has returned.
  * ------------------------------------------------------------------------- */
 typedef struct bsm_server_s *bsm_server;
 
@@ -269,12 +270,13 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
                       const int32_t *blk_row, const int32_t *blk_col, const double *values,
                       double eps, int64_t *id);
 
-/* Retire finished requests and admit queued ones; never blocks on the device
- * (an admission uploads its request). *completed: requests finished by this call. */
+/* Never blocks. *completed: requests finished since the previous call (the
+ * lanes admit and run requests by themselves). */
 int bsm_server_progress(bsm_server s, int32_t *completed);
 
-/* State of a request; latency_ms (submit to completion) once done, and the
- * result's block and value counts. */
+/* State of a request; once done (or failed): latency_ms (submit to
+ * completion) and the result's block and value counts, else -1, 0, 0. A failed
+ * request returns its error code. */
 int bsm_server_poll(bsm_server s, int64_t id, int32_t *state, double *latency_ms,
                     int64_t *nblocks, int64_t *nnz);
 

@@ -3,18 +3,19 @@
 // with continuous batching.
 //
 // The server owns `slots` lanes, each a libbsm context (own stream and
-// workspace) driven by a worker thread of its own. A request waits in a FIFO
-// queue until a lane is free and its device-memory footprint fits the budget
-// next to the requests already held; the lane's worker then uploads it, runs
-// the multiply, copies the result to host memory and releases the device
-// memory, while the other lanes do the same with their requests: requests of
-// different sizes overlap on the device, and a request that arrives while
-// others run starts as soon as a lane and memory free up (no waiting for a
-// batch to drain). Host work of a request (validation, upload, read-back)
-// blocks only its own lane. The footprint is an upper bound computed before
-// the multiply (A, a dense-or-candidate bound on C, the product records), held
-// from admission to completion. Every step goes through the public C ABI, so a
-// request's result is computed by exactly the kernels a lone bsm_multiply uses.
+// workspace) driven by a worker thread of its own. Requests wait in a FIFO
+// queue; a free worker takes the head of the queue as soon as its device-memory
+// footprint fits the budget next to the requests already held, uploads it,
+// runs the multiply, leaves the result in page-locked host memory and releases
+// the device memory, while the other lanes do the same with theirs: requests
+// of different sizes overlap on the device, and a request that arrives while
+// others run starts the moment a lane and memory free up (no waiting for a
+// batch to drain, nor for the caller to poll). Host work of a request
+// (validation, upload, read-back) blocks only its own lane. The footprint is an
+// upper bound computed at submission (A, a dense-or-candidate bound on C, the
+// product records), held from admission to completion. Every step goes through
+// the public C ABI, so a request's result is computed by exactly the kernels a
+// lone bsm_multiply uses.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,12 +47,13 @@ struct Request {
   double eps = 0;
   int64_t footprint = 0;  // bytes held on the device while admitted
   int64_t c_vals_bound = 0;  // upper bound of the result's value count
-  int state = kQueued;    // changed by the caller's thread only
+  int state = kQueued;    // under the server's lock
   int err = BSM_OK;
   int slot = -1;
   double t_submit = 0, t_start = 0, t_done = 0;
+  // written by the lane's worker while running; read by others once done
   int64_t nblk = 0, nnz = 0;
-  // the result, once the lane is done: page-locked host blocks of the server's pool
+  // the result: page-locked host blocks of the server's pool
   int32_t *res_row = nullptr, *res_col = nullptr;
   double *res_val = nullptr;
 };
@@ -115,16 +117,10 @@ struct PinnedPool {
   }
 };
 
-// A lane: a context and the worker thread that runs one request at a time on
-// it. `req` is handed over by the caller's thread and returned with `finished`.
+// A lane: a context and the worker thread that runs one request at a time on it.
 struct Slot {
   bsm_ctx ctx = nullptr;
   std::thread worker;
-  std::mutex mu;
-  std::condition_variable cv;
-  Request *req = nullptr;
-  bool finished = false;
-  bool stop = false;
 };
 
 // Upper bound of the device bytes a request C = A.A can hold.
@@ -156,13 +152,20 @@ int64_t footprint_bound(const Request &r, int64_t *c_vals_bound) {
 struct bsm_server_s {
   int device = 0;
   int precision = BSM_PREC_FP64;
-  int64_t budget = 0, in_use = 0, peak = 0;
+  int64_t budget = 0;
   std::vector<Slot> slots;
+  PinnedPool pinned;
+  // everything below, and each request's state, under `mu`; `cv` wakes the
+  // workers when a request arrives, memory is released or the server stops
+  std::mutex mu;
+  std::condition_variable cv;
+  int64_t in_use = 0, peak = 0;
   std::deque<Request *> queue;
   std::map<int64_t, Request *> reqs;
   int64_t next_id = 1;
-  int64_t completed = 0;
-  PinnedPool pinned;
+  int64_t completed = 0, reported = 0;
+  int64_t running = 0;
+  bool stop = false;
 };
 
 static void drop_result(bsm_server s, Request *r) {
@@ -221,22 +224,40 @@ static void run_request(bsm_server s, Slot &sl, Request *r) {
   r->t_done = now_ms();
 }
 
-static void worker_loop(bsm_server s, Slot *sl) {
+// A lane's worker: takes the head of the queue once it fits the budget, runs
+// it, and returns its memory to the budget.
+static void worker_loop(bsm_server s, int lane) {
   cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    Request *r;
-    {
-      std::unique_lock<std::mutex> lk(sl->mu);
-      sl->cv.wait(lk, [&] { return sl->stop || (sl->req && !sl->finished); });
-      if (!sl->req || sl->finished) return;  // stop with nothing to run
-      r = sl->req;
-    }
-    run_request(s, *sl, r);
-    {
-      std::lock_guard<std::mutex> lk(sl->mu);
-      sl->finished = true;
-    }
+    s->cv.wait(lk, [&] {
+      return s->stop ||
+             (!s->queue.empty() && s->in_use + s->queue.front()->footprint <= s->budget);
+    });
+    if (s->stop) return;  // queued requests are dropped by bsm_server_destroy
+    Request *r = s->queue.front();
+    s->queue.pop_front();
+    s->in_use += r->footprint;
+    s->peak = std::max(s->peak, s->in_use);
+    s->running++;
+    r->state = kRunning;
+    r->slot = lane;
+    r->t_start = now_ms();
+    lk.unlock();
+    run_request(s, s->slots[lane], r);
+    lk.lock();
+    s->in_use -= r->footprint;  // the lane released the request's device memory
+    r->footprint = 0;
+    r->state = r->err == BSM_OK ? kDone : kFailed;
+    s->running--;
+    s->completed++;
+    s->cv.notify_all();  // a head that waited for memory may fit now
   }
+}
+
+static void forget(bsm_server s, Request *r) {
+  drop_result(s, r);
+  delete r;
 }
 
 extern "C" {
@@ -266,7 +287,7 @@ int bsm_server_create(int device, const bsm_server_opts *opts, bsm_server *out) 
       return rc;
     }
   }
-  for (Slot &sl : s->slots) sl.worker = std::thread(worker_loop, s, &sl);
+  for (int i = 0; i < o.slots; i++) s->slots[i].worker = std::thread(worker_loop, s, i);
   *out = s;
   return BSM_OK;
 }
@@ -274,19 +295,16 @@ int bsm_server_create(int device, const bsm_server_opts *opts, bsm_server *out) 
 int bsm_server_destroy(bsm_server s) {
   if (!s) return BSM_ERR_INVALID_ARG;
   cudaSetDevice(s->device);
-  for (Slot &sl : s->slots) {  // a running request is finished first
-    {
-      std::lock_guard<std::mutex> lk(sl.mu);
-      sl.stop = true;
-    }
-    sl.cv.notify_one();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  for (Slot &sl : s->slots)  // a running request is finished first
     if (sl.worker.joinable()) sl.worker.join();
-  }
-  for (auto &kv : s->reqs) {
-    drop_result(s, kv.second);
-    delete kv.second;
-  }
+  for (auto &kv : s->reqs) forget(s, kv.second);
   s->reqs.clear();
+  s->queue.clear();
   for (Slot &sl : s->slots)
     if (sl.ctx) bsm_ctx_destroy(sl.ctx);
   s->pinned.clear();
@@ -300,126 +318,98 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
   if (!s || !id || nbrows < 0 || nblocks < 0 || (nbrows > 0 && !sizes) ||
       (nblocks > 0 && (!blk_row || !blk_col || !values)))
     return BSM_ERR_INVALID_ARG;
-  Request *r = new (std::nothrow) Request();
-  if (!r) return BSM_ERR_NOMEM;
-  r->sizes.assign(sizes, sizes + nbrows);
-  r->brow.assign(blk_row, blk_row + nblocks);
-  r->bcol.assign(blk_col, blk_col + nblocks);
+  for (int32_t b = 0; b < nbrows; b++)
+    if (sizes[b] <= 0) return BSM_ERR_INVALID_ARG;
   int64_t nv = 0;
   for (int64_t b = 0; b < nblocks; b++) {
-    if (blk_row[b] < 0 || blk_row[b] >= nbrows || blk_col[b] < 0 || blk_col[b] >= nbrows) {
-      delete r;
+    if (blk_row[b] < 0 || blk_row[b] >= nbrows || blk_col[b] < 0 || blk_col[b] >= nbrows)
       return BSM_ERR_OUT_OF_RANGE;
-    }
     nv += (int64_t)sizes[blk_row[b]] * sizes[blk_col[b]];
   }
-  for (int32_t v : r->sizes)
-    if (v <= 0) {
-      delete r;
-      return BSM_ERR_INVALID_ARG;
-    }
-  r->vals.assign(values, values + nv);
+  // the copies are made before the lock: a large request does not hold up the lanes
+  Request *r = new (std::nothrow) Request();
+  if (!r) return BSM_ERR_NOMEM;
+  try {
+    r->sizes.assign(sizes, sizes + nbrows);
+    r->brow.assign(blk_row, blk_row + nblocks);
+    r->bcol.assign(blk_col, blk_col + nblocks);
+    r->vals.assign(values, values + nv);
+  } catch (const std::bad_alloc &) {
+    delete r;
+    return BSM_ERR_NOMEM;
+  }
   r->eps = eps;
   r->footprint = footprint_bound(*r, &r->c_vals_bound);
   if (r->footprint > s->budget) {  // could never be admitted
     delete r;
     return BSM_ERR_NOMEM;
   }
-  r->id = s->next_id++;
-  r->t_submit = now_ms();
-  s->reqs[r->id] = r;
-  s->queue.push_back(r);
-  *id = r->id;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    r->t_submit = now_ms();
+    s->reqs[r->id] = r;
+    s->queue.push_back(r);
+    *id = r->id;
+  }
+  s->cv.notify_all();
   return BSM_OK;
 }
 
 int bsm_server_progress(bsm_server s, int32_t *completed) {
   if (!s) return BSM_ERR_INVALID_ARG;
-  int32_t done = 0;
-  // 1. retire the requests the lanes have finished
-  for (Slot &sl : s->slots) {
-    Request *r = nullptr;
-    {
-      std::lock_guard<std::mutex> lk(sl.mu);
-      if (sl.req && sl.finished) {
-        r = sl.req;
-        sl.req = nullptr;
-        sl.finished = false;
-      }
-    }
-    if (!r) continue;
-    r->state = r->err == BSM_OK ? kDone : kFailed;
-    s->in_use -= r->footprint;  // the lane released the request's device memory
-    r->footprint = 0;
-    s->completed++;
-    done++;
-  }
-  // 2. admit from the head of the queue while a lane and memory are free
-  for (Slot &sl : s->slots) {
-    if (s->queue.empty()) break;
-    {
-      std::lock_guard<std::mutex> lk(sl.mu);
-      if (sl.req) continue;
-    }
-    Request *r = s->queue.front();
-    if (s->in_use + r->footprint > s->budget) break;  // FIFO: wait for memory
-    s->queue.pop_front();
-    s->in_use += r->footprint;
-    s->peak = std::max(s->peak, s->in_use);
-    r->state = kRunning;
-    r->slot = (int)(&sl - s->slots.data());
-    r->t_start = now_ms();
-    {
-      std::lock_guard<std::mutex> lk(sl.mu);
-      sl.req = r;
-    }
-    sl.cv.notify_one();
-  }
-  if (completed) *completed = done;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (completed) *completed = (int32_t)(s->completed - s->reported);
+  s->reported = s->completed;
   return BSM_OK;
 }
 
 int bsm_server_poll(bsm_server s, int64_t id, int32_t *state, double *latency_ms,
                     int64_t *nblocks, int64_t *nnz) {
   if (!s || !state) return BSM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return BSM_ERR_INVALID_ARG;
-  Request *r = it->second;
+  const Request *r = it->second;
+  const bool fin = r->state >= kDone;
   *state = r->state;
-  if (latency_ms) *latency_ms = (r->state >= kDone) ? r->t_done - r->t_submit : -1.0;
-  if (nblocks) *nblocks = r->nblk;
-  if (nnz) *nnz = r->nnz;
+  if (latency_ms) *latency_ms = fin ? r->t_done - r->t_submit : -1.0;
+  if (nblocks) *nblocks = fin ? r->nblk : 0;
+  if (nnz) *nnz = fin ? r->nnz : 0;
   return r->state == kFailed ? r->err : BSM_OK;
 }
 
 int bsm_server_take(bsm_server s, int64_t id, int64_t cap_blk, int32_t *blk_row,
                     int32_t *blk_col, int64_t cap_nnz, double *values) {
   if (!s) return BSM_ERR_INVALID_ARG;
-  auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return BSM_ERR_INVALID_ARG;
-  Request *r = it->second;
-  if (r->state == kFailed) {
-    const int err = r->err;
-    s->reqs.erase(it);
-    drop_result(s, r);
-    delete r;
-    return err;
+  Request *r;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return BSM_ERR_INVALID_ARG;
+    r = it->second;
+    if (r->state == kFailed) {
+      const int err = r->err;
+      s->reqs.erase(it);
+      forget(s, r);
+      return err;
+    }
+    if (r->state != kDone) return BSM_ERR_INVALID_ARG;
+    if (((blk_row || blk_col) && cap_blk < r->nblk) || (values && cap_nnz < r->nnz))
+      return BSM_ERR_INVALID_ARG;  // the result stays until taken
+    s->reqs.erase(it);  // from here on only this call sees the request
   }
-  if (r->state != kDone) return BSM_ERR_INVALID_ARG;
-  if (((blk_row || blk_col) && cap_blk < r->nblk) || (values && cap_nnz < r->nnz))
-    return BSM_ERR_INVALID_ARG;  // the result stays until taken
   if (blk_row) std::copy(r->res_row, r->res_row + r->nblk, blk_row);
   if (blk_col) std::copy(r->res_col, r->res_col + r->nblk, blk_col);
   if (values) std::copy(r->res_val, r->res_val + r->nnz, values);
-  s->reqs.erase(it);
-  drop_result(s, r);
-  delete r;
+  forget(s, r);
   return BSM_OK;
 }
 
 int bsm_server_result(bsm_server s, int64_t id, const int32_t **blk_row, const int32_t **blk_col,
                       const double **values, int64_t *nblocks, int64_t *nnz) {
   if (!s) return BSM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->reqs.find(id);
   if (it == s->reqs.end() || it->second->state != kDone) return BSM_ERR_INVALID_ARG;
   const Request *r = it->second;
@@ -433,21 +423,23 @@ int bsm_server_result(bsm_server s, int64_t id, const int32_t **blk_row, const i
 
 int bsm_server_release(bsm_server s, int64_t id) {
   if (!s) return BSM_ERR_INVALID_ARG;
-  auto it = s->reqs.find(id);
-  if (it == s->reqs.end() || it->second->state < kDone) return BSM_ERR_INVALID_ARG;
-  Request *r = it->second;
-  s->reqs.erase(it);
-  drop_result(s, r);
-  delete r;
+  Request *r;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end() || it->second->state < kDone) return BSM_ERR_INVALID_ARG;
+    r = it->second;
+    s->reqs.erase(it);
+  }
+  forget(s, r);
   return BSM_OK;
 }
 
 int bsm_server_get_info(bsm_server s, bsm_server_info *out) {
   if (!s || !out) return BSM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
   out->queued = (int64_t)s->queue.size();
-  int64_t running = 0;
-  for (const Slot &sl : s->slots) running += sl.req ? 1 : 0;
-  out->running = running;
+  out->running = s->running;
   out->completed = s->completed;
   out->bytes_in_use = s->in_use;
   out->bytes_peak = s->peak;
