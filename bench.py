@@ -6,8 +6,10 @@ diagonal), eps = 1e-10, FP64, one seed. It stands in for the paper's
 H2O-DFT-LS matrices (Table 1), which are not available.
 
 A "step" is one whole multiply (block norms, symbolic phase with the filter,
-grouping of the products, numeric block products). Inputs stay resident in HBM;
-A (272 MB) and C (1.6 GB) are larger than the 129 MB L2, so no flush is done.
+grouping of the products, numeric block products). Inputs stay resident in HBM.
+For the default workload A (272 MB) and C (1.6 GB) are larger than the 129 MB
+L2 and no flush is done; workloads whose A and C together fit in twice the L2
+get 256 MB written between the timed steps.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -39,6 +41,7 @@ WORKLOADS = {
     "dense4096": dict(kind="dense", n=128, bs=32, seed=3, eps=1e-10),
     "se40000": dict(kind="sparse", n=40000, bs=6, occ=5e-4, seed=5, eps=1e-10),
 }
+L2_BYTES = 128 << 20  # GB300 L2 (129 MB), rounded down
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
 # FP64 numeric kernels (BSM_FP64_*): name -> (number, kernel symbol)
 FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64_t16"),
@@ -603,23 +606,36 @@ def main():
     for _ in range(args.warmup):
         ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stream=s, **kw)
     s.synchronize()
+    # A and C larger than L2 together: no flush; else a 256 MB buffer is written
+    # between timed steps (outside the timed intervals) so each step starts cold
+    a_bytes, c_bytes = 8 * len(A.values), 8 * dC.nblocks()[1]
+    flush = None
+    if a_bytes + c_bytes < 2 * L2_BYTES:
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    l2_note = (f"A {a_bytes / 1e6:.0f} MB, C {c_bytes / 1e6:.0f} MB: "
+               + ("L2 flushed between steps (256 MB written)" if flush is not None
+                  else "inputs larger than the 129 MB L2; no flush"))
     ctx.profile(True)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ev[0].record(s)
         for k in range(args.steps):
+            if flush is not None:
+                with torch.cuda.stream(s):
+                    flush.fill_(k)
+            ev[k][0].record(s)
             ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stream=s, **kw)
-            ev[k + 1].record(s)
+            ev[k][1].record(s)
         s.synchronize()
         torch.cuda.synchronize()
     clocks = clk.summary()
     if dist is not None:
         dist.barrier()
-    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[args.steps])
+    per_step = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = sum(per_step)
     prof = ctx.profile_read()
     ctx.profile(False)
     launches = prof.launches
@@ -661,10 +677,13 @@ def main():
         # operand slices read once (A = B: left and right layouts)
         rs = A.row_sizes.astype(np.int64)
         r, c = rs[A.blk_row], A.col_sizes.astype(np.int64)[A.blk_col]
+        # rows padded along k to 16 bytes (8 BF16 / 4 TF32 values), per layout
+        def up(x, q):
+            return (x + q - 1) // q * q
         if args.precision == "bf16x3":
-            slice_bytes = 2 * 3 * 2 * int(((r + (r & 1)) * (c + (c & 1))).sum())
+            slice_bytes = 3 * 2 * int((r * up(c, 8) + c * up(r, 8)).sum())
         else:
-            slice_bytes = 2 * 2 * 4 * int((r * c).sum())
+            slice_bytes = 2 * 4 * int((r * up(c, 4) + c * up(r, 4)).sum())
         nbytes = 8 * nnz_c + slice_bytes
         achieved = nbytes / (num_ms / 1e3) / 1e9
         peak = measured_peak("hbm_gbs", 6800.0)
@@ -746,7 +765,7 @@ def main():
                        "a_blocks": A.nblk, "c_blocks": nb_c, "c_nnz": nnz_c,
                        "kept_products": st.kept, "dropped_products": st.dropped,
                        "gflop_per_multiply": round(flops / 1e9, 4),
-                       "l2": "inputs larger than L2 (A 272 MB, C 1.6 GB); no flush",
+                       "l2": l2_note,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "multiplies_per_s": round(1e3 * args.steps * world / total_ms, 3),
             "latency_ms": {"p50": round(statistics.median(per_step), 4), "p99": round(p99, 4),

@@ -874,6 +874,10 @@ static int resolve(bsm_mat M, bsm_stats *timed) {
   CK(cudaEventSynchronize(ctx->slot_ev[p.slot]));
   DevStatus h = ctx->h_slots[p.slot];
   M->pend.active = false;
+  if (h.error) {  // a bounded device-side wait gave up: the result is incomplete
+    M->nblk = M->nnz = 0;
+    return BSM_ERR_TIMEOUT;
+  }
   M->hint_blk = std::max(M->hint_blk, h.nblk_c);
   M->hint_nnz = std::max(M->hint_nnz, h.nnz_c);
   ctx->hint_prod = std::max(ctx->hint_prod, h.nprod);

@@ -160,12 +160,14 @@ cudaError_t launch_add(int stage, DevMat A, DevMat Cin, int use_cin, double alph
 cudaError_t numeric_split_init();
 
 // Slice storage of an operand block b starts at a fixed multiple of its FP64
-// offset blk_off[b], 16-byte aligned so whole blocks can be copied with
-// 16-byte asynchronous copies: BF16x3 at halfword 16*blk_off (32 bytes per
-// value; the 3 padded planes take at most 24), TF32x2 at word 4*blk_off (16
-// bytes per value; the 2 planes take 8).
-constexpr int64_t kBf16HalfwordsPerValue = 16;
-constexpr int64_t kTf32WordsPerValue = 4;
+// offset blk_off[b], 16-byte aligned so whole blocks can be copied with bulk
+// asynchronous copies. Each slice plane of an r x c block is stored as rows
+// with k contiguous, every row padded with zeros to 16 bytes: BF16x3 at
+// halfword 24*blk_off (3 planes of r rows of ceil8(c) halfwords take at most
+// 24 per value, reached for c = 1), TF32x2 at word 8*blk_off (2 planes of
+// ceil4(c) words per row, at most 8 per value).
+constexpr int64_t kBf16HalfwordsPerValue = 24;
+constexpr int64_t kTf32WordsPerValue = 8;
 inline int64_t split_bytes_per_value(int precision) {
   return precision == BSM_PREC_SPLIT_BF16X3 ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue;
 }

@@ -16,17 +16,21 @@
 // filter and the norms stay in FP64 (k_symbolic.cu).
 //
 // Slice layout. For every block b of r x c values (FP64 offset blk_off[b]),
-// the slices live at a fixed multiple of the FP64 offset, so no extra offset
-// table is needed:
-//   BF16: 3 planes of rp x cp elements (rp, cp = r, c rounded up to even;
-//         padding is zero) at 16-bit index 16*blk_off[b] (rp*cp <= 4*r*c);
-//         "left" layout (the block as a left operand) is row-major with
-//         stride cp, "right" layout (as a right operand) column-major with
-//         stride rp, so the two k-adjacent values of an MMA fragment register
-//         are one aligned 32-bit word.
-//   TF32: 2 planes of r x c 32-bit elements at 32-bit index 4*blk_off[b];
-//         left row-major, right column-major.
+// the slices live at a fixed multiple of the FP64 offset (no extra offset
+// table). An operand is seen as `rows` rows along the k index:
+//   "left" layout (the block as a left operand, k = its columns): r rows of
+//         c values; "right" layout (as a right operand, k = its rows): c rows
+//         (the block's columns) of r values.
+// k is cut into 16-byte pieces (8 BF16 or 4 TF32 values, zero past the end),
+// and a plane stores the pieces k-piece-major: piece (row, kp) at
+// (kp * rows + row) * 16 bytes. Eight consecutive rows of one k-piece, the
+// 8 x 8 unit of the tensor cores' fragment loads (ldmatrix), are then 128
+// contiguous bytes (no shared-memory bank conflict), and a whole operand (all
+// planes) is one contiguous, 16-byte aligned run for a bulk copy.
+//   BF16: 3 planes of rows * ceil8(k) halfwords at halfword 24*blk_off[b];
+//   TF32: 2 planes of rows * ceil4(k) words at word 8*blk_off[b].
 #include <cstdint>
+#include <cstdlib>
 
 #include "bsm_internal.h"
 
@@ -91,6 +95,8 @@ __device__ __forceinline__ Slices<NS, BITS> split_value(double x) {
 // Split every block of a matrix into the left and/or right slice layouts.
 // One warp per block (grid-stride), lanes over the padded positions.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int round_up(int x, int q) { return (x + q - 1) / q * q; }
+
 __global__ void k_split_bf16x3(const int32_t *__restrict__ row_sizes,
                                const int32_t *__restrict__ col_sizes,
                                const int32_t *__restrict__ blk_row,
@@ -104,19 +110,24 @@ __global__ void k_split_bf16x3(const int32_t *__restrict__ row_sizes,
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = w0; b < nblk; b += nw) {
     const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
-    const int rp = r + (r & 1), cp = c + (c & 1);
-    const int plane = rp * cp;
     const int64_t base = kBf16HalfwordsPerValue * blk_off[b];
     const double *x = vals + blk_off[b];
-    for (int e = lane; e < plane; e += 32) {
-      // position (row xr, col yc) in the padded rp x cp block, column-major order
-      const int xr = e % rp, yc = e / rp;
-      const double v = (xr < r && yc < c) ? x[xr + (int64_t)yc * r] : 0.0;
-      const Slices<3, 8> sl = split_value<3, 8>(v);
+    if (left) {  // r rows along k = the block's columns
+      const int plane = r * round_up(c, 8);
+      for (int e = lane; e < plane; e += 32) {
+        const int p = e >> 3, kp = p / r, row = p - kp * r, k = 8 * kp + (e & 7);
+        const Slices<3, 8> sl = split_value<3, 8>(k < c ? x[row + (int64_t)k * r] : 0.0);
 #pragma unroll
-      for (int q = 0; q < 3; q++) {
-        if (left) left[base + (int64_t)q * plane + xr * cp + yc] = (uint16_t)sl.s[q];
-        if (right) right[base + (int64_t)q * plane + yc * rp + xr] = (uint16_t)sl.s[q];
+        for (int q = 0; q < 3; q++) left[base + (int64_t)q * plane + e] = (uint16_t)sl.s[q];
+      }
+    }
+    if (right) {  // c rows (the block's columns) along k = the block's rows
+      const int plane = c * round_up(r, 8);
+      for (int e = lane; e < plane; e += 32) {
+        const int p = e >> 3, kp = p / c, col = p - kp * c, k = 8 * kp + (e & 7);
+        const Slices<3, 8> sl = split_value<3, 8>(k < r ? x[k + (int64_t)col * r] : 0.0);
+#pragma unroll
+        for (int q = 0; q < 3; q++) right[base + (int64_t)q * plane + e] = (uint16_t)sl.s[q];
       }
     }
   }
@@ -135,16 +146,24 @@ __global__ void k_split_tf32x2(const int32_t *__restrict__ row_sizes,
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = w0; b < nblk; b += nw) {
     const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
-    const int plane = r * c;
     const int64_t base = kTf32WordsPerValue * blk_off[b];
     const double *x = vals + blk_off[b];
-    for (int e = lane; e < plane; e += 32) {
-      const int xr = e % r, yc = e / r;
-      const Slices<2, 11> sl = split_value<2, 11>(x[e]);
+    if (left) {
+      const int plane = r * round_up(c, 4);
+      for (int e = lane; e < plane; e += 32) {
+        const int p = e >> 2, kp = p / r, row = p - kp * r, k = 4 * kp + (e & 3);
+        const Slices<2, 11> sl = split_value<2, 11>(k < c ? x[row + (int64_t)k * r] : 0.0);
 #pragma unroll
-      for (int q = 0; q < 2; q++) {
-        if (left) left[base + (int64_t)q * plane + xr * c + yc] = sl.s[q];
-        if (right) right[base + (int64_t)q * plane + e] = sl.s[q];
+        for (int q = 0; q < 2; q++) left[base + (int64_t)q * plane + e] = sl.s[q];
+      }
+    }
+    if (right) {
+      const int plane = c * round_up(r, 4);
+      for (int e = lane; e < plane; e += 32) {
+        const int p = e >> 2, kp = p / c, col = p - kp * c, k = 4 * kp + (e & 3);
+        const Slices<2, 11> sl = split_value<2, 11>(k < r ? x[k + (int64_t)col * r] : 0.0);
+#pragma unroll
+        for (int q = 0; q < 2; q++) right[base + (int64_t)q * plane + e] = sl.s[q];
       }
     }
   }
@@ -238,7 +257,8 @@ struct Frag {
   uint32_t b[NSL][NT][2];
 };
 
-// Fragments of one BF16 step (k values kk..kk+15, or kk..kk+7 when k8).
+// Fragments of one BF16 step (k values kk..kk+15, or kk..kk+7 when k8). L has
+// Mp rows, R has Np rows, k padded to sp (a multiple of 8), pieces k-major.
 template <int MT, int NT>
 __device__ __forceinline__ void load_bf16(Frag<3, MT, NT> &f, const uint16_t *__restrict__ Lb,
                                           const uint16_t *__restrict__ Rb, int Mp, int Np, int sp,
@@ -246,23 +266,26 @@ __device__ __forceinline__ void load_bf16(Frag<3, MT, NT> &f, const uint16_t *__
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const int k0 = kk + 2 * t, k1 = k0 + 8;
+  // 32-bit word of (row, k even): halfword ((k >> 3) * rows + row) * 8 + (k & 7)
+  const int wl0 = (((k0 >> 3) * Mp) << 2) + t, wl1 = wl0 + (Mp << 2);
+  const int wr0 = (((k0 >> 3) * Np) << 2) + t, wr1 = wr0 + (Np << 2);
 #pragma unroll
   for (int q = 0; q < 3; q++) {
     const uint32_t *P = reinterpret_cast<const uint32_t *>(Lb + (int64_t)q * lplane);
 #pragma unroll
     for (int mt = 0; mt < MT; mt++) {
       const int r0 = mt * 16 + g, r1 = r0 + 8;
-      f.a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + ((r0 * sp + k0) >> 1)) : 0u;
-      f.a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + ((r1 * sp + k0) >> 1)) : 0u;
-      f.a[q][mt][2] = (!k8 && r0 < Mp && k1 < sp) ? __ldg(P + ((r0 * sp + k1) >> 1)) : 0u;
-      f.a[q][mt][3] = (!k8 && r1 < Mp && k1 < sp) ? __ldg(P + ((r1 * sp + k1) >> 1)) : 0u;
+      f.a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + wl0 + 4 * r0) : 0u;
+      f.a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + wl0 + 4 * r1) : 0u;
+      f.a[q][mt][2] = (!k8 && r0 < Mp && k1 < sp) ? __ldg(P + wl1 + 4 * r0) : 0u;
+      f.a[q][mt][3] = (!k8 && r1 < Mp && k1 < sp) ? __ldg(P + wl1 + 4 * r1) : 0u;
     }
     const uint32_t *Q = reinterpret_cast<const uint32_t *>(Rb + (int64_t)q * rplane);
 #pragma unroll
     for (int nt = 0; nt < NT; nt++) {
       const int c = nt * 8 + g;
-      f.b[q][nt][0] = (c < Np && k0 < sp) ? __ldg(Q + ((c * sp + k0) >> 1)) : 0u;
-      f.b[q][nt][1] = (!k8 && c < Np && k1 < sp) ? __ldg(Q + ((c * sp + k1) >> 1)) : 0u;
+      f.b[q][nt][0] = (c < Np && k0 < sp) ? __ldg(Q + wr0 + 4 * c) : 0u;
+      f.b[q][nt][1] = (!k8 && c < Np && k1 < sp) ? __ldg(Q + wr1 + 4 * c) : 0u;
     }
   }
 }
@@ -288,31 +311,34 @@ __device__ __forceinline__ void mma_bf16(float (&acc)[MT][NT][4], const Frag<3, 
     }
 }
 
-// Fragments of one TF32 step (k values kk..kk+7).
+// Fragments of one TF32 step (k values kk..kk+7); k padded to sp (a multiple
+// of 4), pieces k-major: word ((k >> 2) * rows + row) * 4 + (k & 3).
 template <int MT, int NT>
 __device__ __forceinline__ void load_tf32(Frag<2, MT, NT> &f, const uint32_t *__restrict__ Lb,
-                                          const uint32_t *__restrict__ Rb, int Mp, int Np, int s,
+                                          const uint32_t *__restrict__ Rb, int Mp, int Np, int sp,
                                           int kk, int lplane, int rplane) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const int k0 = kk + t, k1 = k0 + 4;
+  const int wl0 = (((k0 >> 2) * Mp) << 2) + t, wl1 = wl0 + (Mp << 2);
+  const int wr0 = (((k0 >> 2) * Np) << 2) + t, wr1 = wr0 + (Np << 2);
 #pragma unroll
   for (int q = 0; q < 2; q++) {
     const uint32_t *P = Lb + (int64_t)q * lplane;
 #pragma unroll
     for (int mt = 0; mt < MT; mt++) {
       const int r0 = mt * 16 + g, r1 = r0 + 8;
-      f.a[q][mt][0] = (r0 < Mp && k0 < s) ? __ldg(P + r0 * s + k0) : 0u;
-      f.a[q][mt][1] = (r1 < Mp && k0 < s) ? __ldg(P + r1 * s + k0) : 0u;
-      f.a[q][mt][2] = (r0 < Mp && k1 < s) ? __ldg(P + r0 * s + k1) : 0u;
-      f.a[q][mt][3] = (r1 < Mp && k1 < s) ? __ldg(P + r1 * s + k1) : 0u;
+      f.a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + wl0 + 4 * r0) : 0u;
+      f.a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + wl0 + 4 * r1) : 0u;
+      f.a[q][mt][2] = (r0 < Mp && k1 < sp) ? __ldg(P + wl1 + 4 * r0) : 0u;
+      f.a[q][mt][3] = (r1 < Mp && k1 < sp) ? __ldg(P + wl1 + 4 * r1) : 0u;
     }
     const uint32_t *Q = Rb + (int64_t)q * rplane;
 #pragma unroll
     for (int nt = 0; nt < NT; nt++) {
       const int c = nt * 8 + g;
-      f.b[q][nt][0] = (c < Np && k0 < s) ? __ldg(Q + c * s + k0) : 0u;
-      f.b[q][nt][1] = (c < Np && k1 < s) ? __ldg(Q + c * s + k1) : 0u;
+      f.b[q][nt][0] = (c < Np && k0 < sp) ? __ldg(Q + wr0 + 4 * c) : 0u;
+      f.b[q][nt][1] = (c < Np && k1 < sp) ? __ldg(Q + wr1 + 4 * c) : 0u;
     }
   }
 }
@@ -366,37 +392,33 @@ __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, c
     for (int nt = 0; nt < NT; nt++)
 #pragma unroll
       for (int x = 0; x < 4; x++) hi[mt][nt][x] = lo[mt][nt][x] = acc[mt][nt][x] = 0.f;
-  const int mp2 = m + (m & 1), np2 = n + (n & 1);
 
-  // operand pointers and planes of product (aoff, boff, s) for this block
+  // operand pointers and planes of product (aoff, boff, s) for this block:
+  // L has Mp rows, R has Np rows, both of the padded row length of k = s
   auto operands = [&](int64_t aoff, int64_t boff, int s, const void *&L, const void *&R,
                       int &lplane, int &rplane) {
-    if (BF) {
-      const uint16_t *Al = static_cast<const uint16_t *>(a_left) + kBf16HalfwordsPerValue * aoff;
-      const uint16_t *Br = static_cast<const uint16_t *>(b_right) + kBf16HalfwordsPerValue * boff;
-      const int sp = s + (s & 1);
-      const int ap = mp2 * sp, bpl = sp * np2;
-      L = tr ? (const void *)Br : (const void *)Al;
-      R = tr ? (const void *)Al : (const void *)Br;
-      lplane = tr ? bpl : ap;
-      rplane = tr ? ap : bpl;
-    } else {
-      const uint32_t *Al = static_cast<const uint32_t *>(a_left) + kTf32WordsPerValue * aoff;
-      const uint32_t *Br = static_cast<const uint32_t *>(b_right) + kTf32WordsPerValue * boff;
-      L = tr ? (const void *)Br : (const void *)Al;
-      R = tr ? (const void *)Al : (const void *)Br;
-      lplane = tr ? s * n : m * s;
-      rplane = tr ? m * s : s * n;
-    }
+    const int sp = BF ? (s + 7) & ~7 : (s + 3) & ~3;
+    const void *Al = BF ? (const void *)(static_cast<const uint16_t *>(a_left) +
+                                         kBf16HalfwordsPerValue * aoff)
+                        : (const void *)(static_cast<const uint32_t *>(a_left) +
+                                         kTf32WordsPerValue * aoff);
+    const void *Br = BF ? (const void *)(static_cast<const uint16_t *>(b_right) +
+                                         kBf16HalfwordsPerValue * boff)
+                        : (const void *)(static_cast<const uint32_t *>(b_right) +
+                                         kTf32WordsPerValue * boff);
+    L = tr ? Br : Al;
+    R = tr ? Al : Br;
+    lplane = Mp * sp;
+    rplane = Np * sp;
   };
   auto load = [&](Frag<NSL, MT, NT> &f, const void *L, const void *R, int lplane, int rplane,
                   int s, int kk) {
     if constexpr (BF)
       load_bf16<MT, NT>(f, static_cast<const uint16_t *>(L), static_cast<const uint16_t *>(R), Mp,
-                        Np, s + (s & 1), kk, (s - kk) <= 8, lplane, rplane);
+                        Np, (s + 7) & ~7, kk, (s - kk) <= 8, lplane, rplane);
     else
       load_tf32<MT, NT>(f, static_cast<const uint32_t *>(L), static_cast<const uint32_t *>(R), Mp,
-                        Np, s, kk, lplane, rplane);
+                        Np, (s + 3) & ~3, kk, lplane, rplane);
   };
 
   const int64_t p0 = ws.prod_ptr[gb], p1 = ws.prod_ptr[gb + 1];
@@ -486,18 +508,22 @@ __device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, c
 }
 
 // ---------------------------------------------------------------------------
-// Pipelined kernel for blocks whose MMA problem fits 16 x 16 (the water and
-// small-block case). Each warp streams the slices of its C block's products
-// through a ring of STAGES shared-memory slots with 16-byte asynchronous
-// copies (cp.async), STAGES - 1 products ahead of the tensor-core work, so the
-// L2 latency of a product's operands is hidden behind the products before it.
-// The (A offset, B offset, k) of the products are read 32 at a time into a
-// per-warp table in shared memory.
+// Pipelined kernel for C blocks whose MMA problem fits 16 x 16 (the water and
+// small-block case). Each warp streams its C block's products through a ring
+// of STAGES shared-memory slots. For every product one lane starts two bulk
+// asynchronous copies (cp.async.bulk: all slice planes of the left operand in
+// one, of the right one in the other) whose completion is counted in bytes on
+// the slot's mbarrier, STAGES - 1 products ahead of the tensor-core work, so
+// the L2 latency of a product's operands is hidden behind the products before
+// it; the fragments are read from the slot with ldmatrix, conflict-free thanks
+// to the k-piece-major planes. The (A offset, B offset, k) of the products are
+// read 32 at a time into a per-warp table in shared memory.
 // ---------------------------------------------------------------------------
-// STAGES is chosen per launch from the largest block size: deeper rings hide
-// more latency, shallower ones leave room for more warps per SM, and warps
-// count more once the slots are large (3 stages up to 16 x 16 blocks, else 2).
-inline int pipe_stages(int smax) { return smax <= 16 ? 3 : 2; }
+// STAGES: deeper rings hide more copy latency, shallower ones leave room for
+// more warps per SM. Measured on water (k of 5 and 13): 2 stages with 24
+// warps per SM beat 3 with 20 and 4 or 6 with 16 or 8 (each warp's chain of
+// dependent fragment loads and MMAs needs many warps to fill the issue slots).
+inline int pipe_stages(int) { return 2; }
 constexpr int kPipeWarps = 4;
 // Products summed plainly in FP32 before each compensated fold: a partial sum
 // of kFold products carries kFold times the rounding of one, still far below
@@ -505,34 +531,85 @@ constexpr int kPipeWarps = 4;
 constexpr int kFold = 4;
 constexpr int kMetaEntries = 64;
 constexpr int kMetaBytes = kMetaEntries * (8 + 8 + 4);
+// Polls of a slot's mbarrier before a warp gives up on a copy that does not
+// land: it then raises the status error flag, waits (again bounded) for the
+// copies it has in flight and stops.
+constexpr int kWaitPolls = 1 << 22;
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gptr) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gptr) : "memory");
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+// generic-proxy accesses of shared memory (ldmatrix reads of a slot) before
+// async-proxy writes of it (the next bulk copy into the slot)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
-__device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
-  uint32_t v;
-  asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(saddr));
-  return v;
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kWaitPolls; i++)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3,
+                                        uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n"
+               : "=r"(r0), "=r"(r1)
+               : "r"(addr));
 }
 
-// Bytes of one operand slot: BF16 3 planes of at most 16 x sp halfwords, TF32
-// 2 planes of at most 16 x s words (multiples of 16 bytes).
+// Bytes of one 16-byte k-piece column of a plane per row, and of one operand
+// slot: all planes of at most 16 rows of k up to smax.
+__host__ __device__ __forceinline__ int pipe_row_bytes(int precision, int s) {
+  return precision == BSM_PREC_SPLIT_BF16X3 ? 2 * ((s + 7) & ~7) : 4 * ((s + 3) & ~3);
+}
 __host__ __device__ __forceinline__ int pipe_operand_bytes(int precision, int smax) {
-  return precision == BSM_PREC_SPLIT_BF16X3 ? 96 * (smax + (smax & 1)) : 128 * smax;
+  return (precision == BSM_PREC_SPLIT_BF16X3 ? 3 : 2) * 16 * pipe_row_bytes(precision, smax);
 }
+// per warp: the slots, the product table, one mbarrier per slot (16-byte multiple)
 __host__ __device__ __forceinline__ int pipe_warp_bytes(int precision, int smax, int stages) {
-  return stages * 2 * pipe_operand_bytes(precision, smax) + kMetaBytes;
+  return stages * 2 * pipe_operand_bytes(precision, smax) + kMetaBytes + ((8 * stages + 15) & ~15);
+}
+
+// Minimum resident blocks per SM the register budget is fitted to: the kernel
+// is bound by instruction issue and latency, so more resident warps pay.
+// (the TF32 slots are larger: 5 blocks of 2 stages fill the shared memory).
+template <int PREC, int STAGES>
+constexpr int pipe_min_blocks() {
+  return PREC == BSM_PREC_SPLIT_BF16X3 ? (STAGES == 2 ? 6 : STAGES == 3 ? 5 : 4)
+                                       : (STAGES == 2 ? 5 : 4);
 }
 
 template <int PREC, int STAGES>
-__global__ void __launch_bounds__(kPipeWarps * 32)
+__global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>())
     k_numeric_split_pipe(DevMat A, DevMat B, DevOut C, DevMat Cin, const void *__restrict__ a_left,
                          const void *__restrict__ b_right, double alpha, double beta, DevWs ws,
                          const DevStatus *st, const int32_t *__restrict__ items,
@@ -540,7 +617,9 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
                          unsigned long long *work) {
   if (st->overflow) return;
   constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
-  constexpr int KSTEP = BF ? 16 : 8;
+  constexpr int NSL = BF ? 3 : 2;
+  // slice bytes per FP64 value of an operand's offset
+  constexpr int64_t kUnit = BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue;
   extern __shared__ __align__(16) unsigned char smem_pipe[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -550,6 +629,18 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
   int64_t *meta_b = meta_a + kMetaEntries;
   int *meta_s = reinterpret_cast<int *>(meta_b + kMetaEntries);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(wbase);
+  const uint32_t bar0 = sbase + (uint32_t)(STAGES * 2 * opb + kMetaBytes);
+  if (lane == 0) {
+#pragma unroll
+    for (int x = 0; x < STAGES; x++) mbar_init(bar0 + 8 * x, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  // which 8 x 8 piece (rows 0-7 or 8-15, k piece 0 or 1 of the step) this
+  // lane addresses in ldmatrix: "a" order for the left operand (and for the
+  // right one in BF16 k8 steps), "b" order for the right one
+  const int ra = (lane & 7) + ((lane >> 3) & 1) * 8, pa = lane >> 4;
+  const int rb_ = (lane & 7) + (lane >> 4) * 8, pb = (lane >> 3) & 1;
 
   int64_t wb = 0, we = st->nblk_c;
   if (seg) {
@@ -557,12 +648,16 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
     we = seg[1];
   }
   const bool plain = (alpha == 1.0 && beta == 0.0);
-  // C blocks come one at a time from the work counter (zero at launch)
+  uint32_t issued = 0, consumed = 0;  // products this warp has started / waited for
+  bool failed = false;
+  // C blocks come one at a time from the work counter (zero at launch); the
+  // next index is fetched while the current block runs
+  unsigned long long next = 0;
+  if (lane == 0) next = atomicAdd(work, 1ull);
   for (;;) {
-    unsigned long long got = 0;
-    if (lane == 0) got = atomicAdd(work, 1ull);
-    const int64_t w = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    const int64_t w = wb + (int64_t)__shfl_sync(0xffffffffu, next, 0);
     if (w >= we) break;
+    if (lane == 0) next = atomicAdd(work, 1ull);
     const int64_t gb = items ? items[w] : w;
     const int i = C.blk_row[gb], j = C.col_idx[gb];
     const int m = C.row_sizes[i], n = C.col_sizes[j];
@@ -571,9 +666,9 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
     const bool tr = tiles_t < tiles_n;
     const int Mp = tr ? n : m, Np = tr ? m : n;
     if (only_small && !(Mp <= 16 && Np <= 16)) continue;
-    const int mp2 = m + (m & 1), np2 = n + (n & 1);
     const int64_t p0 = ws.prod_ptr[gb];
     const int np = (int)(ws.prod_ptr[gb + 1] - p0);
+    const uint32_t u0 = issued;  // ring position of this block's first product
 
     float hi[2][4], lo[2][4], acc[2][4];
 #pragma unroll
@@ -581,111 +676,133 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
 #pragma unroll
       for (int x = 0; x < 4; x++) hi[nt][x] = lo[nt][x] = acc[nt][x] = 0.f;
 
-    // copies of product q into slot q % STAGES; always commits one group
+    // start the copies of product q into slot (u0 + q) % STAGES (all lanes call)
     auto issue = [&](int q) {
-      if (q < np) {
-        if ((q & 31) == 0) {  // the next 32 products' offsets and k
-          const int qq = q + lane;
-          if (qq < np) {
-            const int2 pr = ws.prods[p0 + qq];
-            meta_a[qq & (kMetaEntries - 1)] = A.blk_off[pr.x];
-            meta_b[qq & (kMetaEntries - 1)] = B.blk_off[pr.y];
-            meta_s[qq & (kMetaEntries - 1)] = A.col_sizes[A.col_idx[pr.x]];
-          }
-          __syncwarp();
+      if (q >= np) return;
+      if ((q & 31) == 0) {  // the next 32 products' offsets and k
+        const int qq = q + lane;
+        if (qq < np) {
+          const int2 pr = ws.prods[p0 + qq];
+          meta_a[qq & (kMetaEntries - 1)] = A.blk_off[pr.x];
+          meta_b[qq & (kMetaEntries - 1)] = B.blk_off[pr.y];
+          meta_s[qq & (kMetaEntries - 1)] = A.col_sizes[A.col_idx[pr.x]];
         }
-        const int s = meta_s[q & (kMetaEntries - 1)];
-        const int sp = s + (s & 1);
-        const unsigned char *srcA = static_cast<const unsigned char *>(a_left) +
-                                    (BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue) *
-                                        meta_a[q & (kMetaEntries - 1)];
-        const unsigned char *srcB = static_cast<const unsigned char *>(b_right) +
-                                    (BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue) *
-                                        meta_b[q & (kMetaEntries - 1)];
-        const int bytesA = BF ? 6 * mp2 * sp : 8 * m * s;
-        const int bytesB = BF ? 6 * sp * np2 : 8 * s * n;
-        const uint32_t dst = sbase + (uint32_t)((q % STAGES) * 2 * opb);
-        for (int c = lane; c < (bytesA + 15) >> 4; c += 32) cp_async16(dst + 16 * c, srcA + 16 * c);
-        for (int c = lane; c < (bytesB + 15) >> 4; c += 32)
-          cp_async16(dst + opb + 16 * c, srcB + 16 * c);
+        __syncwarp();
       }
-      cp_async_commit();
+      if (lane == 0) {
+        const int e = q & (kMetaEntries - 1);
+        const int rb = pipe_row_bytes(PREC, meta_s[e]);
+        const uint32_t bytes_a = (uint32_t)(NSL * m * rb), bytes_b = (uint32_t)(NSL * n * rb);
+        const uint32_t slot = (u0 + (uint32_t)q) % STAGES;
+        const uint32_t dst = sbase + slot * 2 * (uint32_t)opb, bar = bar0 + 8 * slot;
+        fence_proxy_async_smem();
+        mbar_expect_tx(bar, bytes_a + bytes_b);
+        bulk_copy_g2s(dst, static_cast<const unsigned char *>(a_left) + kUnit * meta_a[e], bytes_a,
+                      bar);
+        bulk_copy_g2s(dst + (uint32_t)opb,
+                      static_cast<const unsigned char *>(b_right) + kUnit * meta_b[e], bytes_b, bar);
+      }
+      issued++;
     };
 
+    __syncwarp();  // every lane is past its reads of the slots about to be refilled
 #pragma unroll
     for (int q = 0; q < STAGES - 1; q++) issue(q);
     for (int q = 0; q < np; q++) {
-      cp_async_wait<STAGES - 2>();
+      const uint32_t u = u0 + (uint32_t)q, slot = u % STAGES;
+      if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8 * slot, (u / STAGES) & 1u))) {
+        failed = true;
+        break;
+      }
+      consumed++;
       __syncwarp();
-      issue(q + STAGES - 1);  // into the slot consumed by the previous product
+      issue(q + STAGES - 1);  // into the slot the previous product used
       const int s = meta_s[q & (kMetaEntries - 1)];
-      const int sp = s + (s & 1);
-      const uint32_t sA = sbase + (uint32_t)((q % STAGES) * 2 * opb), sB = sA + opb;
-      // L (M' x s, row-major) and R (s x N', column-major) in the slot
+      const int rb = pipe_row_bytes(PREC, s);
+      const uint32_t sA = sbase + slot * 2 * (uint32_t)opb, sB = sA + (uint32_t)opb;
+      // L (Mp rows) and R (Np rows) in the slot; plane strides rows * rb
       const uint32_t sL = tr ? sB : sA, sR = tr ? sA : sB;
+      const uint32_t lpl = (uint32_t)(Mp * rb), rpl = (uint32_t)(Np * rb);
+      // this lane's piece address at k step 0; a k piece column is rows * 16 bytes
+      const uint32_t adL = sL + 16u * (uint32_t)(pa * Mp + ra);
+      const uint32_t adR = sR + 16u * (uint32_t)(pb * Np + rb_);
+      const uint32_t adR2 = sR + 16u * (uint32_t)ra;  // "a" order on R (half steps)
+      const bool two = Np > 8;  // a second 8-column tile
+      // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
+      // (BF16); (2,1) (1,2) (1,1) (TF32)
       if (BF) {
-        const int lplane = 2 * (tr ? sp * np2 : mp2 * sp), rplane = 2 * (tr ? mp2 * sp : sp * np2);
-        for (int kk = 0; kk < s; kk += KSTEP) {
-          const bool k8 = (s - kk) <= 8;
-          const int k0 = kk + 2 * t, k1 = k0 + 8;
-          const int r0 = g, r1 = g + 8;
-          uint32_t a[3][4], b[3][2][2];
+        constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
+        constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+        for (int kk = 0; kk < s; kk += 16) {
+          const uint32_t koL = 16u * (uint32_t)((kk >> 3) * Mp), koR = 16u * (uint32_t)((kk >> 3) * Np);
+          if (s - kk <= 8) {  // one k piece left: m16n8k8
+            uint32_t a[3][2], b[3][2];
 #pragma unroll
-          for (int q3 = 0; q3 < 3; q3++) {
-            const uint32_t P = sL + q3 * lplane, Q = sR + q3 * rplane;
-            a[q3][0] = (r0 < Mp && k0 < sp) ? lds32(P + 2 * (r0 * sp + k0)) : 0u;
-            a[q3][1] = (r1 < Mp && k0 < sp) ? lds32(P + 2 * (r1 * sp + k0)) : 0u;
-            a[q3][2] = (!k8 && r0 < Mp && k1 < sp) ? lds32(P + 2 * (r0 * sp + k1)) : 0u;
-            a[q3][3] = (!k8 && r1 < Mp && k1 < sp) ? lds32(P + 2 * (r1 * sp + k1)) : 0u;
-#pragma unroll
-            for (int nt = 0; nt < 2; nt++) {
-              const int c = nt * 8 + g;
-              b[q3][nt][0] = (c < Np && k0 < sp) ? lds32(Q + 2 * (c * sp + k0)) : 0u;
-              b[q3][nt][1] = (!k8 && c < Np && k1 < sp) ? lds32(Q + 2 * (c * sp + k1)) : 0u;
+            for (int q3 = 0; q3 < 3; q3++) {
+              ldsm_x2(a[q3][0], a[q3][1], adL + q3 * lpl + koL);
+              ldsm_x2(b[q3][0], b[q3][1], adR2 + q3 * rpl + koR);
             }
-          }
-          constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
-          constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+            if (two) {
 #pragma unroll
-          for (int nt = 0; nt < 2; nt++) {
-            if (nt * 8 >= Np) continue;
+              for (int pq = 0; pq < 6; pq++) {
+                mma_bf16_k8(acc[0], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][0]);
+                mma_bf16_k8(acc[1], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][1]);
+              }
+            } else {
 #pragma unroll
-            for (int pq = 0; pq < 6; pq++) {
-              if (k8)
-                mma_bf16_k8(acc[nt], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][nt][0]);
-              else
-                mma_bf16_k16(acc[nt], a[PA[pq]], b[PB[pq]][nt][0], b[PB[pq]][nt][1]);
+              for (int pq = 0; pq < 6; pq++)
+                mma_bf16_k8(acc[0], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][0]);
+            }
+          } else {
+            uint32_t a[3][4], b[3][4];
+#pragma unroll
+            for (int q3 = 0; q3 < 3; q3++) {
+              ldsm_x4(a[q3][0], a[q3][1], a[q3][2], a[q3][3], adL + q3 * lpl + koL);
+              ldsm_x4(b[q3][0], b[q3][1], b[q3][2], b[q3][3], adR + q3 * rpl + koR);
+            }
+            if (two) {
+#pragma unroll
+              for (int pq = 0; pq < 6; pq++) {
+                mma_bf16_k16(acc[0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
+                mma_bf16_k16(acc[1], a[PA[pq]], b[PB[pq]][2], b[PB[pq]][3]);
+              }
+            } else {
+#pragma unroll
+              for (int pq = 0; pq < 6; pq++)
+                mma_bf16_k16(acc[0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
             }
           }
         }
       } else {
-        const int lplane = 4 * (tr ? s * n : m * s), rplane = 4 * (tr ? m * s : s * n);
-        for (int kk = 0; kk < s; kk += KSTEP) {
-          const int k0 = kk + t, k1 = k0 + 4;
-          const int r0 = g, r1 = g + 8;
-          uint32_t a[2][4], b[2][2][2];
+        constexpr int PA[3] = {1, 0, 0};
+        constexpr int PB[3] = {0, 1, 0};
+        for (int kk = 0; kk < s; kk += 8) {
+          const uint32_t koL = 16u * (uint32_t)((kk >> 2) * Mp), koR = 16u * (uint32_t)((kk >> 2) * Np);
+          uint32_t a[2][4], b[2][4];
+          if (s - kk <= 4) {  // one k piece left: the other half is zero
 #pragma unroll
-          for (int q2 = 0; q2 < 2; q2++) {
-            const uint32_t P = sL + q2 * lplane, Q = sR + q2 * rplane;
-            a[q2][0] = (r0 < Mp && k0 < s) ? lds32(P + 4 * (r0 * s + k0)) : 0u;
-            a[q2][1] = (r1 < Mp && k0 < s) ? lds32(P + 4 * (r1 * s + k0)) : 0u;
-            a[q2][2] = (r0 < Mp && k1 < s) ? lds32(P + 4 * (r0 * s + k1)) : 0u;
-            a[q2][3] = (r1 < Mp && k1 < s) ? lds32(P + 4 * (r1 * s + k1)) : 0u;
+            for (int q2 = 0; q2 < 2; q2++) {
+              ldsm_x2(a[q2][0], a[q2][1], adL + q2 * lpl + koL);
+              ldsm_x2(b[q2][0], b[q2][2], adR2 + q2 * rpl + koR);
+              a[q2][2] = a[q2][3] = b[q2][1] = b[q2][3] = 0u;
+            }
+          } else {
 #pragma unroll
-            for (int nt = 0; nt < 2; nt++) {
-              const int c = nt * 8 + g;
-              b[q2][nt][0] = (c < Np && k0 < s) ? lds32(Q + 4 * (c * s + k0)) : 0u;
-              b[q2][nt][1] = (c < Np && k1 < s) ? lds32(Q + 4 * (c * s + k1)) : 0u;
+            for (int q2 = 0; q2 < 2; q2++) {
+              ldsm_x4(a[q2][0], a[q2][1], a[q2][2], a[q2][3], adL + q2 * lpl + koL);
+              ldsm_x4(b[q2][0], b[q2][1], b[q2][2], b[q2][3], adR + q2 * rpl + koR);
             }
           }
-          constexpr int PA[3] = {1, 0, 0};
-          constexpr int PB[3] = {0, 1, 0};
+          if (two) {
 #pragma unroll
-          for (int nt = 0; nt < 2; nt++) {
-            if (nt * 8 >= Np) continue;
+            for (int pq = 0; pq < 3; pq++) {
+              mma_tf32_k8(acc[0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
+              mma_tf32_k8(acc[1], a[PA[pq]], b[PB[pq]][2], b[PB[pq]][3]);
+            }
+          } else {
 #pragma unroll
             for (int pq = 0; pq < 3; pq++)
-              mma_tf32_k8(acc[nt], a[PA[pq]], b[PB[pq]][nt][0], b[PB[pq]][nt][1]);
+              mma_tf32_k8(acc[0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
           }
         }
       }
@@ -701,8 +818,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
           }
       }
     }
-    cp_async_wait<0>();
-    __syncwarp();
+    if (failed) break;
 
     const int cin = ws.c_cin[gb];
     const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
@@ -727,6 +843,10 @@ __global__ void __launch_bounds__(kPipeWarps * 32)
         }
       }
   }
+  if (failed && lane == 0) atomicOr(const_cast<int32_t *>(&st->error), 1);
+  // copies still in flight into this warp's slots (none unless a wait gave up)
+  for (uint32_t u = consumed; u < issued; u++)
+    if (!mbar_wait(bar0 + 8 * (u % STAGES), (u / STAGES) & 1u)) break;
 }
 
 // One warp per C block (dynamically assigned). SIZES selects the
@@ -774,6 +894,33 @@ __global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOu
   }
 }
 
+// Ring depth of the pipelined kernel: pipe_stages(smax), or 2, 3, 4 or 6 from
+// the environment variable BSM_SPLIT_STAGES (a tuning override; read once).
+static int pipe_stages_for(int smax) {
+  static const int forced = [] {
+    const char *v = getenv("BSM_SPLIT_STAGES");
+    const int x = v ? atoi(v) : 0;
+    return (x == 2 || x == 3 || x == 4 || x == 6) ? x : 0;
+  }();
+  if (forced && kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, smax, forced) <= 200 * 1024)
+    return forced;
+  return pipe_stages(smax);
+}
+
+// [precision: BF16x3, TF32x2][stages: 2, 3, 4, 6]
+static const void *const (&pipe_instances())[2][4] {
+  static const void *const inst[2][4] = {
+      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 3>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 4>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 6>},
+      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 3>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 4>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 6>}};
+  return inst;
+}
+
 cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, DevOut C,
                                  DevMat Cin, const void *a_left, const void *b_right, double alpha,
                                  double beta, DevWs ws, const DevStatus *st, const int32_t *items,
@@ -789,15 +936,11 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
           A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, work);
     return cudaGetLastError();
   }
-  const int stages = pipe_stages(smax);
+  const int stages = pipe_stages_for(smax);
   const size_t smem = (size_t)kPipeWarps * pipe_warp_bytes(precision, smax, stages);
-  const void *fn;
-  if (precision == BSM_PREC_SPLIT_BF16X3)
-    fn = stages == 3 ? (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 3>
-                     : (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2>;
-  else
-    fn = stages == 3 ? (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 3>
-                     : (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2>;
+  const int pi = precision == BSM_PREC_SPLIT_BF16X3 ? 0 : 1;
+  const int si = stages == 2 ? 0 : stages == 3 ? 1 : stages == 4 ? 2 : 3;
+  const void *fn = pipe_instances()[pi][si];
   int per_sm = 1;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPipeWarps * 32, smem);
   if (e != cudaSuccess) return e;
@@ -806,40 +949,37 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
 #define BSM_SPLIT_PIPE(P, S)                                                                \
   k_numeric_split_pipe<P, S><<<grid, kPipeWarps * 32, smem, stream>>>(                      \
       A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, only_small, work)
-  if (precision == BSM_PREC_SPLIT_BF16X3) {
-    if (stages == 3)
-      BSM_SPLIT_PIPE(BSM_PREC_SPLIT_BF16X3, 3);
-    else
-      BSM_SPLIT_PIPE(BSM_PREC_SPLIT_BF16X3, 2);
-  } else {
-    if (stages == 3)
-      BSM_SPLIT_PIPE(BSM_PREC_SPLIT_TF32X2, 3);
-    else
-      BSM_SPLIT_PIPE(BSM_PREC_SPLIT_TF32X2, 2);
+#define BSM_SPLIT_PIPE_S(P)            \
+  switch (stages) {                    \
+    case 2: BSM_SPLIT_PIPE(P, 2); break; \
+    case 3: BSM_SPLIT_PIPE(P, 3); break; \
+    case 4: BSM_SPLIT_PIPE(P, 4); break; \
+    default: BSM_SPLIT_PIPE(P, 6); break; \
   }
+  if (precision == BSM_PREC_SPLIT_BF16X3) {
+    BSM_SPLIT_PIPE_S(BSM_PREC_SPLIT_BF16X3);
+  } else {
+    BSM_SPLIT_PIPE_S(BSM_PREC_SPLIT_TF32X2);
+  }
+#undef BSM_SPLIT_PIPE_S
 #undef BSM_SPLIT_PIPE
   return cudaGetLastError();
 }
 
 cudaError_t numeric_split_init() {
-  // the largest slot layout of each instance: k up to 32
-  const struct {
-    const void *fn;
-    int bytes;
-  } inst[4] = {
-      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 3>,
-       kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_BF16X3, 32, 3)},
-      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2>,
-       kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_BF16X3, 32, 2)},
-      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 3>,
-       kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, 32, 3)},
-      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2>,
-       kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, 32, 2)},
-  };
-  for (const auto &x : inst) {
-    cudaError_t e = cudaFuncSetAttribute(x.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, x.bytes);
-    if (e != cudaSuccess) return e;
-  }
+  // the largest slot layout of each instance (k up to 32), and the whole
+  // shared memory of an SM for the carveout (the rings decide occupancy)
+  for (int pi = 0; pi < 2; pi++)
+    for (int si = 0; si < 4; si++) {
+      const int prec = pi == 0 ? BSM_PREC_SPLIT_BF16X3 : BSM_PREC_SPLIT_TF32X2;
+      const int stages = si == 0 ? 2 : si == 1 ? 3 : si == 2 ? 4 : 6;
+      const void *fn = pipe_instances()[pi][si];
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kPipeWarps * pipe_warp_bytes(prec, 32, stages));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      if (e != cudaSuccess) return e;
+    }
   return cudaSuccess;
 }
 

@@ -37,12 +37,23 @@ def gpu_mult(ctx, A, B, prec, alpha=1.0, beta=0.0, C=None, eps=0.0):
     return r, c, v, st
 
 
+# block size sets: rows of A / inner k / columns of B. "mixed" has C blocks
+# beyond 16 (two launches: small C blocks pipelined, large ones direct);
+# "small" keeps everything within 16 (one pipelined launch, 3-stage ring, the
+# half k steps of k <= 8 (BF16) and k <= 4 (TF32)); "wide_k" has C blocks
+# within 16 but k up to 32 (one pipelined launch, 2-stage ring).
+SIZE_SETS = {"mixed": ((1, 2, 5, 9, 13, 23, 32),) * 3,
+             "small": ((1, 2, 3, 4, 5, 7, 8, 13, 16),) * 3,
+             "wide_k": ((1, 3, 5, 13, 16), (4, 9, 17, 24, 31, 32), (2, 5, 8, 13, 16))}
+
+
 @pytest.mark.parametrize("prec", sorted(PRECS))
+@pytest.mark.parametrize("sizes", sorted(SIZE_SETS))
 @pytest.mark.parametrize("seed", range(3))
-def test_split_integer_exact(gpu_ctx, oracle_mod, prec, seed):
+def test_split_integer_exact(gpu_ctx, oracle_mod, prec, sizes, seed):
     rng = np.random.default_rng(700 + seed)
-    sizes = (1, 2, 5, 9, 13, 23, 32)
-    rs, ks, cs = rng.choice(sizes, 7), rng.choice(sizes, 8), rng.choice(sizes, 6)
+    rsz, ksz, csz = SIZE_SETS[sizes]
+    rs, ks, cs = rng.choice(rsz, 7), rng.choice(ksz, 8), rng.choice(csz, 6)
     A = synth.random_blocks(rng, rs, ks, 0.5, kind="int", shuffle=True)
     B = synth.random_blocks(rng, ks, cs, 0.5, kind="int", shuffle=True)
     ref = oracle_mod.multiply(A, B, eps=0.0)
@@ -71,6 +82,26 @@ def test_split_water_bound(gpu_ctx, oracle_mod, prec):
     assert rel <= REL_F[prec], rel
     # the largest error, relative to the largest element
     assert np.max(np.abs(v - ref.values)) <= REL_F[prec] * np.max(np.abs(ref.values))
+
+
+@pytest.mark.parametrize("prec", sorted(PRECS))
+@pytest.mark.parametrize("sizes", sorted(SIZE_SETS))
+def test_split_general_values(gpu_ctx, oracle_mod, prec, sizes):
+    """Normal values on each size set: every slice plane takes part, so a
+    misplaced plane, row or k piece shows as an error far above the bound."""
+    rng = np.random.default_rng(800)
+    rsz, ksz, csz = SIZE_SETS[sizes]
+    rs, ks, cs = rng.choice(rsz, 12), rng.choice(ksz, 14), rng.choice(csz, 10)
+    A = synth.random_blocks(rng, rs, ks, 0.5, kind="normal", shuffle=True)
+    B = synth.random_blocks(rng, ks, cs, 0.5, kind="normal", shuffle=True)
+    ref = oracle_mod.multiply(A, B, eps=0.0)
+    absref = oracle_mod.multiply(_abs(A), _abs(B), eps=0.0)
+    r, c, v, st = gpu_mult(gpu_ctx, A, B, prec)
+    assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+    K = int(ks.sum())
+    bound = (U_SPLIT[prec] + K * 2.0 ** -23) * absref.values + 1e-300
+    assert np.all(np.abs(v - ref.values) <= bound)
+    assert H.rel_frobenius(v, ref.values) <= REL_F[prec]
 
 
 @pytest.mark.parametrize("prec", sorted(PRECS))
