@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "../../include/bsm.h"
+#include "bsm_internal.h"
 
 namespace {
 
@@ -124,7 +125,7 @@ struct Slot {
 };
 
 // Upper bound of the device bytes a request C = A.A can hold.
-int64_t footprint_bound(const Request &r, int64_t *c_vals_bound) {
+int64_t footprint_bound(const Request &r, int precision, int64_t *c_vals_bound) {
   const int64_t nbr = (int64_t)r.sizes.size();
   std::vector<int64_t> row_nblk(nbr, 0), row_cols(nbr, 0);
   for (size_t b = 0; b < r.brow.size(); b++) {
@@ -142,9 +143,12 @@ int64_t footprint_bound(const Request &r, int64_t *c_vals_bound) {
   const int64_t c_blocks = std::min<int64_t>(nbr * nbr, cand);
   const int64_t c_vals = std::min<int64_t>(dim * dim, cand_vals);
   if (c_vals_bound) *c_vals_bound = c_vals;
-  // A (+ slices for the split precisions), C twice (front/back), per-block
-  // metadata, product records
-  return 4 * a_bytes + 2 * (8 * c_vals + 32 * c_blocks) + 8 * cand + 64 * nbr + (1 << 20);
+  // the split precisions keep A's slices in both operand layouts
+  const int64_t slice_bytes =
+      precision == BSM_PREC_FP64 ? 0 : 2 * bsm::split_bytes_per_value(precision) * (int64_t)r.vals.size();
+  // A, C twice (front/back), per-block metadata, product records
+  return 4 * a_bytes + slice_bytes + 2 * (8 * c_vals + 32 * c_blocks) + 8 * cand + 64 * nbr +
+         (1 << 20);
 }
 
 }  // namespace
@@ -339,7 +343,7 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
     return BSM_ERR_NOMEM;
   }
   r->eps = eps;
-  r->footprint = footprint_bound(*r, &r->c_vals_bound);
+  r->footprint = footprint_bound(*r, s->precision, &r->c_vals_bound);
   if (r->footprint > s->budget) {  // could never be admitted
     delete r;
     return BSM_ERR_NOMEM;

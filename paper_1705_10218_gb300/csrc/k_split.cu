@@ -531,10 +531,13 @@ constexpr int kPipeWarps = 4;
 constexpr int kFold = 4;
 constexpr int kMetaEntries = 64;
 constexpr int kMetaBytes = kMetaEntries * (8 + 8 + 4);
-// Polls of a slot's mbarrier before a warp gives up on a copy that does not
-// land: it then raises the status error flag, waits (again bounded) for the
-// copies it has in flight and stops.
-constexpr int kWaitPolls = 1 << 22;
+// A waiting thread is suspended until the phase completes or kWaitHintNs
+// pass (no issue slots spent on polling); after kWaitPolls such waits (about
+// a second) a warp gives up on a copy that does not land: it then raises the
+// status error flag, waits (again bounded) for the copies it has in flight and
+// stops.
+constexpr uint32_t kWaitHintNs = 1000;
+constexpr int kWaitPolls = 1 << 20;
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
@@ -562,10 +565,10 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uin
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kWaitHintNs)
       : "memory");
   return ok != 0;
 }
@@ -599,6 +602,12 @@ __host__ __device__ __forceinline__ int pipe_warp_bytes(int precision, int smax,
   return stages * 2 * pipe_operand_bytes(precision, smax) + kMetaBytes + ((8 * stages + 15) & ~15);
 }
 
+// A C block of the pipelined kernel's stream: gb < 0 marks the end of the work.
+struct PipeBlock {
+  int64_t gb, p0;
+  int np, m, n;
+};
+
 // Minimum resident blocks per SM the register budget is fitted to: the kernel
 // is bound by instruction issue and latency, so more resident warps pay.
 // (the TF32 slots are larger: 5 blocks of 2 stages fill the shared memory).
@@ -625,8 +634,10 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
   const int g = lane >> 2, t = lane & 3;
   const int opb = pipe_operand_bytes(PREC, smax);
   unsigned char *wbase = smem_pipe + warp * pipe_warp_bytes(PREC, smax, STAGES);
-  int64_t *meta_a = reinterpret_cast<int64_t *>(wbase + STAGES * 2 * opb);
-  int64_t *meta_b = meta_a + kMetaEntries;
+  // the product table, a ring indexed by stream position: source addresses of
+  // the two operands' slices and k
+  const unsigned char **meta_a = reinterpret_cast<const unsigned char **>(wbase + STAGES * 2 * opb);
+  const unsigned char **meta_b = meta_a + kMetaEntries;
   int *meta_s = reinterpret_cast<int *>(meta_b + kMetaEntries);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(wbase);
   const uint32_t bar0 = sbase + (uint32_t)(STAGES * 2 * opb + kMetaBytes);
@@ -648,76 +659,109 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
     we = seg[1];
   }
   const bool plain = (alpha == 1.0 && beta == 0.0);
-  uint32_t issued = 0, consumed = 0;  // products this warp has started / waited for
+  // The products of the C blocks a warp takes form one stream; stream position
+  // u uses ring slot u % STAGES (mbarrier phase (u / STAGES) & 1) and table
+  // entry u % kMetaEntries. Copies run STAGES - 1 positions ahead of the
+  // tensor-core work, across C block boundaries (into the next block's first
+  // products), so the ring does not drain between blocks.
+  uint32_t u_issue = 0, u_done = 0;  // next position to copy / to compute
   bool failed = false;
-  // C blocks come one at a time from the work counter (zero at launch); the
-  // next index is fetched while the current block runs
-  unsigned long long next = 0;
+  unsigned long long next = 0;  // the work counter's next index, fetched ahead
   if (lane == 0) next = atomicAdd(work, 1ull);
-  for (;;) {
-    const int64_t w = wb + (int64_t)__shfl_sync(0xffffffffu, next, 0);
-    if (w >= we) break;
-    if (lane == 0) next = atomicAdd(work, 1ull);
-    const int64_t gb = items ? items[w] : w;
-    const int i = C.blk_row[gb], j = C.col_idx[gb];
-    const int m = C.row_sizes[i], n = C.col_sizes[j];
+  PipeBlock cur, nxt;
+  int cur_issued = 0, nxt_issued = 0;  // products of the block started so far
+  bool have_nxt = false;
+
+  // the next C block of this launch (warp-uniform); gb < 0: none left
+  auto take = [&](PipeBlock &b) {
+    for (;;) {
+      const int64_t w = wb + (int64_t)__shfl_sync(0xffffffffu, next, 0);
+      if (w >= we) {
+        b.gb = -1;
+        b.np = 0;
+        return;
+      }
+      if (lane == 0) next = atomicAdd(work, 1ull);
+      const int64_t gb = items ? items[w] : w;
+      const int i = C.blk_row[gb], j = C.col_idx[gb];
+      const int m = C.row_sizes[i], n = C.col_sizes[j];
+      const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
+      const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
+      const bool tr = tiles_t < tiles_n;
+      const int Mp = tr ? n : m, Np = tr ? m : n;
+      if (only_small && !(Mp <= 16 && Np <= 16)) continue;
+      b.gb = gb;
+      b.p0 = ws.prod_ptr[gb];
+      b.np = (int)(ws.prod_ptr[gb + 1] - b.p0);
+      b.m = m;
+      b.n = n;
+      return;
+    }
+  };
+  // start the copies of product q of block b at stream position u_issue (all
+  // lanes call; the table holds the next 32 products of b from q % 32 == 0)
+  auto issue = [&](const PipeBlock &b, int q) {
+    const uint32_t u = u_issue++;
+    if ((q & 31) == 0) {
+      const int qq = q + lane;
+      if (qq < b.np) {
+        const int2 pr = ws.prods[b.p0 + qq];
+        const int e = (int)((u + (uint32_t)lane) & (kMetaEntries - 1));
+        meta_a[e] = static_cast<const unsigned char *>(a_left) + kUnit * A.blk_off[pr.x];
+        meta_b[e] = static_cast<const unsigned char *>(b_right) + kUnit * B.blk_off[pr.y];
+        meta_s[e] = A.col_sizes[A.col_idx[pr.x]];
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      const int e = (int)(u & (kMetaEntries - 1));
+      const int rb = pipe_row_bytes(PREC, meta_s[e]);
+      const uint32_t bytes_a = (uint32_t)(NSL * b.m * rb), bytes_b = (uint32_t)(NSL * b.n * rb);
+      const uint32_t slot = u % STAGES;
+      const uint32_t dst = sbase + slot * 2 * (uint32_t)opb, bar = bar0 + 8 * slot;
+      fence_proxy_async_smem();
+      mbar_expect_tx(bar, bytes_a + bytes_b);
+      bulk_copy_g2s(dst, meta_a[e], bytes_a, bar);
+      bulk_copy_g2s(dst + (uint32_t)opb, meta_b[e], bytes_b, bar);
+    }
+  };
+
+  take(cur);
+  while (cur_issued < cur.np && (int)(u_issue - u_done) < STAGES - 1) issue(cur, cur_issued++);
+  while (cur.gb >= 0) {
+    const int m = cur.m, n = cur.n;
     const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
     const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
     const bool tr = tiles_t < tiles_n;
     const int Mp = tr ? n : m, Np = tr ? m : n;
-    if (only_small && !(Mp <= 16 && Np <= 16)) continue;
-    const int64_t p0 = ws.prod_ptr[gb];
-    const int np = (int)(ws.prod_ptr[gb + 1] - p0);
-    const uint32_t u0 = issued;  // ring position of this block's first product
-
+    const bool two = Np > 8;  // a second 8-column tile
     float hi[2][4], lo[2][4], acc[2][4];
 #pragma unroll
     for (int nt = 0; nt < 2; nt++)
 #pragma unroll
       for (int x = 0; x < 4; x++) hi[nt][x] = lo[nt][x] = acc[nt][x] = 0.f;
 
-    // start the copies of product q into slot (u0 + q) % STAGES (all lanes call)
-    auto issue = [&](int q) {
-      if (q >= np) return;
-      if ((q & 31) == 0) {  // the next 32 products' offsets and k
-        const int qq = q + lane;
-        if (qq < np) {
-          const int2 pr = ws.prods[p0 + qq];
-          meta_a[qq & (kMetaEntries - 1)] = A.blk_off[pr.x];
-          meta_b[qq & (kMetaEntries - 1)] = B.blk_off[pr.y];
-          meta_s[qq & (kMetaEntries - 1)] = A.col_sizes[A.col_idx[pr.x]];
-        }
-        __syncwarp();
-      }
-      if (lane == 0) {
-        const int e = q & (kMetaEntries - 1);
-        const int rb = pipe_row_bytes(PREC, meta_s[e]);
-        const uint32_t bytes_a = (uint32_t)(NSL * m * rb), bytes_b = (uint32_t)(NSL * n * rb);
-        const uint32_t slot = (u0 + (uint32_t)q) % STAGES;
-        const uint32_t dst = sbase + slot * 2 * (uint32_t)opb, bar = bar0 + 8 * slot;
-        fence_proxy_async_smem();
-        mbar_expect_tx(bar, bytes_a + bytes_b);
-        bulk_copy_g2s(dst, static_cast<const unsigned char *>(a_left) + kUnit * meta_a[e], bytes_a,
-                      bar);
-        bulk_copy_g2s(dst + (uint32_t)opb,
-                      static_cast<const unsigned char *>(b_right) + kUnit * meta_b[e], bytes_b, bar);
-      }
-      issued++;
-    };
-
-    __syncwarp();  // every lane is past its reads of the slots about to be refilled
-#pragma unroll
-    for (int q = 0; q < STAGES - 1; q++) issue(q);
-    for (int q = 0; q < np; q++) {
-      const uint32_t u = u0 + (uint32_t)q, slot = u % STAGES;
+    for (int q = 0; q < cur.np; q++) {
+      const uint32_t u = u_done, slot = u % STAGES;
       if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8 * slot, (u / STAGES) & 1u))) {
         failed = true;
         break;
       }
-      consumed++;
+      u_done++;
       __syncwarp();
-      issue(q + STAGES - 1);  // into the slot the previous product used
-      const int s = meta_s[q & (kMetaEntries - 1)];
+      // refill the slot the previous position used: the next product of this
+      // block, else the first ones of the next block
+      if (cur_issued < cur.np) {
+        issue(cur, cur_issued++);
+      } else {
+        if (!have_nxt) {
+          take(nxt);
+          nxt_issued = 0;
+          have_nxt = true;
+        }
+        if (nxt_issued < nxt.np) issue(nxt, nxt_issued++);
+      }
+      const int s = meta_s[u & (kMetaEntries - 1)];
       const int rb = pipe_row_bytes(PREC, s);
       const uint32_t sA = sbase + slot * 2 * (uint32_t)opb, sB = sA + (uint32_t)opb;
       // L (Mp rows) and R (Np rows) in the slot; plane strides rows * rb
@@ -727,7 +771,6 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
       const uint32_t adL = sL + 16u * (uint32_t)(pa * Mp + ra);
       const uint32_t adR = sR + 16u * (uint32_t)(pb * Np + rb_);
       const uint32_t adR2 = sR + 16u * (uint32_t)ra;  // "a" order on R (half steps)
-      const bool two = Np > 8;  // a second 8-column tile
       // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
       // (BF16); (2,1) (1,2) (1,1) (TF32)
       if (BF) {
@@ -808,7 +851,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
       }
       // every kFold products (and after the last): fold the FP32 partial sum
       // into the compensated running sum
-      if ((q % kFold) == kFold - 1 || q == np - 1) {
+      if ((q % kFold) == kFold - 1 || q == cur.np - 1) {
 #pragma unroll
         for (int nt = 0; nt < 2; nt++)
 #pragma unroll
@@ -820,6 +863,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
     }
     if (failed) break;
 
+    const int64_t gb = cur.gb;
     const int cin = ws.c_cin[gb];
     const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
     double *out = C.vals + C.blk_off[gb];
@@ -833,7 +877,8 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
         if (rr < Mp && cc < Np) {
           const int row = tr ? cc : rr, col = tr ? rr : cc;
           const int64_t e = (int64_t)col * m + row;
-          double v = f32_to_f64_exact(hi[nt][x]) + f32_to_f64_exact(lo[nt][x]);
+          // FP32 -> FP64 is exact; hi + lo rounded once in FP64
+          double v = (double)hi[nt][x] + (double)lo[nt][x];
           if (!plain) {
             v = alpha * v;
             if (cinv) v = fma(beta, cinv[e], v);
@@ -842,10 +887,21 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
           if (hblk) hblk[e] = v;
         }
       }
+
+    // the next block (already begun if the ring ran into it)
+    if (!have_nxt) {
+      take(nxt);
+      nxt_issued = 0;
+    }
+    cur = nxt;
+    cur_issued = nxt_issued;
+    have_nxt = false;
+    __syncwarp();  // every lane is past its reads of the slots about to be refilled
+    while (cur_issued < cur.np && (int)(u_issue - u_done) < STAGES - 1) issue(cur, cur_issued++);
   }
   if (failed && lane == 0) atomicOr(const_cast<int32_t *>(&st->error), 1);
   // copies still in flight into this warp's slots (none unless a wait gave up)
-  for (uint32_t u = consumed; u < issued; u++)
+  for (uint32_t u = u_done; u < u_issue; u++)
     if (!mbar_wait(bar0 + 8 * (u % STAGES), (u / STAGES) & 1u)) break;
 }
 
