@@ -350,6 +350,14 @@ int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bsm_dev_csr *
 /* Wait for all work of the context and complete every pending result. */
 int bsm_sync(bsm_ctx ctx);
 
+/* Check of the bounded device-side wait the split-precision kernels use on
+ * their copy barriers (an mbarrier in shared memory): one warp on the
+ * context's stream waits on a barrier that its own lane 0 completes
+ * (never_complete = 0: BSM_OK) or that nothing completes (never_complete = 1:
+ * the wait gives up after its limit, about a second, and the call returns
+ * BSM_ERR_TIMEOUT with the context still usable). Blocking. */
+int bsm_selftest_wait(bsm_ctx ctx, int never_complete);
+
 /* Static text for a BSM_* code. */
 const char *bsm_strerror(int code);
 

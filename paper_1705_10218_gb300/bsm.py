@@ -122,6 +122,7 @@ _SIGS = {
     "bsm_mat_get_pattern": (ctypes.c_int, [_P, _I64, _P, _P]),
     "bsm_mat_get_values": (ctypes.c_int, [_P, _I64, _P]),
     "bsm_sync": (ctypes.c_int, [_P]),
+    "bsm_selftest_wait": (ctypes.c_int, [_P, ctypes.c_int]),
     "bsm_ctx_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "bsm_mat_filter": (ctypes.c_int, [_P, _D]),
     "bsm_mat_assign": (ctypes.c_int, [_P, _I64, _P, _P, _P]),
@@ -229,6 +230,11 @@ class Context:
 
     def sync(self):
         _check(lib().bsm_sync(self._h), "bsm_sync")
+
+    def selftest_wait(self, never_complete: bool):
+        """The split kernels' bounded device-side barrier wait on its own
+        (bsm_selftest_wait): raises BsmError TIMEOUT when it gives up."""
+        _check(lib().bsm_selftest_wait(self._h, int(bool(never_complete))), "bsm_selftest_wait")
 
     def add(self, alpha, A: "Matrix", beta, C: "Matrix"):
         """C = beta*C + alpha*A on the union of the patterns."""

@@ -1484,6 +1484,21 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out) {
   return BSM_OK;
 }
 
+int bsm_selftest_wait(bsm_ctx ctx, int never_complete) {
+  if (!ctx) return BSM_ERR_INVALID_ARG;
+  int rc = ctx_set_device(ctx);
+  if (rc) return rc;
+  int32_t *d_flag = nullptr, h_flag = -1;
+  CK(cudaMalloc((void **)&d_flag, sizeof(int32_t)));
+  cudaError_t e = launch_wait_selftest(never_complete ? 1 : 0, d_flag, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h_flag, d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d_flag);
+  if (e != cudaSuccess) return cuda_fail(e, "wait selftest");
+  return h_flag == 0 ? BSM_OK : BSM_ERR_TIMEOUT;
+}
+
 int bsm_sync(bsm_ctx ctx) {
   if (!ctx) return BSM_ERR_INVALID_ARG;
   int rc = ctx_set_device(ctx);

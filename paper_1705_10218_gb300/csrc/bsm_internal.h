@@ -128,6 +128,10 @@ cudaError_t launch_class_sort(DevOut C, const int32_t *row_cls, const int32_t *c
 
 // Split precision (k_split.cu). left/right: slice layouts of the operand as a
 // left (row-major) or right (column-major) MMA operand; either may be null.
+// One warp waits (bounded) on an mbarrier that it completes itself, or that
+// nothing completes (never_complete); *flag = 1 when the wait gave up.
+cudaError_t launch_wait_selftest(int never_complete, int32_t *flag, cudaStream_t stream);
+
 cudaError_t launch_split(int precision, const int32_t *row_sizes, const int32_t *col_sizes,
                          const int32_t *blk_row, const int32_t *col_idx, const int64_t *blk_off,
                          const double *vals, const int64_t *hdr, void *left, void *right,

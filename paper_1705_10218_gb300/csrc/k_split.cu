@@ -905,6 +905,29 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
     if (!mbar_wait(bar0 + 8 * (u % STAGES), (u / STAGES) & 1u)) break;
 }
 
+// The pipelined kernel's bounded barrier wait on its own: lane 0 completes the
+// phase (a plain arrive), unless never_complete; the warp then waits as the
+// kernel does and records in *flag whether the wait gave up.
+__global__ void k_wait_selftest(int never_complete, int32_t *flag) {
+  __shared__ __align__(8) unsigned long long bar_storage;
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_storage);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  if (lane == 0 && !never_complete)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, 0u));
+  if (lane == 0) *flag = ok ? 0 : 1;
+}
+
+cudaError_t launch_wait_selftest(int never_complete, int32_t *flag, cudaStream_t stream) {
+  k_wait_selftest<<<1, 32, 0, stream>>>(never_complete, flag);
+  return cudaGetLastError();
+}
+
 // One warp per C block (dynamically assigned). SIZES selects the
 // blocks a launch takes: 0 all (every MMA problem fits 16 x 16), 1 those that
 // fit 16 x 16, 2 the others (up to 32 x 32). Small blocks use 1 x 2 tiles with
