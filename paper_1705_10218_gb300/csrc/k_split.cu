@@ -93,9 +93,32 @@ __device__ __forceinline__ Slices<NS, BITS> split_value(double x) {
 
 // ---------------------------------------------------------------------------
 // Split every block of a matrix into the left and/or right slice layouts.
-// One warp per block (grid-stride), lanes over the padded positions.
+// One warp per block (grid-stride), lanes over the positions of the block
+// padded to whole pieces in both directions (ceil8(r) x ceil8(c) for BF16,
+// ceil4 for TF32, column-major): each value is split once and its slices are
+// written to both layouts; the padding positions write the zeros.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int round_up(int x, int q) { return (x + q - 1) / q * q; }
+
+template <int NS, int BITS, int PIECE, typename T>
+__device__ __forceinline__ void split_block(const double *__restrict__ x, int r, int c, int lane,
+                                            T *__restrict__ left, T *__restrict__ right) {
+  const int rp = round_up(r, PIECE), cp = round_up(c, PIECE);
+  const int lplane = r * cp, rplane = c * rp;  // elements per plane
+  for (int e = lane; e < rp * cp; e += 32) {
+    const int yc = e / rp, xr = e - yc * rp;  // (row xr, column yc), column-major
+    const bool in = xr < r && yc < c;
+    const Slices<NS, BITS> sl = split_value<NS, BITS>(in ? x[xr + (int64_t)yc * r] : 0.0);
+    // left: row xr along k = yc; right: row yc along k = xr; pieces k-major
+    const int li = ((yc / PIECE) * r + xr) * PIECE + (yc % PIECE);
+    const int ri = ((xr / PIECE) * c + yc) * PIECE + (xr % PIECE);
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+      if (left && xr < r) left[(int64_t)q * lplane + li] = (T)sl.s[q];
+      if (right && yc < c) right[(int64_t)q * rplane + ri] = (T)sl.s[q];
+    }
+  }
+}
 
 __global__ void k_split_bf16x3(const int32_t *__restrict__ row_sizes,
                                const int32_t *__restrict__ col_sizes,
@@ -109,27 +132,9 @@ __global__ void k_split_bf16x3(const int32_t *__restrict__ row_sizes,
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = w0; b < nblk; b += nw) {
-    const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
     const int64_t base = kBf16HalfwordsPerValue * blk_off[b];
-    const double *x = vals + blk_off[b];
-    if (left) {  // r rows along k = the block's columns
-      const int plane = r * round_up(c, 8);
-      for (int e = lane; e < plane; e += 32) {
-        const int p = e >> 3, kp = p / r, row = p - kp * r, k = 8 * kp + (e & 7);
-        const Slices<3, 8> sl = split_value<3, 8>(k < c ? x[row + (int64_t)k * r] : 0.0);
-#pragma unroll
-        for (int q = 0; q < 3; q++) left[base + (int64_t)q * plane + e] = (uint16_t)sl.s[q];
-      }
-    }
-    if (right) {  // c rows (the block's columns) along k = the block's rows
-      const int plane = c * round_up(r, 8);
-      for (int e = lane; e < plane; e += 32) {
-        const int p = e >> 3, kp = p / c, col = p - kp * c, k = 8 * kp + (e & 7);
-        const Slices<3, 8> sl = split_value<3, 8>(k < r ? x[k + (int64_t)col * r] : 0.0);
-#pragma unroll
-        for (int q = 0; q < 3; q++) right[base + (int64_t)q * plane + e] = (uint16_t)sl.s[q];
-      }
-    }
+    split_block<3, 8, 8>(vals + blk_off[b], row_sizes[blk_row[b]], col_sizes[col_idx[b]], lane,
+                         left ? left + base : nullptr, right ? right + base : nullptr);
   }
 }
 
@@ -145,27 +150,9 @@ __global__ void k_split_tf32x2(const int32_t *__restrict__ row_sizes,
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = w0; b < nblk; b += nw) {
-    const int r = row_sizes[blk_row[b]], c = col_sizes[col_idx[b]];
     const int64_t base = kTf32WordsPerValue * blk_off[b];
-    const double *x = vals + blk_off[b];
-    if (left) {
-      const int plane = r * round_up(c, 4);
-      for (int e = lane; e < plane; e += 32) {
-        const int p = e >> 2, kp = p / r, row = p - kp * r, k = 4 * kp + (e & 3);
-        const Slices<2, 11> sl = split_value<2, 11>(k < c ? x[row + (int64_t)k * r] : 0.0);
-#pragma unroll
-        for (int q = 0; q < 2; q++) left[base + (int64_t)q * plane + e] = sl.s[q];
-      }
-    }
-    if (right) {
-      const int plane = c * round_up(r, 4);
-      for (int e = lane; e < plane; e += 32) {
-        const int p = e >> 2, kp = p / c, col = p - kp * c, k = 4 * kp + (e & 3);
-        const Slices<2, 11> sl = split_value<2, 11>(k < r ? x[k + (int64_t)col * r] : 0.0);
-#pragma unroll
-        for (int q = 0; q < 2; q++) right[base + (int64_t)q * plane + e] = sl.s[q];
-      }
-    }
+    split_block<2, 11, 4>(vals + blk_off[b], row_sizes[blk_row[b]], col_sizes[col_idx[b]], lane,
+                          left ? left + base : nullptr, right ? right + base : nullptr);
   }
 }
 
