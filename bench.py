@@ -37,6 +37,7 @@ WORKLOADS = {
     "water64": dict(kind="water", n=64, seed=0, eps=1e-10),
     "water512": dict(kind="water", n=512, seed=1, eps=1e-10),
     "amorphous4096": dict(kind="amorphous", n=4096, seed=2, eps=1e-8),
+    "amorphous1024": dict(kind="amorphous", n=1024, seed=2, eps=1e-8),  # profiling size
     # Table 1 analogues scaled to one GPU: Dense (block 32, full) and S-E (block 6, 0.05%)
     "dense4096": dict(kind="dense", n=128, bs=32, seed=3, eps=1e-10),
     "se40000": dict(kind="sparse", n=40000, bs=6, occ=5e-4, seed=5, eps=1e-10),

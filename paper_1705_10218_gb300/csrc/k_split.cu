@@ -198,155 +198,21 @@ __device__ __forceinline__ void mma_tf32_k8(float (&d)[4], const uint32_t (&a)[4
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Exact FP32 -> FP64 conversion with integer operations only.
-__device__ __forceinline__ double f32_to_f64_exact(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint64_t sign = (uint64_t)(u >> 31) << 63;
-  const uint32_t ef = (u >> 23) & 0xFFu;
-  const uint64_t man = u & 0x7FFFFFu;
-  uint64_t bits;
-  if (ef == 0) {
-    if (man == 0) {
-      bits = sign;
-    } else {  // FP32 subnormal: man * 2^-149, normal in FP64
-      const int p = 63 - __clzll((long long)man);
-      bits = sign | ((uint64_t)(p - 149 + 1023) << 52) | ((man << (52 - p)) & 0xFFFFFFFFFFFFFull);
-    }
-  } else if (ef == 0xFF) {
-    bits = sign | (0x7FFull << 52) | (man << 29);
-  } else {
-    bits = sign | ((uint64_t)(ef + 896) << 52) | (man << 29);
-  }
-  return __longlong_as_double((long long)bits);
-}
-
 // ---------------------------------------------------------------------------
-// Numeric kernel. One warp per C block; the C block (or its transpose,
-// whichever needs fewer MMA tiles) is covered by MT x NT tiles of 16 x 8.
-// A "step" is one k-step of one product: 16 (BF16; 8 for a final step with at
-// most 8 left) or 8 (TF32) values of k, with all slice products of every tile.
+// Numeric kernel (below). A warp computes one C block at a time, or its
+// transpose, whichever needs fewer 16x8 MMA tiles. Operands: L (Mp rows along
+// k) and R (Np rows along k), both k-piece-major. Not transposed: L = A_ik (A's
+// left layout), R = B_kj (B's right layout); transposed (C^T = B^T A^T): L =
+// B_kj^T (B's right layout), R = A_ik^T (A's left layout). A k step is 16 (BF16;
+// 8 for a last piece) or 8 (TF32) values of k with all slice products of every
+// tile.
 //
-// Operands: L (M' x s) is read from a left layout (row-major), R (s x N')
-// from a right layout (column-major). Not transposed: L = A_ik (A's left
-// layout), R = B_kj (B's right layout). Transposed (C^T = B^T A^T): L = B_kj^T
-// = B's right layout read as row-major, R = A_ik^T = A's left layout read as
-// column-major.
-//
-// Accumulation: every product is summed in a fresh FP32 accumulator by the
-// tensor cores (at most a few MMAs deep), then added to a running sum kept as
-// an unevaluated pair hi + lo of FP32 numbers (TwoSum, error-free), so the
-// long sum over the products of a C block loses no more than FP32 rounding of
-// each product; hi + lo is formed in FP64 at the end.
+// Accumulation: the products are summed in FP32 by the tensor cores, a few at
+// a time, then added to a running sum kept as an unevaluated pair hi + lo of
+// FP32 numbers (TwoSum, error-free), so the long sum over the products of a C
+// block loses no more than FP32 rounding of each partial sum; hi + lo is
+// formed in FP64 at the end (FP32 -> FP64 is exact).
 // ---------------------------------------------------------------------------
-template <int NSL, int MT, int NT>
-struct Frag {
-  uint32_t a[NSL][MT][4];
-  uint32_t b[NSL][NT][2];
-};
-
-// Fragments of one BF16 step (k values kk..kk+15, or kk..kk+7 when k8). L has
-// Mp rows, R has Np rows, k padded to sp (a multiple of 8), pieces k-major.
-template <int MT, int NT>
-__device__ __forceinline__ void load_bf16(Frag<3, MT, NT> &f, const uint16_t *__restrict__ Lb,
-                                          const uint16_t *__restrict__ Rb, int Mp, int Np, int sp,
-                                          int kk, bool k8, int lplane, int rplane) {
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int k0 = kk + 2 * t, k1 = k0 + 8;
-  // 32-bit word of (row, k even): halfword ((k >> 3) * rows + row) * 8 + (k & 7)
-  const int wl0 = (((k0 >> 3) * Mp) << 2) + t, wl1 = wl0 + (Mp << 2);
-  const int wr0 = (((k0 >> 3) * Np) << 2) + t, wr1 = wr0 + (Np << 2);
-#pragma unroll
-  for (int q = 0; q < 3; q++) {
-    const uint32_t *P = reinterpret_cast<const uint32_t *>(Lb + (int64_t)q * lplane);
-#pragma unroll
-    for (int mt = 0; mt < MT; mt++) {
-      const int r0 = mt * 16 + g, r1 = r0 + 8;
-      f.a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + wl0 + 4 * r0) : 0u;
-      f.a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + wl0 + 4 * r1) : 0u;
-      f.a[q][mt][2] = (!k8 && r0 < Mp && k1 < sp) ? __ldg(P + wl1 + 4 * r0) : 0u;
-      f.a[q][mt][3] = (!k8 && r1 < Mp && k1 < sp) ? __ldg(P + wl1 + 4 * r1) : 0u;
-    }
-    const uint32_t *Q = reinterpret_cast<const uint32_t *>(Rb + (int64_t)q * rplane);
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++) {
-      const int c = nt * 8 + g;
-      f.b[q][nt][0] = (c < Np && k0 < sp) ? __ldg(Q + wr0 + 4 * c) : 0u;
-      f.b[q][nt][1] = (!k8 && c < Np && k1 < sp) ? __ldg(Q + wr1 + 4 * c) : 0u;
-    }
-  }
-}
-
-template <int MT, int NT>
-__device__ __forceinline__ void mma_bf16(float (&acc)[MT][NT][4], const Frag<3, MT, NT> &f,
-                                         bool k8, int Mp, int Np) {
-  // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
-  constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
-  constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
-#pragma unroll
-  for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++) {
-      if (mt * 16 >= Mp || nt * 8 >= Np) continue;
-#pragma unroll
-      for (int pq = 0; pq < 6; pq++) {
-        if (k8)
-          mma_bf16_k8(acc[mt][nt], f.a[PA[pq]][mt][0], f.a[PA[pq]][mt][1], f.b[PB[pq]][nt][0]);
-        else
-          mma_bf16_k16(acc[mt][nt], f.a[PA[pq]][mt], f.b[PB[pq]][nt][0], f.b[PB[pq]][nt][1]);
-      }
-    }
-}
-
-// Fragments of one TF32 step (k values kk..kk+7); k padded to sp (a multiple
-// of 4), pieces k-major: word ((k >> 2) * rows + row) * 4 + (k & 3).
-template <int MT, int NT>
-__device__ __forceinline__ void load_tf32(Frag<2, MT, NT> &f, const uint32_t *__restrict__ Lb,
-                                          const uint32_t *__restrict__ Rb, int Mp, int Np, int sp,
-                                          int kk, int lplane, int rplane) {
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int k0 = kk + t, k1 = k0 + 4;
-  const int wl0 = (((k0 >> 2) * Mp) << 2) + t, wl1 = wl0 + (Mp << 2);
-  const int wr0 = (((k0 >> 2) * Np) << 2) + t, wr1 = wr0 + (Np << 2);
-#pragma unroll
-  for (int q = 0; q < 2; q++) {
-    const uint32_t *P = Lb + (int64_t)q * lplane;
-#pragma unroll
-    for (int mt = 0; mt < MT; mt++) {
-      const int r0 = mt * 16 + g, r1 = r0 + 8;
-      f.a[q][mt][0] = (r0 < Mp && k0 < sp) ? __ldg(P + wl0 + 4 * r0) : 0u;
-      f.a[q][mt][1] = (r1 < Mp && k0 < sp) ? __ldg(P + wl0 + 4 * r1) : 0u;
-      f.a[q][mt][2] = (r0 < Mp && k1 < sp) ? __ldg(P + wl1 + 4 * r0) : 0u;
-      f.a[q][mt][3] = (r1 < Mp && k1 < sp) ? __ldg(P + wl1 + 4 * r1) : 0u;
-    }
-    const uint32_t *Q = Rb + (int64_t)q * rplane;
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++) {
-      const int c = nt * 8 + g;
-      f.b[q][nt][0] = (c < Np && k0 < sp) ? __ldg(Q + wr0 + 4 * c) : 0u;
-      f.b[q][nt][1] = (c < Np && k1 < sp) ? __ldg(Q + wr1 + 4 * c) : 0u;
-    }
-  }
-}
-
-template <int MT, int NT>
-__device__ __forceinline__ void mma_tf32(float (&acc)[MT][NT][4], const Frag<2, MT, NT> &f,
-                                         int Mp, int Np) {
-  // (2,1) (1,2) (1,1)
-  constexpr int PA[3] = {1, 0, 0};
-  constexpr int PB[3] = {0, 1, 0};
-#pragma unroll
-  for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++) {
-      if (mt * 16 >= Mp || nt * 8 >= Np) continue;
-#pragma unroll
-      for (int pq = 0; pq < 3; pq++)
-        mma_tf32_k8(acc[mt][nt], f.a[PA[pq]][mt], f.b[PB[pq]][nt][0], f.b[PB[pq]][nt][1]);
-    }
-}
-
 // hi + lo += x, exactly (Knuth's TwoSum in FP32, no fused operations).
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   const float s = __fadd_rn(hi, x);
@@ -356,147 +222,11 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   lo = __fadd_rn(lo, err);
 }
 
-// One C block by one warp: the MMA problem M' x N' in MT x NT tiles. The
-// (A offset, B offset, k) of up to 32 products are read at once, one per lane;
-// with PREFETCH the next step's fragments are loaded while the current step
-// multiplies (twice the fragment registers). st_nnz: the result's value count
-// (the host copy is written when it fits C.host_cap).
-template <int PREC, int MT, int NT, bool PREFETCH>
-__device__ __forceinline__ void split_cblock(const DevMat &A, const DevMat &B, const DevOut &C,
-                                             const DevMat &Cin, const void *__restrict__ a_left,
-                                             const void *__restrict__ b_right, double alpha,
-                                             double beta, const DevWs &ws, int64_t gb, int m,
-                                             int n, bool tr, int Mp, int Np, int64_t st_nnz) {
-  constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
-  constexpr int NSL = BF ? 3 : 2;
-  constexpr int KSTEP = BF ? 16 : 8;
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  float hi[MT][NT][4], lo[MT][NT][4], acc[MT][NT][4];
-#pragma unroll
-  for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++)
-#pragma unroll
-      for (int x = 0; x < 4; x++) hi[mt][nt][x] = lo[mt][nt][x] = acc[mt][nt][x] = 0.f;
-
-  // operand pointers and planes of product (aoff, boff, s) for this block:
-  // L has Mp rows, R has Np rows, both of the padded row length of k = s
-  auto operands = [&](int64_t aoff, int64_t boff, int s, const void *&L, const void *&R,
-                      int &lplane, int &rplane) {
-    const int sp = BF ? (s + 7) & ~7 : (s + 3) & ~3;
-    const void *Al = BF ? (const void *)(static_cast<const uint16_t *>(a_left) +
-                                         kBf16HalfwordsPerValue * aoff)
-                        : (const void *)(static_cast<const uint32_t *>(a_left) +
-                                         kTf32WordsPerValue * aoff);
-    const void *Br = BF ? (const void *)(static_cast<const uint16_t *>(b_right) +
-                                         kBf16HalfwordsPerValue * boff)
-                        : (const void *)(static_cast<const uint32_t *>(b_right) +
-                                         kTf32WordsPerValue * boff);
-    L = tr ? Br : Al;
-    R = tr ? Al : Br;
-    lplane = Mp * sp;
-    rplane = Np * sp;
-  };
-  auto load = [&](Frag<NSL, MT, NT> &f, const void *L, const void *R, int lplane, int rplane,
-                  int s, int kk) {
-    if constexpr (BF)
-      load_bf16<MT, NT>(f, static_cast<const uint16_t *>(L), static_cast<const uint16_t *>(R), Mp,
-                        Np, (s + 7) & ~7, kk, (s - kk) <= 8, lplane, rplane);
-    else
-      load_tf32<MT, NT>(f, static_cast<const uint32_t *>(L), static_cast<const uint32_t *>(R), Mp,
-                        Np, (s + 3) & ~3, kk, lplane, rplane);
-  };
-
-  const int64_t p0 = ws.prod_ptr[gb], p1 = ws.prod_ptr[gb + 1];
-  for (int64_t pb = p0; pb < p1; pb += 32) {
-    const int nb = (p1 - pb < 32) ? (int)(p1 - pb) : 32;
-    int64_t my_a = 0, my_b = 0;
-    int my_s = 1;
-    if (lane < nb) {
-      const int2 pr = ws.prods[pb + lane];
-      my_a = A.blk_off[pr.x];
-      my_b = B.blk_off[pr.y];
-      my_s = A.col_sizes[A.col_idx[pr.x]];
-    }
-    Frag<NSL, MT, NT> cur, nxt;
-    int q = 0, kk = 0;
-    int s = __shfl_sync(0xffffffffu, my_s, 0);
-    const void *L, *R;
-    int lplane, rplane;
-    operands(__shfl_sync(0xffffffffu, my_a, 0), __shfl_sync(0xffffffffu, my_b, 0), s, L, R,
-             lplane, rplane);
-    load(cur, L, R, lplane, rplane, s, 0);
-    while (q < nb) {
-      // the next step: the next k-step of this product, or the next product
-      int nq = q, nkk = kk + KSTEP;
-      if (nkk >= s) {
-        nq = q + 1;
-        nkk = 0;
-      }
-      const int src = nq < nb ? nq : 0;
-      const int ns = __shfl_sync(0xffffffffu, my_s, src);
-      const int64_t na = __shfl_sync(0xffffffffu, my_a, src);
-      const int64_t nbo = __shfl_sync(0xffffffffu, my_b, src);
-      const void *nL = L, *nR = R;
-      int nlp = lplane, nrp = rplane;
-      if (nq < nb && nq != q) operands(na, nbo, ns, nL, nR, nlp, nrp);
-      if (PREFETCH && nq < nb) load(nxt, nL, nR, nlp, nrp, ns, nkk);
-      if constexpr (BF)
-        mma_bf16<MT, NT>(acc, cur, (s - kk) <= 8, Mp, Np);
-      else
-        mma_tf32<MT, NT>(acc, cur, Mp, Np);
-      if (!PREFETCH && nq < nb) load(nxt, nL, nR, nlp, nrp, ns, nkk);
-      if (nq != q) {  // product done: fold it into the running sum
-#pragma unroll
-        for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-          for (int nt = 0; nt < NT; nt++)
-#pragma unroll
-            for (int x = 0; x < 4; x++) {
-              two_sum_acc(hi[mt][nt][x], lo[mt][nt][x], acc[mt][nt][x]);
-              acc[mt][nt][x] = 0.f;
-            }
-      }
-      cur = nxt;
-      q = nq;
-      kk = nkk;
-      s = ns;
-      L = nL, R = nR, lplane = nlp, rplane = nrp;
-    }
-  }
-  // epilogue: C_ij = beta * C_in_ij + alpha * (hi + lo), formed in FP64
-  const bool plain = (alpha == 1.0 && beta == 0.0);
-  const int cin = ws.c_cin[gb];
-  const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
-  double *out = C.vals + C.blk_off[gb];
-  // the second destination (host memory) when the whole result fits it
-  double *hblk = (C.host_vals && st_nnz <= C.host_cap) ? C.host_vals + C.blk_off[gb] : nullptr;
-#pragma unroll
-  for (int mt = 0; mt < MT; mt++)
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++)
-#pragma unroll
-      for (int x = 0; x < 4; x++) {
-        const int rr = mt * 16 + g + ((x >> 1) << 3);
-        const int cc = nt * 8 + 2 * t + (x & 1);
-        if (rr < Mp && cc < Np) {
-          const int row = tr ? cc : rr, col = tr ? rr : cc;
-          const int64_t e = (int64_t)col * m + row;
-          double v = f32_to_f64_exact(hi[mt][nt][x]) + f32_to_f64_exact(lo[mt][nt][x]);
-          if (!plain) {
-            v = alpha * v;
-            if (cinv) v = fma(beta, cinv[e], v);
-          }
-          out[e] = v;
-          if (hblk) hblk[e] = v;
-        }
-      }
-}
-
 // ---------------------------------------------------------------------------
-// Pipelined kernel for C blocks whose MMA problem fits 16 x 16 (the water and
-// small-block case). Each warp streams its C block's products through a ring
+// Pipelined kernel. Two instances: C blocks whose MMA problem fits 16 x 16
+// (the water and small-block case; 1x2 tiles per warp, 16-row slots), and the
+// others up to 32 x 32 (2x4 tiles per warp, 32-row slots, tiles outside the
+// problem skipped). Each warp streams its C blocks' products through a ring
 // of STAGES shared-memory slots. For every product one lane starts two bulk
 // asynchronous copies (cp.async.bulk: all slice planes of the left operand in
 // one, of the right one in the other) whose completion is counted in bytes on
@@ -576,18 +306,24 @@ __device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, uint32_t add
                : "r"(addr));
 }
 
-// Bytes of one 16-byte k-piece column of a plane per row, and of one operand
-// slot: all planes of at most 16 rows of k up to smax.
+// Bytes of one row of a plane (k up to s, whole 16-byte pieces), and of one
+// operand slot: all planes of at most `rows` rows (16, or 32 in the large-block
+// instance) of k up to smax.
 __host__ __device__ __forceinline__ int pipe_row_bytes(int precision, int s) {
   return precision == BSM_PREC_SPLIT_BF16X3 ? 2 * ((s + 7) & ~7) : 4 * ((s + 3) & ~3);
 }
-__host__ __device__ __forceinline__ int pipe_operand_bytes(int precision, int smax) {
-  return (precision == BSM_PREC_SPLIT_BF16X3 ? 3 : 2) * 16 * pipe_row_bytes(precision, smax);
+__host__ __device__ __forceinline__ int pipe_operand_bytes(int precision, int smax, int rows) {
+  return (precision == BSM_PREC_SPLIT_BF16X3 ? 3 : 2) * rows * pipe_row_bytes(precision, smax);
 }
 // per warp: the slots, the product table, one mbarrier per slot (16-byte multiple)
-__host__ __device__ __forceinline__ int pipe_warp_bytes(int precision, int smax, int stages) {
-  return stages * 2 * pipe_operand_bytes(precision, smax) + kMetaBytes + ((8 * stages + 15) & ~15);
+__host__ __device__ __forceinline__ int pipe_warp_bytes(int precision, int smax, int stages,
+                                                        int rows) {
+  return stages * 2 * pipe_operand_bytes(precision, smax, rows) + kMetaBytes +
+         ((8 * stages + 15) & ~15);
 }
+// The large-block instance (MMA problems up to 32x32, 2x4 tiles of 16x8 per
+// warp, 32-row slots): 2 warps per thread block, 2 stages.
+constexpr int kPipeWarpsBig = 2;
 
 // A C block of the pipelined kernel's stream: gb < 0 marks the end of the work.
 struct PipeBlock {
@@ -598,29 +334,36 @@ struct PipeBlock {
 // Minimum resident blocks per SM the register budget is fitted to: the kernel
 // is bound by instruction issue and latency, so more resident warps pay.
 // (the TF32 slots are larger: 5 blocks of 2 stages fill the shared memory).
-template <int PREC, int STAGES>
+// The large-block instance: 4 blocks of 2 warps (up to 255 registers).
+template <int PREC, int STAGES, bool BIG>
 constexpr int pipe_min_blocks() {
-  return PREC == BSM_PREC_SPLIT_BF16X3 ? (STAGES == 2 ? 6 : STAGES == 3 ? 5 : 4)
-                                       : (STAGES == 2 ? 5 : 4);
+  return BIG ? 4
+             : PREC == BSM_PREC_SPLIT_BF16X3 ? (STAGES == 2 ? 5 : STAGES == 3 ? 5 : 4)
+                                             : (STAGES == 2 ? 5 : 4);
 }
 
-template <int PREC, int STAGES>
-__global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>())
+// sel: 0 every C block, 1 those whose MMA problem fits 16x16, 2 the others.
+template <int PREC, int STAGES, bool BIG>
+__global__ void __launch_bounds__((BIG ? kPipeWarpsBig : kPipeWarps) * 32,
+                                  pipe_min_blocks<PREC, STAGES, BIG>())
     k_numeric_split_pipe(DevMat A, DevMat B, DevOut C, DevMat Cin, const void *__restrict__ a_left,
                          const void *__restrict__ b_right, double alpha, double beta, DevWs ws,
                          const DevStatus *st, const int32_t *__restrict__ items,
-                         const int64_t *__restrict__ seg, int smax, int only_small,
+                         const int64_t *__restrict__ seg, int smax, int sel,
                          unsigned long long *work) {
   if (st->overflow) return;
   constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
   constexpr int NSL = BF ? 3 : 2;
+  constexpr int ROWS = BIG ? 32 : 16;  // slot rows
+  constexpr int MT = BIG ? 2 : 1, NT = BIG ? 4 : 2;  // 16x8 tiles per warp
+  constexpr int NP = NT / 2;  // pairs of 8-column tiles (one x4 fragment load)
   // slice bytes per FP64 value of an operand's offset
   constexpr int64_t kUnit = BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue;
   extern __shared__ __align__(16) unsigned char smem_pipe[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int opb = pipe_operand_bytes(PREC, smax);
-  unsigned char *wbase = smem_pipe + warp * pipe_warp_bytes(PREC, smax, STAGES);
+  const int opb = pipe_operand_bytes(PREC, smax, ROWS);
+  unsigned char *wbase = smem_pipe + warp * pipe_warp_bytes(PREC, smax, STAGES, ROWS);
   // the product table, a ring indexed by stream position: source addresses of
   // the two operands' slices and k
   const unsigned char **meta_a = reinterpret_cast<const unsigned char **>(wbase + STAGES * 2 * opb);
@@ -676,7 +419,8 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
       const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
       const bool tr = tiles_t < tiles_n;
       const int Mp = tr ? n : m, Np = tr ? m : n;
-      if (only_small && !(Mp <= 16 && Np <= 16)) continue;
+      const bool small = Mp <= 16 && Np <= 16;
+      if ((sel == 1 && !small) || (sel == 2 && small)) continue;
       b.gb = gb;
       b.p0 = ws.prod_ptr[gb];
       b.np = (int)(ws.prod_ptr[gb + 1] - b.p0);
@@ -722,11 +466,13 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
     const bool tr = tiles_t < tiles_n;
     const int Mp = tr ? n : m, Np = tr ? m : n;
     const bool two = Np > 8;  // a second 8-column tile
-    float hi[2][4], lo[2][4], acc[2][4];
+    float hi[MT][NT][4], lo[MT][NT][4], acc[MT][NT][4];
 #pragma unroll
-    for (int nt = 0; nt < 2; nt++)
+    for (int mt = 0; mt < MT; mt++)
 #pragma unroll
-      for (int x = 0; x < 4; x++) hi[nt][x] = lo[nt][x] = acc[nt][x] = 0.f;
+      for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+        for (int x = 0; x < 4; x++) hi[mt][nt][x] = lo[mt][nt][x] = acc[mt][nt][x] = 0.f;
 
     for (int q = 0; q < cur.np; q++) {
       const uint32_t u = u_done, slot = u % STAGES;
@@ -758,6 +504,107 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
       const uint32_t adL = sL + 16u * (uint32_t)(pa * Mp + ra);
       const uint32_t adR = sR + 16u * (uint32_t)(pb * Np + rb_);
       const uint32_t adR2 = sR + 16u * (uint32_t)ra;  // "a" order on R (half steps)
+      if constexpr (BIG) {
+        // tile (mt, nt) is live when it holds part of the Mp x Np problem
+        bool live[MT][NT];
+#pragma unroll
+        for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+          for (int nt = 0; nt < NT; nt++) live[mt][nt] = mt * 16 < Mp && nt * 8 < Np;
+        if (BF) {
+          constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
+          constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+          for (int kk = 0; kk < s; kk += 16) {
+            const uint32_t koL = 16u * (uint32_t)((kk >> 3) * Mp), koR = 16u * (uint32_t)((kk >> 3) * Np);
+            if (s - kk <= 8) {  // one k piece left: m16n8k8
+              uint32_t a[3][MT][2], b[3][NP][2];
+#pragma unroll
+              for (int q3 = 0; q3 < 3; q3++) {
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++)
+                  ldsm_x2(a[q3][mt][0], a[q3][mt][1], adL + q3 * lpl + koL + 256u * mt);
+#pragma unroll
+                for (int p2 = 0; p2 < NP; p2++)
+                  ldsm_x2(b[q3][p2][0], b[q3][p2][1], adR2 + q3 * rpl + koR + 256u * p2);
+              }
+#pragma unroll
+              for (int pq = 0; pq < 6; pq++)
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+                  for (int nt = 0; nt < NT; nt++)
+                    if (live[mt][nt])
+                      mma_bf16_k8(acc[mt][nt], a[PA[pq]][mt][0], a[PA[pq]][mt][1],
+                                  b[PB[pq]][nt >> 1][nt & 1]);
+            } else {
+              uint32_t a[3][MT][4], b[3][NP][4];
+#pragma unroll
+              for (int q3 = 0; q3 < 3; q3++) {
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++)
+                  ldsm_x4(a[q3][mt][0], a[q3][mt][1], a[q3][mt][2], a[q3][mt][3],
+                          adL + q3 * lpl + koL + 256u * mt);
+#pragma unroll
+                for (int p2 = 0; p2 < NP; p2++)
+                  ldsm_x4(b[q3][p2][0], b[q3][p2][1], b[q3][p2][2], b[q3][p2][3],
+                          adR + q3 * rpl + koR + 256u * p2);
+              }
+#pragma unroll
+              for (int pq = 0; pq < 6; pq++)
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+                  for (int nt = 0; nt < NT; nt++)
+                    if (live[mt][nt])
+                      mma_bf16_k16(acc[mt][nt], a[PA[pq]][mt], b[PB[pq]][nt >> 1][2 * (nt & 1)],
+                                   b[PB[pq]][nt >> 1][2 * (nt & 1) + 1]);
+            }
+          }
+        } else {
+          constexpr int PA[3] = {1, 0, 0};
+          constexpr int PB[3] = {0, 1, 0};
+          for (int kk = 0; kk < s; kk += 8) {
+            const uint32_t koL = 16u * (uint32_t)((kk >> 2) * Mp), koR = 16u * (uint32_t)((kk >> 2) * Np);
+            uint32_t a[2][MT][4], b[2][NP][4];
+            if (s - kk <= 4) {  // one k piece left: the other half is zero
+#pragma unroll
+              for (int q2 = 0; q2 < 2; q2++) {
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++) {
+                  ldsm_x2(a[q2][mt][0], a[q2][mt][1], adL + q2 * lpl + koL + 256u * mt);
+                  a[q2][mt][2] = a[q2][mt][3] = 0u;
+                }
+#pragma unroll
+                for (int p2 = 0; p2 < NP; p2++) {
+                  ldsm_x2(b[q2][p2][0], b[q2][p2][2], adR2 + q2 * rpl + koR + 256u * p2);
+                  b[q2][p2][1] = b[q2][p2][3] = 0u;
+                }
+              }
+            } else {
+#pragma unroll
+              for (int q2 = 0; q2 < 2; q2++) {
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++)
+                  ldsm_x4(a[q2][mt][0], a[q2][mt][1], a[q2][mt][2], a[q2][mt][3],
+                          adL + q2 * lpl + koL + 256u * mt);
+#pragma unroll
+                for (int p2 = 0; p2 < NP; p2++)
+                  ldsm_x4(b[q2][p2][0], b[q2][p2][1], b[q2][p2][2], b[q2][p2][3],
+                          adR + q2 * rpl + koR + 256u * p2);
+              }
+            }
+#pragma unroll
+            for (int pq = 0; pq < 3; pq++)
+#pragma unroll
+              for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+                for (int nt = 0; nt < NT; nt++)
+                  if (live[mt][nt])
+                    mma_tf32_k8(acc[mt][nt], a[PA[pq]][mt], b[PB[pq]][nt >> 1][2 * (nt & 1)],
+                                b[PB[pq]][nt >> 1][2 * (nt & 1) + 1]);
+          }
+        }
+      } else {
       // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
       // (BF16); (2,1) (1,2) (1,1) (TF32)
       if (BF) {
@@ -775,13 +622,13 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
             if (two) {
 #pragma unroll
               for (int pq = 0; pq < 6; pq++) {
-                mma_bf16_k8(acc[0], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][0]);
-                mma_bf16_k8(acc[1], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][1]);
+                mma_bf16_k8(acc[0][0], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][0]);
+                mma_bf16_k8(acc[0][1], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][1]);
               }
             } else {
 #pragma unroll
               for (int pq = 0; pq < 6; pq++)
-                mma_bf16_k8(acc[0], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][0]);
+                mma_bf16_k8(acc[0][0], a[PA[pq]][0], a[PA[pq]][1], b[PB[pq]][0]);
             }
           } else {
             uint32_t a[3][4], b[3][4];
@@ -793,13 +640,13 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
             if (two) {
 #pragma unroll
               for (int pq = 0; pq < 6; pq++) {
-                mma_bf16_k16(acc[0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
-                mma_bf16_k16(acc[1], a[PA[pq]], b[PB[pq]][2], b[PB[pq]][3]);
+                mma_bf16_k16(acc[0][0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
+                mma_bf16_k16(acc[0][1], a[PA[pq]], b[PB[pq]][2], b[PB[pq]][3]);
               }
             } else {
 #pragma unroll
               for (int pq = 0; pq < 6; pq++)
-                mma_bf16_k16(acc[0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
+                mma_bf16_k16(acc[0][0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
             }
           }
         }
@@ -826,26 +673,29 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
           if (two) {
 #pragma unroll
             for (int pq = 0; pq < 3; pq++) {
-              mma_tf32_k8(acc[0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
-              mma_tf32_k8(acc[1], a[PA[pq]], b[PB[pq]][2], b[PB[pq]][3]);
+              mma_tf32_k8(acc[0][0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
+              mma_tf32_k8(acc[0][1], a[PA[pq]], b[PB[pq]][2], b[PB[pq]][3]);
             }
           } else {
 #pragma unroll
             for (int pq = 0; pq < 3; pq++)
-              mma_tf32_k8(acc[0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
+              mma_tf32_k8(acc[0][0], a[PA[pq]], b[PB[pq]][0], b[PB[pq]][1]);
           }
         }
+      }
       }
       // every kFold products (and after the last): fold the FP32 partial sum
       // into the compensated running sum
       if ((q % kFold) == kFold - 1 || q == cur.np - 1) {
 #pragma unroll
-        for (int nt = 0; nt < 2; nt++)
+        for (int mt = 0; mt < MT; mt++)
 #pragma unroll
-          for (int x = 0; x < 4; x++) {
-            two_sum_acc(hi[nt][x], lo[nt][x], acc[nt][x]);
-            acc[nt][x] = 0.f;
-          }
+          for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+            for (int x = 0; x < 4; x++) {
+              two_sum_acc(hi[mt][nt][x], lo[mt][nt][x], acc[mt][nt][x]);
+              acc[mt][nt][x] = 0.f;
+            }
       }
     }
     if (failed) break;
@@ -856,16 +706,18 @@ __global__ void __launch_bounds__(kPipeWarps * 32, pipe_min_blocks<PREC, STAGES>
     double *out = C.vals + C.blk_off[gb];
     double *hblk = (C.host_vals && st->nnz_c <= C.host_cap) ? C.host_vals + C.blk_off[gb] : nullptr;
 #pragma unroll
-    for (int nt = 0; nt < 2; nt++)
+    for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++)
 #pragma unroll
       for (int x = 0; x < 4; x++) {
-        const int rr = g + ((x >> 1) << 3);
+        const int rr = mt * 16 + g + ((x >> 1) << 3);
         const int cc = nt * 8 + 2 * t + (x & 1);
         if (rr < Mp && cc < Np) {
           const int row = tr ? cc : rr, col = tr ? rr : cc;
           const int64_t e = (int64_t)col * m + row;
           // FP32 -> FP64 is exact; hi + lo rounded once in FP64
-          double v = (double)hi[nt][x] + (double)lo[nt][x];
+          double v = (double)hi[mt][nt][x] + (double)lo[mt][nt][x];
           if (!plain) {
             v = alpha * v;
             if (cinv) v = fma(beta, cinv[e], v);
@@ -915,51 +767,6 @@ cudaError_t launch_wait_selftest(int never_complete, int32_t *flag, cudaStream_t
   return cudaGetLastError();
 }
 
-// One warp per C block (dynamically assigned). SIZES selects the
-// blocks a launch takes: 0 all (every MMA problem fits 16 x 16), 1 those that
-// fit 16 x 16, 2 the others (up to 32 x 32). Small blocks use 1 x 2 tiles with
-// prefetching; large ones 2 x 4 tiles without (register budget).
-template <int PREC, int SIZES>
-__global__ void __launch_bounds__(128) k_numeric_split(DevMat A, DevMat B, DevOut C, DevMat Cin,
-                                                       const void *__restrict__ a_left,
-                                                       const void *__restrict__ b_right,
-                                                       double alpha, double beta, DevWs ws,
-                                                       const DevStatus *st,
-                                                       const int32_t *__restrict__ items,
-                                                       const int64_t *__restrict__ seg,
-                                                       unsigned long long *work) {
-  if (st->overflow) return;
-  const int lane = threadIdx.x & 31;
-  int64_t wb = 0, we = st->nblk_c;
-  if (seg) {
-    wb = seg[0];
-    we = seg[1];
-  }
-  // C blocks come one at a time from the work counter (zero at launch)
-  for (;;) {
-    unsigned long long got = 0;
-    if (lane == 0) got = atomicAdd(work, 1ull);
-    const int64_t w = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
-    if (w >= we) break;
-    const int64_t gb = items ? items[w] : w;
-    const int i = C.blk_row[gb], j = C.col_idx[gb];
-    const int m = C.row_sizes[i], n = C.col_sizes[j];
-    const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
-    const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
-    const bool tr = tiles_t < tiles_n;
-    const int Mp = tr ? n : m, Np = tr ? m : n;
-    const bool small = (Mp <= 16 && Np <= 16);
-    if (SIZES == 2) {
-      if (!small)
-        split_cblock<PREC, 2, 4, false>(A, B, C, Cin, a_left, b_right, alpha, beta, ws, gb, m, n,
-                                        tr, Mp, Np, st->nnz_c);
-    } else if (SIZES == 0 || small) {
-      split_cblock<PREC, 1, 2, true>(A, B, C, Cin, a_left, b_right, alpha, beta, ws, gb, m, n, tr,
-                                     Mp, Np, st->nnz_c);
-    }
-  }
-}
-
 // Ring depth of the pipelined kernel: pipe_stages(smax), or 2, 3, 4 or 6 from
 // the environment variable BSM_SPLIT_STAGES (a tuning override; read once).
 static int pipe_stages_for(int smax) {
@@ -968,22 +775,25 @@ static int pipe_stages_for(int smax) {
     const int x = v ? atoi(v) : 0;
     return (x == 2 || x == 3 || x == 4 || x == 6) ? x : 0;
   }();
-  if (forced && kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, smax, forced) <= 200 * 1024)
+  if (forced &&
+      kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, smax, forced, 16) <= 200 * 1024)
     return forced;
   return pipe_stages(smax);
 }
 
-// [precision: BF16x3, TF32x2][stages: 2, 3, 4, 6]
-static const void *const (&pipe_instances())[2][4] {
-  static const void *const inst[2][4] = {
-      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 3>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 4>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 6>},
-      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 3>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 4>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 6>}};
+// [precision: BF16x3, TF32x2][stages: 2, 3, 4, 6; 4: the large-block instance]
+static const void *const (&pipe_instances())[2][5] {
+  static const void *const inst[2][5] = {
+      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2, false>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 3, false>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 4, false>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 6, false>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2, true>},
+      {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2, false>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 3, false>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 4, false>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 6, false>,
+       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2, true>}};
   return inst;
 }
 
@@ -992,35 +802,31 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
                                  double beta, DevWs ws, const DevStatus *st, const int32_t *items,
                                  const int64_t *seg, int smax, int nsm, unsigned long long *work,
                                  cudaStream_t stream) {
-  if (sizes == 2) {  // blocks beyond 16 x 16: direct fragment loads, 2 x 4 tiles
-    const int grid = nsm * 2;
-    if (precision == BSM_PREC_SPLIT_BF16X3)
-      k_numeric_split<BSM_PREC_SPLIT_BF16X3, 2><<<grid, 128, 0, stream>>>(
-          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, work);
-    else
-      k_numeric_split<BSM_PREC_SPLIT_TF32X2, 2><<<grid, 128, 0, stream>>>(
-          A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, work);
-    return cudaGetLastError();
-  }
-  const int stages = pipe_stages_for(smax);
-  const size_t smem = (size_t)kPipeWarps * pipe_warp_bytes(precision, smax, stages);
   const int pi = precision == BSM_PREC_SPLIT_BF16X3 ? 0 : 1;
-  const int si = stages == 2 ? 0 : stages == 3 ? 1 : stages == 4 ? 2 : 3;
+  const bool big = sizes == 2;  // C blocks beyond 16x16: the large-block instance
+  const int stages = big ? 2 : pipe_stages_for(smax);
+  const int warps = big ? kPipeWarpsBig : kPipeWarps;
+  const size_t smem = (size_t)warps * pipe_warp_bytes(precision, smax, stages, big ? 32 : 16);
+  const int si = big ? 4 : stages == 2 ? 0 : stages == 3 ? 1 : stages == 4 ? 2 : 3;
   const void *fn = pipe_instances()[pi][si];
   int per_sm = 1;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPipeWarps * 32, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
   if (e != cudaSuccess) return e;
   const int grid = nsm * (per_sm > 0 ? per_sm : 1);
-  const int only_small = sizes == 1;
-#define BSM_SPLIT_PIPE(P, S)                                                                \
-  k_numeric_split_pipe<P, S><<<grid, kPipeWarps * 32, smem, stream>>>(                      \
-      A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, only_small, work)
-#define BSM_SPLIT_PIPE_S(P)            \
-  switch (stages) {                    \
-    case 2: BSM_SPLIT_PIPE(P, 2); break; \
-    case 3: BSM_SPLIT_PIPE(P, 3); break; \
-    case 4: BSM_SPLIT_PIPE(P, 4); break; \
-    default: BSM_SPLIT_PIPE(P, 6); break; \
+  const int sel = sizes;  // 0 all, 1 small C blocks only, 2 large ones only
+#define BSM_SPLIT_PIPE(P, S, G)                                                                 \
+  k_numeric_split_pipe<P, S, G><<<grid, warps * 32, smem, stream>>>(                            \
+      A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sel, work)
+#define BSM_SPLIT_PIPE_S(P)                   \
+  if (big) {                                  \
+    BSM_SPLIT_PIPE(P, 2, true);               \
+  } else {                                    \
+    switch (stages) {                         \
+      case 2: BSM_SPLIT_PIPE(P, 2, false); break; \
+      case 3: BSM_SPLIT_PIPE(P, 3, false); break; \
+      case 4: BSM_SPLIT_PIPE(P, 4, false); break; \
+      default: BSM_SPLIT_PIPE(P, 6, false); break; \
+    }                                         \
   }
   if (precision == BSM_PREC_SPLIT_BF16X3) {
     BSM_SPLIT_PIPE_S(BSM_PREC_SPLIT_BF16X3);
@@ -1036,12 +842,13 @@ cudaError_t numeric_split_init() {
   // the largest slot layout of each instance (k up to 32), and the whole
   // shared memory of an SM for the carveout (the rings decide occupancy)
   for (int pi = 0; pi < 2; pi++)
-    for (int si = 0; si < 4; si++) {
+    for (int si = 0; si < 5; si++) {
       const int prec = pi == 0 ? BSM_PREC_SPLIT_BF16X3 : BSM_PREC_SPLIT_TF32X2;
-      const int stages = si == 0 ? 2 : si == 1 ? 3 : si == 2 ? 4 : 6;
+      const int stages = si == 0 || si == 4 ? 2 : si == 1 ? 3 : si == 2 ? 4 : 6;
+      const int bytes = si == 4 ? kPipeWarpsBig * pipe_warp_bytes(prec, 32, stages, 32)
+                                : kPipeWarps * pipe_warp_bytes(prec, 32, stages, 16);
       const void *fn = pipe_instances()[pi][si];
-      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           kPipeWarps * pipe_warp_bytes(prec, 32, stages));
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       if (e != cudaSuccess) return e;
