@@ -332,8 +332,9 @@ struct PipeBlock {
 };
 
 // Minimum resident blocks per SM the register budget is fitted to: the kernel
-// is bound by instruction issue and latency, so more resident warps pay.
-// (the TF32 slots are larger: 5 blocks of 2 stages fill the shared memory).
+// is bound by instruction issue and latency, so more resident warps pay, but
+// not at the price of spills (6 blocks of the 2-stage instance spill; the
+// TF32 slots are larger: 5 blocks of 2 stages fill the shared memory).
 // The large-block instance: 4 blocks of 2 warps (up to 255 registers).
 template <int PREC, int STAGES, bool BIG>
 constexpr int pipe_min_blocks() {
