@@ -237,9 +237,9 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 // read 32 at a time into a per-warp table in shared memory.
 // ---------------------------------------------------------------------------
 // STAGES: deeper rings hide more copy latency, shallower ones leave room for
-// more warps per SM. Measured on water (k of 5 and 13): 2 stages with 24
-// warps per SM beat 3 with 20 and 4 or 6 with 16 or 8 (each warp's chain of
-// dependent fragment loads and MMAs needs many warps to fill the issue slots).
+// more warps per SM. Measured on water (k of 5 and 13): 2 stages beat 3, 4
+// and 6 (6 stages leave 8 warps per SM): each warp's chain of dependent
+// fragment loads and MMAs needs many warps to fill the issue slots.
 inline int pipe_stages(int) { return 2; }
 constexpr int kPipeWarps = 4;
 // Products summed plainly in FP32 before each compensated fold: a partial sum
