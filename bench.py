@@ -47,7 +47,7 @@ PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
 # FP64 numeric kernels (BSM_FP64_*): name -> (number, kernel symbol)
 FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64_t16"),
                 "t32": (2, "k_numeric_fp64_t32"), "pk12": (3, "k_numeric_fp64_pk"),
-                "pk16": (4, "k_numeric_fp64_pk")}
+                "pk16": (4, "k_numeric_fp64_pk"), "g8": (5, "k_numeric_fp64_g8")}
 FP64_BY_NUMBER = {v[0]: k for k, v in FP64_KERNELS.items()}
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/): valid only while

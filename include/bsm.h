@@ -74,7 +74,9 @@ enum {
  *   T32: 32 x 32 tiles, synchronous staging;
  *   PK12, PK16: packed lane slots (output element, k-group) over the products
  *        of a C block concatenated along k, 16 x 16 tiles, 12 or 16 slots per
- *        lane, 2 blocks/SM.
+ *        lane, 2 blocks/SM;
+ *   G8: groups of 8 lanes, a lane per C column (up to 8 rows at a time in
+ *        registers), a C block per group: for tiny blocks with few products.
  * All give the same result up to the order of the FP64 additions. */
 enum {
   BSM_FP64_T16_B2 = 0,
@@ -82,7 +84,8 @@ enum {
   BSM_FP64_T32 = 2,
   BSM_FP64_PK12 = 3,
   BSM_FP64_PK16 = 4,
-  BSM_FP64_NUM_KERNELS = 5
+  BSM_FP64_G8 = 5,
+  BSM_FP64_NUM_KERNELS = 6
 };
 
 /* How the numeric stacks are launched. */
@@ -107,13 +110,17 @@ typedef struct {
   int32_t graph;     /* 1: capture the multiply's launches in a CUDA graph the first
                         time a given set of arguments is met and replay it after */
   int32_t fp64_kernel; /* 0, or 1 + BSM_FP64_* to force that FP64 kernel (ignored by
-                          the split precisions); out of range: BSM_ERR_INVALID_ARG */
+                          the split precisions); out of range: BSM_ERR_INVALID_ARG.
+                          Without it (and without a tuned choice): PK12, or where
+                          C blocks have fewer than 4 products on average, G8 when
+                          C's blocks are at most 8 x 8, else T16_B2 */
   double *host_values; /* NULL, or page-locked host memory (cudaHostAlloc /
                           cudaHostRegister, device-mapped) of host_cap doubles that also
                           receives the result's values, in bsm_mat_get_values order,
-                          written by the device while the multiply runs (the packed FP64
-                          kernel stores each C block there as it completes it; the other
-                          kernels are followed by a device copy). Written only if the
+                          written by the device while the multiply runs (the packed and g8
+                          FP64 kernels and the split-precision kernels store each C block
+                          there as they complete it; the other kernels are followed by a
+                          device copy). Written only if the
                           result has at most host_cap values (bsm_mat_nblocks tells); valid
                           once the result is complete (a getter, bsm_sync or a blocking
                           multiply). Memory that is not device-mapped: BSM_ERR_INVALID_ARG.

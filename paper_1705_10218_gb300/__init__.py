@@ -11,6 +11,7 @@ by every tick of Algorithms 1 and 2. Every step runs in the CUDA kernels of
 marshals arguments (see :mod:`paper_1705_10218_gb300.bsm`).
 """
 from .bsm import (  # noqa: F401
+    BSM_FP64_G8,
     BSM_FP64_NUM_KERNELS,
     BSM_FP64_PK12,
     BSM_FP64_PK16,

@@ -30,7 +30,8 @@ BSM_FP64_T16_B3 = 1
 BSM_FP64_T32 = 2
 BSM_FP64_PK12 = 3
 BSM_FP64_PK16 = 4
-BSM_FP64_NUM_KERNELS = 5
+BSM_FP64_G8 = 5
+BSM_FP64_NUM_KERNELS = 6
 
 
 class BsmError(RuntimeError):

@@ -528,14 +528,16 @@ static bool needs_tuning(bsm_ctx ctx, bsm_mat A, bsm_mat B, const bsm_opts &o) {
 
 static_assert(kFp64T16B2 == BSM_FP64_T16_B2 && kFp64T16B3 == BSM_FP64_T16_B3 &&
                   kFp64T32 == BSM_FP64_T32 && kFp64Pk12 == BSM_FP64_PK12 &&
-                  kFp64Pk16 == BSM_FP64_PK16 && kFp64NumVariants == BSM_FP64_NUM_KERNELS,
+                  kFp64Pk16 == BSM_FP64_PK16 && kFp64G8 == BSM_FP64_G8 &&
+                  kFp64NumVariants == BSM_FP64_NUM_KERNELS,
               "public and internal FP64 kernel numbers differ");
 
 // The default FP64 kernel for a result C: the packed kernel, unless the last
 // multiply into C had fewer than 4 block products per C block (the sizes of
 // the previous result, or of this one once the symbolic totals were read).
 static int fp64_default(bsm_ctx ctx, bsm_mat C) {
-  if (C->hint_blk > 0 && ctx->hint_prod < 4 * C->hint_blk) return kFp64T16B2;
+  if (C->hint_blk > 0 && ctx->hint_prod < 4 * C->hint_blk)  // few products per C block
+    return (C->max_row <= 8 && C->max_col <= 8) ? kFp64G8 : kFp64T16B2;
   return kFp64Pk12;
 }
 
@@ -624,7 +626,8 @@ static int launch_numeric(Launch &L, int variant, const int32_t *items, const in
     L.host_written = L.host_written && fp64_variant_writes_host(variant);
     CK(launch_numeric_fp64(variant, L.dA, L.dB, L.out, L.dC, L.alpha, L.beta, L.ws,
                            ctx->d_status, items, seg,
-                           ctx->nsm * fp64_variant_blocks_per_sm(variant), ctx->d_work, L.s));
+                           ctx->nsm * fp64_variant_blocks_per_sm(variant), ctx->d_work, max_m,
+                           L.s));
   }
   ctx->launches++;
   return BSM_OK;

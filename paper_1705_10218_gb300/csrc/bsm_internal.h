@@ -102,7 +102,8 @@ enum {
   kFp64T32 = 2,
   kFp64Pk12 = 3,
   kFp64Pk16 = 4,
-  kFp64NumVariants = 5
+  kFp64G8 = 5,
+  kFp64NumVariants = 6
 };
 int fp64_variant_blocks_per_sm(int variant);
 // Per-device kernel attributes (call with the device current, outside capture).
@@ -112,10 +113,12 @@ cudaError_t numeric_fp64_init();
 // end) into it (default: all C blocks of the multiply, in row order).
 // work: a device counter that must be zero when the launch starts (the t16 and
 // pk variants hand out C blocks dynamically; may be null for t32).
+// max_m: the largest C block row size of the launch (the g8 variant keeps
+// min(max_m, 8) rows in registers).
 cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMat Cin,
                                 double alpha, double beta, DevWs ws, const DevStatus *st,
                                 const int32_t *items, const int64_t *seg, int grid,
-                                unsigned long long *work, cudaStream_t stream);
+                                unsigned long long *work, int max_m, cudaStream_t stream);
 inline bool fp64_variant_uses_work(int variant) { return variant != kFp64T32; }
 
 // Shape classes (k_classes.cu): class of C block g = row_cls[row] * ncc +
@@ -154,7 +157,7 @@ cudaError_t launch_filter_fill(DevMat M, double eps, DevWs ws, DevOut O, const D
 // and the multiply did not overflow.
 cudaError_t launch_copy_out(DevOut O, const DevStatus *st, int nsm, cudaStream_t stream);
 inline bool fp64_variant_writes_host(int variant) {
-  return variant == kFp64Pk12 || variant == kFp64Pk16;
+  return variant == kFp64Pk12 || variant == kFp64Pk16 || variant == kFp64G8;
 }
 
 cudaError_t launch_add(int stage, DevMat A, DevMat Cin, int use_cin, double alpha, double beta,

@@ -282,6 +282,81 @@ __global__ void __launch_bounds__(kSWarps * 32, MINB)
 }
 
 // ----------------------------------------------------------------------------
+// g8: tiny C blocks with few products (semi-empirical-style matrices: blocks
+// of a few rows, about one product per C block). A group of 8 lanes computes
+// one C block, a lane per column (columns c, c + 8, ...), rows MR at a time in
+// registers (MR = 4, 6 or 8, chosen per launch from the largest C row size);
+// a warp is 4 groups and takes 32 C blocks per work-counter grab. Lanes hold
+// no shared state, so the latency of each C block's chain of dependent loads
+// (its products, their operand offsets, the operands) is hidden by the many
+// independent C blocks in flight, not by staging.
+// ----------------------------------------------------------------------------
+constexpr int kG8Warps = 8;
+constexpr int kG8Grab = 32;  // C blocks per warp and grab (8 per group)
+
+template <int MR>
+__global__ void __launch_bounds__(kG8Warps * 32, 4)
+    k_numeric_fp64_g8(DevMat A, DevMat B, DevOut C, DevMat Cin, double alpha, double beta,
+                      DevWs ws, const DevStatus *st, const int32_t *items, const int64_t *seg,
+                      unsigned long long *work) {
+  if (st->overflow) return;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane >> 3, cl = lane & 7;
+  int64_t wb, we;
+  work_range(st, seg, wb, we);
+  // the second destination (host memory) when the whole result fits it
+  double *hout = (C.host_vals && st->nnz_c <= C.host_cap) ? C.host_vals : nullptr;
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(work, (unsigned long long)kG8Grab);
+    const int64_t w0 = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    if (w0 >= we) break;
+    for (int t = 0; t < kG8Grab / 4; t++) {
+      const int64_t w = w0 + grp + 4 * t;  // groups interleave over the grab
+      if (w >= we) break;
+      const int64_t g = items ? items[w] : w;
+      const int i = C.blk_row[g], j = C.col_idx[g];
+      const int m = C.row_sizes[i], n = C.col_sizes[j];
+      const int64_t p0 = ws.prod_ptr[g], p1 = ws.prod_ptr[g + 1];
+      const int cin = ws.c_cin[g];
+      const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+      const int64_t cbase = C.blk_off[g];
+      for (int c = cl; c < n; c += 8) {
+        for (int r0 = 0; r0 < m; r0 += MR) {
+          double acc[MR];
+#pragma unroll
+          for (int r = 0; r < MR; r++) acc[r] = 0.0;
+          for (int64_t p = p0; p < p1; p++) {  // products in ascending k
+            const int2 pr = ws.prods[p];
+            const double *Ab = A.vals + A.blk_off[pr.x] + r0;
+            const int s = A.col_sizes[A.col_idx[pr.x]];
+            const double *Bb = B.vals + B.blk_off[pr.y] + (int64_t)c * s;
+            for (int kk = 0; kk < s; kk++) {
+              const double b = __ldg(Bb + kk);
+              const double *a = Ab + (int64_t)kk * m;
+#pragma unroll
+              for (int r = 0; r < MR; r++)
+                if (r0 + r < m) acc[r] = fma(__ldg(a + r), b, acc[r]);
+            }
+          }
+          // epilogue: C_ij = beta * C_in_ij + alpha * S_ij
+#pragma unroll
+          for (int r = 0; r < MR; r++) {
+            if (r0 + r < m) {
+              const int64_t loc = (int64_t)c * m + r0 + r;
+              double v = alpha * acc[r];
+              if (cinv) v = fma(beta, cinv[loc], v);
+              C.vals[cbase + loc] = v;
+              if (hout) hout[cbase + loc] = v;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // pk
 // ----------------------------------------------------------------------------
 constexpr int kPkWarps = 8;          // warps per thread block (2 blocks per SM)
@@ -584,8 +659,19 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
 cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMat Cin,
                                 double alpha, double beta, DevWs ws, const DevStatus *st,
                                 const int32_t *items, const int64_t *seg, int grid,
-                                unsigned long long *work, cudaStream_t stream) {
+                                unsigned long long *work, int max_m, cudaStream_t stream) {
   switch (variant) {
+    case kFp64G8:
+      if (max_m <= 4)
+        k_numeric_fp64_g8<4><<<grid, kG8Warps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws,
+                                                                 st, items, seg, work);
+      else if (max_m <= 6)
+        k_numeric_fp64_g8<6><<<grid, kG8Warps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws,
+                                                                 st, items, seg, work);
+      else
+        k_numeric_fp64_g8<8><<<grid, kG8Warps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws,
+                                                                 st, items, seg, work);
+      break;
     case kFp64T16B3:
       k_numeric_fp64_t16<3><<<grid, kSWarps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws, st,
                                                                items, seg, work);
@@ -613,6 +699,7 @@ cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMa
 }
 
 int fp64_variant_blocks_per_sm(int variant) {
+  if (variant == kFp64G8) return 4;
   return (variant == kFp64T16B3 || variant == kFp64T32) ? 3 : 2;
 }
 

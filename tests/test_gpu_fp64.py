@@ -205,7 +205,7 @@ def test_torch_stream(gpu_ctx, oracle_mod):
     ref, v, _ = check(gpu_ctx, oracle_mod, A, A, eps=1e-10, stream=s)
 
 
-FP64_KERNELS = range(5)  # BSM_FP64_T16_B2 .. BSM_FP64_PK16
+FP64_KERNELS = range(6)  # BSM_FP64_T16_B2 .. BSM_FP64_G8
 
 
 @pytest.mark.parametrize("kern", FP64_KERNELS)
@@ -245,7 +245,7 @@ def test_fp64_kernel_out_of_range(gpu_ctx, bsm_lib):
     rs = np.array([2, 3], np.int32)
     A = gpu_ctx.matrix(rs, rs, [0, 1], [0, 1], np.ones(13))
     C = gpu_ctx.empty(rs, rs)
-    for bad in (5, -2):
+    for bad in (6, -2):
         with pytest.raises(bsm_lib.BsmError) as e:
             gpu_ctx.multiply(1.0, A, A, 0.0, C, fp64_kernel=bad)
         assert e.value.name == "INVALID_ARG"
@@ -255,12 +255,15 @@ def test_fp64_kernel_out_of_range(gpu_ctx, bsm_lib):
 
 def test_default_fp64_kernel(bsm_lib, oracle_mod):
     """Without a forced or tuned kernel: the packed kernel where C blocks have
-    many products (water), t16 where they have about one (a sparse random
-    pattern); both results equal the oracle's. Fresh contexts: the product
-    count hint is kept per context."""
+    many products (water), g8 where they have about one and at most 8 rows and
+    columns (a sparse random pattern of 6-wide blocks), t16 where they have
+    about one but are larger (13-wide); all results equal the oracle's. Fresh
+    contexts: the product count hint is kept per context."""
     W = synth.water(16, seed=2)
     S = synth.sparse_random(3000, 6, 5e-4, seed=1)
-    for M, want in ((W, bsm_lib.BSM_FP64_PK12), (S, bsm_lib.BSM_FP64_T16_B2)):
+    S13 = synth.sparse_random(1500, 13, 5e-4, seed=2)
+    for M, want in ((W, bsm_lib.BSM_FP64_PK12), (S, bsm_lib.BSM_FP64_G8),
+                    (S13, bsm_lib.BSM_FP64_T16_B2)):
         ctx = bsm_lib.Context(0)
         try:
             ctx.profile(True)
