@@ -41,6 +41,7 @@ WORKLOADS = {
     # Table 1 analogues scaled to one GPU: Dense (block 32, full) and S-E (block 6, 0.05%)
     "dense4096": dict(kind="dense", n=128, bs=32, seed=3, eps=1e-10),
     "se40000": dict(kind="sparse", n=40000, bs=6, occ=5e-4, seed=5, eps=1e-10),
+    "se10000": dict(kind="sparse", n=10000, bs=6, occ=5e-4, seed=5, eps=1e-10),  # profiling size
 }
 L2_BYTES = 128 << 20  # GB300 L2 (129 MB), rounded down
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
