@@ -284,15 +284,19 @@ __global__ void __launch_bounds__(kSWarps * 32, MINB)
 // ----------------------------------------------------------------------------
 // g8: tiny C blocks with few products (semi-empirical-style matrices: blocks
 // of a few rows, about one product per C block). A group of 8 lanes computes
-// one C block, a lane per column (columns c, c + 8, ...), rows MR at a time in
-// registers (MR = 4, 6 or 8, chosen per launch from the largest C row size);
-// a warp is 4 groups and takes 32 C blocks per work-counter grab. Lanes hold
-// no shared state, so the latency of each C block's chain of dependent loads
-// (its products, their operand offsets, the operands) is hidden by the many
-// independent C blocks in flight, not by staging.
+// one C block at a time, a lane per column, the rows in registers (MR = 4, 6
+// or 8, chosen per launch from the largest C row size). The 4 groups of a warp
+// are independent streams: each takes kG8Grab C blocks at a time from the
+// work counter and walks their products one step per loop iteration, closing
+// a C block (epilogue, next block's metadata) in the iteration that ends it,
+// so a group whose block has more products does not hold the other groups at
+// a loop exit. Lanes hold no shared state: the latency of each C block's chain
+// of dependent loads is hidden by the many independent blocks in flight. A C
+// block of more than MR rows or 8 columns (only when the kernel is forced on
+// larger blocks) is done in column and row chunks by its group.
 // ----------------------------------------------------------------------------
 constexpr int kG8Warps = 8;
-constexpr int kG8Grab = 32;  // C blocks per warp and grab (8 per group)
+constexpr int kG8Grab = 16;  // C blocks per group and grab
 
 template <int MR>
 __global__ void __launch_bounds__(kG8Warps * 32, 4)
@@ -302,56 +306,86 @@ __global__ void __launch_bounds__(kG8Warps * 32, 4)
   if (st->overflow) return;
   const int lane = threadIdx.x & 31;
   const int grp = lane >> 3, cl = lane & 7;
+  const unsigned gmask = 0xFFu << (8 * grp);
   int64_t wb, we;
   work_range(st, seg, wb, we);
   // the second destination (host memory) when the whole result fits it
   double *hout = (C.host_vals && st->nnz_c <= C.host_cap) ? C.host_vals : nullptr;
-  for (;;) {
-    unsigned long long got = 0;
-    if (lane == 0) got = atomicAdd(work, (unsigned long long)kG8Grab);
-    const int64_t w0 = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
-    if (w0 >= we) break;
-    for (int t = 0; t < kG8Grab / 4; t++) {
-      const int64_t w = w0 + grp + 4 * t;  // groups interleave over the grab
-      if (w >= we) break;
-      const int64_t g = items ? items[w] : w;
-      const int i = C.blk_row[g], j = C.col_idx[g];
-      const int m = C.row_sizes[i], n = C.col_sizes[j];
-      const int64_t p0 = ws.prod_ptr[g], p1 = ws.prod_ptr[g + 1];
-      const int cin = ws.c_cin[g];
-      const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
-      const int64_t cbase = C.blk_off[g];
-      for (int c = cl; c < n; c += 8) {
+
+  // the group's current grab [w, wend) and C block (group-uniform state)
+  int64_t w = 0, wend = 0, p = 0, p1 = 0, cbase = 0;
+  int m = 0, n = 0;
+  const double *cinv = nullptr;
+  double acc[MR];
+  auto next_block = [&]() -> bool {
+    if (w >= wend) {
+      unsigned long long got = 0;
+      if (cl == 0) got = atomicAdd(work, (unsigned long long)kG8Grab);
+      w = wb + (int64_t)__shfl_sync(gmask, got, 8 * grp);
+      wend = (w + kG8Grab < we) ? w + kG8Grab : we;
+      if (w >= we) return false;
+    }
+    const int64_t g = items ? items[w] : w;
+    w++;
+    m = C.row_sizes[C.blk_row[g]];
+    n = C.col_sizes[C.col_idx[g]];
+    p = ws.prod_ptr[g];
+    p1 = ws.prod_ptr[g + 1];
+    const int cin = ws.c_cin[g];
+    cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+    cbase = C.blk_off[g];
+#pragma unroll
+    for (int r = 0; r < MR; r++) acc[r] = 0.0;
+    return true;
+  };
+  // rows [r0, r0 + MR) of column c of product q, added to acc
+  auto product = [&](int64_t q, int c, int r0) {
+    const int2 pr = ws.prods[q];
+    const double *Ab = A.vals + A.blk_off[pr.x] + r0;
+    const int s = A.col_sizes[A.col_idx[pr.x]];
+    const double *Bb = B.vals + B.blk_off[pr.y] + (int64_t)c * s;
+    for (int kk = 0; kk < s; kk++) {
+      const double bv = __ldg(Bb + kk);
+      const double *a = Ab + (int64_t)kk * m;
+#pragma unroll
+      for (int r = 0; r < MR; r++)
+        if (r0 + r < m) acc[r] = fma(__ldg(a + r), bv, acc[r]);
+    }
+  };
+  // C_ij = beta * C_in_ij + alpha * S_ij for rows [r0, r0 + MR) of column c
+  auto store = [&](int c, int r0) {
+#pragma unroll
+    for (int r = 0; r < MR; r++) {
+      if (r0 + r < m) {
+        const int64_t loc = (int64_t)c * m + r0 + r;
+        double v = alpha * acc[r];
+        if (cinv) v = fma(beta, cinv[loc], v);
+        C.vals[cbase + loc] = v;
+        if (hout) hout[cbase + loc] = v;
+      }
+    }
+  };
+
+  bool have = next_block();
+  while (have) {
+    if (m > MR || n > 8) {  // column and row chunks, the products once per chunk
+      for (int c = cl; c < n; c += 8)
         for (int r0 = 0; r0 < m; r0 += MR) {
-          double acc[MR];
 #pragma unroll
           for (int r = 0; r < MR; r++) acc[r] = 0.0;
-          for (int64_t p = p0; p < p1; p++) {  // products in ascending k
-            const int2 pr = ws.prods[p];
-            const double *Ab = A.vals + A.blk_off[pr.x] + r0;
-            const int s = A.col_sizes[A.col_idx[pr.x]];
-            const double *Bb = B.vals + B.blk_off[pr.y] + (int64_t)c * s;
-            for (int kk = 0; kk < s; kk++) {
-              const double b = __ldg(Bb + kk);
-              const double *a = Ab + (int64_t)kk * m;
-#pragma unroll
-              for (int r = 0; r < MR; r++)
-                if (r0 + r < m) acc[r] = fma(__ldg(a + r), b, acc[r]);
-            }
-          }
-          // epilogue: C_ij = beta * C_in_ij + alpha * S_ij
-#pragma unroll
-          for (int r = 0; r < MR; r++) {
-            if (r0 + r < m) {
-              const int64_t loc = (int64_t)c * m + r0 + r;
-              double v = alpha * acc[r];
-              if (cinv) v = fma(beta, cinv[loc], v);
-              C.vals[cbase + loc] = v;
-              if (hout) hout[cbase + loc] = v;
-            }
-          }
+          for (int64_t q = p; q < p1; q++) product(q, c, r0);
+          store(c, r0);
         }
-      }
+      have = next_block();
+      continue;
+    }
+    if (p < p1) {  // one product of the block (products in ascending k)
+      if (cl < n) product(p, cl, 0);
+      p++;
+    }
+    if (p >= p1) {  // the block is complete
+      if (cl < n) store(cl, 0);
+      have = next_block();
     }
   }
 }
