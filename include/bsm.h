@@ -75,8 +75,9 @@ enum {
  *   PK12, PK16: packed lane slots (output element, k-group) over the products
  *        of a C block concatenated along k, 16 x 16 tiles, 12 or 16 slots per
  *        lane, 2 blocks/SM;
- *   G8: groups of 8 lanes, a lane per C column (up to 8 rows at a time in
- *        registers), a C block per group: for tiny blocks with few products.
+ *   G8: groups of 4, 6 or 8 lanes, a lane per C column (up to 8 rows at a
+ *        time in registers), a C block per group: for tiny blocks with few
+ *        products.
  * All give the same result up to the order of the FP64 additions. */
 enum {
   BSM_FP64_T16_B2 = 0,

@@ -627,7 +627,7 @@ static int launch_numeric(Launch &L, int variant, const int32_t *items, const in
     CK(launch_numeric_fp64(variant, L.dA, L.dB, L.out, L.dC, L.alpha, L.beta, L.ws,
                            ctx->d_status, items, seg,
                            ctx->nsm * fp64_variant_blocks_per_sm(variant), ctx->d_work, max_m,
-                           L.s));
+                           max_n, L.s));
   }
   ctx->launches++;
   return BSM_OK;

@@ -113,12 +113,13 @@ cudaError_t numeric_fp64_init();
 // end) into it (default: all C blocks of the multiply, in row order).
 // work: a device counter that must be zero when the launch starts (the t16 and
 // pk variants hand out C blocks dynamically; may be null for t32).
-// max_m: the largest C block row size of the launch (the g8 variant keeps
-// min(max_m, 8) rows in registers).
+// max_m, max_n: the largest C block row and column sizes of the launch (the
+// g8 variant sizes its register rows and lane groups by them).
 cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMat Cin,
                                 double alpha, double beta, DevWs ws, const DevStatus *st,
                                 const int32_t *items, const int64_t *seg, int grid,
-                                unsigned long long *work, int max_m, cudaStream_t stream);
+                                unsigned long long *work, int max_m, int max_n,
+                                cudaStream_t stream);
 inline bool fp64_variant_uses_work(int variant) { return variant != kFp64T32; }
 
 // Shape classes (k_classes.cu): class of C block g = row_cls[row] * ncc +

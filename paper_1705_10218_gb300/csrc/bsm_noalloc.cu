@@ -214,7 +214,7 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
     return noalloc_cuda_fail(e);
   // block sizes live on the device only: the 32 x 32 tile variant handles any size
   if ((e = launch_numeric_fp64(kFp64T32, dA, dB, out, none, alpha, 0.0, ws, st, nullptr, nullptr,
-                                nsm * 3, nullptr, 32, s)) != cudaSuccess)
+                                nsm * 3, nullptr, 32, 32, s)) != cudaSuccess)
     return noalloc_cuda_fail(e);
 
   DevStatus h{};

@@ -285,28 +285,31 @@ __global__ void __launch_bounds__(kSWarps * 32, MINB)
 // g8: tiny C blocks with few products (semi-empirical-style matrices: blocks
 // of a few rows, about one product per C block). A group of 8 lanes computes
 // one C block at a time, a lane per column, the rows in registers (MR = 4, 6
-// or 8, chosen per launch from the largest C row size). The 4 groups of a warp
-// are independent streams: each takes kG8Grab C blocks at a time from the
+// or 8 rows and GS = 4, 6 or 8 lanes per group, chosen per launch from the
+// largest C block: 5 groups of 6 lanes fill 30 of a warp's 32 lanes for
+// 6-wide blocks, where groups of 8 would leave a quarter of the lanes without
+// a column). The groups of a warp are independent streams: each takes kG8Grab C blocks at a time from the
 // work counter and walks their products one step per loop iteration, closing
 // a C block (epilogue, next block's metadata) in the iteration that ends it,
 // so a group whose block has more products does not hold the other groups at
 // a loop exit. Lanes hold no shared state: the latency of each C block's chain
 // of dependent loads is hidden by the many independent blocks in flight. A C
-// block of more than MR rows or 8 columns (only when the kernel is forced on
+// block of more than MR rows or GS columns (only when the kernel is forced on
 // larger blocks) is done in column and row chunks by its group.
 // ----------------------------------------------------------------------------
 constexpr int kG8Warps = 8;
 constexpr int kG8Grab = 16;  // C blocks per group and grab
 
-template <int MR>
+template <int MR, int GS>
 __global__ void __launch_bounds__(kG8Warps * 32, 4)
     k_numeric_fp64_g8(DevMat A, DevMat B, DevOut C, DevMat Cin, double alpha, double beta,
                       DevWs ws, const DevStatus *st, const int32_t *items, const int64_t *seg,
                       unsigned long long *work) {
   if (st->overflow) return;
   const int lane = threadIdx.x & 31;
-  const int grp = lane >> 3, cl = lane & 7;
-  const unsigned gmask = 0xFFu << (8 * grp);
+  const int grp = lane / GS, cl = lane - grp * GS;
+  if (grp >= 32 / GS) return;  // lanes past the last whole group
+  const unsigned gmask = ((1u << GS) - 1u) << (GS * grp);
   int64_t wb, we;
   work_range(st, seg, wb, we);
   // the second destination (host memory) when the whole result fits it
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kG8Warps * 32, 4)
     if (w >= wend) {
       unsigned long long got = 0;
       if (cl == 0) got = atomicAdd(work, (unsigned long long)kG8Grab);
-      w = wb + (int64_t)__shfl_sync(gmask, got, 8 * grp);
+      w = wb + (int64_t)__shfl_sync(gmask, got, GS * grp);
       wend = (w + kG8Grab < we) ? w + kG8Grab : we;
       if (w >= we) return false;
     }
@@ -368,8 +371,8 @@ __global__ void __launch_bounds__(kG8Warps * 32, 4)
 
   bool have = next_block();
   while (have) {
-    if (m > MR || n > 8) {  // column and row chunks, the products once per chunk
-      for (int c = cl; c < n; c += 8)
+    if (m > MR || n > GS) {  // column and row chunks, the products once per chunk
+      for (int c = cl; c < n; c += GS)
         for (int r0 = 0; r0 < m; r0 += MR) {
 #pragma unroll
           for (int r = 0; r < MR; r++) acc[r] = 0.0;
@@ -693,19 +696,25 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
 cudaError_t launch_numeric_fp64(int variant, DevMat A, DevMat B, DevOut C, DevMat Cin,
                                 double alpha, double beta, DevWs ws, const DevStatus *st,
                                 const int32_t *items, const int64_t *seg, int grid,
-                                unsigned long long *work, int max_m, cudaStream_t stream) {
+                                unsigned long long *work, int max_m, int max_n,
+                                cudaStream_t stream) {
   switch (variant) {
-    case kFp64G8:
-      if (max_m <= 4)
-        k_numeric_fp64_g8<4><<<grid, kG8Warps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws,
-                                                                 st, items, seg, work);
-      else if (max_m <= 6)
-        k_numeric_fp64_g8<6><<<grid, kG8Warps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws,
-                                                                 st, items, seg, work);
-      else
-        k_numeric_fp64_g8<8><<<grid, kG8Warps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws,
-                                                                 st, items, seg, work);
+    case kFp64G8: {
+      const int mr = max_m <= 4 ? 4 : max_m <= 6 ? 6 : 8;
+      const int gs = max_n <= 4 ? 4 : max_n <= 6 ? 6 : 8;
+#define BSM_G8(R, G)                                                                           \
+  k_numeric_fp64_g8<R, G><<<grid, kG8Warps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws, st, \
+                                                              items, seg, work)
+      if (mr == 4) {
+        if (gs == 4) BSM_G8(4, 4); else if (gs == 6) BSM_G8(4, 6); else BSM_G8(4, 8);
+      } else if (mr == 6) {
+        if (gs == 4) BSM_G8(6, 4); else if (gs == 6) BSM_G8(6, 6); else BSM_G8(6, 8);
+      } else {
+        if (gs == 4) BSM_G8(8, 4); else if (gs == 6) BSM_G8(8, 6); else BSM_G8(8, 8);
+      }
+#undef BSM_G8
       break;
+    }
     case kFp64T16B3:
       k_numeric_fp64_t16<3><<<grid, kSWarps * 32, 0, stream>>>(A, B, C, Cin, alpha, beta, ws, st,
                                                                items, seg, work);
