@@ -352,3 +352,29 @@ def test_assign_reuses_matrix(gpu_ctx, bsm_lib, oracle_mod):
     assert np.array_equal(dA.values(), small.values)
     dA.destroy()
     dC.destroy()
+
+
+@pytest.mark.parametrize("top", [4, 6, 8])
+def test_g8_tiny_blocks(gpu_ctx, oracle_mod, bsm_lib, top):
+    """The g8 kernel at each of its register-row and lane-group sizes (blocks up
+    to 4, 6 and 8 wide pick MR = GS = 4, 6, 8): integer inputs, so the result
+    equals the oracle bit for bit; with C_in, alpha and beta; and the default
+    choice on such a matrix with about one product per C block."""
+    rng = np.random.default_rng(1000 + top)
+    sizes = np.arange(1, top + 1)
+    rs, ks, cs = rng.choice(sizes, 60), rng.choice(sizes, 50), rng.choice(sizes, 40)
+    A = synth.random_blocks(rng, rs, ks, 0.15, kind="int", shuffle=True)
+    B = synth.random_blocks(rng, ks, cs, 0.15, kind="int", shuffle=True)
+    C = synth.random_blocks(rng, rs, cs, 0.2, kind="int", shuffle=True)
+    for launch in (0, 1):
+        check(gpu_ctx, oracle_mod, A, B, 2.0, -1.0, C, eps=0.0, exact=True,
+              fp64_kernel=bsm_lib.BSM_FP64_G8, launch=launch)
+    S = synth.sparse_random(800, top, 2e-3, seed=top)
+    ctx = bsm_lib.Context(0)
+    try:
+        ctx.profile(True)
+        _, _, st = check(ctx, oracle_mod, S, S, eps=1e-10)
+        assert st.kept < 4 * st.c_blocks
+        assert ctx.profile_read().last_fp64_kernel == bsm_lib.BSM_FP64_G8
+    finally:
+        ctx.close()
