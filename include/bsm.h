@@ -189,7 +189,9 @@ int bsm_mat_assign(bsm_mat m, int64_t nblocks, const int32_t *blk_row, const int
  * stats the call only enqueues work; C's result is complete at the next
  * getter, bsm_sync, or use of C as an operand. Inputs must stay alive and
  * unchanged until then. Errors: INVALID_ARG, DIM_MISMATCH, ALIAS, NOMEM,
- * CUDA, UNSUPPORTED. */
+ * CUDA, UNSUPPORTED; TIMEOUT (from the call when blocking, else from the
+ * getter or bsm_sync that completes the result) when a split-precision
+ * kernel's bounded wait for an operand copy gave up: C is then left empty. */
 int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, bsm_mat C,
                  double eps, const bsm_opts *opts, bsm_stats *stats);
 
