@@ -11,11 +11,11 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 
 
-def alone(bsm_lib, A, eps):
+def alone(bsm_lib, A, eps, precision=0):
     with bsm_lib.Context(0) as ctx:
         dA = ctx.from_blocks(A)
         dC = ctx.empty(A.row_sizes, A.col_sizes)
-        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, blocking=True)
+        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, blocking=True, precision=precision)
         r, c = dC.pattern()
         return r, c, dC.values()
 
@@ -124,3 +124,22 @@ def test_submit_from_several_threads(bsm_lib):
             ra, ca, va = alone(bsm_lib, A, eps)
             assert np.array_equal(r, ra) and np.array_equal(c, ca) and np.array_equal(v, va)
         assert srv.info()["bytes_in_use"] == 0
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_split_precision_server(bsm_lib, oracle_mod, prec):
+    """A server in a split precision (BF16x3, TF32x2): every result equals the
+    same multiply run alone in that precision (same kernels: bit for bit) and
+    the oracle within the split bound on water."""
+    eps = 1e-10
+    systems = [synth.water(n, seed=5000 + n) for n in (10, 36, 18, 27)]
+    with bsm_lib.Server(0, slots=2, precision=prec, hbm_budget=2 << 30) as srv:
+        ids = [srv.submit(A, eps) for A in systems]
+        drain(srv, ids)
+        for A, i in zip(systems, ids):
+            r, c, v = srv.take(i)
+            ra, ca, va = alone(bsm_lib, A, eps, precision=prec)
+            assert np.array_equal(r, ra) and np.array_equal(c, ca) and np.array_equal(v, va)
+            ref = oracle_mod.multiply(A, A, eps=eps)
+            assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+            assert H.rel_frobenius(v, ref.values) <= 1e-5
