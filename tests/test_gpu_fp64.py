@@ -306,6 +306,25 @@ def test_host_values(gpu_ctx, oracle_mod, kw):
     dC.destroy()
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_host_values_split_large_blocks(gpu_ctx, oracle_mod, prec):
+    """opts.host_values with the split precisions on blocks up to 32 wide: both
+    pipelined instances (small and large C blocks) store their C blocks into
+    host memory from their epilogues."""
+    A = synth.amorphous(60, seed=9, density=0.05, cutoff=6.0)
+    ref = oracle_mod.multiply(A, A, eps=1e-8)
+    dA = gpu_ctx.from_blocks(A)
+    dC = gpu_ctx.empty(A.row_sizes, A.col_sizes)
+    host = _pinned(ref.nnz + 3, np.nan)
+    gpu_ctx.multiply(1.0, dA, dA, 0.0, dC, 1e-8, host_out=host, precision=prec, blocking=True)
+    v = dC.values()
+    assert len(v) == ref.nnz and np.array_equal(host[:ref.nnz], v)
+    assert np.isnan(host[ref.nnz:]).all()
+    assert H.rel_frobenius(v, ref.values) <= 2e-5
+    dA.destroy()
+    dC.destroy()
+
+
 def test_host_values_small_or_pageable(gpu_ctx, bsm_lib, oracle_mod):
     A = synth.water(8, seed=1)
     ref = oracle_mod.multiply(A, A, eps=1e-10)
