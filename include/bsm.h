@@ -52,7 +52,10 @@ enum {
   BSM_ERR_DUPLICATE_BLOCK = -3, /* the same (row, col) listed twice */
   BSM_ERR_OUT_OF_RANGE = -4,    /* a block index outside the block grid */
   BSM_ERR_ALIAS = -5,           /* C is the same handle as A or B (A == B is fine) */
-  BSM_ERR_NOMEM = -6,           /* device or pinned host allocation failed */
+  BSM_ERR_NOMEM = -6,           /* device or pinned host allocation failed (also past
+                                   the cap BSM_DEVICE_MEMORY_CAP=<bytes> in the environment:
+                                   the device bytes the library may hold per device, read
+                                   once per process, for simulating a full device) */
   BSM_ERR_CUDA = -7,            /* a CUDA runtime error (details: bsm_last_cuda_error) */
   BSM_ERR_TIMEOUT = -8,         /* a bounded device-side wait gave up */
   BSM_ERR_UNSUPPORTED = -9      /* valid request the library does not handle */

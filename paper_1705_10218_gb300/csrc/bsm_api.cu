@@ -63,8 +63,20 @@ struct DevCache {
   std::multimap<size_t, void *> free_blocks;     // class -> block
   std::unordered_map<void *, size_t> block_size;  // every block the cache handed out
   size_t cached = 0;
+  size_t held = 0;  // bytes of all blocks in block_size (handed out or cached)
   int contexts = 0;
 };
+
+// Device bytes the library may hold per device: BSM_DEVICE_MEMORY_CAP=<bytes>
+// (read once; unset or 0: no cap). An allocation beyond it fails as if the
+// device were out of memory (BSM_ERR_NOMEM), which simulates a full device.
+size_t device_memory_cap() {
+  static const size_t cap = [] {
+    const char *v = getenv("BSM_DEVICE_MEMORY_CAP");
+    return v ? (size_t)strtoull(v, nullptr, 10) : (size_t)0;
+  }();
+  return cap;
+}
 DevCache g_cache[kCacheDevices];
 
 size_t size_class(size_t b) {
@@ -87,6 +99,7 @@ void cache_flush_locked(DevCache &c) {
     cudaFree(kv.second);
   }
   c.free_blocks.clear();
+  c.held -= c.cached;
   c.cached = 0;
 }
 
@@ -103,6 +116,9 @@ cudaError_t cache_alloc(void **p, size_t bytes) {
     c->cached -= cls;
     return cudaSuccess;
   }
+  const size_t cap = device_memory_cap();
+  if (cap && c->held + cls > cap && c->cached > 0) cache_flush_locked(*c);
+  if (cap && c->held + cls > cap) return cudaErrorMemoryAllocation;  // simulated full device
   cudaError_t e = cudaMalloc(p, cls);
   if (e == cudaErrorMemoryAllocation && c->cached > 0) {  // give the cache back, retry
     cudaGetLastError();
@@ -114,6 +130,7 @@ cudaError_t cache_alloc(void **p, size_t bytes) {
     return e;
   }
   c->block_size[*p] = cls;
+  c->held += cls;
   return cudaSuccess;
 }
 
@@ -136,6 +153,7 @@ void cache_free(void *p) {
     c->cached += cls;
   } else {
     c->block_size.erase(it);
+    c->held -= cls;
     cudaFree(p);
   }
 }
@@ -526,10 +544,10 @@ static bool needs_tuning(bsm_ctx ctx, bsm_mat A, bsm_mat B, const bsm_opts &o) {
   return false;
 }
 
-static_assert(kFp64T16B2 == BSM_FP64_T16_B2 && kFp64T16B3 == BSM_FP64_T16_B3 &&
-                  kFp64T32 == BSM_FP64_T32 && kFp64Pk12 == BSM_FP64_PK12 &&
-                  kFp64Pk16 == BSM_FP64_PK16 && kFp64G8 == BSM_FP64_G8 &&
-                  kFp64NumVariants == BSM_FP64_NUM_KERNELS,
+static_assert((int)kFp64T16B2 == (int)BSM_FP64_T16_B2 && (int)kFp64T16B3 == (int)BSM_FP64_T16_B3 &&
+                  (int)kFp64T32 == (int)BSM_FP64_T32 && (int)kFp64Pk12 == (int)BSM_FP64_PK12 &&
+                  (int)kFp64Pk16 == (int)BSM_FP64_PK16 && (int)kFp64G8 == (int)BSM_FP64_G8 &&
+                  (int)kFp64NumVariants == (int)BSM_FP64_NUM_KERNELS,
               "public and internal FP64 kernel numbers differ");
 
 // The default FP64 kernel for a result C: the packed kernel, unless the last
