@@ -557,7 +557,7 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="tune the FP64 kernel variants first")
     ap.add_argument("--fp64-kernel", default=None, choices=sorted(FP64_KERNELS),
                     help="force one FP64 numeric kernel (default: the library's choice)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true", help="the request-loop benchmark instead")
     ap.add_argument("--next", action="store_true",

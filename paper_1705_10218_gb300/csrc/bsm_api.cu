@@ -22,6 +22,7 @@
 #include <new>
 #include <numeric>
 #include <unordered_map>
+#include <thread>
 #include <vector>
 
 #include "bsm_internal.h"
@@ -31,6 +32,9 @@ using namespace bsm;
 namespace {
 
 thread_local char g_cuda_err[256] = "";
+
+// Host threads for the checks and offsets of long block lists.
+constexpr int kHostThreads = 8;
 
 int cuda_fail(cudaError_t e, const char *where) {
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
@@ -1092,16 +1096,63 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
   int32_t *h_col = reinterpret_cast<int32_t *>(ctx->h_stage + b_ptr);
   int32_t *h_row = reinterpret_cast<int32_t *>(ctx->h_stage + b_ptr + b_col);
   int64_t *h_off = reinterpret_cast<int64_t *>(ctx->h_stage + b_ptr + 2 * b_col);
-  // one pass: range check, sortedness, offsets of the blocks in list order
+  // range check, sortedness and the offsets of the blocks in list order, on
+  // several host threads for long lists (the values' copy waits for nnz)
+  const int nth = nblocks >= (1 << 17) ? kHostThreads : 1;
+  std::vector<int64_t> part(nth + 1, 0);
+  std::vector<char> bad(nth, 0), unsorted(nth, 0);
+  auto chunk = [&](int t, int64_t &b0, int64_t &b1) {
+    b0 = nblocks * t / nth;
+    b1 = nblocks * (t + 1) / nth;
+  };
+  auto check = [&](int t) {  // range, order and the chunk's value count
+    int64_t b0, b1, sum = 0;
+    chunk(t, b0, b1);
+    for (int64_t b = b0; b < b1; b++) {
+      const int32_t i = blk_row[b], j = blk_col[b];
+      if (i < 0 || i >= nbrows || j < 0 || j >= nbcols) {
+        bad[t] = 1;
+        return;
+      }
+      sum += (int64_t)row_sizes[i] * col_sizes[j];
+      if (b > 0 && (blk_row[b - 1] > i || (blk_row[b - 1] == i && blk_col[b - 1] >= j)))
+        unsorted[t] = 1;
+    }
+    part[t + 1] = sum;
+  };
+  auto offsets = [&](int t) {
+    int64_t b0, b1;
+    chunk(t, b0, b1);
+    int64_t o = part[t];
+    for (int64_t b = b0; b < b1; b++) {
+      h_off[b] = o;
+      o += (int64_t)row_sizes[blk_row[b]] * col_sizes[blk_col[b]];
+    }
+  };
+  auto run = [&](auto &&fn) {
+    if (nth == 1) {
+      fn(0);
+      return;
+    }
+    std::vector<std::thread> th;
+    int t = 1;
+    try {
+      for (; t < nth; t++) th.emplace_back(fn, t);
+    } catch (...) {  // no thread could be started: the rest inline
+    }
+    for (int u = t; u < nth; u++) fn(u);
+    fn(0);
+    for (auto &x : th) x.join();
+  };
+  run(check);
   bool sorted = true;
-  h_off[0] = 0;
-  for (int64_t b = 0; b < nblocks; b++) {
-    const int32_t i = blk_row[b], j = blk_col[b];
-    if (i < 0 || i >= nbrows || j < 0 || j >= nbcols) return BSM_ERR_OUT_OF_RANGE;
-    h_off[b + 1] = h_off[b] + (int64_t)row_sizes[i] * col_sizes[j];
-    if (b > 0 && (blk_row[b - 1] > i || (blk_row[b - 1] == i && blk_col[b - 1] >= j)))
-      sorted = false;
+  for (int t = 0; t < nth; t++) {
+    if (bad[t]) return BSM_ERR_OUT_OF_RANGE;
+    sorted = sorted && !unsorted[t];
+    part[t + 1] += part[t];
   }
+  run(offsets);
+  h_off[nblocks] = part[nth];
   const int64_t nnz = h_off[nblocks];
   std::vector<int64_t> order, list_off;
   if (!sorted) {
