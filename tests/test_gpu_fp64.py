@@ -397,3 +397,35 @@ def test_g8_tiny_blocks(gpu_ctx, oracle_mod, bsm_lib, top):
         assert ctx.profile_read().last_fp64_kernel == bsm_lib.BSM_FP64_G8
     finally:
         ctx.close()
+
+
+def test_long_block_lists(gpu_ctx, bsm_lib):
+    """Block lists long enough for the threaded host checks (>= 2^17 blocks):
+    a shuffled list gives the same matrix as the sorted one; an index out of
+    range in the last chunk is reported and leaves the handle unchanged."""
+    n = 600
+    rng = np.random.default_rng(12)
+    rs = rng.choice([1, 2, 3], n).astype(np.int32)
+    mask = rng.random((n, n)) < 0.45
+    r, c = np.nonzero(mask)
+    r, c = r.astype(np.int32), c.astype(np.int32)
+    assert len(r) >= (1 << 17)
+    sizes = rs[r].astype(np.int64) * rs[c]
+    vals = rng.integers(-4, 5, int(sizes.sum())).astype(np.float64)
+    M = gpu_ctx.matrix(rs, rs, r, c, vals)
+    r0, c0 = M.pattern()
+    v0 = M.values()
+    p = rng.permutation(len(r))
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    pv = np.concatenate([vals[off[b]:off[b + 1]] for b in p])
+    M.assign(r[p], c[p], pv)
+    r1, c1 = M.pattern()
+    assert np.array_equal(r0, r1) and np.array_equal(c0, c1) and np.array_equal(v0, M.values())
+    bad = r.copy()
+    bad[-1] = n  # out of range, in the last chunk
+    with pytest.raises(bsm_lib.BsmError) as e:
+        M.assign(bad, c, vals)
+    assert e.value.name == "OUT_OF_RANGE"
+    r2, c2 = M.pattern()
+    assert np.array_equal(r0, r2) and np.array_equal(c0, c2) and np.array_equal(v0, M.values())
+    M.destroy()
