@@ -250,31 +250,33 @@ cudaError_t launch_symbolic_count(DevMat A, DevMat B, DevMat Cin, int use_cin, d
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_symbolic_scan(int32_t nbr, DevWs ws, DevOut C,
                                                         DevStatus *st) {
-  const int T = blockDim.x;
-  const int per = (nbr + T - 1) / T;
-  const int beg = min(nbr, (int)threadIdx.x * per), end = min(nbr, beg + per);
-  int64_t sb = 0, sp = 0, sn = 0, sc = 0, sf = 0;
-  for (int r = beg; r < end; r++) {
-    sb += ws.row_cblk[r];
-    sp += ws.row_prod[r];
-    sn += ws.row_nnz[r];
-    sc += ws.row_cand[r];
-    sf += ws.row_flops[r];
+  // rows in tiles of blockDim.x, a row per thread (coalesced loads), the
+  // running totals carried from tile to tile
+  int64_t tb = 0, tp = 0, tn = 0, sc = 0, sf = 0;
+  for (int base = 0; base < nbr; base += blockDim.x) {
+    const int r = base + (int)threadIdx.x;
+    const bool in = r < nbr;
+    const int64_t b = in ? ws.row_cblk[r] : 0, p = in ? ws.row_prod[r] : 0;
+    const int64_t n = in ? ws.row_nnz[r] : 0;
+    if (in) {
+      sc += ws.row_cand[r];
+      sf += ws.row_flops[r];
+    }
+    int64_t sb, sp, sn;
+    const int64_t eb = block_exclusive_scan(b, &sb);
+    const int64_t ep = block_exclusive_scan(p, &sp);
+    const int64_t en = block_exclusive_scan(n, &sn);
+    if (in) {
+      C.row_ptr[r] = (int32_t)(tb + eb);
+      ws.prod_off[r] = tp + ep;
+      ws.nnz_off[r] = tn + en;
+    }
+    tb += sb;
+    tp += sp;
+    tn += sn;
   }
-  int64_t tb, tp, tn;
-  int64_t ob = block_exclusive_scan(sb, &tb);
-  int64_t op = block_exclusive_scan(sp, &tp);
-  int64_t on = block_exclusive_scan(sn, &tn);
   const int64_t tc = block_sum(sc);
   const int64_t tf = block_sum(sf);
-  for (int r = beg; r < end; r++) {
-    C.row_ptr[r] = (int32_t)ob;
-    ws.prod_off[r] = op;
-    ws.nnz_off[r] = on;
-    ob += ws.row_cblk[r];
-    op += ws.row_prod[r];
-    on += ws.row_nnz[r];
-  }
   if (threadIdx.x == 0) {
     C.row_ptr[nbr] = (int32_t)tb;
     ws.prod_off[nbr] = tp;
