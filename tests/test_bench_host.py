@@ -1,0 +1,50 @@
+"""Host-side logic of the benchmark (CPU): the DRAM traffic of the roofline is
+reported only for the captured kernel variant and workload and only while the
+kernel's source section still hashes to the captured one; the filter-active
+eps comes from the norm products' percentile."""
+import importlib
+import os
+import shutil
+
+import numpy as np
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    import sys
+
+    sys.path.insert(0, ROOT)
+    return importlib.import_module("bench")
+
+
+def test_traffic_reported_only_for_the_captured_source(tmp_path, monkeypatch):
+    bench = _bench()
+    src = "paper_1705_10218_gb300/csrc/k_numeric_fp64.cu"
+    (tmp_path / os.path.dirname(src)).mkdir(parents=True)
+    shutil.copy(os.path.join(ROOT, src), tmp_path / src)
+    entry = dict(bench.MEASURED_TRAFFIC[("pk12", "water2048")])
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    entry["sha256"] = bench.kernel_source_sha(entry["source"], entry["section"])
+    assert entry["sha256"] is not None
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("pk12", "water2048"), entry)
+    assert bench.measured_traffic("pk12", "water2048") == entry["bytes"]
+    assert bench.measured_traffic("pk16", "water2048") is None
+    assert bench.measured_traffic("pk12", "amorphous4096") is None
+    # the kernel changes: the captured counters no longer describe it
+    text = (tmp_path / src).read_text()
+    a = text.index(entry["section"][0])
+    (tmp_path / src).write_text(text[:a + len(entry["section"][0])] + "// edited\n" +
+                                text[a + len(entry["section"][0]):])
+    assert bench.measured_traffic("pk12", "water2048") is None
+
+
+def test_eps_percentile_of_norm_products():
+    bench = _bench()
+    A = synth.water(8, seed=2)
+    eps = bench.norm_product_percentile(A, 30)
+    assert eps > 0 and np.isfinite(eps)
+    # a higher percentile gives a larger threshold
+    assert bench.norm_product_percentile(A, 60) > eps
