@@ -35,7 +35,7 @@ def _worker(rank, world, port, out):
 def test_replica_aggregate_two_ranks():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a multi-threaded process
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     # every rank sees the same job figures: the slowest rank's time, all FLOPs
