@@ -102,13 +102,6 @@ def _load():
         ]
         lib.bsmo_free_result.restype = None
         lib.bsmo_free_result.argtypes = [ctypes.POINTER(_Res)]
-        lib.bsmo_blocks.restype = ctypes.c_int
-        lib.bsmo_blocks.argtypes = [
-            ctypes.POINTER(_Mat), ctypes.POINTER(_Mat), ctypes.POINTER(_Mat),
-            ctypes.c_double, ctypes.c_double, ctypes.c_double,
-            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-            ctypes.c_void_p, ctypes.c_void_p,
-        ]
         lib.bsmo_norms.restype = ctypes.c_int
         lib.bsmo_norms.argtypes = [ctypes.POINTER(_Mat), ctypes.c_void_p]
         lib.bsmo_post_filter.restype = ctypes.c_int
@@ -205,36 +198,6 @@ def multiply(A, B, alpha: float = 1.0, beta: float = 0.0, C=None, eps: float = 0
                       int(res.dropped), float(res.flops))
     finally:
         lib.bsmo_free_result(ctypes.byref(res))
-
-
-def blocks(A, B, pairs, alpha: float = 1.0, beta: float = 0.0, C=None, eps: float = 0.0):
-    """Selected C blocks by the definition. ``pairs`` is an (n, 2) array of
-    (block row, block col). Returns (present[n] bool, list of blocks as
-    column-major 1-D arrays)."""
-    lib = _load()
-    pairs = np.asarray(pairs, dtype=np.int32).reshape(-1, 2)
-    ha, hb = _Held(A), _Held(B)
-    hc = _Held(C) if C is not None else None
-    rs = np.asarray(A.row_sizes, dtype=np.int64)
-    cs = np.asarray(B.col_sizes, dtype=np.int64)
-    req_r = np.ascontiguousarray(pairs[:, 0])
-    req_c = np.ascontiguousarray(pairs[:, 1])
-    if len(pairs) and (req_r.min() < 0 or req_r.max() >= len(rs) or req_c.min() < 0 or req_c.max() >= len(cs)):
-        raise OracleError(-4)
-    lens = rs[req_r] * cs[req_c] if len(pairs) else np.zeros(0, np.int64)
-    offs = np.zeros(len(pairs), dtype=np.int64)
-    if len(pairs):
-        offs[1:] = np.cumsum(lens)[:-1]
-    out = np.zeros(int(lens.sum()) + 1, dtype=np.float64)
-    present = np.zeros(len(pairs), dtype=np.int32)
-    rc = lib.bsmo_blocks(
-        ctypes.byref(ha.s), ctypes.byref(hb.s), ctypes.byref(hc.s) if hc else None,
-        float(alpha), float(beta), float(eps), len(pairs), _ptr(req_r), _ptr(req_c),
-        _ptr(offs), _ptr(out), _ptr(present),
-    )
-    if rc:
-        raise OracleError(rc)
-    return present.astype(bool), [out[o:o + n].copy() for o, n in zip(offs, lens)]
 
 
 def _result(lib, res, pattern_only=False) -> Result:

@@ -488,79 +488,6 @@ void bsmo_free_result(bsmo_result *res) {
   memset(res, 0, sizeof(*res));
 }
 
-/*
- * Single C blocks by the same definition, for checks at sizes where the full
- * oracle is too slow: for each requested (i,j), walk A's row i in ascending k,
- * look B_kj up, filter, and accumulate. present[t] tells whether (i,j) is in
- * the result pattern; out receives the block (column-major) at offsets
- * out_off[t] chosen by the caller.
- */
-int bsmo_blocks(const bsmo_matrix *A, const bsmo_matrix *B, const bsmo_matrix *Cin,
-                double alpha, double beta, double eps, int64_t nreq, const int32_t *req_row,
-                const int32_t *req_col, const int64_t *out_off, double *out, int32_t *present) {
-  if (!A || !B || nreq < 0 || (nreq > 0 && (!req_row || !req_col || !out_off || !out || !present)))
-    return BSMO_ERR_INVALID_ARG;
-  int err;
-  rowview a, b, cin;
-  memset(&cin, 0, sizeof(cin));
-  if ((err = rowview_build(A, 1, &a)) != BSMO_OK) return err;
-  if ((err = rowview_build(B, 1, &b)) != BSMO_OK) {
-    rowview_free(&a);
-    return err;
-  }
-  const int use_cin = (Cin != NULL) && (beta != 0.0);
-  if (use_cin && (err = rowview_build(Cin, 0, &cin)) != BSMO_OK) {
-    rowview_free(&a);
-    rowview_free(&b);
-    return err;
-  }
-  if ((err = check_dims(A, B, use_cin ? Cin : NULL)) != BSMO_OK) goto done;
-  for (int64_t t = 0; t < nreq; t++) {
-    int32_t i = req_row[t], j = req_col[t];
-    if (i < 0 || i >= A->nbr || j < 0 || j >= B->nbc) {
-      err = BSMO_ERR_OUT_OF_RANGE;
-      goto done;
-    }
-    const int32_t m = A->row_sizes[i], n = B->col_sizes[j];
-    const int64_t len = (int64_t)m * n;
-    double *S = (double *)calloc((size_t)len + 1, sizeof(double));
-    if (!S) {
-      err = BSMO_ERR_NOMEM;
-      goto done;
-    }
-    int any = 0;
-    for (int64_t p = a.row_start[i]; p < a.row_start[i + 1]; p++) {
-      int64_t ab = a.order[p];
-      int32_t k = A->blk_col[ab];
-      int64_t bb = rowview_find(&b, k, j);
-      if (bb < 0) continue;
-      if (!keep_product(a.norm[ab], b.norm[bb], eps)) continue;
-      any = 1;
-      int32_t s = A->col_sizes[k];
-      const double *Ab = A->values + a.off[ab];
-      const double *Bb = B->values + b.off[bb];
-      for (int32_t c = 0; c < n; c++)
-        for (int32_t r = 0; r < m; r++)
-          for (int32_t l = 0; l < s; l++) {
-            double prod = Ab[r + (int64_t)l * m] * Bb[l + (int64_t)c * s];
-            S[r + (int64_t)c * m] = S[r + (int64_t)c * m] + prod;
-          }
-    }
-    int64_t src = use_cin ? rowview_find(&cin, i, j) : -1;
-    present[t] = (any || src >= 0) ? 1 : 0;
-    for (int64_t e = 0; e < len; e++) {
-      double base = (src >= 0) ? beta * Cin->values[cin.off[src] + e] : 0.0;
-      out[out_off[t] + e] = base + alpha * S[e];
-    }
-    free(S);
-  }
-done:
-  rowview_free(&a);
-  rowview_free(&b);
-  rowview_free(&cin);
-  return err;
-}
-
 /* The canonical norms of every block of a matrix, in list order. */
 int bsmo_norms(const bsmo_matrix *M, double *out) {
   if (!M || !out) return BSMO_ERR_INVALID_ARG;

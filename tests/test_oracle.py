@@ -282,19 +282,6 @@ def test_rows_and_threads_do_not_change_results(oracle_mod):
     assert np.array_equal(mt.values, full.values) and mt.flops == full.flops
 
 
-def test_single_blocks_match_full(oracle_mod):
-    A = synth.water(8, seed=3)
-    full = oracle_mod.multiply(A, A, eps=1e-10)
-    Rm = H.result_matrix(full, A.row_sizes, A.col_sizes)
-    rng = np.random.default_rng(0)
-    pick = rng.choice(len(full.blk_row), 40, replace=False)
-    pairs = np.stack([full.blk_row[pick], full.blk_col[pick]], 1)
-    pres, blks = oracle_mod.blocks(A, A, pairs, eps=1e-10)
-    assert pres.all()
-    for p, blk in zip(pick, blks):
-        assert np.array_equal(blk, H.block_of(Rm, p).T.reshape(-1))
-
-
 @pytest.mark.parametrize("bad", ["dup", "range", "zero_size", "dims"])
 def test_errors(oracle_mod, bad):
     rs = np.array([2, 3], np.int32)
