@@ -31,7 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "filtered GFLOP/s per SpGEMM vs roofline; multiplies/s + p99 latency, rel err≤1e-12"
-FP64_PEAK_GFLOPS = 1250.0  # nominal FP64 (FMA) rate of one GB300
+# FP64 FMA issue rate of one SM of the GB300 per clock (2 DFMA = 4 FLOP): the
+# FP64 peak is derived as SMs x 4 FLOP x the SM clock sampled under load.
+FP64_FLOP_PER_SM_CLK = 4
 WORKLOADS = {
     "water2048": dict(kind="water", n=2048, seed=1, eps=1e-10),
     "water64": dict(kind="water", n=64, seed=0, eps=1e-10),
@@ -96,6 +98,20 @@ def measured_peak(key, fallback):
             return float(json.load(f)[key]), f"measured ({key}, MEASURED_PEAKS.json)"
     except (OSError, KeyError, ValueError):
         return fallback, "fallback"
+
+
+def fp64_peak_gflops(n_sm, clocks):
+    """FP64 FMA peak derived from the device: SMs x 2 DFMA (4 FLOP) per clock x
+    the median SM clock sampled during the timed region (the maximum clock when
+    no sample was taken). Returns (GFLOP/s, how it was derived)."""
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    src = "sampled median SM clock under load"
+    if not mhz:
+        mhz = measured_peak("sm_max_mhz", 2070.0)[0]
+        src = "maximum SM clock (no clock samples)"
+    peak = n_sm * FP64_FLOP_PER_SM_CLK * float(mhz) / 1e3
+    return peak, (f"derived: {n_sm} SMs x {FP64_FLOP_PER_SM_CLK} FLOP/clk (2 DFMA) x {float(mhz):.0f} MHz "
+                  f"({src})")
 
 
 def make_workload(name):
@@ -666,12 +682,14 @@ def main():
             "symbolic_gcandidates_per_s": round(st.candidates / (phase["symbolic"] / 1e3) / 1e9, 2)}
     if args.precision == "fp64":
         achieved = flops / (num_ms / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+        fp64_peak, fp64_src = fp64_peak_gflops(torch.cuda.get_device_properties(local).multi_processor_count,
+                                               clocks)
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(fp64_peak, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / fp64_peak, 4),
                 "traffic": (measured_traffic(FP64_BY_NUMBER[prof.last_fp64_kernel], args.workload)
                             if prof.multiplies > 0 and args.eps_percentile is None else None),
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + write.sum)",
-                "kernel": kname, "peak_source": "nominal FP64 FMA rate of the GB300 (1.25 TFLOP/s)",
+                "kernel": kname, "peak_source": fp64_src,
                 "algorithmic": "2*m*n*k over kept products per launch", "phase_ms": phase,
                 "phase_rates": phase_rates}
     else:

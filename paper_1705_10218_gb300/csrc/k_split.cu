@@ -30,7 +30,6 @@
 //   BF16: 3 planes of rows * ceil8(k) halfwords at halfword 24*blk_off[b];
 //   TF32: 2 planes of rows * ceil4(k) words at word 8*blk_off[b].
 #include <cstdint>
-#include <cstdlib>
 
 #include "bsm_internal.h"
 
@@ -236,11 +235,11 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 // to the k-piece-major planes. The (A offset, B offset, k) of the products are
 // read 32 at a time into a per-warp table in shared memory.
 // ---------------------------------------------------------------------------
-// STAGES: deeper rings hide more copy latency, shallower ones leave room for
-// more warps per SM. Measured on water (k of 5 and 13): 2 stages beat 3, 4
+// Ring depth: deeper rings hide more copy latency, shallower ones leave room
+// for more warps per SM. Measured on water (k of 5 and 13): 2 stages beat 3, 4
 // and 6 (6 stages leave 8 warps per SM): each warp's chain of dependent
 // fragment loads and MMAs needs many warps to fill the issue slots.
-inline int pipe_stages(int) { return 2; }
+constexpr int kPipeStages = 2;
 constexpr int kPipeWarps = 4;
 // Products summed plainly in FP32 before each compensated fold: a partial sum
 // of kFold products carries kFold times the rounding of one, still far below
@@ -768,32 +767,12 @@ cudaError_t launch_wait_selftest(int never_complete, int32_t *flag, cudaStream_t
   return cudaGetLastError();
 }
 
-// Ring depth of the pipelined kernel: pipe_stages(smax), or 2, 3, 4 or 6 from
-// the environment variable BSM_SPLIT_STAGES (a tuning override; read once).
-static int pipe_stages_for(int smax) {
-  static const int forced = [] {
-    const char *v = getenv("BSM_SPLIT_STAGES");
-    const int x = v ? atoi(v) : 0;
-    return (x == 2 || x == 3 || x == 4 || x == 6) ? x : 0;
-  }();
-  if (forced &&
-      kPipeWarps * pipe_warp_bytes(BSM_PREC_SPLIT_TF32X2, smax, forced, 16) <= 200 * 1024)
-    return forced;
-  return pipe_stages(smax);
-}
-
-// [precision: BF16x3, TF32x2][stages: 2, 3, 4, 6; 4: the large-block instance]
-static const void *const (&pipe_instances())[2][5] {
-  static const void *const inst[2][5] = {
+// [precision: BF16x3, TF32x2][0: the small-block instance, 1: the large-block one]
+static const void *const (&pipe_instances())[2][2] {
+  static const void *const inst[2][2] = {
       {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2, false>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 3, false>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 4, false>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 6, false>,
        (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_BF16X3, 2, true>},
       {(const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2, false>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 3, false>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 4, false>,
-       (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 6, false>,
        (const void *)k_numeric_split_pipe<BSM_PREC_SPLIT_TF32X2, 2, true>}};
   return inst;
 }
@@ -805,36 +784,25 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
                                  cudaStream_t stream) {
   const int pi = precision == BSM_PREC_SPLIT_BF16X3 ? 0 : 1;
   const bool big = sizes == 2;  // C blocks beyond 16x16: the large-block instance
-  const int stages = big ? 2 : pipe_stages_for(smax);
+  constexpr int stages = kPipeStages;
   const int warps = big ? kPipeWarpsBig : kPipeWarps;
   const size_t smem = (size_t)warps * pipe_warp_bytes(precision, smax, stages, big ? 32 : 16);
-  const int si = big ? 4 : stages == 2 ? 0 : stages == 3 ? 1 : stages == 4 ? 2 : 3;
-  const void *fn = pipe_instances()[pi][si];
+  const void *fn = pipe_instances()[pi][big ? 1 : 0];
   int per_sm = 1;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
   if (e != cudaSuccess) return e;
   const int grid = nsm * (per_sm > 0 ? per_sm : 1);
   const int sel = sizes;  // 0 all, 1 small C blocks only, 2 large ones only
-#define BSM_SPLIT_PIPE(P, S, G)                                                                 \
-  k_numeric_split_pipe<P, S, G><<<grid, warps * 32, smem, stream>>>(                            \
+#define BSM_SPLIT_PIPE(P, G)                                                                    \
+  k_numeric_split_pipe<P, stages, G><<<grid, warps * 32, smem, stream>>>(                       \
       A, B, C, Cin, a_left, b_right, alpha, beta, ws, st, items, seg, smax, sel, work)
-#define BSM_SPLIT_PIPE_S(P)                   \
-  if (big) {                                  \
-    BSM_SPLIT_PIPE(P, 2, true);               \
-  } else {                                    \
-    switch (stages) {                         \
-      case 2: BSM_SPLIT_PIPE(P, 2, false); break; \
-      case 3: BSM_SPLIT_PIPE(P, 3, false); break; \
-      case 4: BSM_SPLIT_PIPE(P, 4, false); break; \
-      default: BSM_SPLIT_PIPE(P, 6, false); break; \
-    }                                         \
-  }
   if (precision == BSM_PREC_SPLIT_BF16X3) {
-    BSM_SPLIT_PIPE_S(BSM_PREC_SPLIT_BF16X3);
+    if (big) BSM_SPLIT_PIPE(BSM_PREC_SPLIT_BF16X3, true);
+    else BSM_SPLIT_PIPE(BSM_PREC_SPLIT_BF16X3, false);
   } else {
-    BSM_SPLIT_PIPE_S(BSM_PREC_SPLIT_TF32X2);
+    if (big) BSM_SPLIT_PIPE(BSM_PREC_SPLIT_TF32X2, true);
+    else BSM_SPLIT_PIPE(BSM_PREC_SPLIT_TF32X2, false);
   }
-#undef BSM_SPLIT_PIPE_S
 #undef BSM_SPLIT_PIPE
   return cudaGetLastError();
 }
@@ -843,12 +811,11 @@ cudaError_t numeric_split_init() {
   // the largest slot layout of each instance (k up to 32), and the whole
   // shared memory of an SM for the carveout (the rings decide occupancy)
   for (int pi = 0; pi < 2; pi++)
-    for (int si = 0; si < 5; si++) {
+    for (int big = 0; big < 2; big++) {
       const int prec = pi == 0 ? BSM_PREC_SPLIT_BF16X3 : BSM_PREC_SPLIT_TF32X2;
-      const int stages = si == 0 || si == 4 ? 2 : si == 1 ? 3 : si == 2 ? 4 : 6;
-      const int bytes = si == 4 ? kPipeWarpsBig * pipe_warp_bytes(prec, 32, stages, 32)
-                                : kPipeWarps * pipe_warp_bytes(prec, 32, stages, 16);
-      const void *fn = pipe_instances()[pi][si];
+      const int bytes = big ? kPipeWarpsBig * pipe_warp_bytes(prec, 32, kPipeStages, 32)
+                            : kPipeWarps * pipe_warp_bytes(prec, 32, kPipeStages, 16);
+      const void *fn = pipe_instances()[pi][big];
       cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

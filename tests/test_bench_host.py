@@ -48,3 +48,15 @@ def test_eps_percentile_of_norm_products():
     assert eps > 0 and np.isfinite(eps)
     # a higher percentile gives a larger threshold
     assert bench.norm_product_percentile(A, 60) > eps
+
+
+def test_fp64_peak_derived_from_sms_and_clock():
+    bench = _bench()
+    peak, src = bench.fp64_peak_gflops(152, {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0})
+    assert abs(peak - 152 * 4 * 2.070) < 1e-9 and "derived" in src
+    # a lower sampled clock lowers the peak in proportion
+    low, _ = bench.fp64_peak_gflops(152, {"sm_mhz": 1035.0, "sm_max_mhz": 2070.0})
+    assert abs(low - peak / 2) < 1e-9
+    # no samples: the maximum clock
+    nos, src2 = bench.fp64_peak_gflops(152, {"sm_mhz": None, "sm_max_mhz": None})
+    assert nos > 0 and "no clock samples" in src2
