@@ -349,14 +349,26 @@ typedef struct {
  * C's caller buffers; the C pattern and values are the same as bsm_multiply's
  * with beta = 0. sizes (host, 3 words) receives {C blocks, C values, kept
  * products}. Calls no cudaMalloc, cudaFree or allocating library routine.
- * The first call on a device (with that device current) looks up the device
- * address of the scratch array; make that first call before any stream
- * capture. Calls share the array: calls that overlap on the GPU race. The
- * call enqueues on `stream` (a cudaStream_t, NULL = legacy default) and
- * returns after the work is done. Errors: INVALID_ARG (also when C's
- * capacities are too small: sizes[] then holds what is needed), DIM_MISMATCH,
- * UNSUPPORTED (the problem needs more scratch than BSM_NOALLOC_SCRATCH_BYTES),
- * CUDA. */
+ * Every call looks up the device address of the scratch array on the current
+ * device (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ * device also sets a kernel attribute there: make that first call before any
+ * stream capture. Calls share the array: calls that overlap on the GPU race.
+ * The call enqueues on `stream` (a cudaStream_t, NULL = legacy default) and
+ * returns after the work is done.
+ * The caller's device arrays are checked on the device before any kernel uses
+ * them as indices: row_ptr[0] == 0, row_ptr non-decreasing, row_ptr[nbr] ==
+ * nblk, column indices in [0, nbc) and strictly increasing within a row, block
+ * sizes >= 1, block offsets >= 0, A's column sizes equal to B's row sizes.
+ * Not checked (the library cannot see the allocations' sizes): each block's
+ * values, blk_off[b] .. blk_off[b] + rows*cols, lie inside `values`.
+ * Scratch use: about 24 bytes per block of A and of B, 56 per block row of A,
+ * 20 per block of C's capacity cap_blk, and 8 per kept product; a generous
+ * cap_blk therefore leaves less room for the products.
+ * Errors: INVALID_ARG (malformed row pointers, unsorted or duplicate columns,
+ * a block size below 1, a negative offset; also when C's capacities are too
+ * small: sizes[] then holds what is needed), OUT_OF_RANGE (a column index
+ * outside the block grid), DIM_MISMATCH, UNSUPPORTED (the problem needs more
+ * scratch than BSM_NOALLOC_SCRATCH_BYTES), CUDA. */
 int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bsm_dev_csr *B, double eps,
                          bsm_dev_csr_out *C, int64_t *sizes, void *stream);
 

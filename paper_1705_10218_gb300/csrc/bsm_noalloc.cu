@@ -13,14 +13,21 @@
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds BSM_NOALLOC_SCRATCH_BYTES of it until the process exits.
 // Host code cannot use the array's name as a device address (on the host it
-// names a stand-in object), so the first call on each device, with that device
-// current, looks the address up with cudaGetSymbolAddress and keeps it; that
-// first call should therefore come before any stream capture. All calls share
-// the array and it keeps the contents of the previous call: whatever must
-// start at zero is cleared here, and calls that overlap on the GPU (two
-// streams, two threads) race on it.
+// names a stand-in object), so every call looks the address up with
+// cudaGetSymbolAddress for the current device (no allocation; a device reset
+// between calls is therefore harmless). The first call on a device also sets
+// the numeric kernel's shared-memory attribute; it should come before any
+// stream capture. All calls share the array and it keeps the contents of the
+// previous call: whatever must start at zero is cleared here, and calls that
+// overlap on the GPU (two streams, two threads) race on it.
+//
+// The caller's arrays are device memory the host cannot read cheaply, so a
+// first kernel checks them (row pointers, column indices, block sizes, block
+// offsets) and the call reads the verdict back before any other kernel uses
+// them as indices: a malformed matrix is an error code, not a stray access.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "bsm_internal.h"
@@ -33,7 +40,65 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-unsigned char *g_noalloc_ptr[kMaxDevices] = {};
+bool g_noalloc_init[kMaxDevices] = {};
+
+// Verdict bits of the input check.
+enum : int32_t {
+  kBadRowPtr = 1,   // row_ptr[0] != 0, decreasing, or row_ptr[nbr] != nblk
+  kBadColIdx = 2,   // a column index outside [0, nbc)
+  kBadOrder = 4,    // columns of a row not strictly increasing (unsorted or duplicate)
+  kBadSize = 8,     // a block size below 1
+  kBadDims = 16,    // A's column sizes differ from B's row sizes
+  kBadOffset = 32   // a negative block offset
+};
+
+struct CsrView {
+  int32_t nbr, nbc;
+  const int32_t *row_sizes, *col_sizes, *row_ptr, *col_idx;
+  const int64_t *blk_off;
+  int64_t nblk;
+};
+
+// One operand's blocked CSR: every read stays inside the sizes the caller
+// declared (row_ptr[0..nbr], col_idx / blk_off[0..nblk), the size arrays);
+// the column indices of a row are visited only when its row pointers are
+// inside [0, nblk] and in order.
+__device__ void check_csr(const CsrView &m, int64_t tid, int64_t nth, int32_t *flags) {
+  int32_t bad = 0;
+  if (tid == 0 && (m.row_ptr[0] != 0 || (int64_t)m.row_ptr[m.nbr] != m.nblk)) bad |= kBadRowPtr;
+  for (int64_t i = tid; i < m.nbr; i += nth) {
+    const int64_t a = m.row_ptr[i], b = m.row_ptr[i + 1];
+    if (a < 0 || b < a || b > m.nblk) {
+      bad |= kBadRowPtr;
+      continue;
+    }
+    int32_t prev = -1;
+    for (int64_t x = a; x < b; x++) {
+      const int32_t c = m.col_idx[x];
+      if (c < 0 || c >= m.nbc) bad |= kBadColIdx;
+      else if (c <= prev) bad |= kBadOrder;
+      if (c > prev) prev = c;
+      if (m.blk_off[x] < 0) bad |= kBadOffset;
+    }
+  }
+  for (int64_t i = tid; i < m.nbr; i += nth)
+    if (m.row_sizes[i] < 1) bad |= kBadSize;
+  for (int64_t i = tid; i < m.nbc; i += nth)
+    if (m.col_sizes[i] < 1) bad |= kBadSize;
+  if (bad) atomicOr(flags, bad);
+}
+
+__global__ void k_noalloc_check(CsrView A, CsrView B, int same, int32_t *flags) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  check_csr(A, tid, nth, flags);
+  if (!same) check_csr(B, tid, nth, flags);
+  // A's column block sizes against B's row block sizes (A.nbc == B.nbr here)
+  int32_t bad = 0;
+  for (int64_t k = tid; k < A.nbc; k += nth)
+    if (A.col_sizes[k] != B.row_sizes[k]) bad |= kBadDims;
+  if (bad) atomicOr(flags, bad);
+}
 
 // Expands CSR row pointers into per-block row indices, fills the two-word
 // headers {nblk, nnz} of the operands and clears the status word.
@@ -102,28 +167,55 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
   if (A->nbc != B->nbr) return BSM_ERR_DIM_MISMATCH;
   cudaStream_t s = (cudaStream_t)stream;
 
-  // once per device: the device address of the static array
+  // every call: the device address of the static array on the current device
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_cuda_fail(e);
   if (dev < 0 || dev >= kMaxDevices) return BSM_ERR_UNSUPPORTED;
   unsigned char *scratch;
   {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return noalloc_cuda_fail(e);
+    scratch = static_cast<unsigned char *>(p);
+    // the numeric kernel's shared-memory size attribute, once per device
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      void *p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return noalloc_cuda_fail(e);
-      // the numeric kernel's shared-memory size attribute, also once per device
+    if (!g_noalloc_init[dev]) {
       e = numeric_fp64_init();
       if (e != cudaSuccess) return noalloc_cuda_fail(e);
-      g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+      g_noalloc_init[dev] = true;
     }
-    scratch = g_noalloc_ptr[dev];
+  }
+
+  // A and B are one matrix (its norms and row indices computed once) only when
+  // the descriptors agree field by field
+  const bool same = (A == B) || memcmp(A, B, sizeof(bsm_dev_csr)) == 0;
+  int nsm = 0;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return noalloc_cuda_fail(e);
+
+  // the input check, read back before any kernel indexes with the caller's arrays
+  {
+    int32_t *flags = reinterpret_cast<int32_t *>(scratch);
+    auto cv_of = [](const bsm_dev_csr *m) {
+      return CsrView{m->nbr, m->nbc, m->row_sizes, m->col_sizes, m->row_ptr, m->col_idx,
+                     m->blk_off, m->nblk};
+    };
+    int32_t h_flags = 0;
+    if ((e = cudaMemsetAsync(flags, 0, sizeof(int32_t), s)) != cudaSuccess)
+      return noalloc_cuda_fail(e);
+    k_noalloc_check<<<nsm * 2, 256, 0, s>>>(cv_of(A), cv_of(B), same ? 1 : 0, flags);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&h_flags, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return noalloc_cuda_fail(e);
+    if (h_flags & kBadColIdx) return BSM_ERR_OUT_OF_RANGE;
+    if (h_flags & ~kBadDims) return BSM_ERR_INVALID_ARG;
+    if (h_flags) return BSM_ERR_DIM_MISMATCH;
   }
 
   // layout of the scratch for this problem
-  const bool same = (A == B) || (A->row_ptr == B->row_ptr && A->values == B->values);
   Carve cv{scratch};
   DevStatus *st = cv.take<DevStatus>(1);
   double *norms_a = cv.take<double>(A->nblk);
@@ -155,10 +247,6 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
   const size_t left = (size_t)BSM_NOALLOC_SCRATCH_BYTES - cv.used;
   ws.cap_prod = (int64_t)(left / sizeof(int2));
   ws.prods = reinterpret_cast<int2 *>(scratch + cv.used);
-
-  int nsm = 0;
-  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return noalloc_cuda_fail(e);
 
   k_noalloc_setup<<<nsm * 2, 256, 0, s>>>(A->nbr, A->row_ptr, brow_a, hdr_a, A->nblk, B->nbr,
                                           B->row_ptr, brow_b, hdr_b, B->nblk, st);
