@@ -92,6 +92,16 @@ enum {
   BSM_FP64_NUM_KERNELS = 6
 };
 
+/* Split-precision numeric kernels. bsm_opts.split_kernel = 1 + one of these
+ * forces it; 0 leaves the choice to the library (BLOCKS).
+ *   PANEL:  one C block row at a time as a dense panel product on the
+ *           tcgen05 tensor cores (MMA M = the row's C columns, N = its block
+ *           row size x slices, K = A's row), accumulators in tensor memory;
+ *   BLOCKS: one C block per warp, its products one after another on mma.sync
+ *           tiles, operands streamed through shared memory.
+ * Both multiply the same slice products; they differ in FP32 rounding only. */
+enum { BSM_SPLIT_PANEL = 0, BSM_SPLIT_BLOCKS = 1, BSM_SPLIT_NUM_KERNELS = 2 };
+
 /* How the numeric stacks are launched. */
 enum {
   BSM_LAUNCH_PERSISTENT = 0, /* one persistent launch over all shape classes */
@@ -130,6 +140,9 @@ typedef struct {
                           multiply). Memory that is not device-mapped: BSM_ERR_INVALID_ARG.
                           The caller keeps ownership and must not free it before then. */
   int64_t host_cap;
+  int32_t split_kernel; /* 0, or 1 + BSM_SPLIT_* to force that split-precision kernel
+                           (ignored by FP64); out of range: BSM_ERR_INVALID_ARG */
+  int32_t reserved;     /* 0 */
 } bsm_opts;
 
 /* Counters of one multiply (filled when bsm_stats* is not NULL; this makes
@@ -234,7 +247,8 @@ typedef struct {
   int64_t launches;    /* kernels launched by this context since profiling started */
   int32_t last_fp64_kernel; /* BSM_FP64_* of the last FP64 numeric launch enqueued by the
                                context (forced, tuned or default), -1 if none */
-  int32_t reserved;
+  int32_t last_split_kernel; /* BSM_SPLIT_* of the last split-precision numeric launch, -1 if
+                                none */
 } bsm_profile;
 
 /* enable != 0: start profiling (totals reset); enable == 0: stop. */

@@ -32,6 +32,8 @@ BSM_FP64_PK12 = 3
 BSM_FP64_PK16 = 4
 BSM_FP64_G8 = 5
 BSM_FP64_NUM_KERNELS = 6
+BSM_SPLIT_PANEL = 0
+BSM_SPLIT_BLOCKS = 1
 
 
 class BsmError(RuntimeError):
@@ -56,6 +58,8 @@ class _Opts(ctypes.Structure):
         ("fp64_kernel", ctypes.c_int32),
         ("host_values", ctypes.c_void_p),
         ("host_cap", ctypes.c_int64),
+        ("split_kernel", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -82,7 +86,7 @@ class _Profile(ctypes.Structure):
         ("multiplies", ctypes.c_int64),
         ("launches", ctypes.c_int64),
         ("last_fp64_kernel", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("last_split_kernel", ctypes.c_int32),
     ]
 
 
@@ -95,6 +99,7 @@ class Profile:
     multiplies: int
     launches: int
     last_fp64_kernel: int  # BSM_FP64_* of the last FP64 numeric launch, -1 if none
+    last_split_kernel: int = -1  # BSM_SPLIT_* of the last split-precision numeric launch
 
 
 @dataclass
@@ -207,9 +212,10 @@ class Context:
                  precision: int = BSM_PREC_FP64, launch: int = BSM_LAUNCH_PERSISTENT,
                  blocking: bool = False, autotune: bool = False, stream=None,
                  graph: bool = False, stats: bool = False, fp64_kernel: int | None = None,
-                 host_out: np.ndarray | None = None) -> Stats | None:
+                 host_out: np.ndarray | None = None, split_kernel: int | None = None) -> Stats | None:
         """fp64_kernel: one of BSM_FP64_* to force that FP64 kernel, None for the
-        library's choice. host_out: a float64 array in page-locked host memory
+        library's choice. split_kernel: one of BSM_SPLIT_* likewise for the
+        split precisions. host_out: a float64 array in page-locked host memory
         that also receives C's values (bsm_mat_get_values order) while the
         multiply runs, when they fit; valid once the result is complete."""
         hv, hcap = None, 0
@@ -219,7 +225,8 @@ class Context:
             hv, hcap = host_out.ctypes.data, host_out.size
         o = _Opts(int(precision), int(launch), int(bool(blocking)), int(bool(autotune)),
                   _stream_ptr(stream), int(bool(graph)),
-                  0 if fp64_kernel is None else int(fp64_kernel) + 1, hv, hcap)
+                  0 if fp64_kernel is None else int(fp64_kernel) + 1, hv, hcap,
+                  0 if split_kernel is None else int(split_kernel) + 1, 0)
         st = _Stats() if stats else None
         rc = lib().bsm_multiply(self._h, float(alpha), A._h, B._h, float(beta), C._h, float(eps),
                                 ctypes.byref(o), ctypes.byref(st) if st is not None else None)
@@ -248,7 +255,7 @@ class Context:
         p = _Profile()
         _check(lib().bsm_ctx_profile_read(self._h, ctypes.byref(p)), "bsm_ctx_profile_read")
         return Profile(p.ms_norms, p.ms_symbolic, p.ms_numeric, p.ms_total, p.multiplies, p.launches,
-                       p.last_fp64_kernel)
+                       p.last_fp64_kernel, p.last_split_kernel)
 
     def close(self):
         if self._h:

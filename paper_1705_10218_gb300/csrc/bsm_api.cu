@@ -263,10 +263,15 @@ struct bsm_ctx_s {
   bool prof_pending[kSlots] = {};
   bsm_profile prof_tot{};
   int last_fp64 = -1;  // BSM_FP64_* of the last FP64 numeric launch
+  int last_split = -1;  // BSM_SPLIT_* of the last split-precision numeric launch
   int64_t launches = 0;
   int64_t launches_at_enable = 0;
   // shape-class grouping (per-stack launches)
   int32_t *cls_items = nullptr;  // [cap_cblk]
+  // work of the row-panel split kernel (records, tile entries, tiles per row);
+  // its fallback list reuses cls_items / cls_segs
+  PanelWs pw{};
+  int64_t cap_pw_recs = 0, cap_pw_tiles = 0, cap_pw_rows = 0;
   int32_t *cls_counts = nullptr, *cls_cursor = nullptr;  // [kMaxClasses]
   int64_t *cls_segs = nullptr;   // [2 * kMaxClasses]
   // captured multiplies (opts.graph), keyed by every kernel argument
@@ -366,6 +371,32 @@ static int ws_grow(bsm_ctx ctx, int64_t nblk_c, int64_t nprod) {
     }
     w.cap_prod = n;
   }
+  return BSM_OK;
+}
+
+// The row-panel kernel's work buffers, sized to the workspace's capacities.
+static int panel_ws(bsm_ctx ctx, int64_t nrows) {
+  int rc;
+  if (ctx->cap_pw_recs < ctx->ws.cap_prod) {
+    dev_free(ctx->pw.recs);
+    ctx->cap_pw_recs = 0;
+    if ((rc = dev_alloc(&ctx->pw.recs, ctx->ws.cap_prod))) return rc;
+    ctx->cap_pw_recs = ctx->ws.cap_prod;
+  }
+  if (ctx->cap_pw_tiles < ctx->cap_cblk) {
+    dev_free(ctx->pw.tiles);
+    ctx->cap_pw_tiles = 0;
+    if ((rc = dev_alloc(&ctx->pw.tiles, 4 * ctx->cap_cblk))) return rc;
+    ctx->cap_pw_tiles = ctx->cap_cblk;
+  }
+  if (ctx->cap_pw_rows < nrows) {
+    dev_free(ctx->pw.row_nt);
+    ctx->cap_pw_rows = 0;
+    if ((rc = dev_alloc(&ctx->pw.row_nt, nrows))) return rc;
+    ctx->cap_pw_rows = nrows;
+  }
+  ctx->pw.fb_items = ctx->cls_items;
+  ctx->pw.fb_seg = ctx->cls_segs;
   return BSM_OK;
 }
 
@@ -571,6 +602,16 @@ static int variant_or_default(bsm_ctx ctx, bsm_mat C, const bsm_opts &o,
   return it == ctx->tune.end() ? fp64_default(ctx, C) : it->second;
 }
 
+// The split-precision kernel of a multiply: the forced one, else the per-block
+// kernel (measured faster on the water and amorphous systems); the per-block
+// kernel also when B's slice offsets do not fit the panel's 32-bit records
+// (16-byte units).
+static int split_kernel_of(const bsm_opts &o, bsm_mat B) {
+  const int64_t unit16 = o.precision == BSM_PREC_SPLIT_BF16X3 ? 3 : 2;
+  if (B && B->nnz * unit16 >= (int64_t)INT32_MAX) return BSM_SPLIT_BLOCKS;
+  return o.split_kernel > 0 ? o.split_kernel - 1 : BSM_SPLIT_BLOCKS;
+}
+
 struct Launch {
   bsm_ctx ctx;
   bsm_mat A, B, C;
@@ -624,6 +665,7 @@ static int launch_numeric(Launch &L, int variant, const int32_t *items, const in
                           int max_m, int max_n) {
   bsm_ctx ctx = L.ctx;
   if (L.split) {
+    ctx->last_split = BSM_SPLIT_BLOCKS;
     const int smax = L.A->max_col;
     if (max_m <= 16 && max_n <= 16) {
       CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
@@ -687,7 +729,26 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
                           ctx->nsm * 6, L.s));
   ctx->launches++;
   if (L.prof && record) CK(cudaEventRecord(ctx->prof_ev[L.slot][2], L.s));
-  if (L.o.launch == BSM_LAUNCH_PER_STACK) {
+  if (L.split && split_kernel_of(L.o, L.B) == BSM_SPLIT_PANEL) {
+    // the row-panel kernel takes every C block row in one launch, whatever the
+    // launch mode (its work unit is a row, not a shape class): the prep kernel
+    // orders each tile's products by A block, the panel kernel multiplies, and
+    // the per-block kernel takes the rows the prep left to it (none unless a
+    // row of A has more than 1024 blocks)
+    if ((rc = panel_ws(ctx, L.A->nbr))) return rc;
+    CK(cudaMemsetAsync(ctx->cls_segs, 0, 2 * sizeof(int64_t), L.s));
+    CK(launch_panel_prep(L.o.precision, L.dA, L.dB, L.out, L.ws, ctx->pw, ctx->d_status,
+                         L.A->max_row, ctx->nsm, L.s));
+    ctx->launches++;
+    CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
+    CK(launch_numeric_split_panel(L.o.precision, L.dA, L.dB, L.out, L.dC, L.A->split_left,
+                                  L.B->split_right, L.alpha, L.beta, L.ws, ctx->pw,
+                                  ctx->d_status, L.A->max_row, ctx->nsm, ctx->d_work, L.s));
+    ctx->launches++;
+    if ((rc = launch_numeric(L, 0, ctx->cls_items, ctx->cls_segs, L.A->max_row, L.B->max_col)))
+      return rc;
+    ctx->last_split = BSM_SPLIT_PANEL;
+  } else if (L.o.launch == BSM_LAUNCH_PER_STACK) {
     const int ncc = (int)L.B->col_kinds.size();
     const int ncls = (int)L.A->row_kinds.size() * ncc;
     CK(launch_class_sort(L.out, L.A->row_cls, L.B->col_cls, ncc, ncls, ctx->d_status,
@@ -763,8 +824,10 @@ static void graph_key(const Launch &L, std::vector<uint64_t> &k) {
   put(w.prod_off), put(w.nnz_off), put(w.cnt), put(w.c_cin), put(w.prod_ptr), put(w.prods);
   num(w.cap_prod), num(L.out.cap_blk), num(L.out.cap_nnz);
   put(L.ctx->cls_items), put(L.s);
+  put(L.ctx->pw.recs), put(L.ctx->pw.tiles), put(L.ctx->pw.row_nt);
   dbl(L.alpha), dbl(L.beta), dbl(L.eps);
   num(L.o.precision), num(L.o.launch), num(L.o.fp64_kernel), num((int64_t)L.ctx->tune_version);
+  num(L.o.split_kernel);
   put(L.out.host_vals), num(L.out.host_cap);
   num(fp64_default(L.ctx, L.C));
 }
@@ -808,6 +871,9 @@ static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double 
     L.out.cap_blk = std::min<int64_t>(L.out.cap_blk, std::max<int64_t>(ctx->cap_cblk - 1, 0));
   };
   make_out();
+  // the panel kernel's work buffers before any capture (no allocation inside one)
+  if (L.split && split_kernel_of(o, B) == BSM_SPLIT_PANEL && (rc = panel_ws(ctx, A->nbr)))
+    return rc;
   const bool use_graph = o.graph && !sync_sizes;
   L.prof = ctx->prof && !use_graph;
   if (stats) CK(cudaEventRecord(ctx->ev_t0, L.s));
@@ -990,6 +1056,8 @@ int bsm_ctx_create(int device, bsm_ctx *out) {
   if (rc == BSM_OK) {
     if ((e = numeric_fp64_init()) != cudaSuccess) rc = cuda_fail(e, "numeric_fp64_init");
     else if ((e = numeric_split_init()) != cudaSuccess) rc = cuda_fail(e, "numeric_split_init");
+    else if ((e = numeric_split_panel_init()) != cudaSuccess)
+      rc = cuda_fail(e, "numeric_split_panel_init");
   }
   if (rc == BSM_OK) {
     rc = dev_alloc(&ctx->cls_counts, kMaxClasses);
@@ -1037,6 +1105,9 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   dev_free(ctx->d_status);
   dev_free(ctx->d_work);
   dev_free(ctx->cls_items);
+  dev_free(ctx->pw.recs);
+  dev_free(ctx->pw.tiles);
+  dev_free(ctx->pw.row_nt);
   dev_free(ctx->cls_counts);
   dev_free(ctx->cls_cursor);
   dev_free(ctx->cls_segs);
@@ -1363,6 +1434,7 @@ int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, b
   if (o.launch != BSM_LAUNCH_PERSISTENT && o.launch != BSM_LAUNCH_PER_STACK)
     return BSM_ERR_INVALID_ARG;
   if (o.fp64_kernel < 0 || o.fp64_kernel > BSM_FP64_NUM_KERNELS) return BSM_ERR_INVALID_ARG;
+  if (o.split_kernel < 0 || o.split_kernel > BSM_SPLIT_NUM_KERNELS) return BSM_ERR_INVALID_ARG;
   if (o.host_values) {  // must be device-mapped page-locked host memory
     if (o.host_cap < 0) return BSM_ERR_INVALID_ARG;
     cudaPointerAttributes pa{};
@@ -1552,7 +1624,7 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out) {
   *out = ctx->prof_tot;
   out->launches = ctx->launches - ctx->launches_at_enable;
   out->last_fp64_kernel = ctx->last_fp64;
-  out->reserved = 0;
+  out->last_split_kernel = ctx->last_split;
   return BSM_OK;
 }
 

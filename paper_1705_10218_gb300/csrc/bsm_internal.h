@@ -149,6 +149,35 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
                                  double beta, DevWs ws, const DevStatus *st, const int32_t *items,
                                  const int64_t *seg, int smax, int nsm, unsigned long long *work,
                                  cudaStream_t stream);
+// The row-panel split kernel (k_split_panel.cu). Its work of a multiply:
+//   tiles:  per C block row, its tiles (runs of whole C blocks, at most 128
+//           columns and 32 blocks) as 64-byte entries at the row's first C
+//           block index: {first C block, blocks, first record (int64)},
+//           {end record (int64), columns, 0}, the blocks' column sizes (32 bytes);
+//   row_nt: tiles per row, -1 for a row left to the per-block kernel (more A
+//           blocks than the record sort handles);
+//   recs:   the kept products of each tile ordered by A block: {B's slice
+//           offset in 16-byte units, A block position in the row | slot << 16};
+//   fb_items, fb_seg: C blocks of the rows left to the per-block kernel and
+//           {0, their count} (fb_seg[1] must be zero before the prep kernel).
+struct PanelWs {
+  int2 *recs;       // [cap_prod]
+  int4 *tiles;      // [4 * cap C blocks]
+  int32_t *row_nt;  // [rows]
+  int32_t *fb_items;
+  int64_t *fb_seg;
+};
+cudaError_t launch_panel_prep(int precision, DevMat A, DevMat B, DevOut C, DevWs ws, PanelWs pw,
+                              const DevStatus *st, int max_r, int nsm, cudaStream_t stream);
+// max_r: the largest block row size of A (at most 32). work: a device counter
+// that must be zero when the launch starts.
+cudaError_t launch_numeric_split_panel(int precision, DevMat A, DevMat B, DevOut C, DevMat Cin,
+                                       const void *a_left, const void *b_right, double alpha,
+                                       double beta, DevWs ws, PanelWs pw, const DevStatus *st,
+                                       int max_r, int nsm, unsigned long long *work,
+                                       cudaStream_t stream);
+cudaError_t numeric_split_panel_init();
+
 // Post filter and block-sparse add (k_extra.cu).
 cudaError_t launch_filter_count(DevMat M, double eps, DevWs ws, int nsm, cudaStream_t stream);
 cudaError_t launch_filter_fill(DevMat M, double eps, DevWs ws, DevOut O, const DevStatus *st,

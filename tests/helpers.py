@@ -85,3 +85,69 @@ def select_blocks(M, keep):
     return BlockMatrix(np.asarray(M.row_sizes, np.int32), np.asarray(M.col_sizes, np.int32),
                        np.asarray(M.blk_row, np.int32)[keep].copy(),
                        np.asarray(M.blk_col, np.int32)[keep].copy(), v)
+
+
+# ---------------------------------------------------------------------------
+# Per-element error bound of the split-precision paths.
+#
+# A product a.b of FP64 values is replaced by sum over the kept slice pairs of
+# a_p.b_q. Slices are cut by truncation: BF16x3 leaves a remainder below
+# 2^-23 |a| after three slices and drops pairs (2,3), (3,2), (3,3) whose sum
+# is below 2^-21 |a||b|, together u_s = 3 * 2^-22; TF32x2 leaves 2^-21 |a| per
+# operand and drops a2.b2 (below 2^-20), u_s = 2^-19. Every slice product is
+# exact in FP32; the tensor cores add them in FP32. One MMA with kmma products
+# per output adds at most eta = (kmma + 2) * 2^-23 of |accumulator| + sum of
+# |terms| (a conservative model that also covers truncating adders); an MMA
+# whose terms are all zero adds nothing. |accumulator| never exceeds the sum of
+# |terms| added since it last started from zero, and the slices of a value sum
+# to at most (1 + 2^-7) times its magnitude, so an accumulator that takes W
+# MMAs before it is folded exactly (TwoSum) or read out contributes at most
+# W * eta * (1 + 2^-6) * (|A| |B|)_element.
+#   per-block kernel: folds every 4 products: W = 4 * pairs * k steps of the
+#     largest k block (BF16: 6 pairs, k steps of 16; TF32: 3 pairs, of 8);
+#   panel kernel: one FP32 accumulator per element over the row's K steps;
+#     only steps that hold a product of the element's C block count: a block
+#     of np 16-byte pieces (8 BF16 / 4 TF32 values) spans at most
+#     (np + 2) // 2 steps of 2 pieces, and each step adds the slices' MMAs
+#     (3 for BF16, 2 for TF32) into the element's group.
+# The groups are then combined with one FP32 rounding below 2^-24 of a group
+# 2^-8 smaller than the result and an exact TwoSum, and C is formed in FP64.
+# ---------------------------------------------------------------------------
+def split_block_factors(A, B, prec, kernel, rows=None):
+    """Bound factor per C block of the candidate pattern of A.B (a dict
+    (i, j) -> factor is not needed: returns a function of block row / column
+    arrays). prec: "bf16x3" / "tf32x2"; kernel: "blocks" / "panel"."""
+    import scipy.sparse as sp
+
+    bf = prec == "bf16x3"
+    u_s = 3 * 2.0 ** -22 if bf else 2.0 ** -19
+    kmma = 16 if bf else 8
+    eta = (kmma + 2) * 2.0 ** -23
+    ks = np.asarray(A.col_sizes, np.int64)
+    if kernel == "blocks":
+        w = 4 * (6 if bf else 3) * int(-(-ks.max() // kmma))
+        const = u_s + w * eta * (1 + 2.0 ** -6)
+        return lambda bi, bj: np.full(len(bi), const)
+    piece = 8 if bf else 4
+    nsl = 3 if bf else 2
+    steps = ((-(-ks // piece)) + 2) // 2
+    PA = sp.csr_matrix((np.ones(len(A.blk_row)), (A.blk_row, A.blk_col)), shape=(len(A.row_sizes), len(ks)))
+    PB = sp.csr_matrix((np.ones(len(B.blk_row)), (B.blk_row, B.blk_col)), shape=(len(ks), len(B.col_sizes)))
+    if rows is not None:
+        PA = PA[rows[0]:rows[1]]
+    S = (PA @ sp.diags(steps.astype(np.float64)) @ PB).tocsr()
+    r0 = rows[0] if rows is not None else 0
+
+    def f(bi, bj):
+        n = np.asarray(S[np.asarray(bi) - r0, np.asarray(bj)]).ravel()
+        return u_s + nsl * n * eta * (1 + 2.0 ** -6)
+
+    return f
+
+
+def split_elem_bound(A, B, prec, kernel, blk_row, blk_col, absvals, rows=None):
+    """Per-element bound (the layout of a result's values) for the pattern
+    (blk_row, blk_col) with |A||B| values absvals."""
+    fac = split_block_factors(A, B, prec, kernel, rows)(blk_row, blk_col)
+    lens = np.asarray(A.row_sizes, np.int64)[blk_row] * np.asarray(B.col_sizes, np.int64)[blk_col]
+    return np.repeat(fac, lens) * np.asarray(absvals) + 1e-300

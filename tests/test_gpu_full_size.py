@@ -26,22 +26,31 @@ def gpu_rows(r, v, lens, a, b):
     return lo, hi, v[off[lo]:off[hi]]
 
 
-def check_sampled(ctx, oracle_mod, A, eps, tol=1e-12, split_bound=None, **kw):
+def check_sampled(ctx, oracle_mod, A, eps, tol=1e-12, split=None, **kw):
+    """split: (precision name, kernel name, stated relative Frobenius bound):
+    every sampled element within the kernel's per-element bound instead of
+    the FP64 tolerance."""
     dA = ctx.from_blocks(A)
     dC = ctx.empty(A.row_sizes, A.col_sizes)
     st = ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stats=True, **kw)
     r, c = dC.pattern()
     v = dC.values()
     lens = A.row_sizes.astype(np.int64)[r] * A.col_sizes.astype(np.int64)[c]
+    absA = synth.BlockMatrix(A.row_sizes, A.col_sizes, A.blk_row, A.blk_col, np.abs(A.values))
     for a, b in row_ranges(A.nbr):
         ref = oracle_mod.multiply(A, A, eps=eps, rows=(a, b), nthreads=oracle_mod.max_threads())
         lo, hi, vg = gpu_rows(r, v, lens, a, b)
         assert np.array_equal(r[lo:hi], ref.blk_row) and np.array_equal(c[lo:hi], ref.blk_col)
-        if split_bound is None:
+        if split is None:
             assert H.rel_frobenius(vg, ref.values) <= tol
         else:
-            assert H.rel_frobenius(vg, ref.values) <= split_bound
-            assert np.max(np.abs(vg - ref.values)) <= split_bound * np.max(np.abs(ref.values))
+            prec, kernel, rel_f = split
+            absref = oracle_mod.multiply(absA, absA, eps=eps, rows=(a, b),
+                                         nthreads=oracle_mod.max_threads())
+            bound = H.split_elem_bound(A, A, prec, kernel, ref.blk_row, ref.blk_col, absref.values,
+                                       rows=(a, b))
+            assert np.all(np.abs(vg - ref.values) <= bound)
+            assert H.rel_frobenius(vg, ref.values) <= rel_f
     dA.destroy()
     dC.destroy()
     return st
@@ -68,9 +77,12 @@ def test_water2048_filter_active(gpu_ctx, oracle_mod, water2048):
     assert 0 < st.dropped < st.candidates
 
 
-@pytest.mark.parametrize("prec,bound", [(1, 2e-6), (2, 1e-5)])
-def test_water2048_split(gpu_ctx, oracle_mod, water2048, prec, bound):
-    check_sampled(gpu_ctx, oracle_mod, water2048, 1e-10, split_bound=bound, precision=prec)
+@pytest.mark.parametrize("kernel,sk", [("blocks", 1), ("panel", 0)])
+@pytest.mark.parametrize("prec,name,bound", [(1, "bf16x3", {"blocks": 2e-6, "panel": 1e-5}),
+                                             (2, "tf32x2", {"blocks": 1e-5, "panel": 2e-5})])
+def test_water2048_split(gpu_ctx, oracle_mod, water2048, prec, name, bound, kernel, sk):
+    check_sampled(gpu_ctx, oracle_mod, water2048, 1e-10, split=(name, kernel, bound[kernel]),
+                  precision=prec, split_kernel=sk)
 
 
 @pytest.mark.parametrize("launch", [0, 1])
