@@ -314,20 +314,135 @@ def run_reference(args, rank, world):
     return 0
 
 
-def serve_bench(args):
+def timed_multiplies(ctx, dA, dC, eps, steps, warmup, stream, **kw):
+    """Per-step device times (CUDA events on the launch stream) of steps
+    multiplies C = A.A after warmup untimed ones, and the context's profile."""
+    import torch
+
+    for _ in range(warmup):
+        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stream=stream, **kw)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    ctx.profile(True)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stream=stream, **kw)
+        ev[k][1].record(stream)
+    stream.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    return [a.elapsed_time(b) for a, b in ev], prof
+
+
+def split_slice_bytes(A, precision):
+    """Operand slice bytes of C = A.A (left and right layouts, rows padded
+    along k to 16 bytes: 8 BF16 or 4 TF32 values)."""
+    rs = A.row_sizes.astype(np.int64)
+    r, c = rs[A.blk_row], A.col_sizes.astype(np.int64)[A.blk_col]
+
+    def up(x, q):
+        return (x + q - 1) // q * q
+    if precision == "bf16x3":
+        return 3 * 2 * int((r * up(c, 8) + c * up(r, 8)).sum())
+    return 2 * 4 * int((r * up(c, 4) + c * up(r, 4)).sum())
+
+
+def measure_variants(ctx, A, dA, dC, eps, flops, local, sample=None, steps=10, warmup=3):
+    """The other configurations of the benchmark, measured in the same process
+    after the headline: the split precisions on the same water system (both
+    kernels; errors against the oracle on the CPU baseline's block rows), the
+    mixed-size amorphous system in the launch modes, and a reduced serving
+    replay. Each with its own clock samples."""
+    import torch
+
+    import synth
+
+    s = torch.cuda.Stream()
+    out = {}
+    hbm = measured_peak("hbm_gbs", 6800.0)
+    bf16 = measured_peak("bf16_tflops", 1900.0)
+    split = {}
+    for prec in ("bf16x3", "tf32x2"):
+        for kname, knum in (("blocks", 1), ("panel", 0)):
+            kw = dict(precision=PRECISIONS[prec], split_kernel=knum)
+            with ClockSampler(local) as clk:
+                per, prof = timed_multiplies(ctx, dA, dC, eps, steps, warmup, s, **kw)
+            num_ms = prof.ms_numeric / max(prof.multiplies, 1)
+            ms = statistics.median(per)
+            nnz_c = dC.nblocks()[1]
+            nbytes = 8 * nnz_c + split_slice_bytes(A, prec)
+            pairs = 6 if prec == "bf16x3" else 3
+            # tensor peak of the slices' type: BF16 measured; TF32 at the nominal
+            # ratio 1.1 / 2.25 of it
+            tpeak = bf16[0] * (1.0 if prec == "bf16x3" else 1.1 / 2.25)
+            e = {"value": round(flops / (ms / 1e3) / 1e9, 2), "unit": "GFLOP/s (FP64-equivalent)",
+                 "ms_p50": round(ms, 4), "numeric_ms": round(num_ms, 4),
+                 "vs_fp64_path": None,
+                 "roofline_hbm": {"achieved_gbs": round(nbytes / (num_ms / 1e3) / 1e9, 1),
+                                  "peak_gbs": hbm[0], "frac": round(nbytes / (num_ms / 1e3) / 1e9 / hbm[0], 4),
+                                  "algorithmic": "C written once + operand slices read once"},
+                 "roofline_tensor": {"achieved_tflops": round(pairs * flops / (num_ms / 1e3) / 1e12, 2),
+                                     "peak_tflops": round(tpeak, 1),
+                                     "frac": round(pairs * flops / (num_ms / 1e3) / 1e12 / tpeak, 4),
+                                     "algorithmic": f"{pairs} slice products x 2mnk per kept product"},
+                 "clocks": clk.summary()}
+            if sample is not None:
+                rows, ref = sample
+                gr, gc = dC.pattern()
+                gv = dC.values()
+                nb = int(np.searchsorted(gr, rows))
+                nv = len(ref.values)
+                if np.array_equal(gr[:nb], ref.blk_row) and np.array_equal(gc[:nb], ref.blk_col):
+                    d = gv[:nv] - ref.values
+                    e["rel_frobenius_err"] = float(np.linalg.norm(d) / np.linalg.norm(ref.values))
+                    e["max_abs_err"] = float(np.max(np.abs(d)))
+                    e["max_abs_value"] = float(np.max(np.abs(ref.values)))
+                    e["error_sample"] = f"C block rows 0..{rows} against the oracle (FP64)"
+                else:
+                    e["pattern_differs_on_sample"] = True
+            split[f"{prec}_{kname}"] = e
+    out["split_water"] = split
+
+    # mixed block sizes: one persistent launch vs one launch per shape class
+    B2 = synth.amorphous(4096, seed=2)
+    dB2 = ctx.from_blocks(B2)
+    dC2 = ctx.empty(B2.row_sizes, B2.col_sizes)
+    st2 = ctx.multiply(1.0, dB2, dB2, 0.0, dC2, 1e-8, stats=True)
+    amo = {"workload": "amorphous4096 (block sizes 5/9/13/23/32), eps 1e-8",
+           "gflop_per_multiply": round(st2.flops / 1e9, 3)}
+    for name, kw in (("persistent", dict(launch=0)), ("per_stack", dict(launch=1)),
+                     ("persistent_graph_autotune", dict(launch=0, graph=True, autotune=True))):
+        with ClockSampler(local) as clk:
+            per, prof = timed_multiplies(ctx, dB2, dC2, 1e-8, 5, 3, s, **kw)
+        ms = statistics.median(per)
+        amo[name] = {"value": round(st2.flops / (ms / 1e3) / 1e9, 2), "unit": "GFLOP/s",
+                     "ms_p50": round(ms, 3), "clocks": clk.summary()}
+    dB2.destroy()
+    dC2.destroy()
+    out["amorphous"] = amo
+
+    # serving: a reduced replay of the request stream
+    with ClockSampler(local) as clk:
+        sv = serve_measure(100, 12, 4, 16.0)
+    sv["clocks"] = clk.summary()
+    out["serving"] = sv
+    return out
+
+
+def serve_measure(requests, pool_n, slots, budget_gb, seed=4):
     """Serving: C = A.A for a stream of independent water systems of different
     sizes (log-uniform 32..1024 molecules), replayed with Poisson arrivals at
     0.8 x the measured sequential capacity and as a saturating burst, against
-    sequential per-call execution. Prints one JSON line."""
+    sequential per-call execution. Returns the measurements as a dict."""
     import synth
     from paper_1705_10218_gb300 import Context, Server
 
-    rng = np.random.default_rng(4)
+    rng = np.random.default_rng(seed)
     eps = 1e-10
-    pool_n = args.serve_pool
     sizes = np.rint(np.exp(rng.uniform(np.log(32), np.log(1024), pool_n))).astype(int)
     pool = [synth.water(int(n), seed=1000 + p) for p, n in enumerate(sizes)]
-    pick = rng.integers(0, pool_n, args.requests)
+    pick = rng.integers(0, pool_n, requests)
     gflop = []
 
     # sequential per-call execution through the C ABI: upload, multiply with the
@@ -348,7 +463,7 @@ def serve_bench(args):
     host = torch.empty(max(nnz_of.values()), dtype=torch.float64, pin_memory=True).numpy()
     lat_seq = []
     t0 = time.perf_counter()
-    for r in range(args.requests):
+    for r in range(requests):
         A = pool[pick[r]]
         ts = time.perf_counter()
         dA = ctx.from_blocks(A)
@@ -362,9 +477,9 @@ def serve_bench(args):
         gflop.append(st.flops / 1e9)
     t_seq = time.perf_counter() - t0
     ctx.close()
-    cap = args.requests / t_seq
+    cap = requests / t_seq
 
-    srv = Server(0, slots=args.slots, hbm_budget=int(args.budget_gb * (1 << 30)))
+    srv = Server(0, slots=slots, hbm_budget=int(budget_gb * (1 << 30)))
     # steady state: every distinct system once through the server first (its
     # page-locked result pool and the device-memory cache are then warm)
     warm = [srv.submit(pool[p], eps) for p in sorted(set(pick.tolist()))]
@@ -377,20 +492,20 @@ def serve_bench(args):
 
     def replay(arrivals):
         lat, order = [], []
-        ids = [None] * args.requests
+        ids = [None] * requests
         nxt, done = 0, 0
         t0 = time.perf_counter()
-        while done < args.requests:
+        while done < requests:
             now = time.perf_counter() - t0
             k = 0  # a client thread would submit concurrently: interleave with progress
-            while nxt < args.requests and arrivals[nxt] <= now and k < 8:
+            while nxt < requests and arrivals[nxt] <= now and k < 8:
                 ids[nxt] = srv.submit(pool[pick[nxt]], eps)
                 order.append(nxt)
                 nxt += 1
                 k += 1
             srv.progress()
             # admission is FIFO, so only the oldest outstanding requests can be done
-            for r in order[:4 * args.slots]:
+            for r in order[:4 * slots]:
                 state, l_ms, _, _ = srv.poll(ids[r])
                 if state >= 2:
                     # the result is in host memory: used in place, then released
@@ -405,31 +520,37 @@ def serve_bench(args):
         return lat, makespan, srv.info()["bytes_peak"]
 
     lam = 0.8 * cap
-    gaps = rng.exponential(1.0 / lam, args.requests)
+    gaps = rng.exponential(1.0 / lam, requests)
     arrivals = np.cumsum(gaps) - gaps[0]
     lat_p, span_p, peak_p = replay(arrivals)
-    lat_b, span_b, peak_b = replay(np.zeros(args.requests))
+    lat_b, span_b, peak_b = replay(np.zeros(requests))
     srv.close()
 
     def pct(x, q):
         return round(float(np.percentile(np.asarray(x), q)), 3)
 
     tot_gflop = float(np.sum(gflop))
-    line = {
-        "metric": "multiplies/s + p50/p99 latency (serving, continuous batching)",
-        "value": round(args.requests / span_b, 3), "unit": "multiplies/s", "n_gpus": 1,
-        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "water requests, 32..1024 molecules log-uniform", "requests": args.requests,
-                   "distinct_systems": pool_n, "slots": args.slots, "budget_gb": args.budget_gb,
+    return {
+        "config": {"workload": "water requests, 32..1024 molecules log-uniform", "requests": requests,
+                   "distinct_systems": pool_n, "slots": slots, "budget_gb": budget_gb,
                    "eps": eps, "total_gflop": round(tot_gflop, 2)},
         "sequential": {"multiplies_per_s": round(cap, 3), "p50_ms": pct(lat_seq, 50),
                        "p99_ms": pct(lat_seq, 99), "gflop_per_s": round(tot_gflop / t_seq, 2)},
-        "poisson": {"arrival_rate_per_s": round(lam, 3), "multiplies_per_s": round(args.requests / span_p, 3),
+        "poisson": {"arrival_rate_per_s": round(lam, 3), "multiplies_per_s": round(requests / span_p, 3),
                     "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99), "peak_gb": round(peak_p / 2**30, 3)},
-        "burst": {"multiplies_per_s": round(args.requests / span_b, 3), "p50_ms": pct(lat_b, 50),
+        "burst": {"multiplies_per_s": round(requests / span_b, 3), "p50_ms": pct(lat_b, 50),
                   "p99_ms": pct(lat_b, 99), "gflop_per_s": round(tot_gflop / span_b, 2),
                   "peak_gb": round(peak_b / 2**30, 3)},
     }
+
+
+def serve_bench(args):
+    """The request-loop benchmark on its own: one JSON line."""
+    m = serve_measure(args.requests, args.serve_pool, args.slots, args.budget_gb)
+    line = {
+        "metric": "multiplies/s + p50/p99 latency (serving, continuous batching)",
+        "value": m["burst"]["multiplies_per_s"], "unit": "multiplies/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic", **m}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -575,6 +696,8 @@ def main():
                     help="force one FP64 numeric kernel (default: the library's choice)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other configurations (split precisions, amorphous, serving)")
     ap.add_argument("--serve", action="store_true", help="the request-loop benchmark instead")
     ap.add_argument("--next", action="store_true",
                     help="post filter, block-sparse add and sign iteration instead")
@@ -769,6 +892,17 @@ def main():
             cpu["gpu_max_abs_err_on_sample"] = float(np.max(np.abs(gv[:nv] - r.values)))
             cpu["max_abs_value_on_sample"] = float(np.max(np.abs(r.values)))
 
+    variants = None
+    if rank == 0 and world == 1 and not args.no_variants and args.workload == "water2048" \
+            and args.precision == "fp64":
+        sample = None
+        if cpu is not None and cpu.get("gpu_pattern_equal_on_sample"):
+            sample = (rows, r)
+        variants = measure_variants(ctx, A, dA, dC, eps, flops, local, sample)
+        fp64_ms = total_ms / args.steps
+        for e in variants["split_water"].values():
+            e["vs_fp64_path"] = round(fp64_ms / e["ms_p50"], 3)
+
     if rank == 0:
         srt = sorted(per_step)
         p99 = srt[min(len(srt) - 1, int(np.ceil(0.99 * len(srt))) - 1)]
@@ -795,6 +929,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(launches - 0),
             "clocks": clocks,
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
