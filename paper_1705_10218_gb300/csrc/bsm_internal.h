@@ -156,12 +156,12 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
 //           {end record (int64), columns, 0}, the blocks' column sizes (32 bytes);
 //   row_nt: tiles per row, -1 for a row left to the per-block kernel (more A
 //           blocks than the record sort handles);
-//   recs:   the kept products of each tile ordered by A block: {B's slice
-//           offset in 16-byte units, A block position in the row | slot << 16};
+//   recs:   the kept products of each tile ordered by A block, with their
+//           places in the staged copies (16-byte records, see k_split_panel.cu);
 //   fb_items, fb_seg: C blocks of the rows left to the per-block kernel and
 //           {0, their count} (fb_seg[1] must be zero before the prep kernel).
 struct PanelWs {
-  int2 *recs;       // [cap_prod]
+  int4 *recs;       // [cap_prod]
   int4 *tiles;      // [4 * cap C blocks]
   int32_t *row_nt;  // [rows]
   int32_t *fb_items;

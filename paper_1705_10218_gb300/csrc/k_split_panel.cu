@@ -221,8 +221,10 @@ __host__ __device__ constexpr uint32_t mma_idesc(uint32_t ab, uint32_t n, uint32
 // ---------------------------------------------------------------------------
 // Configuration and shared-memory layout
 // ---------------------------------------------------------------------------
-constexpr int kWarps = 10;
-constexpr int kGatherWarp0 = 0, kEpiWarp0 = 4, kMmaWarp = 8, kLoaderWarp = 9;
+constexpr int kWarps = 11;
+constexpr int kGatherWarp0 = 0, kEpiWarp0 = 4, kMmaWarp = 8, kLoaderWarp = 9;  // loaders: 9, 10
+constexpr int kMaxSegChunks = 256;  // chunks of one segment (at most its pieces)
+constexpr int kMailWords = 8;       // the loaders' shared words (multiple of 4: 16-byte layout)
 constexpr int kTileCols = 128;      // MMA M: C columns per tile
 constexpr int kMaxSlots = 32;       // C blocks per tile
 constexpr int kChunkPieces = 8;     // K pieces (16 bytes of every slice) per chunk
@@ -230,8 +232,8 @@ static_assert(kChunkPieces % 4 == 0 && kChunkPieces <= 32, "chunk table rows of 
 constexpr int kStages = 3;          // loader -> gather stages
 constexpr int kStageBytes = 16384;  // B blocks of one (tile, chunk)
 constexpr int kTileRing = 4;        // tile headers in flight
-constexpr int kTaStages = 3;        // TMEM operand stages
-constexpr int kNaMax = 1024;        // A blocks per row of the panel path (longer rows: per-block kernel)
+constexpr int kTaMax = 6;           // TMEM operand stages at most (as many as the columns allow)
+constexpr int kNaMax = 512;         // A blocks per row of the panel path (longer rows: per-block kernel)
 constexpr int kRecMax = kNaMax;     // so every tile has at most this many product records
 constexpr uint32_t kTmemCols = 512;
 constexpr int kSmemLimit = 232448;  // dynamic shared memory of one CTA (227 KB)
@@ -258,18 +260,17 @@ struct PanelCfg {
   static constexpr int PC = 4 * kChunkPieces;   // TMEM columns of one slice plane of a stage
   static constexpr int AC = NSL * PC;           // TMEM columns of an operand stage
   static constexpr int ABASE = 2 * DC;          // operand stages follow two accumulators
-  static_assert(ABASE + kTaStages * AC <= (int)kTmemCols, "TMEM columns");
+  static constexpr int TA = ((int)kTmemCols - ABASE) / AC < kTaMax ? ((int)kTmemCols - ABASE) / AC : kTaMax;
+  static_assert(TA >= 2 && ABASE + TA * AC <= (int)kTmemCols, "TMEM columns");
 };
 
 struct ChunkHdr {
   int32_t flags, tile, pi0, npieces;
-  int32_t nblk, pad[3];
-  uint32_t piece[kChunkPieces];  // block within the chunk | kp << 8 | pieces of the block << 16
-  // per slot and chunk block: byte offset in the stage, -1 no product, <= -2:
-  // B block -2-x read from global memory (the stage was full)
-  int32_t table[kMaxSlots][kChunkPieces];
+  // per slot and K piece of a product the stage had no room for: the piece's
+  // first row in B's slices in 16-byte units (the gather reads global memory)
+  int32_t farb[kMaxSlots][kChunkPieces];
   // per slot and K piece of the chunk: 0 no product; else kPiecePresent |
-  // (kPieceFar: in global memory, see table) | the piece's first row in the
+  // (kPieceFar: in global memory, see farb) | the piece's first row in the
   // stage in 16-byte units (bits 0-10) | the slice plane stride in 16-byte
   // units (bits 11-19)
   int32_t ptab[kMaxSlots][kChunkPieces];
@@ -287,7 +288,7 @@ struct TaNote {
 };
 struct Bars {
   uint64_t stg_full[kStages], stg_empty[kStages];
-  uint64_t ta_full[kTaStages], ta_empty[kTaStages];
+  uint64_t ta_full[kTaMax], ta_empty[kTaMax];
   uint64_t d_full[2], d_empty[2];
   uint64_t tile_full[kTileRing], tile_empty[kTileRing];
   uint64_t bop_full, bop_free, fin;
@@ -299,9 +300,10 @@ static_assert(sizeof(ChunkHdr) % 16 == 0 && sizeof(TileHdr) % 16 == 0, "16-byte 
 // bytes after the B operand buffer: segment block table (pmax words), stages,
 // record buffers, tile entries, headers, notes, barriers
 __host__ __device__ constexpr int panel_fixed_bytes(int pmax) {
-  return ((pmax * 4 + 15) & ~15) + kStages * kStageBytes + 2 * kRecMax * 8 + 3 * 64 +
-         kStages * (int)sizeof(ChunkHdr) + kTileRing * (int)sizeof(TileHdr) +
-         kTaStages * (int)sizeof(TaNote) + (((int)sizeof(Bars) + 15) & ~15);
+  return ((pmax * 4 + 15) & ~15) + kStages * kStageBytes + 2 * kRecMax * 16 + 3 * 64 +
+         kMaxSegChunks * 16 + ((pmax * 2 + 15) & ~15) + ((2 * (kMaxSegChunks + 1) + 15) & ~15) +
+         kMailWords * 4 + kStages * (int)sizeof(ChunkHdr) + kTileRing * (int)sizeof(TileHdr) +
+         kTaMax * (int)sizeof(TaNote) + (((int)sizeof(Bars) + 15) & ~15);
 }
 // the largest K pieces per segment that fit, one of them the zero pad piece
 __host__ __device__ constexpr int panel_pmax(int pb) {
@@ -326,8 +328,13 @@ struct PanelSmem {
   unsigned char *bop;     // B operand: pmax pieces x PB bytes
   int32_t *sblk;          // per block of the segment: first piece << 8 | pieces
   unsigned char *stage;   // kStages x kStageBytes
-  int2 *rbuf;             // 2 x kRecMax product records of tiles
+  int4 *rbuf;             // 2 x kRecMax product records of tiles
   int4 *ering;            // 3 tile entries of 64 bytes
+  int4 *sch;              // the segment's chunks: {first piece, pieces, first block, blocks}
+  int16_t *cho;           // chunk of each block of the segment
+  int16_t *crs;           // first record of each chunk of the current tile (+ end)
+  int32_t *mail;          // kMailWords: the loaders' row, segment end, pieces, chunks, failed flag
+
   ChunkHdr *chdr;
   TileHdr *thdr;
   TaNote *note;
@@ -342,16 +349,24 @@ __device__ __forceinline__ PanelSmem panel_carve(unsigned char *base, int pmax, 
   x += (pmax * 4 + 15) & ~15;
   p.stage = x;
   x += kStages * kStageBytes;
-  p.rbuf = reinterpret_cast<int2 *>(x);
-  x += 2 * kRecMax * 8;
+  p.rbuf = reinterpret_cast<int4 *>(x);
+  x += 2 * kRecMax * 16;
   p.ering = reinterpret_cast<int4 *>(x);
   x += 3 * 64;
+  p.sch = reinterpret_cast<int4 *>(x);
+  x += kMaxSegChunks * 16;
+  p.cho = reinterpret_cast<int16_t *>(x);
+  x += (pmax * 2 + 15) & ~15;
+  p.crs = reinterpret_cast<int16_t *>(x);
+  x += (2 * (kMaxSegChunks + 1) + 15) & ~15;
+  p.mail = reinterpret_cast<int32_t *>(x);
+  x += kMailWords * 4;
   p.chdr = reinterpret_cast<ChunkHdr *>(x);
   x += kStages * sizeof(ChunkHdr);
   p.thdr = reinterpret_cast<TileHdr *>(x);
   x += kTileRing * sizeof(TileHdr);
   p.note = reinterpret_cast<TaNote *>(x);
-  x += kTaStages * sizeof(TaNote);
+  x += kTaMax * sizeof(TaNote);
   p.bars = reinterpret_cast<Bars *>(x);
   return p;
 }
@@ -405,17 +420,28 @@ __device__ int panel_next_tile(const DevOut &C, const DevWs &ws, int cb, int c1,
 // cut by the same rule as in the loader (segments: blocks with at most pmax - 2
 // pieces; chunks: blocks with at most kChunkPieces pieces, never across a
 // segment).
-// A record: x = B's slice offset in 16-byte units; y = the A block's position
-// in the row (bits 0-11) | the C block's slot in the tile (bits 12-16) | the
-// byte offset / 16 of the B block in its chunk's stage (bits 17-26) | 1 << 27
-// when the stage has no room for it (the gather then reads global memory).
+// A record (16 bytes):
+//   x = the B block's slice offset in 16-byte units;
+//   y = the A block's position in the row (bits 0-11) | the C block's slot in
+//       the tile (bits 12-16) | its offset in the chunk's stage in 16-byte
+//       units (bits 17-26) | 1 << 27 when the stage had no room (the gather
+//       reads it from global memory) | 1 << 28 on the first record of a copy
+//       group;
+//   z = on a group's first record: the group's length in 16-byte units (the
+//       records of one A block in a tile, contiguous in B's row: one copy);
+//   w = the block's first K piece in the chunk (bits 0-3) | its pieces (bits
+//       4-7) | the slice plane stride in 16-byte units, columns x pieces
+//       (bits 8-16).
 // ---------------------------------------------------------------------------
 constexpr int kPrepThreads = 256;
 __device__ __forceinline__ int rec_apos(int y) { return y & 0xFFF; }
 __device__ __forceinline__ int rec_slot(int y) { return (y >> 12) & 31; }
-__device__ __forceinline__ int rec_off(int y) { return ((y >> 17) & 1023) * 16; }
-__device__ __forceinline__ bool rec_global(int y) { return (y >> 27) & 1; }
-static_assert(kNaMax <= 4096 && kMaxSlots <= 32 && kStageBytes <= 16384, "record bit fields");
+__device__ __forceinline__ int rec_off16(int y) { return (y >> 17) & 1023; }
+__device__ __forceinline__ bool rec_far(int y) { return (y >> 27) & 1; }
+__device__ __forceinline__ bool rec_head(int y) { return (y >> 28) & 1; }
+constexpr int kRecFar = 1 << 27, kRecHead = 1 << 28;
+static_assert(kNaMax <= 4096 && kMaxSlots <= 32 && kStageBytes <= 16384 && kChunkPieces <= 15,
+              "record bit fields");
 
 __global__ void __launch_bounds__(kPrepThreads) k_panel_prep(DevMat A, DevMat B, DevOut C, DevWs ws,
                                                               PanelWs pw, const DevStatus *st,
@@ -424,12 +450,13 @@ __global__ void __launch_bounds__(kPrepThreads) k_panel_prep(DevMat A, DevMat B,
   if (st->overflow) return;
   __shared__ int32_t hist[kNaMax];
   __shared__ uint8_t np_s[kNaMax];
+  __shared__ int16_t pi_s[kNaMax];   // a block's first piece in its segment
   __shared__ int16_t cs[kNaMax + 1];
-  __shared__ int2 srec[kRecMax];
+  __shared__ int4 srec[kRecMax];
   __shared__ int64_t sstart[kMaxSlots + 1];
   __shared__ int32_t t_ns, t_width, t_nch;
   __shared__ int64_t t_P0, t_P1;
-  __shared__ uint8_t t_cj[kMaxSlots];
+  __shared__ __align__(16) uint8_t t_cj[kMaxSlots];  // also read as two 16-byte words
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = blockIdx.x; i < A.nbr; i += gridDim.x) {
     const int32_t c0 = C.row_ptr[i], c1 = C.row_ptr[i + 1];
@@ -463,6 +490,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_panel_prep(DevMat A, DevMat B,
           cs[nch++] = (int16_t)b;
           chunk = 0;
         }
+        pi_s[b] = (int16_t)seg;
         chunk += np;
         seg += np;
       }
@@ -528,27 +556,47 @@ __global__ void __launch_bounds__(kPrepThreads) k_panel_prep(DevMat A, DevMat B,
           else hi = mid;
         }
         const int pos = atomicAdd(&hist[apos], 1);  // hist[a] ends as the start of a + 1
-        srec[pos] = make_int2((int)(unit16 * B.blk_off[pr.y]), apos | (lo << 12));
+        srec[pos] = make_int4((int)(unit16 * B.blk_off[pr.y]), apos | (lo << 12), 0, 0);
       }
       __syncthreads();
-      // stage offsets: one warp per chunk, the chunk's records in order
-      for (int c = warp; c < nch; c += kPrepThreads / 32) {
-        const int r0 = cs[c] == 0 ? 0 : hist[cs[c] - 1], r1 = hist[cs[c + 1] - 1];
-        int used = 0;
-        for (int r = r0; r < r1; r += 32) {
-          const int k = r + lane;
-          int bytes = 0;
-          int2 rec = make_int2(0, 0);
-          if (k < r1) {
-            rec = srec[k];
-            bytes = nsl * (int)t_cj[rec_slot(rec.y)] * (int)np_s[rec_apos(rec.y)] * 16;
+      // within one A block, ascending B offsets: the records of a block are then
+      // consecutive blocks of B's row k, one contiguous range
+      for (int x = tid; x < na; x += kPrepThreads) {
+        const int b0 = x == 0 ? 0 : hist[x - 1], b1 = hist[x];
+        for (int u = b0 + 1; u < b1; u++) {
+          const int4 key = srec[u];
+          int v = u - 1;
+          while (v >= b0 && srec[v].x > key.x) {
+            srec[v + 1] = srec[v];
+            v--;
           }
-          const int incl = warp_incl_scan(bytes, lane);
-          const int off = used + incl - bytes;
-          if (k < r1)
-            srec[k].y = rec.y | (off + bytes <= kStageBytes ? (off >> 4) << 17 : 1 << 27);
-          const int st_bytes = (k < r1 && off + bytes <= kStageBytes) ? bytes : 0;
-          used += __reduce_add_sync(0xffffffffu, st_bytes);
+          srec[v + 1] = key;
+        }
+      }
+      __syncthreads();
+      // copy groups and stage offsets: one thread per chunk, its records in order
+      for (int c = tid; c < nch; c += kPrepThreads) {
+        const int r0 = cs[c] == 0 ? 0 : hist[cs[c] - 1], r1 = hist[cs[c + 1] - 1];
+        const int pi0 = pi_s[cs[c]];
+        int used = 0;  // 16-byte units
+        for (int k = r0; k < r1;) {
+          const int apos = rec_apos(srec[k].y);
+          int g1 = k + 1;
+          while (g1 < r1 && rec_apos(srec[g1].y) == apos) g1++;
+          const int np = np_s[apos];
+          const int last = g1 - 1;
+          const int len = srec[last].x + nsl * (int)t_cj[rec_slot(srec[last].y)] * np - srec[k].x;
+          const bool staged = (used + len) * 16 <= kStageBytes;
+          for (int u = k; u < g1; u++) {
+            int4 rc = srec[u];
+            const int cjs = t_cj[rec_slot(rc.y)];
+            rc.y |= (staged ? (used + rc.x - srec[k].x) << 17 : kRecFar) | (u == k ? kRecHead : 0);
+            rc.z = (u == k && staged) ? len : 0;
+            rc.w = (pi_s[apos] - pi0) | (np << 4) | ((cjs * np) << 8);
+            srec[u] = rc;
+          }
+          if (staged) used += len;
+          k = g1;
         }
       }
       __syncthreads();
@@ -592,71 +640,131 @@ __device__ __forceinline__ TileEntry read_entry(const int4 *e) {
   return t;
 }
 
+// the two loader warps
+__device__ __forceinline__ void loaders_sync() {
+  __syncwarp();  // the aligned barrier wants the warp converged
+  asm volatile("bar.sync 1, 64;\n" ::: "memory");
+}
+
 template <int PREC, int NR>
-__device__ bool panel_loader(const PanelArgs &a, const PanelSmem &sm, int lane) {
+__device__ bool panel_loader(const PanelArgs &a, const PanelSmem &sm, int lw, int lane) {
   using Cfg = PanelCfg<PREC, NR>;
   const DevMat &A = a.A;
   const DevOut &C = a.C;
   const int pmax = a.pmax;
-  uint32_t chunk_seq = 0, tile_seq = 0, seg_seq = 0;
+  uint32_t seq_base = 0, tile_seq = 0, seg_seq = 0;
   const uint32_t bop = smem_u32(sm.bop);
   const uint32_t sblk_u = smem_u32(sm.sblk);
+  volatile int32_t *mail = sm.mail;  // [0] row, [1] segment end, [2] its pieces, [3] its chunks, [4] failed
+  if (lw == 0 && lane == 0) mail[4] = 0;
+  loaders_sync();
+  bool failed = false;
+  // a wait that gives up marks the loaders failed; they keep to the barrier
+  // protocol (no further waits) until both leave the row loop together
+  auto wait = [&](uint32_t bar, uint32_t parity) {
+    if (failed) return false;
+    if (pb_wait(bar, parity)) return true;
+    failed = true;
+    mail[4] = 1;
+    return false;
+  };
   for (;;) {
-    unsigned long long w = 0;
-    if (lane == 0) w = atomicAdd(a.work, 1ull);
-    w = __shfl_sync(0xffffffffu, w, 0);
-    if (w >= (unsigned long long)A.nbr) break;
-    const int i = (int)w;
-    const int32_t c0 = C.row_ptr[i];
+    if (lw == 0 && lane == 0) {
+      const unsigned long long w = atomicAdd(a.work, 1ull);
+      mail[0] = (int)(w < (unsigned long long)A.nbr ? w : (unsigned long long)A.nbr);
+    }
+    loaders_sync();
+    const int i = mail[0];
+    failed = mail[4] != 0;
+    loaders_sync();  // both have read the mailbox before it changes
+    if (i >= A.nbr || failed) break;
     const int nt = a.pw.row_nt[i];
     if (nt <= 0) continue;  // no C blocks, or left to the per-block kernel
+    const int32_t c0 = C.row_ptr[i];
     const int32_t a0 = A.row_ptr[i], na = A.row_ptr[i + 1] - a0;
     const int r = A.row_sizes[i];
     if (r > NR) {  // the host routes such rows elsewhere; never silently wrong
-      if (lane == 0) atomicOr(const_cast<int32_t *>(&a.st->error), 2);
+      if (lw == 0 && lane == 0) atomicOr(const_cast<int32_t *>(&a.st->error), 2);
       continue;
     }
     int sa = 0;
     for (;;) {  // segments of A's row
-      // blocks [sa, sb): at most pmax - 2 pieces (pieces P and P + 1 are zero
-      // pads: a chunk's last K step may reach one piece past the segment, an
-      // empty row's only step two)
-      int sb = sa, P = 0;
-      for (;;) {
-        const int b = sb + lane;
-        int np = 0;
-        if (b < na) np = (A.col_sizes[A.col_idx[a0 + b]] + Cfg::PIECE - 1) / Cfg::PIECE;
-        const int incl = warp_incl_scan(np, lane);
-        const bool fits = b < na && P + incl <= pmax - 2;
-        const int k = __popc(__ballot_sync(0xffffffffu, fits));
-        if (fits) sm.sblk[b - sa] = ((P + incl - np) << 8) | np;
-        if (k > 0) P += __shfl_sync(0xffffffffu, incl, k - 1);
-        sb += k;
-        if (k < 32) break;
-      }
-      // the B operand of the segment, once the previous segment's MMAs are done
-      if (seg_seq > 0 && !pb_wait(PB_BAR(bop_free), (seg_seq - 1) & 1u)) return false;
-      {
-        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        for (int x = lane; x < 2 * Cfg::PB / 16; x += 32)
-          reinterpret_cast<uint4 *>(sm.bop + (size_t)P * Cfg::PB)[x] = z;
-        fence_async_smem();
-        __syncwarp();
-        for (int b = sa + lane; b < sb; b += 32) {
-          const int e = sm.sblk[b - sa], pi = e >> 8, np = e & 255;
-          const unsigned char *src = a.a_left + Cfg::UNIT * A.blk_off[a0 + b];
-          const uint32_t bytes = (uint32_t)(r * 16);
-          for (int q = 0; q < Cfg::NSL; q++)
-            for (int kp = 0; kp < np; kp++) {
-              pb_expect_tx(PB_BAR(bop_full), bytes);
-              bulk_g2s(bop + (uint32_t)((pi + kp) * Cfg::PB + q * NR * 16),
-                       src + (size_t)(q * np + kp) * r * 16, bytes, PB_BAR(bop_full));
-            }
+      if (lw == 0) {
+        // blocks [sa, sb): at most pmax - 2 pieces (pieces P and P + 1 are zero
+        // pads: a chunk's last K step may reach one piece past the segment, an
+        // empty row's only step two)
+        int sb = sa, P = 0;
+        for (;;) {
+          const int b = sb + lane;
+          int np = 0;
+          if (b < na) np = (A.col_sizes[A.col_idx[a0 + b]] + Cfg::PIECE - 1) / Cfg::PIECE;
+          const int incl = warp_incl_scan(np, lane);
+          const bool fits = b < na && P + incl <= pmax - 2;
+          const int k = __popc(__ballot_sync(0xffffffffu, fits));
+          if (fits) sm.sblk[b - sa] = ((P + incl - np) << 8) | np;
+          if (k > 0) P += __shfl_sync(0xffffffffu, incl, k - 1);
+          sb += k;
+          if (k < 32) break;
         }
         __syncwarp();
-        if (lane == 0) pb_arrive(PB_BAR(bop_full));
+        // the segment's chunks: whole blocks, at most kChunkPieces pieces each
+        // (the same cut as the prep kernel's)
+        if (lane == 0) {
+          int n = 0, cp = 0;
+          for (int b = sa; b < sb; b++) {
+            const int e = sm.sblk[b - sa], np = e & 255;
+            if (b == sa || cp + np > kChunkPieces) {
+              if (n == kMaxSegChunks) {  // cannot happen: chunks average over 4 pieces
+                atomicOr(const_cast<int32_t *>(&a.st->error), 2);
+                break;
+              }
+              if (n > 0) sm.sch[n - 1].y = cp;
+              sm.sch[n] = make_int4(e >> 8, 0, b, 0);
+              n++;
+              cp = 0;
+            }
+            sm.cho[b - sa] = (int16_t)(n - 1);
+            cp += np;
+            sm.sch[n - 1].w++;
+          }
+          if (n > 0) sm.sch[n - 1].y = cp;
+          if (n == 0) {  // an empty row: one chunk of no pieces per tile
+            sm.sch[0] = make_int4(P, 0, sa, 0);
+            n = 1;
+          }
+          mail[1] = sb;
+          mail[2] = P;
+          mail[3] = n;
+        }
+        // the B operand of the segment, once the previous segment's MMAs are done
+        if (seg_seq > 0) wait(PB_BAR(bop_free), (seg_seq - 1) & 1u);
+        if (!failed) {
+          const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+          for (int x = lane; x < 2 * Cfg::PB / 16; x += 32)
+            reinterpret_cast<uint4 *>(sm.bop + (size_t)P * Cfg::PB)[x] = z;
+          fence_async_smem();
+          __syncwarp();
+          for (int b = sa + lane; b < sb; b += 32) {
+            const int e = sm.sblk[b - sa], pi = e >> 8, np = e & 255;
+            const unsigned char *src = a.a_left + Cfg::UNIT * A.blk_off[a0 + b];
+            const uint32_t bytes = (uint32_t)(r * 16);
+            for (int q = 0; q < Cfg::NSL; q++)
+              for (int kp = 0; kp < np; kp++) {
+                pb_expect_tx(PB_BAR(bop_full), bytes);
+                bulk_g2s(bop + (uint32_t)((pi + kp) * Cfg::PB + q * NR * 16),
+                         src + (size_t)(q * np + kp) * r * 16, bytes, PB_BAR(bop_full));
+              }
+          }
+          __syncwarp();
+          if (lane == 0) pb_arrive(PB_BAR(bop_full));
+        }
       }
-      // tile entries two ahead, records one ahead (asynchronous copies)
+      loaders_sync();
+      const int sb = mail[1], P = mail[2], nch = mail[3];
+      failed = mail[4] != 0;
+      // tiles: loader 0 fetches the tile entries two ahead and the records one
+      // ahead (asynchronous copies), writes the tile header and each chunk's
+      // first record; both loaders then take alternate chunks
       const int4 *entries = a.pw.tiles + 4 * (int64_t)c0;
       auto fetch_entry = [&](int t) {
         if (t < nt && lane < 4)
@@ -666,176 +774,152 @@ __device__ bool panel_loader(const PanelArgs &a, const PanelSmem &sm, int lane) 
       auto fetch_recs = [&](int t) {
         if (t < nt) {
           const TileEntry e = read_entry(sm.ering + 4 * (t % 3));
-          const int64_t n = e.P1 - e.P0;
-          const int cnt = (int)n;  // at most kRecMax
-          int2 *dst = sm.rbuf + (t & 1) * kRecMax;
-          for (int k = lane; k < cnt; k += 32) cp_async8(smem_u32(dst + k), a.pw.recs + e.P0 + k);
+          const int cnt = (int)(e.P1 - e.P0);  // at most kRecMax
+          int4 *dst = sm.rbuf + (t & 1) * kRecMax;
+          for (int k = lane; k < cnt; k += 32) cp_async16(smem_u32(dst + k), a.pw.recs + e.P0 + k);
         }
         cp_commit();
       };
-      fetch_entry(0);
-      fetch_entry(1);
-      cp_wait1();
-      __syncwarp();
-      fetch_recs(0);
+      if (lw == 0) {
+        fetch_entry(0);
+        fetch_entry(1);
+        cp_wait1();
+        __syncwarp();
+        fetch_recs(0);
+      }
       for (int t = 0; t < nt; t++) {
-        fetch_entry(t + 2);
-        cp_wait1();  // the records of tile t and the entry of tile t + 1 are in
-        __syncwarp();
-        fetch_recs(t + 1);
-        const TileEntry e = read_entry(sm.ering + 4 * (t % 3));
-        const uint8_t *ecj = reinterpret_cast<const uint8_t *>(sm.ering + 4 * (t % 3) + 2);
         const uint32_t rb_u = smem_u32(sm.rbuf + (t & 1) * kRecMax);
-        const int64_t nrec = e.P1 - e.P0;
-        const int nslots = e.ns;
-        const bool last_tile = t == nt - 1;
         const int tt = (int)(tile_seq % kTileRing);
-        if (tile_seq >= (uint32_t)kTileRing &&
-            !pb_wait(PB_BAR(tile_empty[tt]), (tile_seq / kTileRing - 1) & 1u)) {
-          cp_wait0();
-          return false;
-        }
-        TileHdr &T = sm.thdr[tt];
-        const uint32_t tcj_u = smem_u32(&T) + (uint32_t)offsetof(TileHdr, cj);
-        const bool in = lane < nslots;
-        const int cj = in ? ecj[lane] : 0;
-        const int cincl = warp_incl_scan(cj, lane);
-        if (in) {
-          T.gb[lane] = e.cb0 + lane;
-          T.cj[lane] = (uint8_t)cj;
-          T.mst[lane] = (uint8_t)(cincl - cj);
-          for (int c = 0; c < cj; c++) T.col_slot[cincl - cj + c] = (uint8_t)lane;
-        }
-        for (int m = e.width + lane; m < kTileCols; m += 32) T.col_slot[m] = 255;
-        if (lane == 0) {
-          T.flags = (sa > 0 ? kAccum : 0) | (sb >= na ? kLastSeg : 0);
-          T.r = r;
-          T.nslots = nslots;
-        }
-        __syncwarp();
-        if (lane == 0) pb_arrive(PB_BAR(tile_full[tt]));
-        // the first record of the segment (records are in ascending block order)
-        int64_t rc = 0;
-        if (sa > 0) {
-          for (;;) {
-            const int64_t k = rc + lane;
-            const bool before = k < nrec && rec_apos(lds64(rb_u + 8u * (uint32_t)k).y) < sa;
-            const int cnt = __popc(__ballot_sync(0xffffffffu, before));
-            rc += cnt;
-            if (cnt < 32) break;
+        if (lw == 0) {
+          fetch_entry(t + 2);
+          cp_wait1();  // the records of tile t and the entry of tile t + 1 are in
+          __syncwarp();
+          fetch_recs(t + 1);
+          const TileEntry e = read_entry(sm.ering + 4 * (t % 3));
+          const uint8_t *ecj = reinterpret_cast<const uint8_t *>(sm.ering + 4 * (t % 3) + 2);
+          const int nrec = (int)(e.P1 - e.P0);
+          if (tile_seq >= (uint32_t)kTileRing)
+            wait(PB_BAR(tile_empty[tt]), (tile_seq / kTileRing - 1) & 1u);
+          TileHdr &T = sm.thdr[tt];
+          const bool in = lane < e.ns;
+          const int cj = in ? ecj[lane] : 0;
+          const int cincl = warp_incl_scan(cj, lane);
+          if (in) {
+            T.gb[lane] = e.cb0 + lane;
+            T.cj[lane] = (uint8_t)cj;
+            T.mst[lane] = (uint8_t)(cincl - cj);
+            for (int c = 0; c < cj; c++) T.col_slot[cincl - cj + c] = (uint8_t)lane;
           }
-        }
-        int pb = sa;
-        bool first = true;
-        do {
-          const int sg = (int)(chunk_seq % kStages);
-          if (chunk_seq >= (uint32_t)kStages &&
-              !pb_wait(PB_BAR(stg_empty[sg]), (chunk_seq / kStages - 1) & 1u)) {
-            cp_wait0();
-            return false;
+          for (int m = e.width + lane; m < kTileCols; m += 32) T.col_slot[m] = 255;
+          if (lane == 0) {
+            T.flags = (sa > 0 ? kAccum : 0) | (sb >= na ? kLastSeg : 0);
+            T.r = r;
+            T.nslots = e.ns;
           }
-          fence_async_smem();  // the gather's reads of the stage before the copies into it
+          // each chunk's first record: records are in ascending block order
+          auto chunk_of = [&](int k) {
+            const int ap = rec_apos(lds32(rb_u + 16u * (uint32_t)k + 4u));
+            return ap < sa ? -1 : ap >= sb ? nch : (int)sm.cho[ap - sa];
+          };
+          for (int k = lane; k < nrec; k += 32) {
+            const int ck = chunk_of(k), cprev = k == 0 ? -1 : chunk_of(k - 1);
+            for (int cc = cprev + 1; cc <= ck && cc <= nch; cc++) sm.crs[cc] = (int16_t)k;
+          }
+          if (lane == 0) {  // chunks after the last record's: empty, ending at nrec
+            const int clast = nrec == 0 ? -1 : chunk_of(nrec - 1);
+            if (clast < nch)
+              for (int cc = clast + 1; cc <= nch; cc++) sm.crs[cc] = (int16_t)nrec;
+          }
+          __syncwarp();
+          if (lane == 0 && !failed) pb_arrive(PB_BAR(tile_full[tt]));
+        }
+        loaders_sync();  // the tile's header, records and chunk starts are ready
+        failed = mail[4] != 0;
+        for (int c = lw; c < nch && !failed; c += 2) {
+          const uint32_t seq = seq_base + (uint32_t)c;
+          const int sg = (int)(seq % kStages);
+          if (seq >= (uint32_t)kStages && !wait(PB_BAR(stg_empty[sg]), (seq / kStages - 1) & 1u))
+            break;
+          const int4 ch = sm.sch[c];  // {first piece, pieces, first block, blocks}
           ChunkHdr &H = sm.chdr[sg];
           const uint32_t stage = smem_u32(sm.stage + (size_t)sg * kStageBytes);
           const uint32_t full = PB_BAR(stg_full[sg]);
-          // the chunk's A blocks: from pb, at most kChunkPieces pieces
-          const int pi0 = pb < sb ? (sm.sblk[pb - sa] >> 8) : P;
-          const int bj = pb + lane;
-          const int ej = (lane < kChunkPieces && bj < sb) ? lds32(sblk_u + 4u * (uint32_t)(bj - sa)) : 0;
-          const int pij = ej >> 8, npj = ej & 255;
-          const bool fit = lane < kChunkPieces && bj < sb && pij + npj - pi0 <= kChunkPieces;
-          const int nbk = __popc(__ballot_sync(0xffffffffu, fit));
-          const int pend_pieces = __shfl_sync(0xffffffffu, pij + npj, nbk > 0 ? nbk - 1 : 0);
-          const int npieces = nbk > 0 ? pend_pieces - pi0 : 0;
-          if (fit)
-            for (int kp = 0; kp < npj; kp++)
-              H.piece[pij - pi0 + kp] = (uint32_t)(lane | (kp << 8) | (npj << 16));
 #pragma unroll
-          for (int x = 0; x < kChunkPieces / 4; x++) {
-            reinterpret_cast<int4 *>(H.table[lane])[x] = make_int4(-1, -1, -1, -1);
+          for (int x = 0; x < kChunkPieces / 4; x++)
             reinterpret_cast<int4 *>(H.ptab[lane])[x] = make_int4(0, 0, 0, 0);
-          }
           __syncwarp();
-          const int pend = pb + nbk;
+          const int r0 = sm.crs[c], r1 = sm.crs[c + 1];
           uint32_t used = 0;
-          for (;;) {  // the chunk's records, 32 at a time (a prefix: ascending blocks)
-            const int64_t k = rc + lane;
-            int2 rec = make_int2(0, 0);
-            bool valid = false;
-            if (k < nrec) {
-              rec = lds64(rb_u + 8u * (uint32_t)k);
-              valid = rec_apos(rec.y) < pend;
-            }
-            const int nv = __popc(__ballot_sync(0xffffffffu, valid));
+          for (int k0 = r0; k0 < r1; k0 += 32) {
+            const int k = k0 + lane;
             uint32_t staged = 0;
-            if (valid) {
-              const int apos = rec_apos(rec.y), slot = rec_slot(rec.y);
-              const int eb = lds32(sblk_u + 4u * (uint32_t)(apos - sa));
-              const int np = eb & 255, ip0 = (eb >> 8) - pi0;
-              const int cjs = lds8(tcj_u + (uint32_t)slot);
-              int32_t ent, pe;
-              if (!rec_global(rec.y)) {
-                ent = rec_off(rec.y);
-                staged = (uint32_t)(Cfg::NSL * cjs * np * 16);
-                bulk_g2s(stage + (uint32_t)ent, a.b_right + 16 * (int64_t)rec.x, staged, full);
-                pe = kPiecePresent | ((ent >> 4) + 0) | ((cjs * np) << 11);
+            if (k < r1) {
+              const uint4 rec = lds128(rb_u + 16u * (uint32_t)k);
+              const int y = (int)rec.y, w = (int)rec.w;
+              const int slot = rec_slot(y), ip0 = w & 15, np = (w >> 4) & 15, pstr = (w >> 8) & 511;
+              const int cjs = pstr / np;
+              if (!rec_far(y)) {
+                const int off16 = rec_off16(y);
+                if (rec_head(y)) {
+                  staged = rec.z * 16u;
+                  bulk_g2s(stage + 16u * (uint32_t)off16, a.b_right + 16 * (int64_t)rec.x, staged, full);
+                }
+                for (int kp = 0; kp < np; kp++)
+                  H.ptab[slot][ip0 + kp] = kPiecePresent | (off16 + kp * cjs) | (pstr << 11);
               } else {  // no room in the stage: the gather reads it from global memory
-                ent = -2 - rec.x;
-                pe = kPiecePresent | kPieceFar;
+                for (int kp = 0; kp < np; kp++) {
+                  H.ptab[slot][ip0 + kp] = kPiecePresent | kPieceFar | (pstr << 11);
+                  H.farb[slot][ip0 + kp] = (int)rec.x + kp * cjs;
+                }
               }
-              H.table[slot][apos - pb] = ent;
-              for (int kp = 0; kp < np; kp++)
-                H.ptab[slot][ip0 + kp] = (pe & kPieceFar) ? pe : pe + kp * cjs;
             }
             used += __reduce_add_sync(0xffffffffu, staged);
-            rc += nv;
-            if (nv < 32) break;
           }
-          const bool last_chunk = pend >= sb;
           if (lane == 0) {
-            H.flags = (first ? kFirstChunk : 0) | (last_chunk ? kLastChunk : 0) |
-                      (first && t == 0 ? kFirstSegChunk : 0) |
-                      (last_chunk && last_tile ? kLastSegChunk : 0);
+            H.flags = (c == 0 ? kFirstChunk : 0) | (c == nch - 1 ? kLastChunk : 0) |
+                      (t == 0 && c == 0 ? kFirstSegChunk : 0) |
+                      (t == nt - 1 && c == nch - 1 ? kLastSegChunk : 0);
             H.tile = (int32_t)tile_seq;
-            H.pi0 = pi0;
-            H.npieces = npieces;
-            H.nblk = nbk;
+            H.pi0 = ch.x;
+            H.npieces = ch.y;
           }
           __syncwarp();
           // one arrival with the chunk's staged bytes (copies that landed already
           // took the transaction count below zero; it returns to zero here)
           if (lane == 0) pb_arrive_expect_tx(full, used);
-          chunk_seq++;
-          first = false;
-          pb = pend;
-        } while (pb < sb);
+        }
+        loaders_sync();  // both are done with the tile's records and chunk starts
+        failed = mail[4] != 0;
+        seq_base += (uint32_t)nch;
         tile_seq++;
       }
-      cp_wait0();
-      __syncwarp();
+      if (lw == 0) {
+        cp_wait0();
+        __syncwarp();
+      }
       seg_seq++;
-      if (sb >= na) break;
+      if (sb >= na || failed) break;
       sa = sb;
     }
   }
+  if (lw != 0) return !failed;
   // no more rows: end markers for the gather (chunk) and the epilogue (tile)
   {
-    const int sg = (int)(chunk_seq % kStages);
-    if (chunk_seq >= (uint32_t)kStages &&
-        !pb_wait(PB_BAR(stg_empty[sg]), (chunk_seq / kStages - 1) & 1u))
+    const int sg = (int)(seq_base % kStages);
+    if (seq_base >= (uint32_t)kStages && !wait(PB_BAR(stg_empty[sg]), (seq_base / kStages - 1) & 1u))
       return false;
     if (lane == 0) sm.chdr[sg].flags = kEnd;
     __syncwarp();
     if (lane == 0) pb_arrive(PB_BAR(stg_full[sg]));
     const int tt = (int)(tile_seq % kTileRing);
     if (tile_seq >= (uint32_t)kTileRing &&
-        !pb_wait(PB_BAR(tile_empty[tt]), (tile_seq / kTileRing - 1) & 1u))
+        !wait(PB_BAR(tile_empty[tt]), (tile_seq / kTileRing - 1) & 1u))
       return false;
     if (lane == 0) sm.thdr[tt].flags = kEnd;
     __syncwarp();
     if (lane == 0) pb_arrive(PB_BAR(tile_full[tt]));
   }
-  return true;
+  return !failed;
 }
 
 // ---------------------------------------------------------------------------
@@ -848,22 +932,22 @@ __device__ bool panel_gather(const PanelArgs &a, const PanelSmem &sm, uint32_t t
   const int m = warp * 32 + lane;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   for (uint32_t seq = 0;; seq++) {
-    const int sg = (int)(seq % kStages), ta = (int)(seq % kTaStages);
+    const int sg = (int)(seq % kStages), ta = (int)(seq % Cfg::TA);
     if (!pb_wait(PB_BAR(stg_full[sg]), (seq / kStages) & 1u)) return false;
     const ChunkHdr &H = sm.chdr[sg];
     const int flags = H.flags;
     if (flags & kEnd) {
       // the MMA has read this stage's previous note once its MMAs completed
-      if (seq >= (uint32_t)kTaStages &&
-          !pb_wait(PB_BAR(ta_empty[ta]), (seq / kTaStages - 1) & 1u))
+      if (seq >= (uint32_t)Cfg::TA &&
+          !pb_wait(PB_BAR(ta_empty[ta]), (seq / Cfg::TA - 1) & 1u))
         return false;
       if (m == 0) sm.note[ta].flags = kEnd;
       __syncwarp();
       if (lane == 0) pb_arrive(PB_BAR(ta_full[ta]));
       return true;
     }
-    if (seq >= (uint32_t)kTaStages &&
-        !pb_wait(PB_BAR(ta_empty[ta]), (seq / kTaStages - 1) & 1u))
+    if (seq >= (uint32_t)Cfg::TA &&
+        !pb_wait(PB_BAR(ta_empty[ta]), (seq / Cfg::TA - 1) & 1u))
       return false;
     tc_after();
     const int tile = H.tile, npieces = H.npieces;
@@ -876,9 +960,7 @@ __device__ bool panel_gather(const PanelArgs &a, const PanelSmem &sm, uint32_t t
       c = m - lds8(tbytes + (uint32_t)offsetof(TileHdr, mst) + (uint32_t)slot);
     }
     const uint32_t hb = smem_u32(&H);
-    const uint32_t trow = hb + (uint32_t)offsetof(ChunkHdr, table) + (uint32_t)(slot & 31) * (4 * kChunkPieces);
     const uint32_t prow = hb + (uint32_t)offsetof(ChunkHdr, ptab) + (uint32_t)(slot & 31) * (4 * kChunkPieces);
-    const uint32_t pmap = hb + (uint32_t)offsetof(ChunkHdr, piece);
     const uint32_t stage = smem_u32(sm.stage + (size_t)sg * kStageBytes);
     const uint32_t zero = smem_u32(&sm.bars->zero);
     const int steps = npieces > 0 ? (npieces + 1) >> 1 : 1;
@@ -921,22 +1003,20 @@ __device__ bool panel_gather(const PanelArgs &a, const PanelSmem &sm, uint32_t t
       }
     }
     if (__any_sync(0xffffffffu, far)) {  // rare: the stage had no room for some products
+      const uint32_t frow = hb + (uint32_t)offsetof(ChunkHdr, farb) + (uint32_t)(slot & 31) * (4 * kChunkPieces);
 #pragma unroll
       for (int ip = 0; ip < kChunkPieces; ip++) {
-        if (ip < npieces && slot != 255) {
-          const int pc = lds32(pmap + 4u * (uint32_t)ip);
-          const int bl = pc & 255, kp = (pc >> 8) & 255, np = pc >> 16;
-          const int ent = lds32(trow + 4u * (uint32_t)bl);
-          if (ent <= -2) {
-            const unsigned char *src = a.b_right + 16 * (int64_t)(-2 - ent) + (kp * cj + c) * 16;
+        if ((pe[ip] & kPiecePresent) && (pe[ip] & kPieceFar)) {
+          const int base = lds32(frow + 4u * (uint32_t)ip);
+          const int pstr = (pe[ip] >> 11) & 511;
+          const unsigned char *src = a.b_right + 16 * ((int64_t)base + c);
 #pragma unroll
-            for (int q = 0; q < Cfg::NSL; q++) {
-              const uint4 x = __ldg(reinterpret_cast<const uint4 *>(src + q * cj * np * 16));
-              v[ip >> 1][q][4 * (ip & 1)] = x.x;
-              v[ip >> 1][q][4 * (ip & 1) + 1] = x.y;
-              v[ip >> 1][q][4 * (ip & 1) + 2] = x.z;
-              v[ip >> 1][q][4 * (ip & 1) + 3] = x.w;
-            }
+          for (int q = 0; q < Cfg::NSL; q++) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(src + 16 * (int64_t)q * pstr));
+            v[ip >> 1][q][4 * (ip & 1)] = x.x;
+            v[ip >> 1][q][4 * (ip & 1) + 1] = x.y;
+            v[ip >> 1][q][4 * (ip & 1) + 2] = x.z;
+            v[ip >> 1][q][4 * (ip & 1) + 3] = x.w;
           }
         }
       }
@@ -978,8 +1058,8 @@ __device__ bool panel_mma(const PanelSmem &sm, uint32_t tmem) {
   uint32_t seg = 0;
   bool ok = true;
   for (uint32_t seq = 0;; seq++) {
-    const int ta = (int)(seq % kTaStages);
-    if (!pb_wait(PB_BAR(ta_full[ta]), (seq / kTaStages) & 1u)) {
+    const int ta = (int)(seq % Cfg::TA);
+    if (!pb_wait(PB_BAR(ta_full[ta]), (seq / Cfg::TA) & 1u)) {
       ok = false;
       break;
     }
@@ -1116,7 +1196,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_numeric_split_panel(PanelArg
       pb_init(smem_u32(&b.stg_full[x]), 1);
       pb_init(smem_u32(&b.stg_empty[x]), 4);
     }
-    for (int x = 0; x < kTaStages; x++) {
+    for (int x = 0; x < kTaMax; x++) {
       pb_init(smem_u32(&b.ta_full[x]), 4);
       pb_init(smem_u32(&b.ta_empty[x]), 1);
     }
@@ -1139,8 +1219,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_numeric_split_panel(PanelArg
   tc_after();
   const uint32_t tmem = sm.bars->tmem_holder;
   bool ok = true;
-  if (warp == kLoaderWarp) {
-    ok = panel_loader<PREC, NR>(a, sm, lane);
+  if (warp >= kLoaderWarp) {
+    ok = panel_loader<PREC, NR>(a, sm, warp - kLoaderWarp, lane);
   } else if (warp == kMmaWarp) {
     if (lane == 0) ok = panel_mma<PREC, NR>(sm, tmem);
   } else if (warp >= kEpiWarp0) {
