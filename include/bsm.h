@@ -261,13 +261,26 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * Request loop (serving). Independent multiplies C = A.A of square block-sparse
  * systems of different sizes (the application's repeated multiplies, Sec. 1)
  * arrive one by one. The server keeps `slots` lanes, each a context with its
- * own stream, workspace and worker thread. Requests wait in a FIFO queue; a
- * free lane takes the head as soon as its device-memory footprint (an upper
- * bound computed at submission) fits the budget beside the requests already
- * held, uploads it, runs it while the other lanes run theirs, leaves the result
- * in page-locked host memory and releases the device memory. Admission needs
- * no call from the caller. Results wait until taken (copied out) or released
- * after use in place. The server functions may be called from any thread;
+ * own stream, workspace and worker thread. A free lane takes the next batch of
+ * queued requests as soon as its device-memory footprint (an upper bound per
+ * request, computed at submission) fits the budget beside the requests already
+ * held. Admission is earliest deadline first, the deadline being the
+ * submission time plus four times the request's estimated run time (from its
+ * exact count of unfiltered multiply-adds): small requests pass large ones that
+ * arrived shortly before, no request is passed by one that arrives after its
+ * deadline, and the earliest-deadline request waits for memory rather than be
+ * passed. A small request (estimated at most 4 ms) shares its multiply with the
+ * other small queued requests of the same eps (up to 16 requests and 8 ms of
+ * estimated work, at most four times the first request's estimate, so that it
+ * still makes its deadline): the batch runs as one multiply of the block-diagonal matrix
+ * of its requests, one launch sequence over all their blocks, and each request
+ * receives its own part of the result, which is bit for bit the result of that
+ * request multiplied alone (the kernels compute each C block from its own
+ * products only). The lanes run concurrently on the device. Inputs are copied
+ * at submission into page-locked host memory (blocks sorted by (row, col)) and
+ * uploaded from there; results wait in page-locked host memory until taken
+ * (copied out) or released after use in place. Admission needs no call from
+ * the caller. The server functions may be called from any thread;
  * bsm_server_destroy only once every other call on the server has returned.
  * ------------------------------------------------------------------------- */
 typedef struct bsm_server_s *bsm_server;
@@ -281,6 +294,7 @@ typedef struct {
 typedef struct {
   int64_t queued, running, completed;
   int64_t bytes_in_use, bytes_peak, budget;
+  int64_t batches; /* multiplies run, each over a batch of one or more requests */
 } bsm_server_info;
 
 /* Request states reported by bsm_server_poll. */
@@ -290,9 +304,11 @@ int bsm_server_create(int device, const bsm_server_opts *opts, bsm_server *out);
 int bsm_server_destroy(bsm_server s);
 
 /* Queue C = A.A for a square matrix given as in bsm_mat_create (block sizes
- * sizes[nbrows] for rows and columns, a block list, column-major values in
- * list order). The arrays are copied. *id receives the request id. NOMEM if
- * the request's footprint bound exceeds the whole budget. */
+ * sizes[nbrows] for rows and columns, a block list in any order, column-major
+ * values in list order). The arrays are copied. *id receives the request id.
+ * OUT_OF_RANGE for an index outside [0, nbrows), DUPLICATE_BLOCK for a block
+ * listed twice, NOMEM if the request's footprint bound exceeds the whole budget
+ * (or page-locked memory for its copy cannot be had). */
 int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_t nblocks,
                       const int32_t *blk_row, const int32_t *blk_col, const double *values,
                       double eps, int64_t *id);

@@ -367,7 +367,8 @@ class _ServerOpts(ctypes.Structure):
 
 class _ServerInfo(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("completed", ctypes.c_int64),
-                ("bytes_in_use", ctypes.c_int64), ("bytes_peak", ctypes.c_int64), ("budget", ctypes.c_int64)]
+                ("bytes_in_use", ctypes.c_int64), ("bytes_peak", ctypes.c_int64), ("budget", ctypes.c_int64),
+                ("batches", ctypes.c_int64)]
 
 
 _SIGS.update({

@@ -1140,18 +1140,25 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
 // and uploads them with the values into M's front buffers (grown when they are
 // too small). Synchronises the context stream before returning, so the
 // caller's arrays may be reused at once.
-static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
-                           const int32_t *blk_col, const double *values, bool exact) {
-  bsm_ctx ctx = M->ctx;
-  const int32_t nbrows = M->nbr, nbcols = M->nbc;
-  const int32_t *row_sizes = M->h_row_sizes.data(), *col_sizes = M->h_col_sizes.data();
-  if (nblocks < 0 || (nblocks > 0 && (!blk_row || !blk_col))) return BSM_ERR_INVALID_ARG;
-  if (nblocks >= (int64_t)INT32_MAX) return BSM_ERR_UNSUPPORTED;
-  // pinned staging: row_ptr | col | row | off (16-byte aligned parts)
+// Page-locked staging of an upload's index arrays: row_ptr | col | row | off,
+// each part 16-byte aligned.
+struct StageLayout {
+  size_t b_ptr, b_col, b_off, need;
+};
+static StageLayout stage_layout(int64_t nbrows, int64_t nblocks) {
   auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  const size_t b_ptr = al(((size_t)nbrows + 1) * 4), b_col = al((size_t)nblocks * 4);
-  const size_t b_off = al(((size_t)nblocks + 1) * 8), need = b_ptr + 2 * b_col + b_off;
-  CK(cudaStreamSynchronize(ctx->stream));  // the staging may still feed an earlier upload
+  StageLayout L;
+  L.b_ptr = al(((size_t)nbrows + 1) * 4);
+  L.b_col = al((size_t)nblocks * 4);
+  L.b_off = al(((size_t)nblocks + 1) * 8);
+  L.need = L.b_ptr + 2 * L.b_col + L.b_off;
+  return L;
+}
+
+// The context's staging, at least `need` bytes, once the copies of an earlier
+// upload that may still read it are done.
+static int stage_reserve(bsm_ctx ctx, size_t need) {
+  CK(cudaStreamSynchronize(ctx->stream));
   if (ctx->h_stage_cap < need) {
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     ctx->h_stage = nullptr;
@@ -1163,6 +1170,21 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
     }
     ctx->h_stage_cap = cap;
   }
+  return BSM_OK;
+}
+
+static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
+                           const int32_t *blk_col, const double *values, bool exact) {
+  bsm_ctx ctx = M->ctx;
+  const int32_t nbrows = M->nbr, nbcols = M->nbc;
+  const int32_t *row_sizes = M->h_row_sizes.data(), *col_sizes = M->h_col_sizes.data();
+  if (nblocks < 0 || (nblocks > 0 && (!blk_row || !blk_col))) return BSM_ERR_INVALID_ARG;
+  if (nblocks >= (int64_t)INT32_MAX) return BSM_ERR_UNSUPPORTED;
+  // pinned staging: row_ptr | col | row | off (16-byte aligned parts)
+  const StageLayout L = stage_layout(nbrows, nblocks);
+  int rc0 = stage_reserve(ctx, L.need);
+  if (rc0) return rc0;
+  const size_t b_ptr = L.b_ptr, b_col = L.b_col;
   int32_t *h_row_ptr = reinterpret_cast<int32_t *>(ctx->h_stage);
   int32_t *h_col = reinterpret_cast<int32_t *>(ctx->h_stage + b_ptr);
   int32_t *h_row = reinterpret_cast<int32_t *>(ctx->h_stage + b_ptr + b_col);
@@ -1654,3 +1676,88 @@ int bsm_sync(bsm_ctx ctx) {
 }
 
 }  // extern "C"
+
+namespace bsm {
+
+int mat_create_diag(bsm_ctx ctx, int nparts, const DiagPart *parts, bsm_mat *out) {
+  if (!ctx || !out || nparts < 0 || (nparts > 0 && !parts)) return BSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  // the parts' first block row, block and value in the whole matrix
+  std::vector<int64_t> row0(nparts + 1, 0), blk0(nparts + 1, 0), val0(nparts + 1, 0);
+  std::vector<int32_t> sizes;
+  for (int p = 0; p < nparts; p++) {
+    const DiagPart &P = parts[p];
+    if (P.nbr < 0 || P.nblk < 0 || (P.nbr > 0 && !P.sizes) ||
+        (P.nblk > 0 && (!P.brow || !P.bcol || !P.vals)))
+      return BSM_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < P.nbr; i++)
+      if (P.sizes[i] <= 0) return BSM_ERR_INVALID_ARG;
+    int64_t nv = 0;
+    for (int64_t b = 0; b < P.nblk; b++) {
+      const int32_t i = P.brow[b], j = P.bcol[b];
+      if (i < 0 || i >= P.nbr || j < 0 || j >= P.nbr) return BSM_ERR_OUT_OF_RANGE;
+      if (b > 0 && (P.brow[b - 1] > i || (P.brow[b - 1] == i && P.bcol[b - 1] >= j)))
+        return BSM_ERR_INVALID_ARG;
+      nv += (int64_t)P.sizes[i] * P.sizes[j];
+    }
+    row0[p + 1] = row0[p] + P.nbr;
+    blk0[p + 1] = blk0[p] + P.nblk;
+    val0[p + 1] = val0[p] + nv;
+    if (row0[p + 1] >= (int64_t)INT32_MAX || blk0[p + 1] >= (int64_t)INT32_MAX)
+      return BSM_ERR_UNSUPPORTED;
+    sizes.insert(sizes.end(), P.sizes, P.sizes + P.nbr);
+  }
+  const int32_t nbr = (int32_t)row0[nparts];
+  const int64_t nblk = blk0[nparts], nnz = val0[nparts];
+  bsm_mat M = nullptr;
+  int rc = bsm_mat_create(ctx, nbr, sizes.data(), nbr, sizes.data(), 0, nullptr, nullptr, nullptr, &M);
+  if (rc) return rc;
+  auto fail = [&](int code) {
+    bsm_mat_destroy(M);
+    return code;
+  };
+  const StageLayout L = stage_layout(nbr, nblk);
+  if ((rc = stage_reserve(ctx, L.need))) return fail(rc);
+  int32_t *h_row_ptr = reinterpret_cast<int32_t *>(ctx->h_stage);
+  int32_t *h_col = reinterpret_cast<int32_t *>(ctx->h_stage + L.b_ptr);
+  int32_t *h_row = reinterpret_cast<int32_t *>(ctx->h_stage + L.b_ptr + L.b_col);
+  int64_t *h_off = reinterpret_cast<int64_t *>(ctx->h_stage + L.b_ptr + 2 * L.b_col);
+  memset(h_row_ptr, 0, ((size_t)nbr + 1) * 4);
+  int64_t g = 0, off = 0;
+  for (int p = 0; p < nparts; p++) {
+    const DiagPart &P = parts[p];
+    const int32_t r0 = (int32_t)row0[p];
+    for (int64_t b = 0; b < P.nblk; b++, g++) {
+      h_row[g] = r0 + P.brow[b];
+      h_col[g] = r0 + P.bcol[b];
+      h_off[g] = off;
+      off += (int64_t)P.sizes[P.brow[b]] * P.sizes[P.bcol[b]];
+      h_row_ptr[h_row[g] + 1]++;
+    }
+  }
+  for (int32_t i = 0; i < nbr; i++) h_row_ptr[i + 1] += h_row_ptr[i];
+  if ((rc = buf_grow(M, M->front, nblk, nnz, true))) return fail(rc);
+  cudaStream_t st = ctx->stream;
+  auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  int64_t hdr[2] = {nblk, nnz};
+  cudaError_t e;
+  for (int p = 0; p < nparts; p++)
+    if ((e = cp(M->front.vals + val0[p], parts[p].vals, (size_t)(val0[p + 1] - val0[p]) * 8)) !=
+        cudaSuccess)
+      return fail(cuda_fail(e, "diagonal upload values"));
+  if ((e = cp(M->front.row_ptr, h_row_ptr, ((size_t)nbr + 1) * 4)) != cudaSuccess ||
+      (e = cp(M->front.col_idx, h_col, (size_t)nblk * 4)) != cudaSuccess ||
+      (e = cp(M->front.blk_row, h_row, (size_t)nblk * 4)) != cudaSuccess ||
+      (e = cp(M->front.blk_off, h_off, (size_t)nblk * 8)) != cudaSuccess ||
+      (e = cp(M->front.hdr, hdr, sizeof(hdr))) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(cuda_fail(e, "diagonal upload"));
+  M->nblk = nblk;
+  M->nnz = nnz;
+  *out = M;
+  return BSM_OK;
+}
+
+}  // namespace bsm

@@ -209,4 +209,20 @@ inline int64_t split_bytes_per_value(int precision) {
   return precision == BSM_PREC_SPLIT_BF16X3 ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue;
 }
 
+// One diagonal part of a block-diagonal matrix (the request loop's batches).
+struct DiagPart {
+  int32_t nbr;                 // block rows of the part (= its block columns)
+  const int32_t *sizes;        // [nbr]
+  int64_t nblk;                // blocks, sorted by (row, col), no duplicates
+  const int32_t *brow, *bcol;  // [nblk] indices within the part
+  const double *vals;          // column-major values in list order (page-locked: DMA)
+};
+
+// diag(P_0, ..., P_{n-1}) as one square matrix on ctx: the block rows and
+// columns of part p follow those of the parts before it. Each part's values go
+// to the device with one copy of their own (no host-side concatenation).
+// INVALID_ARG for a null argument, a non-positive size or a part whose blocks
+// are not strictly sorted; OUT_OF_RANGE for an index outside its part.
+int mat_create_diag(bsm_ctx ctx, int nparts, const DiagPart *parts, bsm_mat *out);
+
 }  // namespace bsm

@@ -3,25 +3,34 @@
 // with continuous batching.
 //
 // The server owns `slots` lanes, each a libbsm context (own stream and
-// workspace) driven by a worker thread of its own. Requests wait in a FIFO
-// queue; a free worker takes the head of the queue as soon as its device-memory
-// footprint fits the budget next to the requests already held, uploads it,
-// runs the multiply, leaves the result in page-locked host memory and releases
-// the device memory, while the other lanes do the same with theirs: requests
-// of different sizes overlap on the device, and a request that arrives while
-// others run starts the moment a lane and memory free up (no waiting for a
-// batch to drain, nor for the caller to poll). Host work of a request
-// (validation, upload, read-back) blocks only its own lane. The footprint is an
-// upper bound computed at submission (A, a dense-or-candidate bound on C, the
-// product records), held from admission to completion. Every step goes through
-// the public C ABI, so a request's result is computed by exactly the kernels a
-// lone bsm_multiply uses.
+// workspace) driven by a worker thread of its own. A free lane takes the next
+// batch from the queue as soon as its device-memory footprint (an upper bound
+// computed at submission) fits the budget next to the requests already held.
+// Admission is earliest deadline first: a request's deadline is its submission
+// time plus kStretch times its estimated run time (from the exact count of its
+// unfiltered multiply-adds). Small requests therefore pass large ones that
+// arrived a little earlier, while a large one is never passed by requests that
+// arrive after its deadline. A batch is the earliest-deadline request plus, when
+// it is small, the other small queued requests of the same eps in deadline
+// order, up to kMergeMs of estimated work. The batch runs as one multiply of the
+// block-diagonal matrix diag(A_1, ..., A_n) (one norm, symbolic and numeric
+// launch sequence over all the batch's blocks). diag(A_1..A_n)^2 =
+// diag(A_1^2..A_n^2): the kernels compute every C block from its own product list
+// alone, in an order fixed by that list, so each request's part of the result is
+// bit for bit the result of the request run alone. The lanes run their batches
+// concurrently on the device, and a request that arrives while others run
+// starts the moment a lane and memory free up. Inputs are copied at submission
+// into page-locked host memory and uploaded from there by DMA, one copy per
+// request into the batch's matrix. Results go to page-locked host memory (the
+// multiply stores the values there directly when they fit) and wait there
+// until taken or released.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -43,12 +52,15 @@ enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 
 struct Request {
   int64_t id = 0;
-  std::vector<int32_t> sizes, brow, bcol;
-  std::vector<double> vals;
+  std::vector<int32_t> sizes, brow, bcol;  // blocks sorted by (row, col)
+  double *vals = nullptr;  // page-locked copy of the values, in block order
+  int64_t nvals = 0;
   double eps = 0;
-  int64_t footprint = 0;  // bytes held on the device while admitted
+  int64_t footprint = 0;     // bytes held on the device while admitted
   int64_t c_vals_bound = 0;  // upper bound of the result's value count
-  int state = kQueued;    // under the server's lock
+  double est_ms = 0;         // estimated run time alone
+  double deadline = 0;       // admission order: t_submit + kStretch * est_ms
+  int state = kQueued;       // under the server's lock
   int err = BSM_OK;
   int slot = -1;
   double t_submit = 0, t_start = 0, t_done = 0;
@@ -58,6 +70,24 @@ struct Request {
   int32_t *res_row = nullptr, *res_col = nullptr;
   double *res_val = nullptr;
 };
+
+// Admission and batching. A request's deadline is its submission time plus
+// kStretch times its estimated run time; requests estimated at most kMergeMs
+// share a multiply with other such requests, up to kMaxBatch requests and a total
+// estimate of kBatchMs, and never more than kStretch times the estimate of the
+// batch's first request (the batch finishes as one, so that request still makes
+// its deadline). The estimate is a fixed cost per multiply plus the exact count of
+// unfiltered multiply-adds at a nominal rate per precision: it orders the queue,
+// it is not a prediction the server relies on.
+constexpr double kStretch = 4.0;
+constexpr double kMergeMs = 4.0;
+constexpr double kBatchMs = 8.0;
+constexpr int kMaxBatch = 16;
+constexpr double kFixedMs = 0.15;
+double est_run_ms(int64_t macs, int precision) {
+  const double flop_per_ms = precision == BSM_PREC_FP64 ? 1.0e9 : 2.5e9;
+  return kFixedMs + 2.0 * (double)macs / flop_per_ms;
+}
 
 // Page-locked host memory for results: the lanes read results back into it at
 // the DMA rate (pageable memory goes through the driver's staging copies), and
@@ -124,8 +154,9 @@ struct Slot {
   std::thread worker;
 };
 
-// Upper bound of the device bytes a request C = A.A can hold.
-int64_t footprint_bound(const Request &r, int precision, int64_t *c_vals_bound) {
+// Upper bound of the device bytes a request C = A.A can hold; also the bound
+// of its result's value count and its unfiltered multiply-adds.
+int64_t footprint_bound(const Request &r, int precision, int64_t *c_vals_bound, int64_t *macs) {
   const int64_t nbr = (int64_t)r.sizes.size();
   std::vector<int64_t> row_nblk(nbr, 0), row_cols(nbr, 0);
   for (size_t b = 0; b < r.brow.size(); b++) {
@@ -134,18 +165,20 @@ int64_t footprint_bound(const Request &r, int precision, int64_t *c_vals_bound) 
   }
   int64_t dim = 0;
   for (int32_t s : r.sizes) dim += s;
-  int64_t cand = 0, cand_vals = 0;
+  int64_t cand = 0, cand_vals = 0, mac = 0;
   for (size_t b = 0; b < r.brow.size(); b++) {
     cand += row_nblk[r.bcol[b]];
     cand_vals += (int64_t)r.sizes[r.brow[b]] * row_cols[r.bcol[b]];
+    mac += (int64_t)r.sizes[r.brow[b]] * r.sizes[r.bcol[b]] * row_cols[r.bcol[b]];
   }
-  const int64_t a_bytes = 8 * (int64_t)r.vals.size() + 32 * (int64_t)r.brow.size();
+  if (macs) *macs = mac;
+  const int64_t a_bytes = 8 * r.nvals + 32 * (int64_t)r.brow.size();
   const int64_t c_blocks = std::min<int64_t>(nbr * nbr, cand);
   const int64_t c_vals = std::min<int64_t>(dim * dim, cand_vals);
   if (c_vals_bound) *c_vals_bound = c_vals;
   // the split precisions keep A's slices in both operand layouts
   const int64_t slice_bytes =
-      precision == BSM_PREC_FP64 ? 0 : 2 * bsm::split_bytes_per_value(precision) * (int64_t)r.vals.size();
+      precision == BSM_PREC_FP64 ? 0 : 2 * bsm::split_bytes_per_value(precision) * r.nvals;
   // A, C twice (front/back), per-block metadata, product records
   return 4 * a_bytes + slice_bytes + 2 * (8 * c_vals + 32 * c_blocks) + 8 * cand + 64 * nbr +
          (1 << 20);
@@ -169,6 +202,7 @@ struct bsm_server_s {
   int64_t next_id = 1;
   int64_t completed = 0, reported = 0;
   int64_t running = 0;
+  int64_t batches = 0;  // multiplies run (a batch of one or more requests each)
   bool stop = false;
 };
 
@@ -180,21 +214,54 @@ static void drop_result(bsm_server s, Request *r) {
   r->res_val = nullptr;
 }
 
-// One request on a lane, in the lane's worker thread: upload, multiply, result
-// to host memory, device memory released.
-static void run_request(bsm_server s, Slot &sl, Request *r) {
+// Hand the part of the batch's result that belongs to request p (block rows
+// [r0, r1) of the whole) to the request, in page-locked blocks of its own.
+// rows/cols/vals: the whole result (pattern sorted by (row, col)).
+static int split_result(bsm_server s, Request *r, int32_t r0, int32_t r1, const int32_t *rows,
+                        const int32_t *cols, const double *vals, int64_t nblk,
+                        const std::vector<int64_t> &voff) {
+  const int64_t b0 = std::lower_bound(rows, rows + nblk, r0) - rows;
+  const int64_t b1 = std::lower_bound(rows, rows + nblk, r1) - rows;
+  r->nblk = b1 - b0;
+  r->nnz = voff[b1] - voff[b0];
+  r->res_row = static_cast<int32_t *>(s->pinned.get(4 * (size_t)r->nblk));
+  r->res_col = static_cast<int32_t *>(s->pinned.get(4 * (size_t)r->nblk));
+  r->res_val = static_cast<double *>(s->pinned.get(8 * (size_t)r->nnz));
+  if (!r->res_row || !r->res_col || !r->res_val) return BSM_ERR_NOMEM;
+  for (int64_t b = b0; b < b1; b++) {  // block-diagonal: the columns lie in [r0, r1) too
+    r->res_row[b - b0] = rows[b] - r0;
+    r->res_col[b - b0] = cols[b] - r0;
+  }
+  std::copy(vals + voff[b0], vals + voff[b1], r->res_val);
+  return BSM_OK;
+}
+
+// One batch on a lane, in the lane's worker thread: the block-diagonal matrix of
+// the batch's requests uploaded, one multiply, each request's part of the
+// result to host memory, device memory released.
+static void run_batch(bsm_server s, Slot &sl, const std::vector<Request *> &batch) {
+  const int n = (int)batch.size();
+  std::vector<bsm::DiagPart> parts(n);
+  std::vector<int32_t> sizes, row0(n + 1, 0);
+  int64_t vals_bound = 0;
+  for (int p = 0; p < n; p++) {
+    const Request *r = batch[p];
+    parts[p] = {(int32_t)r->sizes.size(), r->sizes.data(), (int64_t)r->brow.size(), r->brow.data(),
+                r->bcol.data(), r->vals};
+    sizes.insert(sizes.end(), r->sizes.begin(), r->sizes.end());
+    row0[p + 1] = row0[p] + (int32_t)r->sizes.size();
+    vals_bound += r->c_vals_bound;
+  }
+  const int32_t nbr = row0[n];
   bsm_mat A = nullptr, C = nullptr;
-  const int32_t nbr = (int32_t)r->sizes.size();
-  int rc = bsm_mat_create(sl.ctx, nbr, r->sizes.data(), nbr, r->sizes.data(),
-                          (int64_t)r->brow.size(), r->brow.data(), r->bcol.data(), r->vals.data(),
-                          &A);
+  int rc = bsm::mat_create_diag(sl.ctx, n, parts.data(), &A);
   if (rc == BSM_OK)
-    rc = bsm_mat_create(sl.ctx, nbr, r->sizes.data(), nbr, r->sizes.data(), 0, nullptr, nullptr,
+    rc = bsm_mat_create(sl.ctx, nbr, sizes.data(), nbr, sizes.data(), 0, nullptr, nullptr,
                         nullptr, &C);
   // the values go straight to page-locked host memory while the multiply runs,
   // into a block sized by the bound on the result (up to kHostValuesCap values);
   // a larger result is read back after the multiply
-  const int64_t hv_cap = std::min<int64_t>(std::max<int64_t>(r->c_vals_bound, 1), kHostValuesCap);
+  const int64_t hv_cap = std::min<int64_t>(std::max<int64_t>(vals_bound, 1), kHostValuesCap);
   double *hv = (rc == BSM_OK) ? static_cast<double *>(s->pinned.get(8 * (size_t)hv_cap)) : nullptr;
   if (rc == BSM_OK) {
     bsm_opts o{};
@@ -202,65 +269,131 @@ static void run_request(bsm_server s, Slot &sl, Request *r) {
     o.blocking = 1;
     o.host_values = hv;
     o.host_cap = hv ? hv_cap : 0;
-    rc = bsm_multiply(sl.ctx, 1.0, A, A, 0.0, C, r->eps, &o, nullptr);
+    rc = bsm_multiply(sl.ctx, 1.0, A, A, 0.0, C, batch[0]->eps, &o, nullptr);
   }
-  if (rc == BSM_OK) rc = bsm_mat_nblocks(C, &r->nblk, &r->nnz);
+  int64_t nblk = 0, nnz = 0;
+  if (rc == BSM_OK) rc = bsm_mat_nblocks(C, &nblk, &nnz);
+  int32_t *rows = nullptr, *cols = nullptr;
+  double *vals = nullptr;
+  const bool direct = rc == BSM_OK && hv && nnz <= hv_cap;  // values already in host memory
   if (rc == BSM_OK) {
-    r->res_row = static_cast<int32_t *>(s->pinned.get(4 * (size_t)r->nblk));
-    r->res_col = static_cast<int32_t *>(s->pinned.get(4 * (size_t)r->nblk));
-    const bool direct = hv && r->nnz <= hv_cap;  // the values are already in host memory
+    rows = static_cast<int32_t *>(s->pinned.get(4 * (size_t)nblk));
+    cols = static_cast<int32_t *>(s->pinned.get(4 * (size_t)nblk));
     if (direct) {
-      r->res_val = hv;
+      vals = hv;
       hv = nullptr;
     } else {
-      r->res_val = static_cast<double *>(s->pinned.get(8 * (size_t)r->nnz));
+      vals = static_cast<double *>(s->pinned.get(8 * (size_t)nnz));
     }
-    if (!r->res_row || !r->res_col || !r->res_val) rc = BSM_ERR_NOMEM;
-    if (rc == BSM_OK) rc = bsm_mat_get_pattern(C, r->nblk, r->res_row, r->res_col);
-    if (rc == BSM_OK && !direct) rc = bsm_mat_get_values(C, r->nnz, r->res_val);
-    if (rc != BSM_OK) drop_result(s, r);
+    if (!rows || !cols || !vals) rc = BSM_ERR_NOMEM;
+    if (rc == BSM_OK) rc = bsm_mat_get_pattern(C, nblk, rows, cols);
+    if (rc == BSM_OK && !direct) rc = bsm_mat_get_values(C, nnz, vals);
   }
+  if (rc == BSM_OK && n == 1) {  // the whole result is the request's: no copies
+    Request *r = batch[0];
+    r->nblk = nblk;
+    r->nnz = nnz;
+    r->res_row = rows;
+    r->res_col = cols;
+    r->res_val = vals;
+    rows = cols = nullptr;
+    vals = nullptr;
+  } else if (rc == BSM_OK) {
+    std::vector<int64_t> voff((size_t)nblk + 1, 0);  // first value of each result block
+    for (int64_t b = 0; b < nblk; b++) voff[b + 1] = voff[b] + (int64_t)sizes[rows[b]] * sizes[cols[b]];
+    for (int p = 0; p < n && rc == BSM_OK; p++)
+      rc = split_result(s, batch[p], row0[p], row0[p + 1], rows, cols, vals, nblk, voff);
+  }
+  s->pinned.put(rows);
+  s->pinned.put(cols);
+  s->pinned.put(vals);
   s->pinned.put(hv);
   if (A) bsm_mat_destroy(A);
   if (C) bsm_mat_destroy(C);
-  std::vector<double>().swap(r->vals);  // the host copy of the input is no longer needed
-  r->err = rc;
-  r->t_done = now_ms();
+  const double t = now_ms();
+  for (Request *r : batch) {
+    if (rc != BSM_OK) drop_result(s, r);
+    s->pinned.put(r->vals);  // the host copy of the input is no longer needed
+    r->vals = nullptr;
+    r->err = rc;
+    r->t_done = t;
+  }
 }
 
-// A lane's worker: takes the head of the queue once it fits the budget, runs
-// it, and returns its memory to the budget.
+// The next batch, under the server's lock: the earliest-deadline request once
+// it fits the budget (it waits for memory rather than be passed by later
+// requests), and, when it is small, the other small queued requests of the same
+// eps in deadline order, as far as the work and memory limits allow. The batch
+// leaves the queue. False (batch empty) when nothing can start.
+static bool pick_batch(bsm_server s, std::vector<Request *> &batch) {
+  batch.clear();
+  if (s->queue.empty()) return false;
+  std::vector<Request *> order(s->queue.begin(), s->queue.end());
+  std::stable_sort(order.begin(), order.end(),
+                   [](const Request *a, const Request *b) { return a->deadline < b->deadline; });
+  Request *head = order[0];
+  if (s->in_use + head->footprint > s->budget) return false;
+  batch.push_back(head);
+  int64_t held = head->footprint;
+  double work = head->est_ms;
+  if (head->est_ms <= kMergeMs) {
+    const double limit = std::min(kBatchMs, kStretch * head->est_ms);
+    for (size_t q = 1; q < order.size() && (int)batch.size() < kMaxBatch; q++) {
+      Request *r = order[q];
+      if (r->eps != head->eps || r->est_ms > kMergeMs || work + r->est_ms > limit ||
+          s->in_use + held + r->footprint > s->budget)
+        continue;
+      batch.push_back(r);
+      held += r->footprint;
+      work += r->est_ms;
+    }
+  }
+  for (Request *r : batch) s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+  return true;
+}
+
+// A lane's worker: takes the next batch once it fits the budget, runs it, and
+// returns its memory to the budget.
 static void worker_loop(bsm_server s, int lane) {
   cudaSetDevice(s->device);
+  std::vector<Request *> batch;
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    s->cv.wait(lk, [&] {
-      return s->stop ||
-             (!s->queue.empty() && s->in_use + s->queue.front()->footprint <= s->budget);
-    });
-    if (s->stop) return;  // queued requests are dropped by bsm_server_destroy
-    Request *r = s->queue.front();
-    s->queue.pop_front();
-    s->in_use += r->footprint;
+    s->cv.wait(lk, [&] { return s->stop || pick_batch(s, batch); });
+    if (s->stop) {  // queued requests are dropped by bsm_server_destroy
+      for (Request *r : batch) s->queue.push_front(r);
+      return;
+    }
+    int64_t held = 0;
+    const double t = now_ms();
+    for (Request *r : batch) {
+      held += r->footprint;
+      r->state = kRunning;
+      r->slot = lane;
+      r->t_start = t;
+    }
+    s->in_use += held;
     s->peak = std::max(s->peak, s->in_use);
-    s->running++;
-    r->state = kRunning;
-    r->slot = lane;
-    r->t_start = now_ms();
+    s->running += (int64_t)batch.size();
+    s->batches++;
     lk.unlock();
-    run_request(s, s->slots[lane], r);
+    run_batch(s, s->slots[lane], batch);
     lk.lock();
-    s->in_use -= r->footprint;  // the lane released the request's device memory
-    r->footprint = 0;
-    r->state = r->err == BSM_OK ? kDone : kFailed;
-    s->running--;
-    s->completed++;
+    s->in_use -= held;  // the lane released the batch's device memory
+    for (Request *r : batch) {
+      r->footprint = 0;
+      r->state = r->err == BSM_OK ? kDone : kFailed;
+    }
+    s->running -= (int64_t)batch.size();
+    s->completed += (int64_t)batch.size();
+    batch.clear();
     s->cv.notify_all();  // a head that waited for memory may fit now
   }
 }
 
 static void forget(bsm_server s, Request *r) {
   drop_result(s, r);
+  s->pinned.put(r->vals);
   delete r;
 }
 
@@ -330,28 +463,68 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
       return BSM_ERR_OUT_OF_RANGE;
     nv += (int64_t)sizes[blk_row[b]] * sizes[blk_col[b]];
   }
-  // the copies are made before the lock: a large request does not hold up the lanes
+  // the copies are made before the lock: a large request does not hold up the
+  // lanes. The blocks are kept sorted by (row, col), the order the batch's
+  // matrix is assembled in; the values go to page-locked memory, from where the
+  // lane uploads them by DMA.
+  bool sorted = true;
+  for (int64_t b = 1; b < nblocks && sorted; b++)
+    sorted = blk_row[b - 1] < blk_row[b] || (blk_row[b - 1] == blk_row[b] && blk_col[b - 1] < blk_col[b]);
   Request *r = new (std::nothrow) Request();
   if (!r) return BSM_ERR_NOMEM;
-  try {
-    r->sizes.assign(sizes, sizes + nbrows);
-    r->brow.assign(blk_row, blk_row + nblocks);
-    r->bcol.assign(blk_col, blk_col + nblocks);
-    r->vals.assign(values, values + nv);
-  } catch (const std::bad_alloc &) {
+  r->nvals = nv;
+  r->vals = static_cast<double *>(s->pinned.get(8 * (size_t)std::max<int64_t>(nv, 1)));
+  if (!r->vals) {
     delete r;
     return BSM_ERR_NOMEM;
   }
+  try {
+    r->sizes.assign(sizes, sizes + nbrows);
+    if (sorted) {
+      r->brow.assign(blk_row, blk_row + nblocks);
+      r->bcol.assign(blk_col, blk_col + nblocks);
+      if (nv) memcpy(r->vals, values, (size_t)nv * sizeof(double));
+    } else {
+      std::vector<int64_t> order((size_t)nblocks), off((size_t)nblocks + 1, 0);
+      for (int64_t b = 0; b < nblocks; b++) {
+        order[b] = b;
+        off[b + 1] = off[b] + (int64_t)sizes[blk_row[b]] * sizes[blk_col[b]];
+      }
+      std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        return blk_row[a] != blk_row[b] ? blk_row[a] < blk_row[b] : blk_col[a] < blk_col[b];
+      });
+      r->brow.resize((size_t)nblocks);
+      r->bcol.resize((size_t)nblocks);
+      int64_t at = 0;
+      for (int64_t p = 0; p < nblocks; p++) {
+        const int64_t b = order[p];
+        if (p > 0 && blk_row[b] == r->brow[p - 1] && blk_col[b] == r->bcol[p - 1]) {
+          forget(s, r);
+          return BSM_ERR_DUPLICATE_BLOCK;
+        }
+        r->brow[p] = blk_row[b];
+        r->bcol[p] = blk_col[b];
+        memcpy(r->vals + at, values + off[b], (size_t)(off[b + 1] - off[b]) * sizeof(double));
+        at += off[b + 1] - off[b];
+      }
+    }
+  } catch (const std::bad_alloc &) {
+    forget(s, r);
+    return BSM_ERR_NOMEM;
+  }
   r->eps = eps;
-  r->footprint = footprint_bound(*r, s->precision, &r->c_vals_bound);
+  int64_t macs = 0;
+  r->footprint = footprint_bound(*r, s->precision, &r->c_vals_bound, &macs);
+  r->est_ms = est_run_ms(macs, s->precision);
   if (r->footprint > s->budget) {  // could never be admitted
-    delete r;
+    forget(s, r);
     return BSM_ERR_NOMEM;
   }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
     r->t_submit = now_ms();
+    r->deadline = r->t_submit + kStretch * r->est_ms;
     s->reqs[r->id] = r;
     s->queue.push_back(r);
     *id = r->id;
@@ -448,6 +621,7 @@ int bsm_server_get_info(bsm_server s, bsm_server_info *out) {
   out->bytes_in_use = s->in_use;
   out->bytes_peak = s->peak;
   out->budget = s->budget;
+  out->batches = s->batches;
   return BSM_OK;
 }
 

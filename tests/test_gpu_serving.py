@@ -143,3 +143,91 @@ def test_split_precision_server(bsm_lib, oracle_mod, prec):
             ref = oracle_mod.multiply(A, A, eps=eps)
             assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
             assert H.rel_frobenius(v, ref.values) <= 1e-5
+
+
+def _permuted(A, rng):
+    """The same matrix with its block list in random order (values moved with
+    their blocks)."""
+    lens = A.row_sizes.astype(np.int64)[A.blk_row] * A.col_sizes.astype(np.int64)[A.blk_col]
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    p = rng.permutation(len(lens))
+    vals = np.concatenate([A.values[off[b]:off[b + 1]] for b in p]) if len(p) else A.values
+    return synth.BlockMatrix(A.row_sizes, A.col_sizes, A.blk_row[p], A.blk_col[p], vals)
+
+
+def test_small_requests_share_multiplies(bsm_lib, oracle_mod):
+    """Small requests queued together run as one multiply of their
+    block-diagonal matrix: fewer multiplies than requests, and each request's
+    part equals the request multiplied alone, bit for bit."""
+    eps = 1e-10
+    sizes = [8, 12, 6, 16, 10, 8, 14, 4, 9, 11]
+    systems = [synth.water(n, seed=6000 + r) for r, n in enumerate(sizes)]
+    B = synth.water(128, seed=6100)
+    with bsm_lib.Server(0, slots=1, hbm_budget=4 << 30) as srv:
+        # a larger request first holds the only lane while the small ones queue
+        big = srv.submit(B, eps)
+        while srv.poll(big)[0] == 0:
+            pass
+        ids = [srv.submit(A, eps) for A in systems]
+        drain(srv, [big] + ids)
+        info = srv.info()
+        assert info["completed"] == len(systems) + 1
+        assert info["batches"] < len(systems) + 1  # some of them shared a multiply
+        srv.release(big)
+        results = [srv.take(i) for i in ids]
+    for A, (r, c, v) in zip(systems, results):
+        ra, ca, va = alone(bsm_lib, A, eps)
+        assert np.array_equal(r, ra) and np.array_equal(c, ca)
+        assert np.array_equal(v, va)
+        ref = oracle_mod.multiply(A, A, eps=eps)
+        assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+        assert H.rel_frobenius(v, ref.values) <= 1e-12
+
+
+def test_unsorted_submission_and_duplicates(bsm_lib, oracle_mod):
+    """A block list in any order gives the result of the sorted one; a block
+    listed twice is refused at submission."""
+    eps = 1e-10
+    rng = np.random.default_rng(5)
+    A = synth.water(20, seed=6200)
+    P = _permuted(A, rng)
+    with bsm_lib.Server(0, slots=2, hbm_budget=2 << 30) as srv:
+        ids = [srv.submit(P, eps), srv.submit(A, eps)]
+        drain(srv, ids)
+        r1, c1, v1 = srv.take(ids[0])
+        r2, c2, v2 = srv.take(ids[1])
+        assert np.array_equal(r1, r2) and np.array_equal(c1, c2) and np.array_equal(v1, v2)
+        ref = oracle_mod.multiply(A, A, eps=eps)
+        assert np.array_equal(r1, ref.blk_row) and H.rel_frobenius(v1, ref.values) <= 1e-12
+        n0 = int(A.row_sizes[A.blk_row[0]]) * int(A.col_sizes[A.blk_col[0]])
+        D = synth.BlockMatrix(A.row_sizes, A.col_sizes, np.append(A.blk_row, A.blk_row[0]),
+                              np.append(A.blk_col, A.blk_col[0]), np.append(A.values, A.values[:n0]))
+        with pytest.raises(bsm_lib.BsmError) as e:
+            srv.submit(D, eps)
+        assert e.value.name == "DUPLICATE_BLOCK"
+        assert srv.info()["bytes_in_use"] == 0
+
+
+def test_small_request_passes_earlier_large_one(bsm_lib):
+    """Earliest deadline first: with one lane busy, a small request submitted
+    just after a large one is admitted before it."""
+    eps = 1e-10
+    S = [synth.water(384, seed=6300), synth.water(256, seed=6301), synth.water(8, seed=6302)]
+    with bsm_lib.Server(0, slots=1, hbm_budget=8 << 30) as srv:
+        first = srv.submit(S[0], eps)
+        while srv.poll(first)[0] == 0:  # until it holds the only lane
+            pass
+        large = srv.submit(S[1], eps)
+        small = srv.submit(S[2], eps)
+        order = []
+        for _ in range(10 ** 7):
+            srv.progress()
+            for i in (first, large, small):
+                if i not in order and srv.poll(i)[0] >= 2:
+                    order.append(i)
+            if len(order) == 3:
+                break
+        assert order == [first, small, large]
+        for i in order:
+            srv.release(i)
