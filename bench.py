@@ -54,14 +54,22 @@ FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64
 FP64_BY_NUMBER = {v[0]: k for k, v in FP64_KERNELS.items()}
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/): valid only while
-# the kernel's source section is unchanged (its SHA-256), for that variant
-# (fp64 kernel name or split precision) and workload at its default eps.
+# the code that decides it is unchanged -- the kernel's own source section and,
+# for the FP64 kernels, the row-order work list (SHA-256 of each section) --
+# for that variant (fp64 kernel name or split precision) and workload at its
+# default eps.
 MEASURED_TRAFFIC = {
     ("pk12", "water2048"): dict(
-        source="paper_1705_10218_gb300/csrc/k_numeric_fp64.cu",
-        section=("// pk\n", "cudaError_t launch_numeric_fp64("),
-        sha256="06626473816c4d2631726748450de2df93e9ce80562b03e8b56c1e7bfbdfdf1f",
-        bytes=8.87e9 + 1.59e9),
+        sections=[("paper_1705_10218_gb300/csrc/k_numeric_fp64.cu",
+                   ("// pk\n", "cudaError_t launch_numeric_fp64("),
+                   "d2160908186159496f1b63411fa5b20c48f6a78c57c81b7c774a87167bf5e9f4"),
+                  ("paper_1705_10218_gb300/csrc/k_classes.cu",
+                   ("// Work in a row order.", "}  // namespace bsm"),
+                   "b173af39936271e55c6a2623c0b1222afaca8a97ab34ff8f9a0ec78e9ecdf01b"),
+                  ("paper_1705_10218_gb300/csrc/bsm_api.cu",
+                   ("static void bfs_row_order(", "static uint64_t next_order_id("),
+                   "113dd9175f43cb3ea209f7d880be5023dd9fd7acdf547fa5077ea74319814288")],
+        bytes=2.982e9 + 1.559e9),
 }
 
 
@@ -84,9 +92,9 @@ def kernel_source_sha(source, section):
 
 def measured_traffic(variant, workload):
     """DRAM bytes per launch from the ncu capture, or None when there is none
-    for this variant and workload or the kernel's source changed since."""
+    for this variant and workload or the code behind it changed since."""
     m = MEASURED_TRAFFIC.get((variant, workload))
-    if m is None or kernel_source_sha(m["source"], m["section"]) != m["sha256"]:
+    if m is None or any(kernel_source_sha(src, sec) != sha for src, sec, sha in m["sections"]):
         return None
     return m["bytes"]
 

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -233,6 +234,13 @@ struct bsm_mat_s {
   Buf front, back;
   int64_t nblk = 0, nnz = 0;  // valid when !pend.active
   int64_t hint_blk = 0, hint_nnz = 0;  // sizes of the last result computed into it
+  // a breadth-first order of the block rows over the pattern ([2 nbr]: the row
+  // at each position, then each row's position), the order in which the
+  // numeric phase takes the C blocks of a multiply with this matrix on the left;
+  // valid while order_id != 0. A result inherits the order of its left operand
+  // (same block rows).
+  int32_t *row_order = nullptr;
+  uint64_t order_id = 0;
   Pending pend;
 };
 
@@ -268,6 +276,7 @@ struct bsm_ctx_s {
   int64_t launches_at_enable = 0;
   // shape-class grouping (per-stack launches)
   int32_t *cls_items = nullptr;  // [cap_cblk]
+  int32_t *ord_start = nullptr;  // [cap_rows] first item of each position of a row order
   // work of the row-panel split kernel (records, tile entries, tiles per row);
   // its fallback list reuses cls_items / cls_segs
   PanelWs pw{};
@@ -329,12 +338,13 @@ static int ws_rows(bsm_ctx ctx, int64_t nrows) {
   dev_free(w.row_flops);
   dev_free(w.prod_off);
   dev_free(w.nnz_off);
+  dev_free(ctx->ord_start);
   const int64_t n = std::max<int64_t>(nrows + 1, 1024);
   int rc;
   if ((rc = dev_alloc(&w.row_cblk, n)) || (rc = dev_alloc(&w.row_prod, n)) ||
       (rc = dev_alloc(&w.row_nnz, n)) || (rc = dev_alloc(&w.row_cand, n)) ||
       (rc = dev_alloc(&w.row_flops, n)) || (rc = dev_alloc(&w.prod_off, n)) ||
-      (rc = dev_alloc(&w.nnz_off, n))) {
+      (rc = dev_alloc(&w.nnz_off, n)) || (rc = dev_alloc(&ctx->ord_start, n))) {
     ctx->cap_rows = 0;
     return rc;
   }
@@ -785,7 +795,15 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
       }
       tune_save(ctx, key, best, best_ms);
     }
-    if ((rc = launch_numeric(L, variant_or_default(ctx, L.C, L.o, key), nullptr, nullptr, L.A->max_row,
+    // C blocks in A's row order where A has one, else in C's row order
+    const int32_t *items = nullptr;
+    if (!L.split && L.A->order_id) {
+      CK(launch_order_items(L.out, L.A->row_order, L.A->row_order + L.A->nbr, L.A->nbr,
+                            ctx->d_status, ctx->ord_start, ctx->cls_items, ctx->nsm, L.s));
+      ctx->launches += 2;
+      items = ctx->cls_items;
+    }
+    if ((rc = launch_numeric(L, variant_or_default(ctx, L.C, L.o, key), items, nullptr, L.A->max_row,
                              L.B->max_col)))
       return rc;
   }
@@ -823,7 +841,8 @@ static void graph_key(const Launch &L, std::vector<uint64_t> &k) {
   put(w.row_cblk), put(w.row_prod), put(w.row_nnz), put(w.row_cand), put(w.row_flops);
   put(w.prod_off), put(w.nnz_off), put(w.cnt), put(w.c_cin), put(w.prod_ptr), put(w.prods);
   num(w.cap_prod), num(L.out.cap_blk), num(L.out.cap_nnz);
-  put(L.ctx->cls_items), put(L.s);
+  put(L.ctx->cls_items), put(L.ctx->ord_start), put(L.s);
+  put(L.A->row_order), num((int64_t)L.A->order_id);
   put(L.ctx->pw.recs), put(L.ctx->pw.tiles), put(L.ctx->pw.row_nt);
   dbl(L.alpha), dbl(L.beta), dbl(L.eps);
   num(L.o.precision), num(L.o.launch), num(L.o.fp64_kernel), num((int64_t)L.ctx->tune_version);
@@ -854,6 +873,14 @@ static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double 
   if (L.split) {
     if ((rc = split_buffers(A, o.precision, true, B == A))) return rc;
     if (B != A && (rc = split_buffers(B, o.precision, false, true))) return rc;
+  }
+  // C's block rows are A's: C inherits A's row order (a hint for the multiply
+  // that takes C on the left next)
+  if (A->order_id && C->order_id != A->order_id && C->nbr == A->nbr) {
+    if (!C->row_order && (rc = dev_alloc(&C->row_order, 2 * (int64_t)C->nbr))) return rc;
+    CK(cudaMemcpyAsync(C->row_order, A->row_order, 2 * (size_t)C->nbr * sizeof(int32_t),
+                       cudaMemcpyDeviceToDevice, L.s));
+    C->order_id = A->order_id;
   }
   L.dA = dev_view(A), L.dB = dev_view(B), L.dC = dev_view(C);
   double *host_dev = nullptr;  // device address of o.host_values
@@ -1105,6 +1132,7 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   dev_free(ctx->d_status);
   dev_free(ctx->d_work);
   dev_free(ctx->cls_items);
+  dev_free(ctx->ord_start);
   dev_free(ctx->pw.recs);
   dev_free(ctx->pw.tiles);
   dev_free(ctx->pw.row_nt);
@@ -1171,6 +1199,40 @@ static int stage_reserve(bsm_ctx ctx, size_t need) {
     ctx->h_stage_cap = cap;
   }
   return BSM_OK;
+}
+
+// Square matrices of at least this many block rows get a row order (below it
+// the operands of a multiply stay in L2 in any order).
+constexpr int32_t kOrderMinRows = 1024;
+
+// Breadth-first order of the block rows of a square pattern in blocked CSR
+// (row i adjacent to the rows named by its column indices): each component
+// from its lowest unvisited row, neighbours in column order. order[p] is the
+// row at position p, pos[r] the position of row r. O(rows + blocks).
+static void bfs_row_order(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t *order,
+                          int32_t *pos) {
+  std::fill(pos, pos + n, -1);
+  int32_t head = 0, tail = 0;
+  for (int32_t s = 0; s < n; s++) {
+    if (pos[s] >= 0) continue;
+    pos[s] = tail;
+    order[tail++] = s;
+    while (head < tail) {
+      const int32_t v = order[head++];
+      for (int32_t b = row_ptr[v]; b < row_ptr[v + 1]; b++) {
+        const int32_t k = col[b];
+        if (pos[k] < 0) {
+          pos[k] = tail;
+          order[tail++] = k;
+        }
+      }
+    }
+  }
+}
+
+static uint64_t next_order_id() {
+  static std::atomic<uint64_t> ids{0};
+  return ++ids;
 }
 
 static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
@@ -1292,6 +1354,17 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
     }
   }
   for (int32_t i = 0; i < nbrows; i++) h_row_ptr[i + 1] += h_row_ptr[i];
+  // the row order of the numeric phase (host BFS over the sorted pattern)
+  std::vector<int32_t> h_order;
+  M->order_id = 0;
+  if (nbrows == nbcols && nbrows >= kOrderMinRows) {
+    h_order.resize(2 * (size_t)nbrows);
+    bfs_row_order(nbrows, h_row_ptr, h_col, h_order.data(), h_order.data() + nbrows);
+    if (!M->row_order && (rc = dev_alloc(&M->row_order, 2 * (int64_t)nbrows))) return rc;
+    if ((e = cp(M->row_order, h_order.data(), h_order.size() * 4)) != cudaSuccess)
+      return cuda_fail(e, "matrix upload row order");
+    M->order_id = next_order_id();
+  }
   int64_t hdr[2] = {nblocks, nnz};
   if ((e = cp(M->front.row_ptr, h_row_ptr, ((size_t)nbrows + 1) * 4)) != cudaSuccess ||
       (e = cp(M->front.col_idx, h_col, (size_t)nblocks * 4)) != cudaSuccess ||
@@ -1434,6 +1507,7 @@ int bsm_mat_destroy(bsm_mat m) {
   dev_free(m->col_sizes);
   dev_free(m->row_cls);
   dev_free(m->col_cls);
+  dev_free(m->row_order);
   // captured multiplies may name this matrix's buffers
   for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   ctx->graphs.clear();

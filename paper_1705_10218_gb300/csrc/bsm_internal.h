@@ -130,6 +130,14 @@ cudaError_t launch_class_sort(DevOut C, const int32_t *row_cls, const int32_t *c
                               int ncls, const DevStatus *st, int32_t *counts, int32_t *cursor,
                               int64_t *segs, int32_t *items, int nsm, cudaStream_t stream);
 
+// C blocks in the order of a permutation of C's block rows (k_classes.cu):
+// row_order[p] = the row at position p, row_pos[r] = the position of row r;
+// items[nblk_c] receives the blocks row by row in that order, start[nbr] is
+// scratch. Two launches.
+cudaError_t launch_order_items(DevOut C, const int32_t *row_order, const int32_t *row_pos,
+                               int32_t nbr, const DevStatus *st, int32_t *start, int32_t *items,
+                               int nsm, cudaStream_t stream);
+
 // Split precision (k_split.cu). left/right: slice layouts of the operand as a
 // left (row-major) or right (column-major) MMA operand; either may be null.
 // One warp waits (bounded) on an mbarrier that it completes itself, or that

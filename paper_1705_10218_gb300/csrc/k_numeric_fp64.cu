@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
           auto load_batch = [&]() {
             nb = (p1 - pb < 32) ? (int)(p1 - pb) : 32;
             if (lane < nb) {
-              const int2 pr = ws.prods[pb + lane];
+              const int2 pr = __ldcs(ws.prods + pb + lane);  // read once: evict first
               my_a = A.blk_off[pr.x];
               my_b = B.blk_off[pr.y];
               my_s = A.col_sizes[A.col_idx[pr.x]];
@@ -677,8 +677,10 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
             const int64_t loc = (int64_t)(c0 + c) * m + r0 + r;
             v = alpha * v;
             if (cinv) v = fma(beta, cinv[loc], v);
-            out[loc] = v;
-            if (hblk) hblk[loc] = v;
+            // written once, not read by this multiply: streaming stores keep the
+            // operand rows, which the next C blocks read, in L2
+            __stcs(out + loc, v);
+            if (hblk) __stcs(hblk + loc, v);
             c += dq_tm;
             r += dr_tm;
             if (r >= tm) {

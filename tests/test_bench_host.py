@@ -21,24 +21,29 @@ def _bench():
 
 
 def test_traffic_reported_only_for_the_captured_source(tmp_path, monkeypatch):
+    """The stored DRAM traffic is reported while every code section that
+    decides it (the kernel, the row-order work list, the host order) is
+    unchanged, and dropped when any of them changes."""
     bench = _bench()
-    src = "paper_1705_10218_gb300/csrc/k_numeric_fp64.cu"
-    (tmp_path / os.path.dirname(src)).mkdir(parents=True)
-    shutil.copy(os.path.join(ROOT, src), tmp_path / src)
     entry = dict(bench.MEASURED_TRAFFIC[("pk12", "water2048")])
+    for src, _, _ in entry["sections"]:
+        (tmp_path / os.path.dirname(src)).mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(ROOT, src), tmp_path / src)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    entry["sha256"] = bench.kernel_source_sha(entry["source"], entry["section"])
-    assert entry["sha256"] is not None
+    entry["sections"] = [(src, sec, bench.kernel_source_sha(src, sec)) for src, sec, _ in entry["sections"]]
+    assert all(sha is not None for _, _, sha in entry["sections"])
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, ("pk12", "water2048"), entry)
     assert bench.measured_traffic("pk12", "water2048") == entry["bytes"]
     assert bench.measured_traffic("pk16", "water2048") is None
     assert bench.measured_traffic("pk12", "amorphous4096") is None
-    # the kernel changes: the captured counters no longer describe it
-    text = (tmp_path / src).read_text()
-    a = text.index(entry["section"][0])
-    (tmp_path / src).write_text(text[:a + len(entry["section"][0])] + "// edited\n" +
-                                text[a + len(entry["section"][0]):])
-    assert bench.measured_traffic("pk12", "water2048") is None
+    # one section changes: the captured counters no longer describe the code
+    for src, sec, _ in entry["sections"]:
+        text = (tmp_path / src).read_text()
+        a = text.index(sec[0]) + len(sec[0])
+        (tmp_path / src).write_text(text[:a] + "// edited\n" + text[a:])
+        assert bench.measured_traffic("pk12", "water2048") is None
+        (tmp_path / src).write_text(text)
+        assert bench.measured_traffic("pk12", "water2048") == entry["bytes"]
 
 
 def test_eps_percentile_of_norm_products():

@@ -429,3 +429,41 @@ def test_long_block_lists(gpu_ctx, bsm_lib):
     r2, c2 = M.pattern()
     assert np.array_equal(r0, r2) and np.array_equal(c0, c2) and np.array_equal(v0, M.values())
     M.destroy()
+
+
+@pytest.mark.parametrize("kern", ["pk12", "t16b2", "g8"])
+def test_row_order_changes_no_result(gpu_ctx, oracle_mod, bsm_lib, kern):
+    """A square matrix of at least 1024 block rows carries a breadth-first row
+    order, and the persistent launch takes the C blocks in that order. Every
+    block is still computed alone: the values equal, bit for bit, those of the
+    per-shape-class launch with the same kernel (another order), and the
+    oracle's within 1e-12. C = A.A inherits A's order; D = C.A takes its
+    blocks in the inherited order. The pattern has several components and is
+    not symmetric, so the order covers rows the search reaches late."""
+    K = {"pk12": bsm_lib.BSM_FP64_PK12, "t16b2": bsm_lib.BSM_FP64_T16_B2, "g8": bsm_lib.BSM_FP64_G8}[kern]
+    rng = np.random.default_rng(41)
+    n = 1100
+    rs = rng.choice([2, 3, 5, 8], n).astype(np.int32)
+    A = synth.random_blocks(rng, rs, rs, 4.0 / n, kind="normal")
+    ctx = gpu_ctx
+    dA = ctx.from_blocks(A)
+    res = {}
+    for launch in (bsm_lib.BSM_LAUNCH_PERSISTENT, bsm_lib.BSM_LAUNCH_PER_STACK):
+        C = ctx.empty(A.row_sizes, A.col_sizes)
+        D = ctx.empty(A.row_sizes, A.col_sizes)
+        ctx.multiply(1.0, dA, dA, 0.0, C, 0.0, launch=launch, fp64_kernel=K)
+        ctx.multiply(1.0, C, dA, 0.0, D, 0.0, launch=launch, fp64_kernel=K)
+        res[launch] = (C.pattern(), C.values(), D.pattern(), D.values())
+        C.destroy()
+        D.destroy()
+    p, q = res[bsm_lib.BSM_LAUNCH_PERSISTENT], res[bsm_lib.BSM_LAUNCH_PER_STACK]
+    for a, b in ((p[0], q[0]), (p[2], q[2])):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(p[1], q[1]) and np.array_equal(p[3], q[3])
+    ref_c = oracle_mod.multiply(A, A)
+    assert np.array_equal(p[0][0], ref_c.blk_row) and np.array_equal(p[0][1], ref_c.blk_col)
+    assert H.rel_frobenius(p[1], ref_c.values) <= TOL
+    ref_d = oracle_mod.multiply(H.result_matrix(ref_c, A.row_sizes, A.col_sizes), A)
+    assert np.array_equal(p[2][0], ref_d.blk_row) and np.array_equal(p[2][1], ref_d.blk_col)
+    assert H.rel_frobenius(p[3], ref_d.values) <= TOL
+    dA.destroy()
