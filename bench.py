@@ -37,6 +37,7 @@ FP64_FLOP_PER_SM_CLK = 4
 WORKLOADS = {
     "water2048": dict(kind="water", n=2048, seed=1, eps=1e-10),
     "water64": dict(kind="water", n=64, seed=0, eps=1e-10),
+    "water32": dict(kind="water", n=32, seed=0, eps=1e-10),  # the smallest serving request
     "water512": dict(kind="water", n=512, seed=1, eps=1e-10),
     "amorphous4096": dict(kind="amorphous", n=4096, seed=2, eps=1e-8),
     "amorphous1024": dict(kind="amorphous", n=1024, seed=2, eps=1e-8),  # profiling size

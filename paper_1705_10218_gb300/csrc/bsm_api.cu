@@ -226,6 +226,7 @@ struct bsm_mat_s {
   // shape kinds: the distinct block row / column sizes (at most 32; more are
   // folded into one kind) and each block row's / column's kind index
   std::vector<int32_t> row_kinds, col_kinds;
+  bool kinds_exact = true;  // every kind is one size (not folded)
   int32_t *row_cls = nullptr, *col_cls = nullptr;
   // slices of the values for the split precisions (left / right operand layouts)
   void *split_left = nullptr, *split_right = nullptr;
@@ -292,8 +293,14 @@ struct bsm_ctx_s {
   };
   std::vector<GraphEntry> graphs;
   uint64_t graph_clock = 0;
-  // autotuner: key -> FP64 variant
+  // autotuner: key -> FP64 variant, or for a tile key the packed kernel's
+  // slot shape nT << 8 | G
   std::map<std::string, int> tune;
+  // slot shapes of the packed kernels (12 slots, then 16) per tile (tm, tn):
+  // the formula's, replaced by tuned ones; on the device once one is tuned
+  // (ws.pk_tab)
+  uint16_t pk_tab[2 * kPkTabSize] = {};
+  uint16_t *d_pk_tab = nullptr;
   std::string tune_path;
   uint64_t tune_version = 0;
 };
@@ -546,6 +553,20 @@ static std::string tune_key_class(int m, int n) {
   return "fp64/class/" + std::to_string(m) + "x" + std::to_string(n);
 }
 
+static std::string tune_key_tile(int slots, int m, int n) {
+  return "pk" + std::to_string(slots) + "tile:" + std::to_string(m) + "x" + std::to_string(n);
+}
+
+// A slot shape the packed kernel with `slots` slots per lane can run for a
+// tile of te elements.
+static bool pk_shape_ok(int slots, int te, int nt, int g) {
+  return nt >= 1 && nt <= slots && g >= 1 && g <= kPkMaxGroups && te * g <= 32 * nt;
+}
+static int pk_slots(int variant) { return variant == kFp64Pk16 ? 16 : 12; }
+static int pk_tab_at(int slots, int m, int n) {
+  return (slots == 16 ? kPkTabSize : 0) + m * kPkTabEdge + n;
+}
+
 static std::string tune_key_all(bsm_mat A, bsm_mat B) {
   std::string k = "fp64/all/";
   for (int32_t r : A->row_kinds) k += std::to_string(r) + ",";
@@ -556,17 +577,39 @@ static std::string tune_key_all(bsm_mat A, bsm_mat B) {
   return k;
 }
 
+// Entries of the cache file: "key value ms" per line; lines starting with '#'
+// are notes. A tile entry sets the packed kernel's slot shape of that tile.
 static void tune_load(bsm_ctx ctx) {
   const char *p = getenv("BSM_AUTOTUNE_CACHE");
   if (!p || !*p) return;
   ctx->tune_path = p;
   FILE *f = fopen(p, "r");
   if (!f) return;
-  char key[512];
-  int v;
+  char line[640], key[512];
+  int v, m, n;
   double ms;
-  while (fscanf(f, "%511s %d %lf", key, &v, &ms) == 3)
-    if (v >= 0 && v < kFp64NumVariants) ctx->tune[key] = v;
+  while (fgets(line, sizeof(line), f)) {
+    if (line[0] == '#' || sscanf(line, "%511s %d %lf", key, &v, &ms) != 3) continue;
+    int slots = 0;
+    if (sscanf(key, "pk%dtile:%dx%d", &slots, &m, &n) == 3) {
+      if ((slots == 12 || slots == 16) && m >= 1 && m < kPkTabEdge && n >= 1 && n < kPkTabEdge &&
+          v >= 0 && pk_shape_ok(slots, m * n, v >> 8, v & 0xFF)) {
+        ctx->tune[key] = v;
+        ctx->pk_tab[pk_tab_at(slots, m, n)] = (uint16_t)v;
+      }
+    } else if (v >= 0 && v < kFp64NumVariants) {
+      ctx->tune[key] = v;
+    }
+  }
+  fclose(f);
+}
+
+// A note line in the cache file (kept for the record, ignored when loading).
+static void tune_note(bsm_ctx ctx, const std::string &text) {
+  if (ctx->tune_path.empty()) return;
+  FILE *f = fopen(ctx->tune_path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "# %s\n", text.c_str());
   fclose(f);
 }
 
@@ -580,9 +623,25 @@ static void tune_save(bsm_ctx ctx, const std::string &key, int v, double ms) {
   fclose(f);
 }
 
+// A packed kernel's slot shapes are tuned per (m, n) class of C blocks that
+// are one tile (m, n <= 16), where the shape kinds are exact.
+static bool tiles_need_tuning(bsm_ctx ctx, bsm_mat A, bsm_mat B, int variant) {
+  if ((variant != kFp64Pk12 && variant != kFp64Pk16) || !A->kinds_exact || !B->kinds_exact)
+    return false;
+  for (int32_t m : A->row_kinds)
+    for (int32_t n : B->col_kinds)
+      if (m < kPkTabEdge && n < kPkTabEdge &&
+          !ctx->tune.count(tune_key_tile(pk_slots(variant), m, n)))
+        return true;
+  return false;
+}
+
 static bool needs_tuning(bsm_ctx ctx, bsm_mat A, bsm_mat B, const bsm_opts &o) {
   if (!o.autotune || o.precision != BSM_PREC_FP64 || o.fp64_kernel) return false;
-  if (o.launch != BSM_LAUNCH_PER_STACK) return !ctx->tune.count(tune_key_all(A, B));
+  if (o.launch != BSM_LAUNCH_PER_STACK) {
+    auto it = ctx->tune.find(tune_key_all(A, B));
+    return it == ctx->tune.end() || tiles_need_tuning(ctx, A, B, it->second);
+  }
   for (int32_t m : A->row_kinds)
     for (int32_t n : B->col_kinds)
       if (!ctx->tune.count(tune_key_class(m, n))) return true;
@@ -730,6 +789,75 @@ static int time_variant(Launch &L, int variant, const int32_t *items, const int6
   return rc;
 }
 
+// Fewest C blocks of a class for its slot shape to be timed (below, the
+// formula's shape is kept and recorded).
+constexpr int64_t kTileTuneMinBlocks = 256;
+
+// Tune the packed kernel's (variant: 12 or 16 slots) slot shape (nT, G) of
+// every one-tile class (m, n <= 16) of this multiply that has no entry yet: the
+// C blocks are grouped by class, and each candidate -- every G up to the
+// largest with the fewest passes nT = ceil(m n G / 32) <= slots -- is timed on
+// the class's blocks alone
+// (best of two runs after one warm-up) with the table entry set to it. The
+// fastest is kept in the table the persistent launch reads (and in the cache
+// file, with the formula's time beside it as a note). Blocking.
+static int tune_pk_tiles(Launch &L, int variant) {
+  bsm_ctx ctx = L.ctx;
+  const int slots = pk_slots(variant);
+  const int ncc = (int)L.B->col_kinds.size();
+  const int ncls = (int)L.A->row_kinds.size() * ncc;
+  if (ncls > kMaxClasses) return BSM_OK;
+  CK(launch_class_sort(L.out, L.A->row_cls, L.B->col_cls, ncc, ncls, ctx->d_status,
+                       ctx->cls_counts, ctx->cls_cursor, ctx->cls_segs, ctx->cls_items, ctx->nsm,
+                       L.s));
+  ctx->launches += 3;
+  std::vector<int64_t> segs(2 * (size_t)ncls);
+  CK(cudaMemcpyAsync(segs.data(), ctx->cls_segs, segs.size() * sizeof(int64_t),
+                     cudaMemcpyDeviceToHost, L.s));
+  CK(cudaStreamSynchronize(L.s));
+  L.ws.pk_tab = ctx->d_pk_tab;
+  for (int c = 0; c < ncls; c++) {
+    const int m = L.A->row_kinds[c / ncc], n = L.B->col_kinds[c % ncc];
+    const std::string key = tune_key_tile(slots, m, n);
+    if (m >= kPkTabEdge || n >= kPkTabEdge || ctx->tune.count(key)) continue;
+    const int idx = pk_tab_at(slots, m, n), te = m * n;
+    const uint16_t formula = ctx->pk_tab[idx];
+    uint16_t best = formula;
+    double best_ms = 0, formula_ms = 0;
+    std::string tried;  // "nT/G/ms" of every candidate, for the note
+    if (segs[2 * c + 1] - segs[2 * c] >= kTileTuneMinBlocks) {
+      best_ms = 1e30;
+      for (int g = 1; g <= kPkMaxGroups; g++) {
+        const int nt = (te * g + 31) / 32;
+        if (nt > slots) break;
+        if (!pk_shape_ok(slots, te, nt, g)) continue;
+        const uint16_t v = (uint16_t)(nt << 8 | g);
+        CK(cudaMemcpyAsync(ctx->d_pk_tab + idx, &v, sizeof(v), cudaMemcpyHostToDevice, L.s));
+        double ms;
+        int rc = time_variant(L, variant, ctx->cls_items, ctx->cls_segs + 2 * c, m, n, &ms);
+        if (rc) return rc;
+        if (v == formula) formula_ms = ms;
+        if (ms < best_ms) best_ms = ms, best = v;
+        char one[48];
+        snprintf(one, sizeof(one), " %d/%d/%.4f", nt, g, ms);
+        tried += one;
+      }
+      char note[160];
+      snprintf(note, sizeof(note), "%s %lld blocks: formula nT=%d G=%d %.4f ms, tuned nT=%d G=%d %.4f ms;",
+               key.c_str(), (long long)(segs[2 * c + 1] - segs[2 * c]), formula >> 8, formula & 0xFF,
+               formula_ms, best >> 8, best & 0xFF, best_ms);
+      tune_note(ctx, std::string(note) + " nT/G/ms:" + tried);
+    }
+    ctx->pk_tab[idx] = best;
+    CK(cudaMemcpyAsync(ctx->d_pk_tab + idx, &ctx->pk_tab[idx], sizeof(uint16_t),
+                       cudaMemcpyHostToDevice, L.s));
+    CK(cudaStreamSynchronize(L.s));
+    tune_save(ctx, key, best, best_ms);
+  }
+  ctx->ws.pk_tab = ctx->d_pk_tab;
+  return BSM_OK;
+}
+
 // fill, shape-class grouping (per-stack), numeric
 static int stage_b(Launch &L, bool record, bool may_tune) {
   bsm_ctx ctx = L.ctx;
@@ -795,6 +923,10 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
       }
       tune_save(ctx, key, best, best_ms);
     }
+    const int variant = variant_or_default(ctx, L.C, L.o, key);
+    if (may_tune && L.o.autotune && !L.o.fp64_kernel && !L.split &&
+        tiles_need_tuning(ctx, L.A, L.B, variant) && (rc = tune_pk_tiles(L, variant)))
+      return rc;
     // C blocks in A's row order where A has one, else in C's row order
     const int32_t *items = nullptr;
     if (!L.split && L.A->order_id) {
@@ -803,9 +935,7 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
       ctx->launches += 2;
       items = ctx->cls_items;
     }
-    if ((rc = launch_numeric(L, variant_or_default(ctx, L.C, L.o, key), items, nullptr, L.A->max_row,
-                             L.B->max_col)))
-      return rc;
+    if ((rc = launch_numeric(L, variant, items, nullptr, L.A->max_row, L.B->max_col))) return rc;
   }
   // the host copy of the values, where a numeric kernel did not store it
   if (L.out.host_vals && !L.host_written) {
@@ -1091,7 +1221,22 @@ int bsm_ctx_create(int device, bsm_ctx *out) {
     if (rc == BSM_OK) rc = dev_alloc(&ctx->cls_cursor, kMaxClasses);
     if (rc == BSM_OK) rc = dev_alloc(&ctx->cls_segs, 2 * kMaxClasses);
   }
-  if (rc == BSM_OK) tune_load(ctx);
+  if (rc == BSM_OK) {  // the packed kernel's slot shapes: the formula, then tuned entries
+    for (int slots : {12, 16})
+      for (int tm = 1; tm < kPkTabEdge; tm++)
+        for (int tn = 1; tn < kPkTabEdge; tn++) {
+          int nt, g;
+          pk_formula_shape(slots, tm * tn, &nt, &g);
+          ctx->pk_tab[pk_tab_at(slots, tm, tn)] = (uint16_t)(nt << 8 | g);
+        }
+    tune_load(ctx);
+    rc = dev_alloc(&ctx->d_pk_tab, 2 * kPkTabSize);
+    if (rc == BSM_OK && (e = cudaMemcpy(ctx->d_pk_tab, ctx->pk_tab, sizeof(ctx->pk_tab),
+                                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      rc = cuda_fail(e, "slot shape table");
+    for (auto &kv : ctx->tune)
+      if (rc == BSM_OK && kv.first.find("tile:") != std::string::npos) ctx->ws.pk_tab = ctx->d_pk_tab;
+  }
   if (rc == BSM_OK) {
     memset(ctx->h_slots, 0, kSlots * sizeof(DevStatus));
     e = cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), ctx->stream);
@@ -1133,6 +1278,7 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   dev_free(ctx->d_work);
   dev_free(ctx->cls_items);
   dev_free(ctx->ord_start);
+  dev_free(ctx->d_pk_tab);
   dev_free(ctx->pw.recs);
   dev_free(ctx->pw.tiles);
   dev_free(ctx->pw.row_nt);
@@ -1424,14 +1570,15 @@ int bsm_mat_create(bsm_ctx ctx, int32_t nbrows, const int32_t *row_sizes, int32_
   for (int32_t v : M->h_row_sizes) M->max_row = std::max(M->max_row, v);
   for (int32_t v : M->h_col_sizes) M->max_col = std::max(M->max_col, v);
   // shape kinds of the block rows and columns
-  auto kinds = [](const std::vector<int32_t> &sizes, std::vector<int32_t> &kind,
-                  std::vector<int32_t> &cls) {
+  auto kinds = [&](const std::vector<int32_t> &sizes, std::vector<int32_t> &kind,
+                   std::vector<int32_t> &cls) {
     kind = sizes;
     std::sort(kind.begin(), kind.end());
     kind.erase(std::unique(kind.begin(), kind.end()), kind.end());
     cls.resize(sizes.size());
     if ((int)kind.size() > kMaxKinds) {  // too many sizes: one kind, keyed by the largest
       kind = {kind.back()};
+      M->kinds_exact = false;
       std::fill(cls.begin(), cls.end(), 0);
       return;
     }

@@ -65,7 +65,13 @@ struct DevWs {
   int2 *prods;         // [cap_prod] (A block, B block) per kept product
   int64_t cap_prod;
   int64_t cap_rows;
+  // slot shapes of the packed kernels per tile (tm, tn): entry
+  // (slots == 16) * kPkTabSize + tm * kPkTabEdge + tn = nT << 8 | G (tuned), or
+  // null: the built-in formula
+  const uint16_t *pk_tab;
 };
+constexpr int kPkTabEdge = 17;
+constexpr int kPkTabSize = kPkTabEdge * kPkTabEdge;
 
 // Device status of one multiply (written by the device, copied to pinned host).
 struct DevStatus {
@@ -106,6 +112,11 @@ enum {
   kFp64NumVariants = 6
 };
 int fp64_variant_blocks_per_sm(int variant);
+// The packed kernel's built-in slot shape (nT, G) of a tile of te elements
+// (1..256) with at most `slots` (12 or 16) slots per lane.
+void pk_formula_shape(int slots, int te, int *nt, int *g);
+// Largest number of k-groups of the packed kernel.
+constexpr int kPkMaxGroups = 8;
 // Per-device kernel attributes (call with the device current, outside capture).
 cudaError_t numeric_fp64_init();
 

@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kG8Warps * 32, 4)
 constexpr int kPkWarps = 8;          // warps per thread block (2 blocks per SM)
 constexpr int kPkTile = 16;          // output tile edge
 constexpr int kPkMaxSlots = 16;      // accumulator slots per lane (largest nT) of the pk16 variant
-constexpr int kPkMaxG = 8;           // largest number of k-groups
+constexpr int kPkMaxG = kPkMaxGroups;  // largest number of k-groups
 constexpr int kPkMaxKC = 64;         // largest chunk (k positions)
 // Doubles per stage (two stages per warp; 2 blocks of 8 warps fit an SM). A
 // tile of tm x tn takes chunks of KC k positions with KC * tm + tn * (KC + 1)
@@ -434,6 +434,14 @@ constexpr PkShapes make_pk_shapes(int slots) {
 }
 __constant__ PkShapes c_pk_shapes12 = make_pk_shapes(12);
 __constant__ PkShapes c_pk_shapes16 = make_pk_shapes(16);
+static_assert(kPkTabEdge == kPkTile + 1, "the tuned table covers every tile shape");
+
+void pk_formula_shape(int slots, int te, int *nt, int *g) {
+  static const PkShapes s12 = make_pk_shapes(12), s16 = make_pk_shapes(16);
+  const PkShapes &s = (slots == 12) ? s12 : s16;
+  *nt = s.nt[te];
+  *g = s.g[te];
+}
 
 // floor(x / d) as (x * r) >> 16 with r = ceil(2^16 / d): exact while
 // x * (r * d - 2^16) < 2^16, i.e. for d <= 16 and x < 4096 (the error term is
@@ -486,6 +494,7 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
   if (st->overflow) return;
   constexpr int kStage = kPkStage;
   const PkShapes &shapes = (SLOTS == 12) ? c_pk_shapes12 : c_pk_shapes16;
+  const bool scale = alpha != 1.0;
   extern __shared__ double smem_pk[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double *wbuf = smem_pk + warp * 2 * kStage;
@@ -514,7 +523,12 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
         for (int c0 = 0; c0 < n; c0 += kPkTile) {
           const int tm = min(kPkTile, m - r0), tn = min(kPkTile, n - c0);
           const int te = tm * tn;
-          const int nT = shapes.nt[te], G = shapes.g[te];
+          int nT = shapes.nt[te], G = shapes.g[te];
+          if (ws.pk_tab) {  // a tuned shape (validated by the host)
+            const uint32_t e = ws.pk_tab[(SLOTS == 16 ? kPkTabSize : 0) + tm * kPkTabEdge + tn];
+            nT = (int)(e >> 8);
+            G = (int)(e & 0xFFu);
+          }
           const int used = te * G;
           const uint32_t rtm = rcp16(tm), rg = rcp16(G);
           // chunk length: the largest multiple of G with KC * tm + tn * (KC + 1) <= kStage
@@ -675,7 +689,7 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
             double v = red[e];
             for (int g = 1; g < G; g++) v += red[g * te + e];
             const int64_t loc = (int64_t)(c0 + c) * m + r0 + r;
-            v = alpha * v;
+            if (scale) v = alpha * v;
             if (cinv) v = fma(beta, cinv[loc], v);
             // written once, not read by this multiply: streaming stores keep the
             // operand rows, which the next C blocks read, in L2
