@@ -413,6 +413,23 @@ def measure_variants(ctx, A, dA, dC, eps, flops, local, sample=None, steps=10, w
             split[f"{prec}_{kname}"] = e
     out["split_water"] = split
 
+    # the filter at work: the same water system with eps at the 30th percentile
+    # of the candidate norm products (the headline's eps drops nothing)
+    feps = norm_product_percentile(A, 30.0)
+    dC3 = ctx.empty(A.row_sizes, A.col_sizes)
+    st3 = ctx.multiply(1.0, dA, dA, 0.0, dC3, feps, stats=True, blocking=True)
+    with ClockSampler(local) as clk:
+        per, prof = timed_multiplies(ctx, dA, dC3, feps, steps, warmup, s)
+    ms = statistics.median(per)
+    out["filter_active_water"] = {
+        "workload": "water2048, eps at the 30th percentile of the candidate norm products",
+        "eps": feps, "candidates": st3.candidates, "kept": st3.kept, "dropped": st3.dropped,
+        "c_blocks": st3.c_blocks, "gflop_kept_per_multiply": round(st3.flops / 1e9, 4),
+        "value": round(st3.flops / (ms / 1e3) / 1e9, 2), "unit": "filtered GFLOP/s",
+        "ms_p50": round(ms, 4), "numeric_ms": round(prof.ms_numeric / max(prof.multiplies, 1), 4),
+        "clocks": clk.summary()}
+    dC3.destroy()
+
     # mixed block sizes: one persistent launch vs one launch per shape class
     B2 = synth.amorphous(4096, seed=2)
     dB2 = ctx.from_blocks(B2)
