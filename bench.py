@@ -450,7 +450,7 @@ def measure_variants(ctx, A, dA, dC, eps, flops, local, sample=None, steps=10, w
 
     # serving: a reduced replay of the request stream
     with ClockSampler(local) as clk:
-        sv = serve_measure(100, 12, 4, 16.0)
+        sv = serve_measure(100, 12, 4, 48.0)
     sv["clocks"] = clk.summary()
     out["serving"] = sv
     return out
@@ -747,7 +747,7 @@ def main():
     ap.add_argument("--requests", type=int, default=500)
     ap.add_argument("--serve-pool", type=int, default=48)
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--budget-gb", type=float, default=16.0)
+    ap.add_argument("--budget-gb", type=float, default=48.0)
     args = ap.parse_args()
     if args.serve:
         return serve_bench(args)
