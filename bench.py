@@ -373,7 +373,7 @@ def measure_variants(ctx, A, dA, dC, eps, flops, local, sample=None, steps=10, w
     bf16 = measured_peak("bf16_tflops", 1900.0)
     split = {}
     for prec in ("bf16x3", "tf32x2"):
-        for kname, knum in (("blocks", 1), ("panel", 0)):
+        for kname, knum in (("blocks", 1), ("chunks", 2), ("panel", 0)):
             kw = dict(precision=PRECISIONS[prec], split_kernel=knum)
             with ClockSampler(local) as clk:
                 per, prof = timed_multiplies(ctx, dA, dC, eps, steps, warmup, s, **kw)

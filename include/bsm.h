@@ -98,9 +98,12 @@ enum {
  *           tcgen05 tensor cores (MMA M = the row's C columns, N = its block
  *           row size x slices, K = A's row), accumulators in tensor memory;
  *   BLOCKS: one C block per warp, its products one after another on mma.sync
- *           tiles, operands streamed through shared memory.
- * Both multiply the same slice products; they differ in FP32 rounding only. */
-enum { BSM_SPLIT_PANEL = 0, BSM_SPLIT_BLOCKS = 1, BSM_SPLIT_NUM_KERNELS = 2 };
+ *           tiles, each product's operands streamed through shared memory;
+ *   CHUNKS: one C block per warp on mma.sync tiles, its products concatenated
+ *           along k and staged into shared memory in chunks of whole products
+ *           (C blocks larger than 16 x 16 go to the BLOCKS kernel).
+ * All multiply the same slice products; they differ in FP32 rounding only. */
+enum { BSM_SPLIT_PANEL = 0, BSM_SPLIT_BLOCKS = 1, BSM_SPLIT_CHUNKS = 2, BSM_SPLIT_NUM_KERNELS = 3 };
 
 /* How the numeric stacks are launched. */
 enum {

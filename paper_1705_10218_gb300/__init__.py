@@ -24,6 +24,7 @@ from .bsm import (  # noqa: F401
     BSM_PREC_SPLIT_BF16X3,
     BSM_PREC_SPLIT_TF32X2,
     BSM_SPLIT_BLOCKS,
+    BSM_SPLIT_CHUNKS,
     BSM_SPLIT_PANEL,
     BsmError,
     Context,

@@ -34,6 +34,7 @@ BSM_FP64_G8 = 5
 BSM_FP64_NUM_KERNELS = 6
 BSM_SPLIT_PANEL = 0
 BSM_SPLIT_BLOCKS = 1
+BSM_SPLIT_CHUNKS = 2
 
 
 class BsmError(RuntimeError):

@@ -734,8 +734,26 @@ static int launch_numeric(Launch &L, int variant, const int32_t *items, const in
                           int max_m, int max_n) {
   bsm_ctx ctx = L.ctx;
   if (L.split) {
-    ctx->last_split = BSM_SPLIT_BLOCKS;
     const int smax = L.A->max_col;
+    if (split_kernel_of(L.o, L.B) == BSM_SPLIT_CHUNKS) {
+      ctx->last_split = BSM_SPLIT_CHUNKS;
+      // the C blocks whose MMA problem fits 16 x 16; the others (if any) to
+      // the large-block instance of the per-block kernel
+      CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
+      CK(launch_numeric_split_cat(L.o.precision, L.dA, L.dB, L.out, L.dC, L.A->split_left,
+                                  L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items,
+                                  seg, smax, ctx->nsm, ctx->d_work, L.s));
+      if (!(max_m <= 16 && max_n <= 16)) {
+        ctx->launches++;
+        CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
+        CK(launch_numeric_split(L.o.precision, 2, L.dA, L.dB, L.out, L.dC, L.A->split_left,
+                                L.B->split_right, L.alpha, L.beta, L.ws, ctx->d_status, items,
+                                seg, smax, ctx->nsm, ctx->d_work, L.s));
+      }
+      ctx->launches++;
+      return BSM_OK;
+    }
+    ctx->last_split = BSM_SPLIT_BLOCKS;
     if (max_m <= 16 && max_n <= 16) {
       CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), L.s));
       CK(launch_numeric_split(L.o.precision, 0, L.dA, L.dB, L.out, L.dC, L.A->split_left,

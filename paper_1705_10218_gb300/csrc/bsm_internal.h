@@ -160,6 +160,16 @@ cudaError_t launch_split(int precision, const int32_t *row_sizes, const int32_t 
                          const double *vals, const int64_t *hdr, void *left, void *right,
                          int grid, cudaStream_t stream);
 
+// The chunked split kernel: the C blocks whose MMA problem fits 16 x 16, each
+// block's products concatenated along k in shared-memory chunks (the others
+// are skipped: the large-block instance of launch_numeric_split takes them).
+// smax: the largest k of the launch (at most 32; picks the chunk size).
+cudaError_t launch_numeric_split_cat(int precision, DevMat A, DevMat B, DevOut C, DevMat Cin,
+                                     const void *a_left, const void *b_right, double alpha,
+                                     double beta, DevWs ws, const DevStatus *st,
+                                     const int32_t *items, const int64_t *seg, int smax, int nsm,
+                                     unsigned long long *work, cudaStream_t stream);
+
 // sizes: 0 = every block's MMA problem fits 16 x 16 (one launch covers all);
 // 1 = only the blocks that fit 16 x 16; 2 = only the larger ones (<= 32 x 32).
 // smax: the largest k (column size of A) the launch can meet, at most 32.

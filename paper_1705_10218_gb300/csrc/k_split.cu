@@ -744,6 +744,264 @@ __global__ void __launch_bounds__((BIG ? kPipeWarpsBig : kPipeWarps) * 32,
     if (!mbar_wait(bar0 + 8 * (u % STAGES), (u / STAGES) & 1u)) break;
 }
 
+// ---------------------------------------------------------------------------
+// Chunked kernel: the products of a C block concatenated along k. A warp
+// computes one C block at a time (or its transpose, as the pipelined kernel
+// chooses), for the C blocks whose MMA problem fits 16 x 16. The k pieces of
+// the block's products, in ascending k, are staged chunk by chunk into shared
+// memory. A chunk holds whole products, at most PCMAX 16-byte pieces of k, and
+// each slice plane of L (and of R) is one k-piece-major plane of Mp (Np) rows
+// in it, so the MMA loop runs over the chunk's pieces as over one long k
+// whatever the products' boundaries: every product's pieces are zero past its
+// own k. The copies are 16-byte cp.async from all lanes (one loop per operand
+// and product over all its planes), double buffered as in the FP64 packed
+// kernel, and the tensor cores' FP32 sums are folded into the compensated
+// running sum once per chunk. Per product this leaves the copy loop and a
+// table entry; the waits, the fold and the loop control come per chunk.
+// ---------------------------------------------------------------------------
+constexpr int kCatWarps = 4;
+constexpr int kCatMeta = 32;  // product table entries (one batch)
+
+// Bytes of one operand buffer: every plane of up to 16 rows and PCMAX pieces,
+// and 256 bytes beyond, which the fragment loads of rows past Mp (or Np) in the
+// last plane may touch (their results are never used).
+template <int PREC, int PCMAX>
+__host__ __device__ constexpr int cat_operand_bytes() {
+  return (PREC == BSM_PREC_SPLIT_BF16X3 ? 3 : 2) * 16 * PCMAX * 16 + 256;
+}
+template <int PREC, int PCMAX>
+__host__ __device__ constexpr int cat_warp_bytes() {
+  return 2 * 2 * cat_operand_bytes<PREC, PCMAX>() + kCatMeta * (8 + 8 + 4);
+}
+
+__device__ __forceinline__ void cpa16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int PREC, int PCMAX>
+__global__ void __launch_bounds__(kCatWarps * 32)
+    k_numeric_split_cat(DevMat A, DevMat B, DevOut C, DevMat Cin, const void *__restrict__ a_left,
+                        const void *__restrict__ b_right, double alpha, double beta, DevWs ws,
+                        const DevStatus *st, const int32_t *__restrict__ items,
+                        const int64_t *__restrict__ seg, unsigned long long *work) {
+  if (st->overflow) return;
+  constexpr bool BF = (PREC == BSM_PREC_SPLIT_BF16X3);
+  constexpr int NSL = BF ? 3 : 2;
+  constexpr int VPP = BF ? 8 : 4;  // k values per 16-byte piece
+  // a product's k (at most 16 for the small instances, 32 for the others)
+  // fits one chunk; the launcher picks the instance by the largest k
+  static_assert(PCMAX * VPP >= 16, "a chunk must hold the longest product (k <= 16 or 32)");
+  constexpr int64_t kUnit = BF ? 2 * kBf16HalfwordsPerValue : 4 * kTf32WordsPerValue;
+  constexpr int OPB = cat_operand_bytes<PREC, PCMAX>();
+  extern __shared__ __align__(16) unsigned char smem_cat[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  unsigned char *wbase = smem_cat + warp * cat_warp_bytes<PREC, PCMAX>();
+  const unsigned char **meta_a = reinterpret_cast<const unsigned char **>(wbase + 4 * OPB);
+  const unsigned char **meta_b = meta_a + kCatMeta;
+  int *meta_k = reinterpret_cast<int *>(meta_b + kCatMeta);  // pieces of k
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(wbase);
+  // ldmatrix lane roles (as in the pipelined kernel)
+  const int ra = (lane & 7) + ((lane >> 3) & 1) * 8, pa = lane >> 4;
+  const int rb_ = (lane & 7) + (lane >> 4) * 8, pb = (lane >> 3) & 1;
+  int64_t wb = 0, we = st->nblk_c;
+  if (seg) {
+    wb = seg[0];
+    we = seg[1];
+  }
+  const bool plain = (alpha == 1.0 && beta == 0.0);
+  double *hout = (C.host_vals && st->nnz_c <= C.host_cap) ? C.host_vals : nullptr;
+
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(work, 1ull);
+    const int64_t w = wb + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+    if (w >= we) break;
+    const int64_t gb = items ? items[w] : w;
+    const int i = C.blk_row[gb], j = C.col_idx[gb];
+    const int m = C.row_sizes[i], n = C.col_sizes[j];
+    const int tiles_n = ((m + 15) >> 4) * ((n + 7) >> 3);
+    const int tiles_t = ((n + 15) >> 4) * ((m + 7) >> 3);
+    const bool tr = tiles_t < tiles_n;
+    const int Mp = tr ? n : m, Np = tr ? m : n;
+    if (Mp > 16 || Np > 16) continue;  // the large-block instance of the pipelined kernel
+    const bool two = Np > 8;
+    const int64_t p0 = ws.prod_ptr[gb], p1 = ws.prod_ptr[gb + 1];
+    // chunk plane strides of L (Mp rows) and R (Np rows)
+    const uint32_t lpl = (uint32_t)(Mp * PCMAX * 16), rpl = (uint32_t)(Np * PCMAX * 16);
+    float hi[2][4], lo[2][4], acc[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+      for (int x = 0; x < 4; x++) hi[nt][x] = lo[nt][x] = acc[nt][x] = 0.f;
+
+    // product cursor: the next product to stage and the table batch holding it
+    int64_t pq = p0, tbase = p0;
+    int tcount = 0;
+    // all planes of one operand of a product (rows x pk pieces each,
+    // contiguous, planes one after another) into the chunk at piece poff
+    auto copy_operand = [&](uint32_t dst, uint32_t plane, const unsigned char *src, int rows, int pk,
+                            int poff) {
+      const int U = rows * pk;  // 16-byte units of one plane
+      const uint32_t d0 = dst + 16u * (uint32_t)(poff * rows);
+      for (int u = lane; u < NSL * U; u += 32) {
+        const int q = (u >= U) + ((NSL == 3 && u >= 2 * U) ? 1 : 0);
+        cpa16(d0 + (uint32_t)q * plane + 16u * (uint32_t)(u - q * U), src + 16 * (int64_t)u);
+      }
+    };
+    // stage whole products into buffer buf while they fit; returns the pieces
+    auto fill = [&](int buf) -> int {
+      const uint32_t dL = sbase + (uint32_t)(buf * 2 * OPB), dR = dL + (uint32_t)OPB;
+      int poff = 0;
+      while (pq < p1) {
+        if (pq == tbase + tcount) {  // the next batch of the product table
+          tbase = pq;
+          tcount = (p1 - pq < kCatMeta) ? (int)(p1 - pq) : kCatMeta;
+          __syncwarp();  // every lane is past its reads of the old batch
+          if (lane < tcount) {
+            const int2 pr = ws.prods[pq + lane];
+            meta_a[lane] = static_cast<const unsigned char *>(a_left) + kUnit * A.blk_off[pr.x];
+            meta_b[lane] = static_cast<const unsigned char *>(b_right) + kUnit * B.blk_off[pr.y];
+            meta_k[lane] = (A.col_sizes[A.col_idx[pr.x]] + VPP - 1) / VPP;
+          }
+          __syncwarp();
+        }
+        const int e = (int)(pq - tbase);
+        const int pk = meta_k[e];
+        if (pk > PCMAX) {  // longer than a chunk (the launcher rules it out): error, block skipped
+          if (lane == 0) atomicOr(const_cast<int32_t *>(&st->error), 1);
+          pq = p1;
+          break;
+        }
+        if (poff + pk > PCMAX) break;
+        // not transposed: L = A_ik (left layout, m rows), R = B_kj (right layout, n rows)
+        const unsigned char *sa = meta_a[e], *sb = meta_b[e];
+        copy_operand(dL, lpl, tr ? sb : sa, Mp, pk, poff);
+        copy_operand(dR, rpl, tr ? sa : sb, Np, pk, poff);
+        poff += pk;
+        pq++;
+      }
+      return poff;
+    };
+
+    int cur = fill(0);
+    cpa_commit();
+    for (int ch = 0;; ch++) {
+      const int buf = ch & 1;
+      const int nxt = (pq < p1) ? fill(buf ^ 1) : 0;
+      cpa_commit();
+      cpa_wait<1>();  // the current chunk has landed
+      __syncwarp();
+      const uint32_t sL = sbase + (uint32_t)(buf * 2 * OPB), sR = sL + (uint32_t)OPB;
+      const uint32_t adL = sL + 16u * (uint32_t)(pa * Mp + ra);
+      const uint32_t adR = sR + 16u * (uint32_t)(pb * Np + rb_);
+      const uint32_t adR2 = sR + 16u * (uint32_t)ra;  // "a" order on R (single pieces)
+      if (BF) {
+        // slice products, smallest first: (3,1) (2,2) (1,3) (2,1) (1,2) (1,1)
+        constexpr int PA[6] = {2, 1, 0, 1, 0, 0};
+        constexpr int PB[6] = {0, 1, 2, 0, 1, 0};
+        for (int p = 0; p < cur; p += 2) {
+          const uint32_t koL = 16u * (uint32_t)(p * Mp), koR = 16u * (uint32_t)(p * Np);
+          if (cur - p == 1) {  // one piece left: m16n8k8
+            uint32_t a[3][2], b[3][2];
+#pragma unroll
+            for (int q3 = 0; q3 < 3; q3++) {
+              ldsm_x2(a[q3][0], a[q3][1], adL + q3 * lpl + koL);
+              ldsm_x2(b[q3][0], b[q3][1], adR2 + q3 * rpl + koR);
+            }
+#pragma unroll
+            for (int x = 0; x < 6; x++) {
+              mma_bf16_k8(acc[0], a[PA[x]][0], a[PA[x]][1], b[PB[x]][0]);
+              if (two) mma_bf16_k8(acc[1], a[PA[x]][0], a[PA[x]][1], b[PB[x]][1]);
+            }
+          } else {
+            uint32_t a[3][4], b[3][4];
+#pragma unroll
+            for (int q3 = 0; q3 < 3; q3++) {
+              ldsm_x4(a[q3][0], a[q3][1], a[q3][2], a[q3][3], adL + q3 * lpl + koL);
+              ldsm_x4(b[q3][0], b[q3][1], b[q3][2], b[q3][3], adR + q3 * rpl + koR);
+            }
+#pragma unroll
+            for (int x = 0; x < 6; x++) {
+              mma_bf16_k16(acc[0], a[PA[x]], b[PB[x]][0], b[PB[x]][1]);
+              if (two) mma_bf16_k16(acc[1], a[PA[x]], b[PB[x]][2], b[PB[x]][3]);
+            }
+          }
+        }
+      } else {
+        // (2,1) (1,2) (1,1)
+        constexpr int PA[3] = {1, 0, 0};
+        constexpr int PB[3] = {0, 1, 0};
+        for (int p = 0; p < cur; p += 2) {
+          const uint32_t koL = 16u * (uint32_t)(p * Mp), koR = 16u * (uint32_t)(p * Np);
+          uint32_t a[2][4], b[2][4];
+          if (cur - p == 1) {  // one piece left: the other half of the k step is zero
+#pragma unroll
+            for (int q2 = 0; q2 < 2; q2++) {
+              ldsm_x2(a[q2][0], a[q2][1], adL + q2 * lpl + koL);
+              ldsm_x2(b[q2][0], b[q2][2], adR2 + q2 * rpl + koR);
+              a[q2][2] = a[q2][3] = b[q2][1] = b[q2][3] = 0u;
+            }
+          } else {
+#pragma unroll
+            for (int q2 = 0; q2 < 2; q2++) {
+              ldsm_x4(a[q2][0], a[q2][1], a[q2][2], a[q2][3], adL + q2 * lpl + koL);
+              ldsm_x4(b[q2][0], b[q2][1], b[q2][2], b[q2][3], adR + q2 * rpl + koR);
+            }
+          }
+#pragma unroll
+          for (int x = 0; x < 3; x++) {
+            mma_tf32_k8(acc[0], a[PA[x]], b[PB[x]][0], b[PB[x]][1]);
+            if (two) mma_tf32_k8(acc[1], a[PA[x]], b[PB[x]][2], b[PB[x]][3]);
+          }
+        }
+      }
+      // the chunk's FP32 partial sums into the compensated running sum
+#pragma unroll
+      for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+          two_sum_acc(hi[nt][x], lo[nt][x], acc[nt][x]);
+          acc[nt][x] = 0.f;
+        }
+      __syncwarp();  // the buffer is read before it is filled again
+      if (nxt == 0) break;
+      cur = nxt;
+    }
+    cpa_wait<0>();
+    __syncwarp();
+
+    const int cin = ws.c_cin[gb];
+    const double *cinv = (cin >= 0) ? Cin.vals + Cin.blk_off[cin] : nullptr;
+    double *out = C.vals + C.blk_off[gb];
+    double *hblk = hout ? hout + C.blk_off[gb] : nullptr;
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int rr = g + ((x >> 1) << 3);
+        const int cc = nt * 8 + 2 * t + (x & 1);
+        if (rr < Mp && cc < Np) {
+          const int row = tr ? cc : rr, col = tr ? rr : cc;
+          const int64_t e = (int64_t)col * m + row;
+          // FP32 -> FP64 is exact; hi + lo rounded once in FP64
+          double v = (double)hi[nt][x] + (double)lo[nt][x];
+          if (!plain) {
+            v = alpha * v;
+            if (cinv) v = fma(beta, cinv[e], v);
+          }
+          out[e] = v;
+          if (hblk) hblk[e] = v;
+        }
+      }
+  }
+}
+
 // The pipelined kernel's bounded barrier wait on its own: lane 0 completes the
 // phase (a plain arrive), unless never_complete; the warp then waits as the
 // kernel does and records in *flag whether the wait gave up.
@@ -807,7 +1065,65 @@ cudaError_t launch_numeric_split(int precision, int sizes, DevMat A, DevMat B, D
   return cudaGetLastError();
 }
 
+// Chunk capacity (16-byte pieces of k) of the chunked instances: the smaller
+// where every k is at most 16 (the water blocks), the larger for k up to 32.
+// Smaller chunks leave more warps per SM, which this kernel needs (water2048,
+// BF16x3: 8 pieces 29.0 ms, 4 pieces 17.8 ms, 2 pieces 17.6 ms; TF32x2: 8
+// pieces 23.4 ms, 4 pieces 18.8 ms).
+constexpr int kCatPiecesBf16Small = 2, kCatPiecesBf16 = 4;
+constexpr int kCatPiecesTf32Small = 4, kCatPiecesTf32 = 8;
+template <int PREC, int PCMAX>
+static const void *cat_fn() {
+  return (const void *)k_numeric_split_cat<PREC, PCMAX>;
+}
+
+cudaError_t launch_numeric_split_cat(int precision, DevMat A, DevMat B, DevOut C, DevMat Cin,
+                                     const void *a_left, const void *b_right, double alpha,
+                                     double beta, DevWs ws, const DevStatus *st,
+                                     const int32_t *items, const int64_t *seg, int smax, int nsm,
+                                     unsigned long long *work, cudaStream_t stream) {
+  const bool bf = precision == BSM_PREC_SPLIT_BF16X3, small = smax <= 16;
+  constexpr int BF = BSM_PREC_SPLIT_BF16X3, TF = BSM_PREC_SPLIT_TF32X2;
+  const void *fn = bf ? (small ? cat_fn<BF, kCatPiecesBf16Small>() : cat_fn<BF, kCatPiecesBf16>())
+                      : (small ? cat_fn<TF, kCatPiecesTf32Small>() : cat_fn<TF, kCatPiecesTf32>());
+  const size_t smem =
+      (size_t)kCatWarps * (bf ? (small ? cat_warp_bytes<BF, kCatPiecesBf16Small>() : cat_warp_bytes<BF, kCatPiecesBf16>())
+                              : (small ? cat_warp_bytes<TF, kCatPiecesTf32Small>() : cat_warp_bytes<TF, kCatPiecesTf32>()));
+  int per_sm = 1;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCatWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = nsm * (per_sm > 0 ? per_sm : 1);
+#define BSM_SPLIT_CAT(P, PC)                                                              \
+  k_numeric_split_cat<P, PC><<<grid, kCatWarps * 32, smem, stream>>>(A, B, C, Cin, a_left, \
+                                                                    b_right, alpha, beta, ws, \
+                                                                    st, items, seg, work)
+  if (bf) {
+    if (small) BSM_SPLIT_CAT(BF, kCatPiecesBf16Small);
+    else BSM_SPLIT_CAT(BF, kCatPiecesBf16);
+  } else {
+    if (small) BSM_SPLIT_CAT(TF, kCatPiecesTf32Small);
+    else BSM_SPLIT_CAT(TF, kCatPiecesTf32);
+  }
+#undef BSM_SPLIT_CAT
+  return cudaGetLastError();
+}
+
 cudaError_t numeric_split_init() {
+  {
+    constexpr int BF = BSM_PREC_SPLIT_BF16X3, TF = BSM_PREC_SPLIT_TF32X2;
+    const void *fn[4] = {cat_fn<BF, kCatPiecesBf16Small>(), cat_fn<BF, kCatPiecesBf16>(),
+                         cat_fn<TF, kCatPiecesTf32Small>(), cat_fn<TF, kCatPiecesTf32>()};
+    const int bytes[4] = {kCatWarps * cat_warp_bytes<BF, kCatPiecesBf16Small>(),
+                          kCatWarps * cat_warp_bytes<BF, kCatPiecesBf16>(),
+                          kCatWarps * cat_warp_bytes<TF, kCatPiecesTf32Small>(),
+                          kCatWarps * cat_warp_bytes<TF, kCatPiecesTf32>()};
+    for (int x = 0; x < 4; x++) {
+      cudaError_t e = cudaFuncSetAttribute(fn[x], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[x]);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn[x], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      if (e != cudaSuccess) return e;
+    }
+  }
   // the largest slot layout of each instance (k up to 32), and the whole
   // shared memory of an SM for the carveout (the rings decide occupancy)
   for (int pi = 0; pi < 2; pi++)

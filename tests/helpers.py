@@ -116,7 +116,7 @@ def select_blocks(M, keep):
 def split_block_factors(A, B, prec, kernel, rows=None):
     """Bound factor per C block of the candidate pattern of A.B (a dict
     (i, j) -> factor is not needed: returns a function of block row / column
-    arrays). prec: "bf16x3" / "tf32x2"; kernel: "blocks" / "panel"."""
+    arrays). prec: "bf16x3" / "tf32x2"; kernel: "blocks" / "chunks" / "panel"."""
     import scipy.sparse as sp
 
     bf = prec == "bf16x3"
@@ -124,8 +124,14 @@ def split_block_factors(A, B, prec, kernel, rows=None):
     kmma = 16 if bf else 8
     eta = (kmma + 2) * 2.0 ** -23
     ks = np.asarray(A.col_sizes, np.int64)
-    if kernel == "blocks":
+    if kernel in ("blocks", "chunks"):
+        # per-block kernel: 4 products between folds, each ceil(k / kmma) k steps
+        # of every slice pair into one FP32 accumulator
         w = 4 * (6 if bf else 3) * int(-(-ks.max() // kmma))
+        if kernel == "chunks":
+            # chunks of 8 pieces of k (two per k step): 4 k steps of every slice
+            # pair between folds; C blocks beyond 16 x 16 take the per-block kernel
+            w = max(w, 4 * (6 if bf else 3))
         const = u_s + w * eta * (1 + 2.0 ** -6)
         return lambda bi, bj: np.full(len(bi), const)
     piece = 8 if bf else 4

@@ -77,9 +77,10 @@ def test_water2048_filter_active(gpu_ctx, oracle_mod, water2048):
     assert 0 < st.dropped < st.candidates
 
 
-@pytest.mark.parametrize("kernel,sk", [("blocks", 1), ("panel", 0)])
-@pytest.mark.parametrize("prec,name,bound", [(1, "bf16x3", {"blocks": 2e-6, "panel": 1e-5}),
-                                             (2, "tf32x2", {"blocks": 1e-5, "panel": 2e-5})])
+@pytest.mark.parametrize("kernel,sk", [("blocks", 1), ("panel", 0), ("chunks", 2)])
+@pytest.mark.parametrize("prec,name,bound",
+                         [(1, "bf16x3", {"blocks": 2e-6, "panel": 1e-5, "chunks": 2e-6}),
+                          (2, "tf32x2", {"blocks": 1e-5, "panel": 2e-5, "chunks": 1e-5})])
 def test_water2048_split(gpu_ctx, oracle_mod, water2048, prec, name, bound, kernel, sk):
     check_sampled(gpu_ctx, oracle_mod, water2048, 1e-10, split=(name, kernel, bound[kernel]),
                   precision=prec, split_kernel=sk)

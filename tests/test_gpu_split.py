@@ -1,6 +1,6 @@
 """GPU parity of the split-precision paths (BF16x3, TF32x2) against the CPU
-oracle, through the C ABI, for both split-precision kernels (the per-block
-mma.sync kernel and the tcgen05 row-panel kernel).
+oracle, through the C ABI, for the three split-precision kernels (the per-block
+and the chunked mma.sync kernels, the tcgen05 row-panel kernel).
 
 * Small integers (|a| <= 4): every slice after the first is zero, every slice
   product is exact and all FP32 partial sums stay far below 2^24, so the result
@@ -19,10 +19,11 @@ from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 PRECS = {"bf16x3": 1, "tf32x2": 2}
-KERNELS = {"blocks": 1, "panel": 0}  # BSM_SPLIT_BLOCKS, BSM_SPLIT_PANEL
+KERNELS = {"blocks": 1, "panel": 0, "chunks": 2}  # BSM_SPLIT_BLOCKS, _PANEL, _CHUNKS
 # stated relative Frobenius bounds on water (measured: blocks 6.4e-7 / 8.4e-7,
 # panel 2.2e-6 / 4.4e-6 on water2048)
 REL_F = {("blocks", "bf16x3"): 2e-6, ("blocks", "tf32x2"): 1e-5,
+         ("chunks", "bf16x3"): 2e-6, ("chunks", "tf32x2"): 1e-5,
          ("panel", "bf16x3"): 1e-5, ("panel", "tf32x2"): 2e-5}
 
 
