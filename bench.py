@@ -48,6 +48,7 @@ WORKLOADS = {
 }
 L2_BYTES = 128 << 20  # GB300 L2 (129 MB), rounded down
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
+SPLIT_KERNELS = {"panel": 0, "blocks": 1, "chunks": 2}  # BSM_SPLIT_*
 # FP64 numeric kernels (BSM_FP64_*): name -> (number, kernel symbol)
 FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64_t16"),
                 "t32": (2, "k_numeric_fp64_t32"), "pk12": (3, "k_numeric_fp64_pk"),
@@ -735,6 +736,8 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="tune the FP64 kernel variants first")
     ap.add_argument("--fp64-kernel", default=None, choices=sorted(FP64_KERNELS),
                     help="force one FP64 numeric kernel (default: the library's choice)")
+    ap.add_argument("--split-kernel", default=None, choices=sorted(SPLIT_KERNELS),
+                    help="force a split-precision kernel (default: the library's choice)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
@@ -781,8 +784,10 @@ def main():
     dC = ctx.empty(A.row_sizes, A.col_sizes)
     fk = None if args.fp64_kernel is None else FP64_KERNELS[args.fp64_kernel][0]
     kw = dict(precision=prec, launch=launch, graph=args.graph, autotune=args.autotune, fp64_kernel=fk)
-    st = ctx.multiply(1.0, dA, dA, 0.0, dC, eps, precision=prec, launch=launch,
-                      autotune=args.autotune, fp64_kernel=fk, stats=True)
+    if args.split_kernel is not None:
+        kw["split_kernel"] = SPLIT_KERNELS[args.split_kernel]
+    st = ctx.multiply(1.0, dA, dA, 0.0, dC, eps, stats=True,
+                      **{k: v for k, v in kw.items() if k != "graph"})
     flops = st.flops
     s = torch.cuda.Stream()
     for _ in range(args.warmup):
@@ -954,6 +959,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else args.precision, "data": "synthetic",
             "config": {"workload": args.workload, "atoms": A.nbr, "dimension": int(A.row_sizes.sum()),
                        "eps": eps, "precision": args.precision, "launch": args.launch,
+                       "split_kernel": args.split_kernel,
                        "graph": bool(args.graph), "autotune": bool(args.autotune),
                        "fp64_kernel": (FP64_BY_NUMBER.get(prof.last_fp64_kernel)
                                        if args.precision == "fp64" else None),
