@@ -272,7 +272,9 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * exact count of unfiltered multiply-adds): small requests pass large ones that
  * arrived shortly before, no request is passed by one that arrives after its
  * deadline, and the earliest-deadline request waits for memory rather than be
- * passed. A small request (estimated at most 4 ms) shares its multiply with the
+ * passed. A large request (estimated at least 8 ms) fills the GPU alone: one
+ * runs at a time, and a large earliest-deadline request waits only for the
+ * running one, while the other lanes take small requests. A small request (estimated at most 4 ms) shares its multiply with the
  * other small queued requests of the same eps (up to 16 requests and 8 ms of
  * estimated work, at most four times the first request's estimate, so that it
  * still makes its deadline): the batch runs as one multiply of the block-diagonal matrix

@@ -494,7 +494,6 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
   if (st->overflow) return;
   constexpr int kStage = kPkStage;
   const PkShapes &shapes = (SLOTS == 12) ? c_pk_shapes12 : c_pk_shapes16;
-  const bool scale = alpha != 1.0;
   extern __shared__ double smem_pk[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double *wbuf = smem_pk + warp * 2 * kStage;
@@ -689,7 +688,7 @@ __global__ void __launch_bounds__(kPkWarps * 32, 2)
             double v = red[e];
             for (int g = 1; g < G; g++) v += red[g * te + e];
             const int64_t loc = (int64_t)(c0 + c) * m + r0 + r;
-            if (scale) v = alpha * v;
+            v = alpha * v;
             if (cinv) v = fma(beta, cinv[loc], v);
             // written once, not read by this multiply: streaming stores keep the
             // operand rows, which the next C blocks read, in L2
