@@ -49,6 +49,7 @@ WORKLOADS = {
 L2_BYTES = 128 << 20  # GB300 L2 (129 MB), rounded down
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x2": 2}
 SPLIT_KERNELS = {"panel": 0, "blocks": 1, "chunks": 2}  # BSM_SPLIT_*
+SPLIT_KERNEL_SYMBOLS = {0: "k_numeric_split_panel", 1: "k_numeric_split_pipe", 2: "k_numeric_split_cat"}
 # FP64 numeric kernels (BSM_FP64_*): name -> (number, kernel symbol)
 FP64_KERNELS = {"t16b2": (0, "k_numeric_fp64_t16"), "t16b3": (1, "k_numeric_fp64_t16"),
                 "t32": (2, "k_numeric_fp64_t32"), "pk12": (3, "k_numeric_fp64_pk"),
@@ -834,7 +835,7 @@ def main():
     if prof.multiplies > 0:
         num_ms = prof.ms_numeric / prof.multiplies
         kname = (FP64_KERNELS[FP64_BY_NUMBER[prof.last_fp64_kernel]][1] if args.precision == "fp64"
-                 else "k_numeric_split_pipe")
+                 else SPLIT_KERNEL_SYMBOLS.get(prof.last_split_kernel, "k_numeric_split_pipe"))
     else:
         num_ms = total_ms / args.steps
         kname = "whole multiply (CUDA graph replay)"
