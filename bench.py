@@ -65,14 +65,14 @@ MEASURED_TRAFFIC = {
     ("pk12", "water2048"): dict(
         sections=[("paper_1705_10218_gb300/csrc/k_numeric_fp64.cu",
                    ("// pk\n", "cudaError_t launch_numeric_fp64("),
-                   "d2160908186159496f1b63411fa5b20c48f6a78c57c81b7c774a87167bf5e9f4"),
+                   "7bbcdcfe0e18d9a1b4f6759ea308f217cc9b13f32aaa2edbd5433183548b5194"),
                   ("paper_1705_10218_gb300/csrc/k_classes.cu",
                    ("// Work in a row order.", "}  // namespace bsm"),
                    "b173af39936271e55c6a2623c0b1222afaca8a97ab34ff8f9a0ec78e9ecdf01b"),
                   ("paper_1705_10218_gb300/csrc/bsm_api.cu",
                    ("static void bfs_row_order(", "static uint64_t next_order_id("),
                    "113dd9175f43cb3ea209f7d880be5023dd9fd7acdf547fa5077ea74319814288")],
-        bytes=2.982e9 + 1.559e9),
+        bytes=2.983e9 + 1.559e9),
 }
 
 
