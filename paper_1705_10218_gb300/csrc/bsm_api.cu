@@ -242,6 +242,9 @@ struct bsm_mat_s {
   // (same block rows).
   int32_t *row_order = nullptr;
   uint64_t order_id = 0;
+  // the pattern (row pointers, column indices) the order was computed from: an
+  // upload of the same pattern keeps the order without a new search
+  std::vector<int32_t> order_ptr, order_col;
   Pending pend;
 };
 
@@ -1029,6 +1032,8 @@ static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double 
     CK(cudaMemcpyAsync(C->row_order, A->row_order, 2 * (size_t)C->nbr * sizeof(int32_t),
                        cudaMemcpyDeviceToDevice, L.s));
     C->order_id = A->order_id;
+    C->order_ptr.clear();  // not computed from C's own pattern
+    C->order_col.clear();
   }
   L.dA = dev_view(A), L.dB = dev_view(B), L.dC = dev_view(C);
   double *host_dev = nullptr;  // device address of o.host_values
@@ -1518,16 +1523,28 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
     }
   }
   for (int32_t i = 0; i < nbrows; i++) h_row_ptr[i + 1] += h_row_ptr[i];
-  // the row order of the numeric phase (host BFS over the sorted pattern)
+  // the row order of the numeric phase (host BFS over the sorted pattern),
+  // kept as it is when the pattern is the one it was computed from (an
+  // iteration that assigns new values to the same pattern)
   std::vector<int32_t> h_order;
-  M->order_id = 0;
   if (nbrows == nbcols && nbrows >= kOrderMinRows) {
-    h_order.resize(2 * (size_t)nbrows);
-    bfs_row_order(nbrows, h_row_ptr, h_col, h_order.data(), h_order.data() + nbrows);
-    if (!M->row_order && (rc = dev_alloc(&M->row_order, 2 * (int64_t)nbrows))) return rc;
-    if ((e = cp(M->row_order, h_order.data(), h_order.size() * 4)) != cudaSuccess)
-      return cuda_fail(e, "matrix upload row order");
-    M->order_id = next_order_id();
+    const bool same = M->order_id && M->order_ptr.size() == (size_t)nbrows + 1 &&
+                      M->order_col.size() == (size_t)nblocks &&
+                      !memcmp(M->order_ptr.data(), h_row_ptr, ((size_t)nbrows + 1) * 4) &&
+                      (nblocks == 0 || !memcmp(M->order_col.data(), h_col, (size_t)nblocks * 4));
+    if (!same) {
+      M->order_id = 0;
+      h_order.resize(2 * (size_t)nbrows);
+      bfs_row_order(nbrows, h_row_ptr, h_col, h_order.data(), h_order.data() + nbrows);
+      if (!M->row_order && (rc = dev_alloc(&M->row_order, 2 * (int64_t)nbrows))) return rc;
+      if ((e = cp(M->row_order, h_order.data(), h_order.size() * 4)) != cudaSuccess)
+        return cuda_fail(e, "matrix upload row order");
+      M->order_ptr.assign(h_row_ptr, h_row_ptr + nbrows + 1);
+      M->order_col.assign(h_col, h_col + nblocks);
+      M->order_id = next_order_id();
+    }
+  } else {
+    M->order_id = 0;
   }
   int64_t hdr[2] = {nblocks, nnz};
   if ((e = cp(M->front.row_ptr, h_row_ptr, ((size_t)nbrows + 1) * 4)) != cudaSuccess ||
