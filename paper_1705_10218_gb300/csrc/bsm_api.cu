@@ -223,6 +223,8 @@ struct bsm_mat_s {
   int32_t nbr = 0, nbc = 0;
   std::vector<int32_t> h_row_sizes, h_col_sizes;
   int32_t max_row = 0, max_col = 0;  // largest block row / column size
+  int64_t max_row_blocks = -1;  // most blocks in one block row (-1: unknown, the
+                                // pattern was made on the device)
   // shape kinds: the distinct block row / column sizes (at most 32; more are
   // folded into one kind) and each block row's / column's kind index
   std::vector<int32_t> row_kinds, col_kinds;
@@ -879,13 +881,26 @@ static int tune_pk_tiles(Launch &L, int variant) {
   return BSM_OK;
 }
 
+// Words of the fill pass's per-row bit matrix: a bound on a C block row's
+// blocks (B's block columns, and A's longest row times B's) times the words of
+// A's longest row; 0 (the largest) where a pattern was made on the device or C
+// enters (beta != 0). Smaller matrices leave room for more resident blocks of
+// the latency-bound placement on very sparse inputs; a row beyond the bound
+// takes the slower per-window passes.
+static int fill_mask_words(const Launch &L) {
+  if (L.use_cin || L.A->max_row_blocks < 0 || L.B->max_row_blocks < 0) return 0;
+  const int64_t cblk = std::min<int64_t>(L.B->nbc, L.A->max_row_blocks * L.B->max_row_blocks);
+  const int64_t words = cblk * ((L.A->max_row_blocks + 31) / 32);
+  return (int)std::min<int64_t>(std::max<int64_t>((words + 31) & ~31ll, 32), 8192);
+}
+
 // fill, shape-class grouping (per-stack), numeric
 static int stage_b(Launch &L, bool record, bool may_tune) {
   bsm_ctx ctx = L.ctx;
   int rc;
   L.host_written = true;  // the split kernels store it; FP64 launches update this
   CK(launch_symbolic_fill(L.dA, L.dB, L.dC, L.use_cin ? 1 : 0, L.eps, L.ws, L.out, ctx->d_status,
-                          ctx->nsm * 6, L.s));
+                          ctx->nsm, fill_mask_words(L), L.s));
   ctx->launches++;
   if (L.prof && record) CK(cudaEventRecord(ctx->prof_ev[L.slot][2], L.s));
   if (L.split && split_kernel_of(L.o, L.B) == BSM_SPLIT_PANEL) {
@@ -1036,6 +1051,7 @@ static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double 
     C->order_col.clear();
   }
   L.dA = dev_view(A), L.dB = dev_view(B), L.dC = dev_view(C);
+  C->max_row_blocks = -1;  // the result's pattern is made on the device
   double *host_dev = nullptr;  // device address of o.host_values
   if (o.host_values) {
     cudaPointerAttributes pa{};
@@ -1522,6 +1538,9 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
       h_row_ptr[blk_row[b] + 1]++;
     }
   }
+  M->max_row_blocks = 0;
+  for (int32_t i = 0; i < nbrows; i++)
+    M->max_row_blocks = std::max<int64_t>(M->max_row_blocks, h_row_ptr[i + 1]);
   for (int32_t i = 0; i < nbrows; i++) h_row_ptr[i + 1] += h_row_ptr[i];
   // the row order of the numeric phase (host BFS over the sorted pattern),
   // kept as it is when the pattern is the one it was computed from (an
@@ -1873,6 +1892,11 @@ int bsm_mat_add(bsm_ctx ctx, double alpha, bsm_mat A, double beta, bsm_mat C) {
   C->nnz = h.nnz_c;
   C->hint_blk = std::max(C->hint_blk, h.nblk_c);
   C->hint_nnz = std::max(C->hint_nnz, h.nnz_c);
+  // the union of the two patterns (or A's alone)
+  C->max_row_blocks = !use_cin ? A->max_row_blocks
+                      : (A->max_row_blocks < 0 || C->max_row_blocks < 0)
+                          ? -1
+                          : A->max_row_blocks + C->max_row_blocks;
   return BSM_OK;
 }
 
@@ -1991,6 +2015,9 @@ int mat_create_diag(bsm_ctx ctx, int nparts, const DiagPart *parts, bsm_mat *out
       h_row_ptr[h_row[g] + 1]++;
     }
   }
+  M->max_row_blocks = 0;
+  for (int32_t i = 0; i < nbr; i++)
+    M->max_row_blocks = std::max<int64_t>(M->max_row_blocks, h_row_ptr[i + 1]);
   for (int32_t i = 0; i < nbr; i++) h_row_ptr[i + 1] += h_row_ptr[i];
   if ((rc = buf_grow(M, M->front, nblk, nnz, true))) return fail(rc);
   cudaStream_t st = ctx->stream;

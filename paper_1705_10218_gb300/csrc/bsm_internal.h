@@ -97,8 +97,11 @@ cudaError_t launch_symbolic_count(DevMat A, DevMat B, DevMat Cin, int use_cin, d
 cudaError_t launch_symbolic_scan(int32_t nbr, DevWs ws, DevOut C, DevStatus *st,
                                  cudaStream_t stream);
 
+// mask_words: words of the per-row bit matrix of the placement (a bound on C
+// blocks per row times the words per A row; rows beyond it take the slower
+// per-window passes); 0: the largest (8192).
 cudaError_t launch_symbolic_fill(DevMat A, DevMat B, DevMat Cin, int use_cin, double eps,
-                                 DevWs ws, DevOut C, const DevStatus *st, int grid,
+                                 DevWs ws, DevOut C, const DevStatus *st, int nsm, int mask_words,
                                  cudaStream_t stream);
 
 // FP64 numeric kernel variants (k_numeric_fp64.cu).

@@ -298,7 +298,7 @@ extern "C" int bsm_multiply_noalloc(double alpha, const bsm_dev_csr *A, const bs
     return noalloc_cuda_fail(e);
   if ((e = launch_symbolic_scan(A->nbr, ws, out, st, s)) != cudaSuccess)
     return noalloc_cuda_fail(e);
-  if ((e = launch_symbolic_fill(dA, dB, none, 0, eps, ws, out, st, nsm * 6, s)) != cudaSuccess)
+  if ((e = launch_symbolic_fill(dA, dB, none, 0, eps, ws, out, st, nsm, 0, s)) != cudaSuccess)
     return noalloc_cuda_fail(e);
   // block sizes live on the device only: the 32 x 32 tile variant handles any size
   if ((e = launch_numeric_fp64(kFp64T32, dA, dB, out, none, alpha, 0.0, ws, st, nullptr, nullptr,

@@ -324,7 +324,8 @@ __device__ int word_prefix(const uint32_t *bitmap, int32_t *wpre, int nwords) {
   return (int)total;
 }
 
-// Words of the per-row (C block x A block) bit matrix of the fill pass.
+// Words of the per-row (C block x A block) bit matrix of the fill pass, at
+// most (the launch may ask for fewer, for more resident blocks).
 constexpr int kMaskWords = 8192;
 
 // Rank of column offset jj inside the window among the set bits.
@@ -337,7 +338,8 @@ __device__ __forceinline__ int bit_rank(const uint32_t *bitmap, const int32_t *w
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSymThreads) k_symbolic_fill(DevMat A, DevMat B, DevMat Cin,
                                                                int use_cin, double eps, DevWs ws,
-                                                               DevOut C, const DevStatus *st) {
+                                                               DevOut C, const DevStatus *st,
+                                                               int mask_words) {
   if (st->overflow) return;
   extern __shared__ uint32_t smem_bits[];
   const int nbc = B.nbc;
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(kSymThreads) k_symbolic_fill(DevMat A, DevMat 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int64_t dummy0 = 0, dummy1 = 0, dummy2 = 0;
 
-  uint32_t *mask = smem_bits + 2 * nwords_max;  // kMaskWords words, see below
+  uint32_t *mask = smem_bits + 2 * nwords_max;  // mask_words words, see below
   const EpsBand band = eps_band(eps);
 
   for (int i = blockIdx.x; i < A.nbr; i += gridDim.x) {
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(kSymThreads) k_symbolic_fill(DevMat A, DevMat 
     // (ascending k) is then the popcount of the bits before it, so every
     // product is placed at once, without a pass per A block.
     const int wps = (p1 - p0 + 31) >> 5;  // mask words per C block
-    if (whole && (int64_t)(g1 - g0) * wps <= kMaskWords) {
+    if (whole && (int64_t)(g1 - g0) * wps <= mask_words) {
       const int nwords = (nbc + 31) >> 5;
       row_bitmap<false>(A, B, Cin, use_cin, eps, i, 0, nbc, true, bitmap, nwords, dummy0, dummy1,
                         dummy2);
@@ -554,11 +556,19 @@ __global__ void __launch_bounds__(kSymThreads) k_symbolic_fill(DevMat A, DevMat 
 }
 
 cudaError_t launch_symbolic_fill(DevMat A, DevMat B, DevMat Cin, int use_cin, double eps,
-                                 DevWs ws, DevOut C, const DevStatus *st, int grid,
+                                 DevWs ws, DevOut C, const DevStatus *st, int nsm, int mask_words,
                                  cudaStream_t stream) {
   const int nwords = (min(B.nbc, kWindowCols) + 31) / 32;
-  const size_t smem = ((size_t)max(nwords, 1) * 2 + kMaskWords) * sizeof(uint32_t);
-  k_symbolic_fill<<<grid, kSymThreads, smem, stream>>>(A, B, Cin, use_cin, eps, ws, C, st);
+  const int mw = (mask_words > 0 && mask_words < kMaskWords) ? mask_words : kMaskWords;
+  const size_t smem = ((size_t)max(nwords, 1) * 2 + mw) * sizeof(uint32_t);
+  // one wave of resident blocks (rows taken in a grid stride): more resident
+  // blocks hide more of each row's load latency, a second wave only adds a tail
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_symbolic_fill,
+                                                                kSymThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = nsm * (per_sm > 0 ? per_sm : 1);
+  k_symbolic_fill<<<grid, kSymThreads, smem, stream>>>(A, B, Cin, use_cin, eps, ws, C, st, mw);
   return cudaGetLastError();
 }
 
