@@ -145,7 +145,11 @@ typedef struct {
   int64_t host_cap;
   int32_t split_kernel; /* 0, or 1 + BSM_SPLIT_* to force that split-precision kernel
                            (ignored by FP64); out of range: BSM_ERR_INVALID_ARG */
-  int32_t reserved;     /* 0 */
+  int32_t numeric_slices; /* 0 or 1: the numeric phase in one launch; n > 1 (at most 64):
+                             the FP64 persistent launch in n launches over consecutive
+                             ranges of the C blocks, so that other streams' kernels can
+                             run between them (the request loop slices large requests);
+                             out of range: BSM_ERR_INVALID_ARG */
 } bsm_opts;
 
 /* Counters of one multiply (filled when bsm_stats* is not NULL; this makes
@@ -274,7 +278,11 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * deadline, and the earliest-deadline request waits for memory rather than be
  * passed. A large request (estimated at least 8 ms) fills the GPU alone: one
  * runs at a time, and a large earliest-deadline request waits only for the
- * running one, while the other lanes take small requests. A small request (estimated at most 4 ms) shares its multiply with the
+ * running one, while the other lanes take small requests. A large request's
+ * numeric phase runs in slices of about 4 ms (bsm_opts.numeric_slices) and
+ * small batches on a stream of the highest priority, so a small request
+ * arriving meanwhile starts at the next slice boundary. Latency and deadline
+ * count from the start of bsm_server_submit. A small request (estimated at most 4 ms) shares its multiply with the
  * other small queued requests of the same eps (up to 16 requests and 8 ms of
  * estimated work, at most four times the first request's estimate, so that it
  * still makes its deadline): the batch runs as one multiply of the block-diagonal matrix

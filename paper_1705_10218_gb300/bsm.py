@@ -60,7 +60,7 @@ class _Opts(ctypes.Structure):
         ("host_values", ctypes.c_void_p),
         ("host_cap", ctypes.c_int64),
         ("split_kernel", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("numeric_slices", ctypes.c_int32),
     ]
 
 
@@ -213,7 +213,8 @@ class Context:
                  precision: int = BSM_PREC_FP64, launch: int = BSM_LAUNCH_PERSISTENT,
                  blocking: bool = False, autotune: bool = False, stream=None,
                  graph: bool = False, stats: bool = False, fp64_kernel: int | None = None,
-                 host_out: np.ndarray | None = None, split_kernel: int | None = None) -> Stats | None:
+                 host_out: np.ndarray | None = None, split_kernel: int | None = None,
+                 numeric_slices: int = 0) -> Stats | None:
         """fp64_kernel: one of BSM_FP64_* to force that FP64 kernel, None for the
         library's choice. split_kernel: one of BSM_SPLIT_* likewise for the
         split precisions. host_out: a float64 array in page-locked host memory
@@ -227,7 +228,7 @@ class Context:
         o = _Opts(int(precision), int(launch), int(bool(blocking)), int(bool(autotune)),
                   _stream_ptr(stream), int(bool(graph)),
                   0 if fp64_kernel is None else int(fp64_kernel) + 1, hv, hcap,
-                  0 if split_kernel is None else int(split_kernel) + 1, 0)
+                  0 if split_kernel is None else int(split_kernel) + 1, int(numeric_slices))
         st = _Stats() if stats else None
         rc = lib().bsm_multiply(self._h, float(alpha), A._h, B._h, float(beta), C._h, float(eps),
                                 ctypes.byref(o), ctypes.byref(st) if st is not None else None)

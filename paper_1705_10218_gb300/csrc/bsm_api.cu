@@ -971,7 +971,18 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
       ctx->launches += 2;
       items = ctx->cls_items;
     }
-    if ((rc = launch_numeric(L, variant, items, nullptr, L.A->max_row, L.B->max_col))) return rc;
+    if (!L.split && L.o.numeric_slices > 1) {
+      // consecutive ranges of the C blocks (of the work list) in launches of their own
+      const int n = L.o.numeric_slices;
+      CK(launch_slice_segs(ctx->d_status, n, ctx->cls_segs, L.s));
+      ctx->launches++;
+      for (int x = 0; x < n; x++)
+        if ((rc = launch_numeric(L, variant, items, ctx->cls_segs + 2 * x, L.A->max_row,
+                                 L.B->max_col)))
+          return rc;
+    } else if ((rc = launch_numeric(L, variant, items, nullptr, L.A->max_row, L.B->max_col))) {
+      return rc;
+    }
   }
   // the host copy of the values, where a numeric kernel did not store it
   if (L.out.host_vals && !L.host_written) {
@@ -1012,7 +1023,7 @@ static void graph_key(const Launch &L, std::vector<uint64_t> &k) {
   put(L.ctx->pw.recs), put(L.ctx->pw.tiles), put(L.ctx->pw.row_nt);
   dbl(L.alpha), dbl(L.beta), dbl(L.eps);
   num(L.o.precision), num(L.o.launch), num(L.o.fp64_kernel), num((int64_t)L.ctx->tune_version);
-  num(L.o.split_kernel);
+  num(L.o.split_kernel), num(L.o.numeric_slices);
   put(L.out.host_vals), num(L.out.host_cap);
   num(fp64_default(L.ctx, L.C));
 }
@@ -1732,6 +1743,7 @@ int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, b
     return BSM_ERR_INVALID_ARG;
   if (o.fp64_kernel < 0 || o.fp64_kernel > BSM_FP64_NUM_KERNELS) return BSM_ERR_INVALID_ARG;
   if (o.split_kernel < 0 || o.split_kernel > BSM_SPLIT_NUM_KERNELS) return BSM_ERR_INVALID_ARG;
+  if (o.numeric_slices < 0 || o.numeric_slices > 64) return BSM_ERR_INVALID_ARG;
   if (o.host_values) {  // must be device-mapped page-locked host memory
     if (o.host_cap < 0) return BSM_ERR_INVALID_ARG;
     cudaPointerAttributes pa{};

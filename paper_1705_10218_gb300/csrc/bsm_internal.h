@@ -151,6 +151,9 @@ cudaError_t launch_class_sort(DevOut C, const int32_t *row_cls, const int32_t *c
 cudaError_t launch_order_items(DevOut C, const int32_t *row_order, const int32_t *row_pos,
                                int32_t nbr, const DevStatus *st, int32_t *start, int32_t *items,
                                int nsm, cudaStream_t stream);
+// segs[2s..2s+1] = the s-th of n consecutive ranges of the multiply's C blocks
+// (one thread block; n <= 64).
+cudaError_t launch_slice_segs(const DevStatus *st, int n, int64_t *segs, cudaStream_t stream);
 
 // Split precision (k_split.cu). left/right: slice layouts of the operand as a
 // left (row-major) or right (column-major) MMA operand; either may be null.

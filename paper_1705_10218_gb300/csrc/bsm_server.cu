@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -89,6 +90,12 @@ constexpr int kMaxBatch = 16;
 // at most kMaxLarge run at a time, while the other lanes take small requests.
 constexpr double kLargeMs = 8.0;
 constexpr int kMaxLarge = 1;
+// A large request's numeric phase runs in slices of about kSliceMs of
+// estimated work (consecutive ranges of its C blocks, each a launch of its
+// own), and small batches run on a stream of the highest priority: a small
+// request that arrives while a large one runs gets SMs at the next slice
+// boundary instead of after the whole multiply.
+constexpr double kSliceMs = 4.0;
 constexpr double kFixedMs = 0.15;
 double est_run_ms(int64_t macs, int precision) {
   const double flop_per_ms = precision == BSM_PREC_FP64 ? 1.0e9 : 2.5e9;
@@ -154,9 +161,11 @@ struct PinnedPool {
   }
 };
 
-// A lane: a context and the worker thread that runs one request at a time on it.
+// A lane: a context and the worker thread that runs one batch at a time on
+// it; small batches launch on the lane's high-priority stream.
 struct Slot {
   bsm_ctx ctx = nullptr;
+  cudaStream_t hi = nullptr;
   std::thread worker;
 };
 
@@ -276,6 +285,10 @@ static void run_batch(bsm_server s, Slot &sl, const std::vector<Request *> &batc
     o.blocking = 1;
     o.host_values = hv;
     o.host_cap = hv ? hv_cap : 0;
+    if (batch[0]->est_ms >= kLargeMs)  // a large request runs alone, sliced
+      o.numeric_slices = (int)std::min(64.0, std::ceil(batch[0]->est_ms / kSliceMs));
+    else
+      o.stream = sl.hi;
     rc = bsm_multiply(sl.ctx, 1.0, A, A, 0.0, C, batch[0]->eps, &o, nullptr);
   }
   int64_t nblk = 0, nnz = 0;
@@ -433,8 +446,16 @@ int bsm_server_create(int device, const bsm_server_opts *opts, bsm_server *out) 
   s->precision = o.precision;
   s->budget = o.hbm_budget;
   s->slots = std::vector<Slot>(o.slots);
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
   for (Slot &sl : s->slots) {
     int rc = bsm_ctx_create(device, &sl.ctx);
+    if (rc == BSM_OK &&
+        cudaStreamCreateWithPriority(&sl.hi, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+      cudaGetLastError();
+      sl.hi = nullptr;
+      rc = BSM_ERR_CUDA;
+    }
     if (rc != BSM_OK) {
       bsm_server_destroy(s);
       return rc;
@@ -458,8 +479,10 @@ int bsm_server_destroy(bsm_server s) {
   for (auto &kv : s->reqs) forget(s, kv.second);
   s->reqs.clear();
   s->queue.clear();
-  for (Slot &sl : s->slots)
+  for (Slot &sl : s->slots) {
     if (sl.ctx) bsm_ctx_destroy(sl.ctx);
+    if (sl.hi) cudaStreamDestroy(sl.hi);
+  }
   s->pinned.clear();
   delete s;
   return BSM_OK;
@@ -468,6 +491,9 @@ int bsm_server_destroy(bsm_server s) {
 int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_t nblocks,
                       const int32_t *blk_row, const int32_t *blk_col, const double *values,
                       double eps, int64_t *id) {
+  // the request arrives now: its latency and deadline count from here, not from
+  // the end of the copies below (which may wait for page-locked memory)
+  const double t_arrive = now_ms();
   if (!s || !id || nbrows < 0 || nblocks < 0 || (nbrows > 0 && !sizes) ||
       (nblocks > 0 && (!blk_row || !blk_col || !values)))
     return BSM_ERR_INVALID_ARG;
@@ -539,7 +565,7 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
-    r->t_submit = now_ms();
+    r->t_submit = t_arrive;
     r->deadline = r->t_submit + kStretch * r->est_ms;
     s->reqs[r->id] = r;
     s->queue.push_back(r);

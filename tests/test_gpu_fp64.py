@@ -467,3 +467,25 @@ def test_row_order_changes_no_result(gpu_ctx, oracle_mod, bsm_lib, kern):
     assert np.array_equal(p[2][0], ref_d.blk_row) and np.array_equal(p[2][1], ref_d.blk_col)
     assert H.rel_frobenius(p[3], ref_d.values) <= TOL
     dA.destroy()
+
+
+@pytest.mark.parametrize("slices", [2, 7, 64])
+def test_numeric_slices(gpu_ctx, oracle_mod, bsm_lib, slices):
+    """The FP64 numeric phase in several launches over consecutive ranges of
+    the C blocks: every block is still computed alone, so the values equal
+    the single launch's bit for bit and the oracle's within 1e-12; a slice
+    count out of range is refused."""
+    A = synth.water(40, seed=12)
+    ref = oracle_mod.multiply(A, A, eps=1e-10)
+    r1, c1, v1, _ = run_gpu(gpu_ctx, A, A, eps=1e-10)
+    r, c, v, st = run_gpu(gpu_ctx, A, A, eps=1e-10, numeric_slices=slices)
+    assert np.array_equal(r, r1) and np.array_equal(c, c1) and np.array_equal(v, v1)
+    assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+    assert H.rel_frobenius(v, ref.values) <= TOL
+    dA = gpu_ctx.from_blocks(A)
+    dC = gpu_ctx.empty(A.row_sizes, A.col_sizes)
+    with pytest.raises(bsm_lib.BsmError) as e:
+        gpu_ctx.multiply(1.0, dA, dA, 0.0, dC, 1e-10, numeric_slices=65)
+    assert e.value.name == "INVALID_ARG"
+    dA.destroy()
+    dC.destroy()

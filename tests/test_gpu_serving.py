@@ -213,13 +213,19 @@ def test_small_request_passes_earlier_large_one(bsm_lib):
     """Earliest deadline first: with one lane busy, a small request submitted
     just after a large one is admitted before it."""
     eps = 1e-10
-    S = [synth.water(384, seed=6300), synth.water(256, seed=6301), synth.water(8, seed=6302)]
-    with bsm_lib.Server(0, slots=1, hbm_budget=8 << 30) as srv:
+    S = [synth.water(1024, seed=6300), synth.water(256, seed=6301), synth.water(8, seed=6302)]
+    with bsm_lib.Server(0, slots=1, hbm_budget=48 << 30) as srv:
+        # a request of the large one's size first: its page-locked block is then
+        # cached, so that submitting the large one below takes a copy, no allocation
+        w = srv.submit(S[1], eps)
+        drain(srv, [w])
+        srv.release(w)
         first = srv.submit(S[0], eps)
         while srv.poll(first)[0] == 0:  # until it holds the only lane
             pass
         large = srv.submit(S[1], eps)
         small = srv.submit(S[2], eps)
+        assert srv.poll(first)[0] == 1  # both queued while the lane is busy
         order = []
         for _ in range(10 ** 7):
             srv.progress()
