@@ -23,7 +23,7 @@
 //
 // The caller's arrays are device memory the host cannot read cheaply, so a
 // first kernel checks them (row pointers, column indices, block sizes, block
-// offsets) and the call reads the verdict back before any other kernel uses
+// offsets) and the call reads the outcome back before any other kernel uses
 // them as indices: a malformed matrix is an error code, not a stray access.
 #include <cuda_runtime.h>
 
@@ -42,7 +42,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 bool g_noalloc_init[kMaxDevices] = {};
 
-// Verdict bits of the input check.
+// Outcome bits of the input check.
 enum : int32_t {
   kBadRowPtr = 1,   // row_ptr[0] != 0, decreasing, or row_ptr[nbr] != nblk
   kBadColIdx = 2,   // a column index outside [0, nbc)
