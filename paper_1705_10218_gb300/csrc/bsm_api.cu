@@ -965,7 +965,7 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
       return rc;
     // C blocks in A's row order where A has one, else in C's row order
     const int32_t *items = nullptr;
-    if (!L.split && L.A->order_id) {
+    if (L.A->order_id) {
       CK(launch_order_items(L.out, L.A->row_order, L.A->row_order + L.A->nbr, L.A->nbr,
                             ctx->d_status, ctx->ord_start, ctx->cls_items, ctx->nsm, L.s));
       ctx->launches += 2;
