@@ -66,6 +66,22 @@ cudaError_t launch_class_sort(DevOut C, const int32_t *row_cls, const int32_t *c
   return cudaGetLastError();
 }
 
+// segs[2s], segs[2s + 1]: the s-th of n consecutive, nearly equal ranges of
+// the multiply's C blocks (the count is known on the device only).
+__global__ void k_slice_segs(const DevStatus *st, int n, int64_t *__restrict__ segs) {
+  if (st->overflow) return;
+  const int64_t total = st->nblk_c;
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    segs[2 * s] = total * s / n;
+    segs[2 * s + 1] = total * (s + 1) / n;
+  }
+}
+
+cudaError_t launch_slice_segs(const DevStatus *st, int n, int64_t *segs, cudaStream_t stream) {
+  k_slice_segs<<<1, 64, 0, stream>>>(st, n, segs);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Work in a row order. row_order[p] is the C block row at position p of a
 // permutation of the rows, row_pos[r] the position of row r. items receives
@@ -127,22 +143,6 @@ __global__ void k_order_fill(DevOut C, const int32_t *__restrict__ row_pos, cons
     const int32_t r = C.blk_row[g];
     items[start[row_pos[r]] + (int32_t)(g - C.row_ptr[r])] = (int32_t)g;
   }
-}
-
-// segs[2s], segs[2s + 1]: the s-th of n consecutive, nearly equal ranges of
-// the multiply's C blocks (the count is known on the device only).
-__global__ void k_slice_segs(const DevStatus *st, int n, int64_t *__restrict__ segs) {
-  if (st->overflow) return;
-  const int64_t total = st->nblk_c;
-  for (int s = threadIdx.x; s < n; s += blockDim.x) {
-    segs[2 * s] = total * s / n;
-    segs[2 * s + 1] = total * (s + 1) / n;
-  }
-}
-
-cudaError_t launch_slice_segs(const DevStatus *st, int n, int64_t *segs, cudaStream_t stream) {
-  k_slice_segs<<<1, 64, 0, stream>>>(st, n, segs);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_order_items(DevOut C, const int32_t *row_order, const int32_t *row_pos,
