@@ -277,8 +277,9 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * arrived shortly before, no request is passed by one that arrives after its
  * deadline, and the earliest-deadline request waits for memory rather than be
  * passed. A large request (estimated at least 8 ms) fills the GPU alone: one
- * runs at a time, and a large earliest-deadline request waits only for the
- * running one, while the other lanes take small requests. A large request's
+ * runs at a time (two when only large requests, at least two, wait), and a
+ * large earliest-deadline request waits only for the running one, while the
+ * other lanes take small requests. A large request's
  * numeric phase runs in slices of about 4 ms (bsm_opts.numeric_slices) and
  * small batches on a stream of the highest priority, so a small request
  * arriving meanwhile starts at the next slice boundary. Latency and deadline

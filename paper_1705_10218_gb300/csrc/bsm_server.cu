@@ -84,12 +84,14 @@ constexpr double kStretch = 4.0;
 constexpr double kMergeMs = 4.0;
 constexpr double kBatchMs = 8.0;
 constexpr int kMaxBatch = 16;
-// A large request (estimated at least kLargeMs) fills every SM on its own, and
-// two of them running at once only contend (a 100-request water replay: 84.6
-// requests/s with 4 lanes free to run large ones together, 94.4 with 2 lanes):
-// at most kMaxLarge run at a time, while the other lanes take small requests.
+// A large request (estimated at least kLargeMs) fills every SM on its own: at
+// most one large request runs, so that the small ones get the SMs between its
+// slices, unless a backlog of large requests waits and no small one does (the
+// tail of a burst): then two may run, the second's upload and read-back
+// overlapping the first's products (a 100-request water replay: 84.6 requests/s
+// with 4 lanes free to run large ones together, 94.4 with 2 lanes).
 constexpr double kLargeMs = 8.0;
-constexpr int kMaxLarge = 1;
+constexpr int kMaxLarge = 1, kMaxLargeAlone = 2;
 // A large request's numeric phase runs in slices of about kSliceMs of
 // estimated work (consecutive ranges of its C blocks, each a launch of its
 // own), and small batches run on a stream of the highest priority: a small
@@ -341,7 +343,8 @@ static void run_batch(bsm_server s, Slot &sl, const std::vector<Request *> &batc
 }
 
 // The next batch, under the server's lock: the earliest-deadline request that
-// may start -- a large one only while fewer than kMaxLarge large ones run --
+// may start -- a large one only while fewer than kMaxLarge large ones run
+// (kMaxLargeAlone when only large requests, two or more, wait) --
 // once it fits the budget (it waits for memory rather than be passed by later
 // requests), and, when it is small, the other small queued requests of the same
 // eps in deadline order, as far as the work and memory limits allow. The batch
@@ -352,9 +355,12 @@ static bool pick_batch(bsm_server s, std::vector<Request *> &batch) {
   std::vector<Request *> order(s->queue.begin(), s->queue.end());
   std::stable_sort(order.begin(), order.end(),
                    [](const Request *a, const Request *b) { return a->deadline < b->deadline; });
+  int small_waiting = 0, large_waiting = 0;
+  for (const Request *r : order) (r->est_ms < kLargeMs ? small_waiting : large_waiting)++;
+  const int max_large = (small_waiting == 0 && large_waiting >= 2) ? kMaxLargeAlone : kMaxLarge;
   Request *head = nullptr;
   for (Request *r : order)
-    if (r->est_ms < kLargeMs || s->running_large < kMaxLarge) {
+    if (r->est_ms < kLargeMs || s->running_large < max_large) {
       head = r;
       break;
     }
