@@ -132,9 +132,11 @@ def test_split_mixed_sizes_alpha_beta(gpu_ctx, oracle_mod, kernel, prec):
     assert np.all(np.abs(Rg - Rr) <= bound)
 
 
-def test_split_panel_empty_rows_and_cin_only_blocks(gpu_ctx, oracle_mod):
+@pytest.mark.parametrize("kernel", sorted(KERNELS))
+def test_split_empty_rows_and_cin_only_blocks(gpu_ctx, oracle_mod, kernel):
     """Rows of A without blocks and C blocks that come only from C_in
-    (beta != 0): the panel kernel's empty chunks give exact zeros."""
+    (beta != 0): blocks with no products (empty chunks, an empty product
+    stream) give exactly beta * C_in."""
     rng = np.random.default_rng(9)
     rs = np.array([5, 13, 5, 13, 7, 3], np.int32)
     A = synth.random_blocks(rng, rs, rs, 0.4, kind="int")
@@ -143,7 +145,7 @@ def test_split_panel_empty_rows_and_cin_only_blocks(gpu_ctx, oracle_mod):
     C = synth.random_blocks(rng, rs, rs, 0.5, kind="int")
     for prec in PRECS:
         ref = oracle_mod.multiply(A, A, alpha=1.0, beta=2.0, C=C, eps=0.0)
-        r, c, v, st = gpu_mult(gpu_ctx, A, A, prec, "panel", alpha=1.0, beta=2.0, C=C)
+        r, c, v, st = gpu_mult(gpu_ctx, A, A, prec, kernel, alpha=1.0, beta=2.0, C=C)
         assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
         assert np.array_equal(v, ref.values)
 
