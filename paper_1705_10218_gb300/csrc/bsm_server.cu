@@ -10,9 +10,12 @@
 // time plus kStretch times its estimated run time (from the exact count of its
 // unfiltered multiply-adds). Small requests therefore pass large ones that
 // arrived a little earlier, while a large one is never passed by requests that
-// arrive after its deadline. A batch is the earliest-deadline request plus, when
-// it is small, the other small queued requests of the same eps in deadline
-// order, up to kMergeMs of estimated work. The batch runs as one multiply of the
+// arrive after its deadline. Large requests (kLargeMs) run one at a time (two
+// for a backlog of large ones only), their numeric phase in slices, while small
+// batches launch on a high-priority stream and get the SMs between the slices.
+// A batch is the earliest-deadline request plus, when it is small (kMergeMs),
+// the other small queued requests of the same eps in deadline order, within the
+// batch limits below. The batch runs as one multiply of the
 // block-diagonal matrix diag(A_1, ..., A_n) (one norm, symbolic and numeric
 // launch sequence over all the batch's blocks). diag(A_1..A_n)^2 =
 // diag(A_1^2..A_n^2): the kernels compute every C block from its own product list
