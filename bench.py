@@ -520,7 +520,7 @@ def serve_measure(requests, pool_n, slots, budget_gb, seed=4):
                 warm.remove(i)
 
     def replay(arrivals):
-        lat, order = [], []
+        lat, order, parts = [], [], []
         ids = [None] * requests
         nxt, done = 0, 0
         t0 = time.perf_counter()
@@ -542,12 +542,13 @@ def serve_measure(requests, pool_n, slots, budget_gb, seed=4):
                     rows, cols, vals = srv.result(ids[r])
                     if len(vals) and not np.isfinite(vals[-1]):
                         raise RuntimeError("non-finite result")
+                    parts.append(srv.timing(ids[r]))
                     srv.release(ids[r])
                     lat.append(l_ms)
                     order.remove(r)
                     done += 1
         makespan = time.perf_counter() - t0
-        return lat, makespan, srv.info()["bytes_peak"]
+        return lat, makespan, srv.info()["bytes_peak"], np.asarray(parts)
 
     def poisson(rate):
         gaps = rng.exponential(1.0 / rate, requests)
@@ -555,17 +556,21 @@ def serve_measure(requests, pool_n, slots, budget_gb, seed=4):
 
     lam = 0.8 * cap
     b0 = srv.info()["batches"]
-    lat_p, span_p, peak_p = replay(poisson(lam))
+    lat_p, span_p, peak_p, parts_p = replay(poisson(lam))
     b1 = srv.info()["batches"]
-    lat_b, span_b, peak_b = replay(np.zeros(requests))
+    lat_b, span_b, peak_b, parts_b = replay(np.zeros(requests))
     b2 = srv.info()["batches"]
     lam_s = 0.8 * requests / span_b  # 0.8 x the server's own capacity
-    lat_s, span_s, peak_s = replay(poisson(lam_s))
+    lat_s, span_s, peak_s, parts_s = replay(poisson(lam_s))
     b3 = srv.info()["batches"]
     srv.close()
 
     def pct(x, q):
         return round(float(np.percentile(np.asarray(x), q)), 3)
+
+    def split(parts):  # medians of the time in submit, queued and running
+        return {k: pct(parts[:, c], 50) for c, k in enumerate(("submit_p50_ms", "wait_p50_ms",
+                                                               "run_p50_ms"))}
 
     tot_gflop = float(np.sum(gflop))
     return {
@@ -576,14 +581,15 @@ def serve_measure(requests, pool_n, slots, budget_gb, seed=4):
                        "p99_ms": pct(lat_seq, 99), "gflop_per_s": round(tot_gflop / t_seq, 2)},
         "poisson": {"arrival_rate_per_s": round(lam, 3), "multiplies_per_s": round(requests / span_p, 3),
                     "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99), "peak_gb": round(peak_p / 2**30, 3),
-                    "batches": b1 - b0},
+                    "batches": b1 - b0, **split(parts_p)},
         "burst": {"multiplies_per_s": round(requests / span_b, 3), "p50_ms": pct(lat_b, 50),
                   "p99_ms": pct(lat_b, 99), "gflop_per_s": round(tot_gflop / span_b, 2),
-                  "peak_gb": round(peak_b / 2**30, 3), "batches": b2 - b1},
+                  "peak_gb": round(peak_b / 2**30, 3), "batches": b2 - b1, **split(parts_b)},
         "poisson_at_server_rate": {"arrival_rate_per_s": round(lam_s, 3),
                                    "multiplies_per_s": round(requests / span_s, 3),
                                    "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
-                                   "peak_gb": round(peak_s / 2**30, 3), "batches": b3 - b2},
+                                   "peak_gb": round(peak_s / 2**30, 3), "batches": b3 - b2,
+                                   **split(parts_s)},
     }
 
 

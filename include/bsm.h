@@ -280,10 +280,13 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * runs at a time (two when only large requests, at least two, wait), and a
  * large earliest-deadline request waits only for the running one, while the
  * other lanes take small requests. A large request's
- * numeric phase runs in slices of about 4 ms (bsm_opts.numeric_slices) and
- * small batches on a stream of the highest priority, so a small request
- * arriving meanwhile starts at the next slice boundary. Latency and deadline
- * count from the start of bsm_server_submit. A small request (estimated at most 4 ms) shares its multiply with the
+ * numeric phase runs in slices of about 2 ms (bsm_opts.numeric_slices), each
+ * launched once the one before has finished and, while small batches are on
+ * the device, held back until they finish (at most 4 ms per slice); small
+ * batches run on a stream of the highest priority. A small request arriving
+ * meanwhile therefore starts at the next slice boundary and finds the SMs
+ * free. Latency and deadline count from the start of bsm_server_submit
+ * (bsm_server_timing splits it). A small request (estimated at most 4 ms) shares its multiply with the
  * other small queued requests of the same eps (up to 16 requests and 8 ms of
  * estimated work, at most four times the first request's estimate, so that it
  * still makes its deadline): the batch runs as one multiply of the block-diagonal matrix
@@ -291,8 +294,8 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * receives its own part of the result, which is bit for bit the result of that
  * request multiplied alone (the kernels compute each C block from its own
  * products only). The lanes run concurrently on the device. Inputs are copied
- * at submission into page-locked host memory (blocks sorted by (row, col)) and
- * uploaded from there; results wait in page-locked host memory until taken
+ * at submission into page-locked host memory (blocks sorted by (row, col);
+ * large copies on several threads) and uploaded from there; results wait in page-locked host memory until taken
  * (copied out) or released after use in place. Admission needs no call from
  * the caller. The server functions may be called from any thread;
  * bsm_server_destroy only once every other call on the server has returned.
@@ -336,6 +339,15 @@ int bsm_server_progress(bsm_server s, int32_t *completed);
  * request returns its error code. */
 int bsm_server_poll(bsm_server s, int64_t id, int32_t *state, double *latency_ms,
                     int64_t *nblocks, int64_t *nnz);
+
+/* Where a finished (done or failed) request's latency went, in milliseconds:
+ * submit_ms inside bsm_server_submit (checks, sorting, the copy into
+ * page-locked memory), wait_ms queued until a lane took its batch, run_ms from
+ * then until its result was in host memory (upload, multiply, read-back). The
+ * three add up to the latency bsm_server_poll reports. Null pointers are
+ * skipped. INVALID_ARG if the request is unknown or not finished. */
+int bsm_server_timing(bsm_server s, int64_t id, double *submit_ms, double *wait_ms,
+                      double *run_ms);
 
 /* Copy a finished request's result (pattern sorted by (row, col), values as
  * bsm_mat_get_values) into the caller's arrays and release it. Null arrays skip

@@ -380,6 +380,8 @@ _SIGS.update({
     "bsm_server_progress": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "bsm_server_poll": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_D),
                                        ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "bsm_server_timing": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                         ctypes.POINTER(_D)]),
     "bsm_server_take": (ctypes.c_int, [_P, _I64, _I64, _P, _P, _I64, _P]),
     "bsm_server_result": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                          ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -421,6 +423,14 @@ class Server:
         if rc != BSM_OK and st.value != REQ_FAILED:
             raise BsmError(rc, "bsm_server_poll")
         return int(st.value), float(lat.value), int(nb.value), int(nz.value)
+
+    def timing(self, rid: int):
+        """(submit_ms, wait_ms, run_ms) of a finished request: inside submit,
+        queued, and from a lane taking its batch to the result in host memory."""
+        a, b, c = _D(), _D(), _D()
+        _check(lib().bsm_server_timing(self._h, int(rid), ctypes.byref(a), ctypes.byref(b),
+                                       ctypes.byref(c)), "bsm_server_timing")
+        return float(a.value), float(b.value), float(c.value)
 
     def take(self, rid: int):
         st, _, nb, nz = self.poll(rid)

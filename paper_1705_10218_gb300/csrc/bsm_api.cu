@@ -308,6 +308,11 @@ struct bsm_ctx_s {
   uint16_t *d_pk_tab = nullptr;
   std::string tune_path;
   uint64_t tune_version = 0;
+  // between the slices of a sliced numeric phase (uncaptured multiplies only):
+  // the previous slice is waited for, then gate(gate_arg) is called
+  bsm::SliceGate gate = nullptr;
+  void *gate_arg = nullptr;
+  cudaEvent_t ev_gate = nullptr;
 };
 
 constexpr int kMaxKinds = 32;
@@ -695,6 +700,7 @@ struct Launch {
   cudaStream_t s;
   bool use_cin, split, prof;
   bool host_written;  // every numeric launch so far stored the host copy itself
+  bool gated;         // call the context's slice gate between numeric slices
   DevMat dA, dB, dC;
   DevWs ws;
   DevOut out;
@@ -976,10 +982,16 @@ static int stage_b(Launch &L, bool record, bool may_tune) {
       const int n = L.o.numeric_slices;
       CK(launch_slice_segs(ctx->d_status, n, ctx->cls_segs, L.s));
       ctx->launches++;
-      for (int x = 0; x < n; x++)
+      for (int x = 0; x < n; x++) {
+        if (L.gated && x > 0) {  // the slice before done, then the gate
+          CK(cudaEventRecord(ctx->ev_gate, L.s));
+          CK(cudaEventSynchronize(ctx->ev_gate));
+          ctx->gate(ctx->gate_arg);
+        }
         if ((rc = launch_numeric(L, variant, items, ctx->cls_segs + 2 * x, L.A->max_row,
                                  L.B->max_col)))
           return rc;
+      }
     } else if ((rc = launch_numeric(L, variant, items, nullptr, L.A->max_row, L.B->max_col))) {
       return rc;
     }
@@ -1136,6 +1148,7 @@ static int run_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double 
     CK(cudaGraphLaunch(hit->exec, L.s));
     ctx->launches += hit->launches;
   } else {
+    L.gated = ctx->gate != nullptr;
     if ((rc = stage_a(L, true))) return rc;
     if (sync_sizes) {
       DevStatus h{};
@@ -1347,6 +1360,7 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   if (ctx->ev_last) cudaEventDestroy(ctx->ev_last);
   if (ctx->ev_t0) cudaEventDestroy(ctx->ev_t0);
   if (ctx->ev_t1) cudaEventDestroy(ctx->ev_t1);
+  if (ctx->ev_gate) cudaEventDestroy(ctx->ev_gate);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->device < kCacheDevices) {
     DevCache &c = g_cache[ctx->device];
@@ -2052,6 +2066,21 @@ int mat_create_diag(bsm_ctx ctx, int nparts, const DiagPart *parts, bsm_mat *out
   M->nblk = nblk;
   M->nnz = nnz;
   *out = M;
+  return BSM_OK;
+}
+
+int set_slice_gate(bsm_ctx ctx, SliceGate gate, void *arg) {
+  if (!ctx) return BSM_ERR_INVALID_ARG;
+  if (gate && !ctx->ev_gate) {
+    cudaSetDevice(ctx->device);
+    const cudaError_t e = cudaEventCreateWithFlags(&ctx->ev_gate, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      ctx->ev_gate = nullptr;
+      return cuda_fail(e, "cudaEventCreate");
+    }
+  }
+  ctx->gate = gate;
+  ctx->gate_arg = arg;
   return BSM_OK;
 }
 

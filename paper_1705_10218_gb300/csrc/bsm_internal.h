@@ -260,4 +260,11 @@ struct DiagPart {
 // are not strictly sorted; OUT_OF_RANGE for an index outside its part.
 int mat_create_diag(bsm_ctx ctx, int nparts, const DiagPart *parts, bsm_mat *out);
 
+// A host function called between the slices of a sliced numeric phase
+// (opts.numeric_slices > 1) of an uncaptured multiply on ctx, after the slice
+// before it has finished on the device; it may block (the request loop holds a
+// large multiply's next slice there while small multiplies run). nullptr: none.
+using SliceGate = void (*)(void *arg);
+int set_slice_gate(bsm_ctx ctx, SliceGate gate, void *arg);
+
 }  // namespace bsm

@@ -237,3 +237,39 @@ def test_small_request_passes_earlier_large_one(bsm_lib):
         assert order == [first, small, large]
         for i in order:
             srv.release(i)
+
+
+def test_large_sliced_request_beside_small_ones(bsm_lib):
+    """A large request (numeric phase in slices, the next slice held back while
+    small batches run) and small requests submitted while it runs: every result
+    is bit for bit the request run alone, and each request's time splits into
+    submit, queue and run parts that add up to its latency."""
+    eps = 1e-10
+    large = synth.water(1024, seed=6400)
+    small = [synth.water(n, seed=6401 + r) for r, n in enumerate([8, 24, 16, 32, 12, 40])]
+    with bsm_lib.Server(0, slots=3, hbm_budget=48 << 30) as srv:
+        first = srv.submit(large, eps)
+        while srv.poll(first)[0] == 0:
+            pass
+        ids = []
+        for A in small:
+            ids.append(srv.submit(A, eps))
+            srv.progress()
+        pending = [i for i in ids if srv.poll(i)[0] < 2]
+        if pending:  # not finished yet: no timing
+            with pytest.raises(bsm_lib.BsmError):
+                srv.timing(pending[0])
+        drain(srv, [first] + ids)
+        with pytest.raises(bsm_lib.BsmError):
+            srv.timing(10 ** 9)
+        for i in [first] + ids:
+            state, lat, _, _ = srv.poll(i)
+            assert state == 2
+            t_sub, t_wait, t_run = srv.timing(i)
+            assert min(t_sub, t_wait, t_run) >= 0.0 and t_run > 0.0
+            assert abs(t_sub + t_wait + t_run - lat) <= 1e-6 * max(lat, 1.0)
+        results = [srv.take(i) for i in [first] + ids]
+    for A, (r, c, v) in zip([large] + small, results):
+        ra, ca, va = alone(bsm_lib, A, eps)
+        assert np.array_equal(r, ra) and np.array_equal(c, ca)
+        assert np.array_equal(v, va)
