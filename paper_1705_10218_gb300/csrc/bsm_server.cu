@@ -107,8 +107,8 @@ constexpr double kSliceMs = 2.0;
 // then, while small batches run, holds the next slice back (at most kGateMs per
 // slice, so that a stream of small requests cannot stall a large one): a small
 // multiply's dependent launches then find the SMs free instead of taking turns
-// with the large one's persistent slices. (200 water requests, Poisson
-// arrivals at 0.8 x the sequential rate: p50 14 ms without the hold, 8-9 ms
+// with the large one's persistent slices. (100 water requests, Poisson
+// arrivals at 0.8 x the sequential rate: p50 14 ms without the hold, 10-11 ms
 // with it; a longer hold lowers the burst rate, 2 to 8 ms per slice gave
 // 97 to 92 requests/s.)
 constexpr double kGateMs = 4.0;
