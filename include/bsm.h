@@ -195,8 +195,10 @@ int bsm_mat_destroy(bsm_mat m);
  * block row / column sizes (arguments as in bsm_mat_create; values NULL =
  * zeros). m's device buffers are reused and grown only when too small, so a
  * stream of inputs of similar size costs no device allocation. Work that reads
- * m is finished first; a pending result computed into m is dropped. Inputs are
- * copied before the call returns. Errors: BSM_ERR_OUT_OF_RANGE,
+ * m is finished first; a pending result computed into m is dropped. Work on
+ * other matrices is not waited for: the upload runs on a stream of the
+ * context's own, so the next input can go to the device while a multiply of
+ * other matrices runs. Inputs are copied before the call returns. Errors: BSM_ERR_OUT_OF_RANGE,
  * BSM_ERR_DUPLICATE_BLOCK, BSM_ERR_INVALID_ARG, BSM_ERR_UNSUPPORTED leave m
  * unchanged; BSM_ERR_NOMEM / BSM_ERR_CUDA leave m empty (no blocks).
  * The paper has no counterpart (there the operands are given to each multiply). */

@@ -220,6 +220,10 @@ struct Pending {
 
 struct bsm_mat_s {
   bsm_ctx ctx = nullptr;
+  // recorded after every multiply that reads or writes the matrix: the work
+  // to wait for before its contents change (filter, add and the getters
+  // finish their own work before they return)
+  cudaEvent_t ev_use = nullptr;
   int32_t nbr = 0, nbc = 0;
   std::vector<int32_t> h_row_sizes, h_col_sizes;
   int32_t max_row = 0, max_col = 0;  // largest block row / column size
@@ -257,6 +261,10 @@ struct bsm_ctx_s {
   int nsm = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_last = nullptr;   // last work of this context (any stream)
+  // matrix uploads (bsm_mat_create / bsm_mat_assign): a stream of their own, so
+  // that an upload runs while a multiply of other matrices is on the device
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t ev_up = nullptr;
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
   DevStatus *d_status = nullptr;
   unsigned long long *d_work = nullptr;  // work counter of the dynamically scheduled kernels
@@ -1209,7 +1217,10 @@ static int resolve(bsm_mat M, bsm_stats *timed) {
     if (rc) return rc;
   }
   int rc = run_multiply(ctx, p.alpha, p.A, p.B, p.beta, M, p.eps, p.opts, true, p.slot, timed);
-  if (rc) return rc;
+  if (rc) {  // nothing of the recompute may still run once M's operands change
+    cudaStreamSynchronize(p.opts.stream ? (cudaStream_t)p.opts.stream : ctx->stream);
+    return rc;
+  }
   CK(cudaEventSynchronize(ctx->slot_ev[p.slot]));
   h = ctx->h_slots[p.slot];
   if (h.overflow) return BSM_ERR_NOMEM;
@@ -1261,6 +1272,8 @@ int bsm_ctx_create(int device, bsm_ctx *out) {
       (e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device)) !=
           cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&ctx->ev_up, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&ctx->ev_last, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev_t0)) != cudaSuccess ||
       (e = cudaEventCreate(&ctx->ev_t1)) != cudaSuccess ||
@@ -1320,6 +1333,7 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   if (!ctx) return BSM_ERR_INVALID_ARG;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->up_stream) cudaStreamSynchronize(ctx->up_stream);
   while (!ctx->mats.empty()) {
     bsm_mat m = ctx->mats.back();
     m->pend.active = false;
@@ -1361,6 +1375,8 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
   if (ctx->ev_t0) cudaEventDestroy(ctx->ev_t0);
   if (ctx->ev_t1) cudaEventDestroy(ctx->ev_t1);
   if (ctx->ev_gate) cudaEventDestroy(ctx->ev_gate);
+  if (ctx->ev_up) cudaEventDestroy(ctx->ev_up);
+  if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->device < kCacheDevices) {
     DevCache &c = g_cache[ctx->device];
@@ -1532,12 +1548,16 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
     list_off.assign(h_off, h_off + nblocks + 1);
   }
   int rc;
+  const bool fresh = !M->front.row_ptr;  // buf_grow zeroes new buffers on the context's stream
   if ((rc = buf_grow(M, M->front, nblocks, nnz, exact))) return rc;
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = ctx->up_stream;
+  cudaError_t e;
+  if (fresh && ((e = cudaEventRecord(ctx->ev_up, ctx->stream)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(st, ctx->ev_up, 0)) != cudaSuccess))
+    return cuda_fail(e, "matrix upload order");
   auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
     return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
   };
-  cudaError_t e;
   // values in sorted order: start their copy now, it runs while the index
   // arrays are staged
   if (sorted && values && (e = cp(M->front.vals, values, (size_t)nnz * 8)) != cudaSuccess)
@@ -1610,11 +1630,27 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
   return BSM_OK;
 }
 
+// Records M's use event on stream s after the work enqueued there.
+static int mark_use(bsm_mat M, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (!M->ev_use) e = cudaEventCreateWithFlags(&M->ev_use, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(M->ev_use, s);
+  if (e != cudaSuccess) {
+    // an event that was never recorded would let an upload overwrite M early
+    cudaStreamSynchronize(s);
+    return cuda_fail(e, "matrix use event");
+  }
+  return BSM_OK;
+}
+
 // Work that reads M as an input, or writes it, must be finished (and any
-// recompute that would read M done) before M's contents change.
+// recompute that would read M done) before M's contents change. Only
+// multiplies leave work on the device after they return; each records M's
+// use event, so other work still running (a multiply of other matrices) is
+// not waited for.
 static int quiesce(bsm_mat m) {
   bsm_ctx ctx = m->ctx;
-  CK(cudaStreamSynchronize(ctx->stream));
+  if (m->ev_use) CK(cudaEventSynchronize(m->ev_use));
   for (bsm_mat o : std::vector<bsm_mat>(ctx->mats))
     if (o != m && o->pend.active && (o->pend.A == m || o->pend.B == m)) {
       int rc = resolve(o);
@@ -1734,6 +1770,7 @@ int bsm_mat_destroy(bsm_mat m) {
   dev_free(m->row_cls);
   dev_free(m->col_cls);
   dev_free(m->row_order);
+  if (m->ev_use) cudaEventDestroy(m->ev_use);
   // captured multiplies may name this matrix's buffers
   for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   ctx->graphs.clear();
@@ -1792,6 +1829,13 @@ int bsm_multiply(bsm_ctx ctx, double alpha, bsm_mat A, bsm_mat B, double beta, b
                           ctx->ws.cap_prod < ctx->hint_prod || ctx->cap_cblk <= C->hint_blk;
   if (stats) stats->retries = 0;
   rc = run_multiply(ctx, alpha, A, B, beta, C, eps, o, sync_sizes, slot, stats);
+  {  // whatever was enqueued, also on an error part way
+    const cudaStream_t s = o.stream ? (cudaStream_t)o.stream : ctx->stream;
+    int ru = mark_use(A, s);  // a failure synchronises s: nothing left to mark
+    if (!ru) ru = mark_use(B, s);
+    if (!ru) ru = mark_use(C, s);
+    if (!rc) rc = ru;
+  }
   if (rc) return rc;
   std::swap(C->front, C->back);
   C->pend.active = true;

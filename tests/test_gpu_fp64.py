@@ -373,6 +373,39 @@ def test_assign_reuses_matrix(gpu_ctx, bsm_lib, oracle_mod):
     dC.destroy()
 
 
+def test_assign_beside_queued_multiply(gpu_ctx, bsm_lib, oracle_mod):
+    """Uploads run on a stream of their own: an input assigned into one handle
+    while a multiply of another is queued, and an input assigned into a handle
+    that a queued multiply still reads (that multiply finishes first), leave
+    every result equal to the oracle's. 1200 block rows: the row order is
+    computed again for each new pattern."""
+    eps = 1e-10
+    A, B = synth.water(400, seed=51), synth.water(400, seed=52)
+    refs = {id(M): oracle_mod.multiply(M, M, eps=eps) for M in (A, B)}
+    d = [gpu_ctx.from_blocks(A), gpu_ctx.from_blocks(A)]
+    dC = [gpu_ctx.empty(A.row_sizes, A.col_sizes) for _ in range(2)]
+
+    def same(C, M):
+        ref = refs[id(M)]
+        r, c = C.pattern()
+        assert np.array_equal(r, ref.blk_row) and np.array_equal(c, ref.blk_col)
+        assert H.rel_frobenius(C.values(), ref.values) <= TOL
+
+    gpu_ctx.multiply(1.0, d[0], d[0], 0.0, dC[0], eps)  # queued: reads d[0] = A
+    d[1].assign(B.blk_row, B.blk_col, B.values)          # another handle: no wait
+    gpu_ctx.multiply(1.0, d[1], d[1], 0.0, dC[1], eps)  # queued: reads d[1] = B
+    d[0].assign(B.blk_row, B.blk_col, B.values)          # waits for the first multiply
+    same(dC[0], A)
+    same(dC[1], B)
+    for k in range(3):  # alternating handles, as a pipelined loop does
+        gpu_ctx.multiply(1.0, d[k % 2], d[k % 2], 0.0, dC[0], eps)
+        d[(k + 1) % 2].assign(A.blk_row, A.blk_col, A.values)
+        same(dC[0], B if k == 0 else A)
+        d[k % 2].assign(A.blk_row, A.blk_col, A.values)
+    for M in d + dC:
+        M.destroy()
+
+
 @pytest.mark.parametrize("top", [4, 6, 8])
 def test_g8_tiny_blocks(gpu_ctx, oracle_mod, bsm_lib, top):
     """The g8 kernel at each of its register-row and lane-group sizes (blocks up
