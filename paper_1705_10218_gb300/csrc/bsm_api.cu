@@ -1397,7 +1397,7 @@ int bsm_ctx_destroy(bsm_ctx ctx) {
 // Page-locked staging of an upload's index arrays: row_ptr | col | row | off,
 // each part 16-byte aligned.
 struct StageLayout {
-  size_t b_ptr, b_col, b_off, need;
+  size_t b_ptr, b_col, b_off, b_hdr, need;
 };
 static StageLayout stage_layout(int64_t nbrows, int64_t nblocks) {
   auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
@@ -1405,14 +1405,19 @@ static StageLayout stage_layout(int64_t nbrows, int64_t nblocks) {
   L.b_ptr = al(((size_t)nbrows + 1) * 4);
   L.b_col = al((size_t)nblocks * 4);
   L.b_off = al(((size_t)nblocks + 1) * 8);
-  L.need = L.b_ptr + 2 * L.b_col + L.b_off;
+  L.b_hdr = 16;  // the (blocks, values) header, last
+  L.need = L.b_ptr + 2 * L.b_col + L.b_off + L.b_hdr;
   return L;
 }
 
 // The context's staging, at least `need` bytes, once the copies of an earlier
-// upload that may still read it are done.
+// upload that may still read it are done. The uploads that use it finish their
+// copies (synchronise their stream) before they return, also when they fail;
+// the upload stream is synchronised here all the same, which costs nothing
+// when it is idle. A multiply still running on the context's stream is not
+// waited for.
 static int stage_reserve(bsm_ctx ctx, size_t need) {
-  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaStreamSynchronize(ctx->up_stream));
   if (ctx->h_stage_cap < need) {
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     ctx->h_stage = nullptr;
@@ -1558,10 +1563,14 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
   auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
     return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
   };
+  auto up_fail = [&](cudaError_t err, const char *where) {  // nothing left in flight
+    cudaStreamSynchronize(st);
+    return cuda_fail(err, where);
+  };
   // values in sorted order: start their copy now, it runs while the index
   // arrays are staged
   if (sorted && values && (e = cp(M->front.vals, values, (size_t)nnz * 8)) != cudaSuccess)
-    return cuda_fail(e, "matrix upload values");
+    return up_fail(e, "matrix upload values");
   std::vector<double> staged;
   if (sorted) {
     memcpy(h_row, blk_row, (size_t)nblocks * 4);
@@ -1600,9 +1609,12 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
       M->order_id = 0;
       h_order.resize(2 * (size_t)nbrows);
       bfs_row_order(nbrows, h_row_ptr, h_col, h_order.data(), h_order.data() + nbrows);
-      if (!M->row_order && (rc = dev_alloc(&M->row_order, 2 * (int64_t)nbrows))) return rc;
+      if (!M->row_order && (rc = dev_alloc(&M->row_order, 2 * (int64_t)nbrows))) {
+        cudaStreamSynchronize(st);
+        return rc;
+      }
       if ((e = cp(M->row_order, h_order.data(), h_order.size() * 4)) != cudaSuccess)
-        return cuda_fail(e, "matrix upload row order");
+        return up_fail(e, "matrix upload row order");
       M->order_ptr.assign(h_row_ptr, h_row_ptr + nbrows + 1);
       M->order_col.assign(h_col, h_col + nblocks);
       M->order_id = next_order_id();
@@ -1610,19 +1622,22 @@ static int upload_contents(bsm_mat M, int64_t nblocks, const int32_t *blk_row,
   } else {
     M->order_id = 0;
   }
-  int64_t hdr[2] = {nblocks, nnz};
+  // page-locked like the rest: a copy from pageable memory may wait for other work
+  int64_t *hdr = reinterpret_cast<int64_t *>(ctx->h_stage + L.need - L.b_hdr);
+  hdr[0] = nblocks;
+  hdr[1] = nnz;
   if ((e = cp(M->front.row_ptr, h_row_ptr, ((size_t)nbrows + 1) * 4)) != cudaSuccess ||
       (e = cp(M->front.col_idx, h_col, (size_t)nblocks * 4)) != cudaSuccess ||
       (e = cp(M->front.blk_row, h_row, (size_t)nblocks * 4)) != cudaSuccess ||
       (e = cp(M->front.blk_off, h_off, (size_t)nblocks * 8)) != cudaSuccess ||
-      (e = cp(M->front.hdr, hdr, sizeof(hdr))) != cudaSuccess)
-    return cuda_fail(e, "matrix upload");
+      (e = cp(M->front.hdr, hdr, 2 * sizeof(int64_t))) != cudaSuccess)
+    return up_fail(e, "matrix upload");
   if (!sorted && values) {
     if ((e = cp(M->front.vals, staged.data(), (size_t)nnz * 8)) != cudaSuccess)
-      return cuda_fail(e, "matrix upload values");
+      return up_fail(e, "matrix upload values");
   } else if (!values && nnz > 0) {
     if ((e = cudaMemsetAsync(M->front.vals, 0, (size_t)nnz * 8, st)) != cudaSuccess)
-      return cuda_fail(e, "matrix upload zero");
+      return up_fail(e, "matrix upload zero");
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "matrix upload sync");
   M->nblk = nblocks;
@@ -1755,8 +1770,10 @@ int bsm_mat_destroy(bsm_mat m) {
   if (!m) return BSM_ERR_INVALID_ARG;
   bsm_ctx ctx = m->ctx;
   cudaSetDevice(ctx->device);
-  // any pending multiply may read this matrix: finish all work first
+  // any pending multiply may read this matrix, an upload may write it: finish
+  // all work first
   cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->up_stream);
   for (bsm_mat o : ctx->mats)
     if (o != m && o->pend.active && (o->pend.A == m || o->pend.B == m)) resolve(o);
   for (int i = 0; i < kSlots; i++)
