@@ -745,7 +745,8 @@ def main():
                     help="force one FP64 numeric kernel (default: the library's choice)")
     ap.add_argument("--split-kernel", default=None, choices=sorted(SPLIT_KERNELS),
                     help="force a split-precision kernel (default: the library's choice)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="end-to-end steps (default: --steps; 0 skips the end-to-end leg)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other configurations (split precisions, amorphous, serving)")
@@ -892,6 +893,8 @@ def main():
     # values from pinned host memory, the multiply, C's values stored into
     # pinned host memory by the device as they are computed.
     e2e = None
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
     if args.e2e_steps > 0:
         pin_vals = torch.empty(len(A.values), dtype=torch.float64, pin_memory=True).numpy()
         pin_vals[:] = A.values

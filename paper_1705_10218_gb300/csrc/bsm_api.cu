@@ -53,10 +53,10 @@ int cuda_fail(cudaError_t e, const char *where) {
 // Device memory. cudaFree synchronises the whole device (every stream of every
 // context), so the library keeps freed blocks in a per-device cache and
 // reuses them instead. Every caller frees a block only after the work that
-// used it has finished (after synchronising the owning context's stream), so
-// a cached block can go to any context. Sizes are rounded up to classes 1/8
-// of a power of two apart (under 12.5% slack); the cache holds at most
-// kCacheCap bytes per device (beyond that blocks are freed), a failed
+// used it has finished (after synchronising the owning context's streams), so
+// a cached block can go to any context and any stream. Sizes are rounded up
+// to classes 1/8 of a power of two apart (under 12.5% slack); the cache holds
+// at most kCacheCap bytes per device (beyond that blocks are freed), a failed
 // cudaMalloc empties it and retries, and it is emptied when the last context
 // on the device is destroyed.
 // ---------------------------------------------------------------------------
@@ -410,8 +410,13 @@ static int ws_grow(bsm_ctx ctx, int64_t nblk_c, int64_t nprod) {
 }
 
 // The row-panel kernel's work buffers, sized to the workspace's capacities.
+// Buffers are freed (returned to the cache) only once the multiplies that may
+// still read them have finished.
 static int panel_ws(bsm_ctx ctx, int64_t nrows) {
   int rc;
+  if (ctx->cap_pw_recs < ctx->ws.cap_prod || ctx->cap_pw_tiles < ctx->cap_cblk ||
+      ctx->cap_pw_rows < nrows)
+    CK(cudaStreamSynchronize(ctx->stream));
   if (ctx->cap_pw_recs < ctx->ws.cap_prod) {
     dev_free(ctx->pw.recs);
     ctx->cap_pw_recs = 0;
