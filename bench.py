@@ -554,6 +554,18 @@ def serve_measure(requests, pool_n, slots, budget_gb, seed=4):
         gaps = rng.exponential(1.0 / rate, requests)
         return np.cumsum(gaps) - gaps[0]
 
+    # the same requests through the server one at a time (each submitted once
+    # the one before is done): the server's own latency without contention
+    lat_1, parts_1 = [], []
+    for r in range(requests):
+        rid = srv.submit(pool[pick[r]], eps)
+        while srv.poll(rid)[0] < 2:
+            srv.progress()
+        lat_1.append(srv.poll(rid)[1])
+        parts_1.append(srv.timing(rid))
+        srv.release(rid)
+    parts_1 = np.asarray(parts_1)
+
     lam = 0.8 * cap
     b0 = srv.info()["batches"]
     lat_p, span_p, peak_p, parts_p = replay(poisson(lam))
@@ -579,6 +591,8 @@ def serve_measure(requests, pool_n, slots, budget_gb, seed=4):
                    "eps": eps, "total_gflop": round(tot_gflop, 2)},
         "sequential": {"multiplies_per_s": round(cap, 3), "p50_ms": pct(lat_seq, 50),
                        "p99_ms": pct(lat_seq, 99), "gflop_per_s": round(tot_gflop / t_seq, 2)},
+        "server_one_at_a_time": {"p50_ms": pct(lat_1, 50), "p99_ms": pct(lat_1, 99),
+                                 **split(parts_1)},
         "poisson": {"arrival_rate_per_s": round(lam, 3), "multiplies_per_s": round(requests / span_p, 3),
                     "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99), "peak_gb": round(peak_p / 2**30, 3),
                     "batches": b1 - b0, **split(parts_p)},
