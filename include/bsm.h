@@ -295,7 +295,8 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * of its requests, one launch sequence over all their blocks, and each request
  * receives its own part of the result, which is bit for bit the result of that
  * request multiplied alone (the kernels compute each C block from its own
- * products only). The lanes run concurrently on the device. Inputs are copied
+ * products only). The lanes run concurrently on the device, at most two of
+ * them small batches. Inputs are copied
  * at submission into page-locked host memory (blocks sorted by (row, col);
  * large copies on several threads) and uploaded from there; results wait in page-locked host memory until taken
  * (copied out) or released after use in place. Admission needs no call from

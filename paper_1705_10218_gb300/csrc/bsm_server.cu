@@ -22,9 +22,10 @@
 // diag(A_1^2..A_n^2): the kernels compute every C block from its own product list
 // alone, in an order fixed by that list, so each request's part of the result is
 // bit for bit the result of the request run alone. The lanes run their batches
-// concurrently on the device, and a request that arrives while others run
-// starts the moment a lane and memory free up. Inputs are copied at submission
-// into page-locked host memory and uploaded from there by DMA, one copy per
+// concurrently on the device (at most kMaxSmall small ones), and a request that
+// arrives while others run starts the moment a lane and memory free up. Inputs
+// are copied at submission into page-locked host memory (large copies on
+// several threads) and uploaded from there by DMA, one copy per
 // request into the batch's matrix. Results go to page-locked host memory (the
 // multiply stores the values there directly when they fit) and wait there
 // until taken or released.
