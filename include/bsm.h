@@ -296,10 +296,11 @@ int bsm_ctx_profile_read(bsm_ctx ctx, bsm_profile *out);
  * receives its own part of the result, which is bit for bit the result of that
  * request multiplied alone (the kernels compute each C block from its own
  * products only). The lanes run concurrently on the device, at most two of
- * them small batches. Inputs are copied
- * at submission into page-locked host memory (blocks sorted by (row, col);
- * large copies on several threads) and uploaded from there; results wait in page-locked host memory until taken
- * (copied out) or released after use in place. Admission needs no call from
+ * them small batches. Inputs are copied at submission into page-locked host
+ * memory (blocks sorted by (row, col); large copies on several threads) and
+ * uploaded from there, or, submitted with bsm_server_submit_borrowed,
+ * uploaded from the caller's array. Results wait in page-locked host memory
+ * until taken (copied out) or released after use in place. Admission needs no call from
  * the caller. The server functions may be called from any thread;
  * bsm_server_destroy only once every other call on the server has returned.
  * ------------------------------------------------------------------------- */
@@ -332,6 +333,17 @@ int bsm_server_destroy(bsm_server s);
 int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_t nblocks,
                       const int32_t *blk_row, const int32_t *blk_col, const double *values,
                       double eps, int64_t *id);
+
+/* As bsm_server_submit, but the values are not copied: the lane uploads them
+ * from the caller's array when the request runs, which saves the copy into
+ * page-locked memory at submission (part of every request's latency). The
+ * caller keeps `values` alive and unchanged until the request is done or
+ * failed (bsm_server_poll) or the server is destroyed; the other arrays are
+ * copied. The block list must be sorted by (row, col) without duplicates
+ * (INVALID_ARG otherwise). Page-locked values upload fastest. */
+int bsm_server_submit_borrowed(bsm_server s, int32_t nbrows, const int32_t *sizes,
+                               int64_t nblocks, const int32_t *blk_row, const int32_t *blk_col,
+                               const double *values, double eps, int64_t *id);
 
 /* Never blocks. *completed: requests finished since the previous call (the
  * lanes admit and run requests by themselves). */

@@ -377,6 +377,8 @@ _SIGS.update({
     "bsm_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_ServerOpts), ctypes.POINTER(_P)]),
     "bsm_server_destroy": (ctypes.c_int, [_P]),
     "bsm_server_submit": (ctypes.c_int, [_P, _I32, _P, _I64, _P, _P, _P, _D, ctypes.POINTER(_I64)]),
+    "bsm_server_submit_borrowed": (ctypes.c_int, [_P, _I32, _P, _I64, _P, _P, _P, _D,
+                                                  ctypes.POINTER(_I64)]),
     "bsm_server_progress": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "bsm_server_poll": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_D),
                                        ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -399,16 +401,24 @@ class Server:
         o = _ServerOpts(int(slots), int(precision), int(hbm_budget))
         _check(lib().bsm_server_create(int(device), ctypes.byref(o), ctypes.byref(h)), "bsm_server_create")
         self._h = h
+        self._borrowed = {}  # request id -> values array the server reads (borrowed submissions)
 
-    def submit(self, M, eps: float) -> int:
-        """Queue C = M.M for a square block matrix M (row sizes = column sizes)."""
+    def submit(self, M, eps: float, borrow: bool = False) -> int:
+        """Queue C = M.M for a square block matrix M (row sizes = column sizes).
+        borrow: the values are uploaded from M's array when the request runs
+        instead of being copied now (bsm_server_submit_borrowed; the block list
+        must be sorted); the array is kept referenced here until the request is
+        released or taken."""
         sz = np.ascontiguousarray(M.row_sizes, dtype=np.int32)
         br = np.ascontiguousarray(M.blk_row, dtype=np.int32)
         bc = np.ascontiguousarray(M.blk_col, dtype=np.int32)
         v = np.ascontiguousarray(M.values, dtype=np.float64)
         rid = _I64()
-        _check(lib().bsm_server_submit(self._h, len(sz), _vp(sz), len(br), _vp(br), _vp(bc), _vp(v),
-                                       float(eps), ctypes.byref(rid)), "bsm_server_submit")
+        fn = "bsm_server_submit_borrowed" if borrow else "bsm_server_submit"
+        _check(getattr(lib(), fn)(self._h, len(sz), _vp(sz), len(br), _vp(br), _vp(bc), _vp(v),
+                                  float(eps), ctypes.byref(rid)), fn)
+        if borrow:
+            self._borrowed[int(rid.value)] = v
         return int(rid.value)
 
     def progress(self) -> int:
@@ -440,6 +450,7 @@ class Server:
         c = np.empty(nb, np.int32)
         v = np.empty(nz, np.float64)
         _check(lib().bsm_server_take(self._h, int(rid), nb, _vp(r), _vp(c), nz, _vp(v)), "bsm_server_take")
+        self._borrowed.pop(int(rid), None)
         return r, c, v
 
     def result(self, rid: int):
@@ -462,6 +473,7 @@ class Server:
     def release(self, rid: int):
         """Forget a finished request; its result views become invalid."""
         _check(lib().bsm_server_release(self._h, int(rid)), "bsm_server_release")
+        self._borrowed.pop(int(rid), None)
 
     def info(self) -> dict:
         i = _ServerInfo()
@@ -472,6 +484,7 @@ class Server:
         if self._h:
             lib().bsm_server_destroy(self._h)
             self._h = None
+            self._borrowed.clear()
 
     def __enter__(self):
         return self

@@ -61,6 +61,7 @@ struct Request {
   int64_t id = 0;
   std::vector<int32_t> sizes, brow, bcol;  // blocks sorted by (row, col)
   double *vals = nullptr;  // page-locked copy of the values, in block order
+  const double *in_vals = nullptr;  // what the lane uploads: vals, or the caller's (borrowed)
   int64_t nvals = 0;
   double eps = 0;
   int64_t footprint = 0;     // bytes held on the device while admitted
@@ -335,7 +336,7 @@ static void run_batch(bsm_server s, Slot &sl, const std::vector<Request *> &batc
   for (int p = 0; p < n; p++) {
     const Request *r = batch[p];
     parts[p] = {(int32_t)r->sizes.size(), r->sizes.data(), (int64_t)r->brow.size(), r->brow.data(),
-                r->bcol.data(), r->vals};
+                r->bcol.data(), r->in_vals};
     sizes.insert(sizes.end(), r->sizes.begin(), r->sizes.end());
     row0[p + 1] = row0[p] + (int32_t)r->sizes.size();
     vals_bound += r->c_vals_bound;
@@ -408,6 +409,7 @@ static void run_batch(bsm_server s, Slot &sl, const std::vector<Request *> &batc
     if (rc != BSM_OK) drop_result(s, r);
     s->pinned.put(r->vals);  // the host copy of the input is no longer needed
     r->vals = nullptr;
+    r->in_vals = nullptr;  // a borrowed input is no longer read
     r->err = rc;
     r->t_done = t;
   }
@@ -569,9 +571,11 @@ int bsm_server_destroy(bsm_server s) {
   return BSM_OK;
 }
 
-int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_t nblocks,
-                      const int32_t *blk_row, const int32_t *blk_col, const double *values,
-                      double eps, int64_t *id) {
+// borrow: the caller's values are uploaded as they are (sorted block lists
+// only), without the copy into page-locked memory.
+static int submit_request(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_t nblocks,
+                          const int32_t *blk_row, const int32_t *blk_col, const double *values,
+                          double eps, bool borrow, int64_t *id) {
   // the request arrives now: its latency and deadline count from here, not from
   // the end of the copies below (which may wait for page-locked memory)
   const double t_arrive = now_ms();
@@ -589,24 +593,30 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
   // the copies are made before the lock: a large request does not hold up the
   // lanes. The blocks are kept sorted by (row, col), the order the batch's
   // matrix is assembled in; the values go to page-locked memory, from where the
-  // lane uploads them by DMA.
+  // lane uploads them by DMA (a borrowed submission's from the caller's array).
   bool sorted = true;
   for (int64_t b = 1; b < nblocks && sorted; b++)
     sorted = blk_row[b - 1] < blk_row[b] || (blk_row[b - 1] == blk_row[b] && blk_col[b - 1] < blk_col[b]);
+  if (borrow && !sorted) return BSM_ERR_INVALID_ARG;
   Request *r = new (std::nothrow) Request();
   if (!r) return BSM_ERR_NOMEM;
   r->nvals = nv;
-  r->vals = static_cast<double *>(s->pinned.get(8 * (size_t)std::max<int64_t>(nv, 1)));
-  if (!r->vals) {
-    delete r;
-    return BSM_ERR_NOMEM;
+  if (borrow) {
+    r->in_vals = values;
+  } else {
+    r->vals = static_cast<double *>(s->pinned.get(8 * (size_t)std::max<int64_t>(nv, 1)));
+    if (!r->vals) {
+      delete r;
+      return BSM_ERR_NOMEM;
+    }
+    r->in_vals = r->vals;
   }
   try {
     r->sizes.assign(sizes, sizes + nbrows);
     if (sorted) {
       r->brow.assign(blk_row, blk_row + nblocks);
       r->bcol.assign(blk_col, blk_col + nblocks);
-      if (nv) copy_parallel(r->vals, values, (size_t)nv * sizeof(double));
+      if (nv && !borrow) copy_parallel(r->vals, values, (size_t)nv * sizeof(double));
     } else {
       std::vector<int64_t> order((size_t)nblocks), off((size_t)nblocks + 1, 0);
       for (int64_t b = 0; b < nblocks; b++) {
@@ -655,6 +665,18 @@ int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_
   }
   s->cv.notify_all();
   return BSM_OK;
+}
+
+int bsm_server_submit(bsm_server s, int32_t nbrows, const int32_t *sizes, int64_t nblocks,
+                      const int32_t *blk_row, const int32_t *blk_col, const double *values,
+                      double eps, int64_t *id) {
+  return submit_request(s, nbrows, sizes, nblocks, blk_row, blk_col, values, eps, false, id);
+}
+
+int bsm_server_submit_borrowed(bsm_server s, int32_t nbrows, const int32_t *sizes,
+                               int64_t nblocks, const int32_t *blk_row, const int32_t *blk_col,
+                               const double *values, double eps, int64_t *id) {
+  return submit_request(s, nbrows, sizes, nblocks, blk_row, blk_col, values, eps, true, id);
 }
 
 int bsm_server_progress(bsm_server s, int32_t *completed) {

@@ -273,3 +273,27 @@ def test_large_sliced_request_beside_small_ones(bsm_lib):
         ra, ca, va = alone(bsm_lib, A, eps)
         assert np.array_equal(r, ra) and np.array_equal(c, ca)
         assert np.array_equal(v, va)
+
+
+def test_borrowed_submission(bsm_lib, oracle_mod):
+    """bsm_server_submit_borrowed: the values are read from the caller's array
+    when the request runs (no copy at submission). Each result equals the
+    request run alone, also beside copied submissions and in merged batches;
+    an unsorted block list is refused."""
+    eps = 1e-10
+    systems = [synth.water(n, seed=6500 + r) for r, n in enumerate([24, 8, 40, 16, 1024])]
+    with bsm_lib.Server(0, slots=3, hbm_budget=48 << 30) as srv:
+        ids = [srv.submit(A, eps, borrow=(r % 2 == 0)) for r, A in enumerate(systems)]
+        drain(srv, ids)
+        results = [srv.take(i) for i in ids]
+        assert not srv._borrowed  # taken requests hold no borrowed arrays
+        P = _permuted(systems[0], np.random.default_rng(9))
+        with pytest.raises(bsm_lib.BsmError) as e:
+            srv.submit(P, eps, borrow=True)
+        assert e.value.name == "INVALID_ARG"
+    for A, (r, c, v) in zip(systems, results):
+        ra, ca, va = alone(bsm_lib, A, eps)
+        assert np.array_equal(r, ra) and np.array_equal(c, ca)
+        assert np.array_equal(v, va)
+    ref = oracle_mod.multiply(systems[0], systems[0], eps=eps)
+    assert np.array_equal(results[0][0], ref.blk_row) and H.rel_frobenius(results[0][2], ref.values) <= 1e-12
