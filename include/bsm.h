@@ -321,7 +321,13 @@ typedef struct {
 /* Request states reported by bsm_server_poll. */
 enum { BSM_REQ_QUEUED = 0, BSM_REQ_RUNNING = 1, BSM_REQ_DONE = 2, BSM_REQ_FAILED = 3 };
 
+/* Start a request loop on `device` (opts NULL: 4 lanes, FP64, an 8 GiB
+ * budget); *out receives the handle, owned by the caller until
+ * bsm_server_destroy. INVALID_ARG for slots above 64, an unknown precision or
+ * device; NOMEM; CUDA. */
 int bsm_server_create(int device, const bsm_server_opts *opts, bsm_server *out);
+/* Finish the requests running, drop the queued ones and free everything the
+ * server holds, results not yet taken and result views included. Blocking. */
 int bsm_server_destroy(bsm_server s);
 
 /* Queue C = A.A for a square matrix given as in bsm_mat_create (block sizes
@@ -381,6 +387,9 @@ int bsm_server_result(bsm_server s, int64_t id, const int32_t **blk_row, const i
 /* Forget a finished (done or failed) request and return its result memory. */
 int bsm_server_release(bsm_server s, int64_t id);
 
+/* The server's counters at the time of the call: requests queued, running and
+ * completed, device bytes held by admitted requests now and at most, the
+ * budget, and the multiplies (batches) run. */
 int bsm_server_get_info(bsm_server s, bsm_server_info *out);
 
 /* ---------------------------------------------------------------------------
