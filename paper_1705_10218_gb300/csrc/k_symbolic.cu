@@ -70,11 +70,7 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int lo, int hi,
 // ----------------------------------------------------------------------------
 // Block norms: canonical Frobenius norm, column-major, no fused multiply-add.
 // One thread per block, grid-stride; the block count is read on the device so
-// a matrix produced by an earlier multiply needs no host round trip. The
-// threads of a warp read 32 different blocks, so every warp load touches 32
-// cache lines: the values are read two per 16-byte load (after a leading one
-// when the block starts on an odd double), half the loads of one per value,
-// in the same order.
+// a matrix produced by an earlier multiply needs no host round trip.
 // ----------------------------------------------------------------------------
 __global__ void k_block_norms(const int32_t *__restrict__ row_sizes,
                               const int32_t *__restrict__ col_sizes,
@@ -89,18 +85,7 @@ __global__ void k_block_norms(const int32_t *__restrict__ row_sizes,
     const int64_t n = (int64_t)row_sizes[blk_row[b]] * col_sizes[col_idx[b]];
     const double *x = vals + blk_off[b];
     double s = 0.0;
-    int64_t e = 0;
-    if (n > 0 && ((uintptr_t)x & 15u)) {  // to a 16-byte boundary
-      const double v = __ldg(x);
-      s = __dadd_rn(s, __dmul_rn(v, v));
-      e = 1;
-    }
-    for (; e + 1 < n; e += 2) {
-      const double2 p = __ldg(reinterpret_cast<const double2 *>(x + e));
-      s = __dadd_rn(s, __dmul_rn(p.x, p.x));
-      s = __dadd_rn(s, __dmul_rn(p.y, p.y));
-    }
-    if (e < n) {
+    for (int64_t e = 0; e < n; e++) {
       const double v = __ldg(x + e);
       s = __dadd_rn(s, __dmul_rn(v, v));
     }
